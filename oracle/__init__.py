@@ -1,0 +1,191 @@
+"""CPU oracle for polynomial-matrix arithmetic over F_p -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()``, the golden-value script under
+``tests/golden/`` and the CPU-baseline leg of ``bench.py`` may import this
+package.  The product library never does: it shares no code with it.
+
+The arithmetic lives in ``oracle.c`` (plain C, unsigned __int128, OpenMP).
+This module only marshals NumPy arrays into it.  Each wrapper names the part
+of the paper its C function follows:
+
+* ``pmat_mul`` / ``pmat_mul_trunc`` / ``pmat_middle_product`` / ``pmat_coeff``:
+  Sec. 2, polynomial (matrix) multiplication and MiddleProduct(F, G, c, d).
+* ``mbasis1``: Algorithm 1.  ``mbasis``: Algorithm 2.  ``pmbasis``: Algorithm 3.
+* ``univ_resultant`` / ``bivariate_resultant``: Sec. 5.2, the direct
+  evaluation / Euclid / interpolation method.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB_PATH, build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < os.path.getmtime(
+            os.path.join(os.path.dirname(__file__), "oracle.c")
+        ):
+            build()
+        L = C.CDLL(LIB_PATH)
+        u64, i64, i32 = C.c_uint64, C.c_int64, C.c_int
+        P = C.c_void_p
+        L.orc_pmat_coeff.restype = u64
+        L.orc_pmat_coeff.argtypes = [u64, i32, i32, i32, P, i64, P, i64, i32, i32, i64]
+        L.orc_pmat_slice.restype = None
+        L.orc_pmat_slice.argtypes = [u64, i32, i32, i32, P, i64, P, i64, i64, i64, P]
+        L.orc_mbasis1.restype = i32
+        L.orc_mbasis1.argtypes = [u64, i32, i32, P, P, P]
+        L.orc_mbasis.restype = None
+        L.orc_mbasis.argtypes = [u64, i32, i32, P, i64, i64, P, P, P]
+        L.orc_pmbasis.restype = None
+        L.orc_pmbasis.argtypes = [u64, i32, i32, P, i64, i64, P, i64, P, P]
+        L.orc_rdeg.restype = None
+        L.orc_rdeg.argtypes = [i32, i32, P, i64, P, P]
+        L.orc_univ_resultant.restype = u64
+        L.orc_univ_resultant.argtypes = [u64, P, i64, P, i64]
+        L.orc_bivariate_resultant.restype = i32
+        L.orc_bivariate_resultant.argtypes = [u64, i32, i32, P, i32, i32, P, P]
+        L.orc_powmod.restype = u64
+        L.orc_powmod.argtypes = [u64, u64, u64]
+        L.orc_invmod.restype = u64
+        L.orc_invmod.argtypes = [u64, u64]
+        _lib = L
+    return _lib
+
+
+def _u64(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x).astype(np.uint64, copy=False))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def pmat_slice(p, A, B, c0, length, threads=None):
+    """Coefficients c0 .. c0+length-1 of A.B (A: m x n x dA, B: n x k x dB)."""
+    A, B = _u64(A), _u64(B)
+    m, n, dA = A.shape
+    n2, k, dB = B.shape
+    assert n == n2
+    Cout = np.zeros((m, k, length), dtype=np.uint64)
+    _with_threads(threads, lambda: lib().orc_pmat_slice(
+        p, m, n, k, _ptr(A), dA, _ptr(B), dB, c0, length, _ptr(Cout)))
+    return Cout
+
+
+def pmat_mul(p, A, B, threads=None):
+    return pmat_slice(p, A, B, 0, A.shape[2] + B.shape[2] - 1, threads)
+
+
+def pmat_mul_trunc(p, A, B, t, threads=None):
+    return pmat_slice(p, A, B, 0, t, threads)
+
+
+def pmat_middle_product(p, A, B, c, d, threads=None):
+    return pmat_slice(p, A, B, c, d, threads)
+
+
+def pmat_coeff(p, A, B, i, k, t):
+    A, B = _u64(A), _u64(B)
+    m, n, dA = A.shape
+    _, kk, dB = B.shape
+    return int(lib().orc_pmat_coeff(p, m, n, kk, _ptr(A), dA, _ptr(B), dB, i, k, t))
+
+
+def mbasis1(p, R, t):
+    """Algorithm 1: returns (Q as m x m x 2 array [const, x-coeff], rank)."""
+    R = _u64(R)
+    m, n = R.shape
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.int64))
+    Q = np.zeros((m, m, 2), dtype=np.uint64)
+    rank = lib().orc_mbasis1(p, m, n, _ptr(R), _ptr(t), _ptr(Q))
+    return Q, rank
+
+
+def mbasis(p, F, d, s, threads=None):
+    """Algorithm 2: returns (P as m x m x (d+1), rdeg_s(P))."""
+    F = _u64(F)
+    m, n, lenF = F.shape
+    s = np.ascontiguousarray(np.asarray(s, dtype=np.int64))
+    P = np.zeros((m, m, d + 1), dtype=np.uint64)
+    rd = np.zeros(m, dtype=np.int64)
+    _with_threads(threads, lambda: lib().orc_mbasis(
+        p, m, n, _ptr(F), lenF, d, _ptr(s), _ptr(P), _ptr(rd)))
+    return P, rd
+
+
+def pmbasis(p, F, d, s, T=32, threads=None):
+    """Algorithm 3 with threshold T: returns (P as m x m x (d+1), rdeg_s(P))."""
+    F = _u64(F)
+    m, n, lenF = F.shape
+    s = np.ascontiguousarray(np.asarray(s, dtype=np.int64))
+    P = np.zeros((m, m, d + 1), dtype=np.uint64)
+    rd = np.zeros(m, dtype=np.int64)
+    _with_threads(threads, lambda: lib().orc_pmbasis(
+        p, m, n, _ptr(F), lenF, d, _ptr(s), T, _ptr(P), _ptr(rd)))
+    return P, rd
+
+
+def rdeg(P, s):
+    P = _u64(P)
+    m, c, length = P.shape
+    s = np.ascontiguousarray(np.asarray(s, dtype=np.int64))
+    out = np.zeros(m, dtype=np.int64)
+    lib().orc_rdeg(m, c, _ptr(P), length, _ptr(s), _ptr(out))
+    return out
+
+
+def univ_resultant(p, a, b):
+    """Res(a, b) for coefficient lists (low degree first) with nonzero leading terms."""
+    a, b = _u64(a), _u64(b)
+    return int(lib().orc_univ_resultant(p, _ptr(a), len(a) - 1, _ptr(b), len(b) - 1))
+
+
+def bivariate_resultant(p, f, g, threads=None):
+    """Res_y(f, g) with f[j, i] = coeff of x^i y^j; returns D+1 coefficients."""
+    f, g = _u64(f), _u64(g)
+    dyf, dxf = f.shape[0] - 1, f.shape[1] - 1
+    dyg, dxg = g.shape[0] - 1, g.shape[1] - 1
+    D = dxf * dyg + dxg * dyf
+    R = np.zeros(D + 1, dtype=np.uint64)
+    rc = []
+    _with_threads(threads, lambda: rc.append(lib().orc_bivariate_resultant(
+        p, dxf, dyf, _ptr(f), dxg, dyg, _ptr(g), _ptr(R))))
+    if rc[0] != 0:
+        raise ValueError("too few evaluation points in F_p")
+    return R
+
+
+def powmod(a, e, p):
+    return int(lib().orc_powmod(a, e, p))
+
+
+def _with_threads(threads, fn):
+    """Run fn with OMP_NUM_THREADS-equivalent control through libgomp."""
+    if threads is None:
+        return fn()
+    try:
+        gomp = C.CDLL("libgomp.so.1")
+        old = gomp.omp_get_max_threads()
+        gomp.omp_set_num_threads(int(threads))
+        try:
+            return fn()
+        finally:
+            gomp.omp_set_num_threads(old)
+    except OSError:
+        return fn()
+
+
+def max_threads() -> int:
+    lib()
+    try:
+        return int(C.CDLL("libgomp.so.1").omp_get_max_threads())
+    except OSError:
+        return 1

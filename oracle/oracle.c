@@ -1,0 +1,434 @@
+/*
+ * oracle.c -- plain, slow, obviously-correct CPU oracle for polynomial-matrix
+ * arithmetic over F_p (Hyun, Neiger, Schost, ISSAC 2019, arXiv 1905.04356).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the tests, the golden-value script and the CPU
+ * baseline leg of the benchmark do.  It shares no code, header, table or
+ * constant with the CUDA path.
+ *
+ * Every value is a uint64_t residue in [0, p), with 2 <= p < 2^63.  All
+ * arithmetic is exact: products are accumulated in unsigned __int128 and
+ * reduced with the compiler's 128-bit remainder.  There is no blocking, no
+ * transform and no reordering beyond what each definition states.
+ *
+ * Layout: a polynomial matrix X with r x c entries of length len is stored
+ * entry-major, row-major: coefficient t of entry (i,j) is X[(i*c + j)*len + t].
+ *
+ * What each function follows:
+ *   orc_pmat_slice   Sec. 2 "Polynomial matrix multiplication" and
+ *                    "Polynomial multiplication": the product A.B, its
+ *                    truncation mod x^t, and MiddleProduct(F,G,c,d) = the
+ *                    coefficients of degrees c..c+d-1 of FG, all read as
+ *                    slices of the plain convolution sum.
+ *   orc_mbasis1      Algorithm 1 (M-Basis-1): the s-Popov approximant basis
+ *                    at order 1, by Gaussian elimination over rows taken in
+ *                    increasing (shift, index) order.
+ *   orc_mbasis       Algorithm 2 (M-Basis): residual = coefficient k of P.F,
+ *                    Q = M-Basis-1(residual, t), P <- Q.P, t <- rdeg_s(P).
+ *   orc_pmbasis      Algorithm 3 (PM-Basis): divide and conquer with the
+ *                    threshold T, the first half of order ceil(d/2), and the
+ *                    residual as a middle product.
+ *   orc_univ_resultant / orc_bivariate_resultant
+ *                    Sec. 5.2, the "Direct" method: evaluate in x, take
+ *                    univariate resultants in y by the Euclidean algorithm,
+ *                    interpolate (Newton divided differences).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+typedef uint64_t u64;
+typedef int64_t i64;
+
+/* ------------------------------------------------------------------ */
+/* Field arithmetic in F_p                                              */
+/* ------------------------------------------------------------------ */
+
+static inline u64 f_add(u64 a, u64 b, u64 p) { u64 s = a + b; return s >= p ? s - p : s; }
+static inline u64 f_sub(u64 a, u64 b, u64 p) { return a >= b ? a - b : a + (p - b); }
+static inline u64 f_mul(u64 a, u64 b, u64 p) { return (u64)(((u128)a * b) % p); }
+static inline u64 f_neg(u64 a, u64 p) { return a ? p - a : 0; }
+
+u64 orc_powmod(u64 a, u64 e, u64 p)
+{
+    u64 r = 1 % p;
+    a %= p;
+    while (e) {
+        if (e & 1) r = f_mul(r, a, p);
+        a = f_mul(a, a, p);
+        e >>= 1;
+    }
+    return r;
+}
+
+/* Inverse by the extended Euclidean algorithm on integers; 0 if a = 0. */
+u64 orc_invmod(u64 a, u64 p)
+{
+    i128 r0 = (i128)p, r1 = (i128)(a % p), s0 = 0, s1 = 1;
+    if (r1 == 0) return 0;
+    while (r1 != 0) {
+        i128 q = r0 / r1, t;
+        t = r0 - q * r1; r0 = r1; r1 = t;
+        t = s0 - q * s1; s0 = s1; s1 = t;
+    }
+    /* r0 = gcd = 1 for prime p; s0 * a = 1 mod p */
+    i128 v = s0 % (i128)p;
+    if (v < 0) v += (i128)p;
+    return (u64)v;
+}
+
+/* Accumulator for sums of products < 2^126: reduced whenever it reaches 2^126. */
+static inline void acc_add(u128 *acc, u64 a, u64 b, u64 p)
+{
+    *acc += (u128)a * b;
+    if (*acc >> 126) *acc %= p;
+}
+
+/* ------------------------------------------------------------------ */
+/* Products: C (m x k, len) = coefficients c0 .. c0+len-1 of A.B        */
+/* A is m x n with entries of length dA; B is n x k with length dB.     */
+/* Coefficient t of entry (i,kk) is sum_l sum_{a+b=t} A_il[a] B_lk[b].  */
+/* pmat_mul is the slice [0, dA+dB-1); pmat_mul_trunc(t) is [0, t);     */
+/* MiddleProduct(A,B,c,d) is [c, c+d).                                   */
+/* ------------------------------------------------------------------ */
+
+u64 orc_pmat_coeff(u64 p, int m, int n, int k, const u64 *A, i64 dA, const u64 *B, i64 dB,
+                   int i, int kk, i64 t)
+{
+    (void)m;
+    u128 acc = 0;
+    if (t < 0 || t > dA + dB - 2) return 0;
+    i64 a_lo = t - (dB - 1) > 0 ? t - (dB - 1) : 0;
+    i64 a_hi = t < dA - 1 ? t : dA - 1;
+    for (int l = 0; l < n; l++) {
+        const u64 *Ail = A + ((i64)i * n + l) * dA;
+        const u64 *Blk = B + ((i64)l * k + kk) * dB;
+        for (i64 a = a_lo; a <= a_hi; a++) acc_add(&acc, Ail[a], Blk[t - a], p);
+    }
+    return (u64)(acc % p);
+}
+
+void orc_pmat_slice(u64 p, int m, int n, int k, const u64 *A, i64 dA, const u64 *B, i64 dB,
+                    i64 c0, i64 len, u64 *C)
+{
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+    for (int i = 0; i < m; i++)
+        for (int kk = 0; kk < k; kk++) {
+            u64 *out = C + ((i64)i * k + kk) * len;
+            for (i64 t = 0; t < len; t++)
+                out[t] = orc_pmat_coeff(p, m, n, k, A, dA, B, dB, i, kk, c0 + t);
+        }
+}
+
+void orc_pmat_mul(u64 p, int m, int n, int k, const u64 *A, i64 dA, const u64 *B, i64 dB, u64 *C)
+{
+    orc_pmat_slice(p, m, n, k, A, dA, B, dB, 0, dA + dB - 1, C);
+}
+
+void orc_pmat_mul_trunc(u64 p, int m, int n, int k, const u64 *A, i64 dA, const u64 *B, i64 dB,
+                        i64 t, u64 *C)
+{
+    orc_pmat_slice(p, m, n, k, A, dA, B, dB, 0, t, C);
+}
+
+void orc_pmat_middle_product(u64 p, int m, int n, int k, const u64 *A, i64 dA, const u64 *B,
+                             i64 dB, i64 c, i64 d, u64 *C)
+{
+    orc_pmat_slice(p, m, n, k, A, dA, B, dB, c, d, C);
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 1, M-Basis-1(R, t): R in F_p^{m x n}, shift t in Z^m.      */
+/* Output Q (m x m, degree <= 1) as Q[(i*m + j)*2 + e], e = 0 constant,  */
+/* e = 1 coefficient of x.  Returns the rank of R.                       */
+/*                                                                     */
+/* Rows are visited in increasing (t_i, i) order (the s-pivot is the     */
+/* rightmost entry reaching the s-degree, so among equal shifts a later  */
+/* index is the pivot of a kernel row).  A row that is independent of    */
+/* the rows before it becomes x.e_i; a dependent row j becomes           */
+/* e_j - sum c_ji e_i, its unique expression over the earlier            */
+/* independent rows.  This is the t-Popov basis of the order-1 module,   */
+/* which is unique.                                                      */
+/* ------------------------------------------------------------------ */
+
+int orc_mbasis1(u64 p, int m, int n, const u64 *R, const i64 *t, u64 *Q)
+{
+    int *order = (int *)malloc(sizeof(int) * m);
+    int *piv = (int *)malloc(sizeof(int) * m);
+    u64 *bv = (u64 *)calloc((size_t)m * n, sizeof(u64));  /* echelon rows, pivot 1 */
+    u64 *bc = (u64 *)calloc((size_t)m * m, sizeof(u64));  /* bv[b] = sum_i bc[b][i] R_i */
+    u64 *v = (u64 *)malloc(sizeof(u64) * n);
+    u64 *tv = (u64 *)malloc(sizeof(u64) * m);
+    int rank = 0;
+
+    /* stable insertion sort of row indices by shift */
+    for (int i = 0; i < m; i++) {
+        int j = i;
+        while (j > 0 && t[order[j - 1]] > t[i]) { order[j] = order[j - 1]; j--; }
+        order[j] = i;
+    }
+    memset(Q, 0, sizeof(u64) * (size_t)m * m * 2);
+
+    for (int oi = 0; oi < m; oi++) {
+        int r = order[oi];
+        for (int c = 0; c < n; c++) v[c] = R[(i64)r * n + c];
+        memset(tv, 0, sizeof(u64) * m);
+        tv[r] = 1;
+        for (int b = 0; b < rank; b++) {
+            u64 f = v[piv[b]];
+            if (!f) continue;
+            for (int c = 0; c < n; c++) v[c] = f_sub(v[c], f_mul(f, bv[(i64)b * n + c], p), p);
+            for (int c = 0; c < m; c++) tv[c] = f_sub(tv[c], f_mul(f, bc[(i64)b * m + c], p), p);
+        }
+        int pc = -1;
+        for (int c = 0; c < n; c++) if (v[c]) { pc = c; break; }
+        if (pc >= 0) {
+            u64 inv = orc_invmod(v[pc], p);
+            for (int c = 0; c < n; c++) bv[(i64)rank * n + c] = f_mul(v[c], inv, p);
+            for (int c = 0; c < m; c++) bc[(i64)rank * m + c] = f_mul(tv[c], inv, p);
+            piv[rank++] = pc;
+            Q[((i64)r * m + r) * 2 + 1] = 1;            /* x . e_r */
+        } else {
+            for (int c = 0; c < m; c++) Q[((i64)r * m + c) * 2 + 0] = tv[c];
+        }
+    }
+    free(order); free(piv); free(bv); free(bc); free(v); free(tv);
+    return rank;
+}
+
+/* rdeg_s(P)_i = max_j (deg P_ij + s_j) over the nonzero entries of row i
+ * (Sec. 3, definition of the s-degree); a zero row gets INT64_MIN. */
+void orc_rdeg(int m, int c, const u64 *P, i64 len, const i64 *s, i64 *out)
+{
+    for (int i = 0; i < m; i++) {
+        i64 best = INT64_MIN;
+        for (int j = 0; j < c; j++) {
+            const u64 *e = P + ((i64)i * c + j) * len;
+            i64 dg = -1;
+            for (i64 a = len - 1; a >= 0; a--) if (e[a]) { dg = a; break; }
+            if (dg >= 0 && dg + s[j] > best) best = dg + s[j];
+        }
+        out[i] = best;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 2, M-Basis(F, d, s).  F is m x n with entries of length     */
+/* lenF (coefficients beyond lenF are zero).  Output P (m x m, length    */
+/* d+1) and rdeg_s(P).                                                   */
+/* ------------------------------------------------------------------ */
+
+void orc_mbasis(u64 p, int m, int n, const u64 *F, i64 lenF, i64 d, const i64 *s,
+                u64 *P, i64 *rdeg)
+{
+    const i64 len = d + 1;
+    u64 *R = (u64 *)malloc(sizeof(u64) * (size_t)m * n);
+    u64 *Q = (u64 *)malloc(sizeof(u64) * (size_t)m * m * 2);
+    u64 *Pn = (u64 *)calloc((size_t)m * m * len, sizeof(u64));
+    i64 *t = (i64 *)malloc(sizeof(i64) * m);
+    i64 degP = 0; /* every entry of P has degree <= degP */
+
+    memset(P, 0, sizeof(u64) * (size_t)m * m * len);
+    for (int i = 0; i < m; i++) P[((i64)i * m + i) * len] = 1;
+    for (int i = 0; i < m; i++) t[i] = s[i];
+
+    for (i64 k = 0; k < d; k++) {
+        /* a. residual R = coefficient of degree k of P.F */
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int i = 0; i < m; i++)
+            for (int j = 0; j < n; j++) {
+                u128 acc = 0;
+                for (int l = 0; l < m; l++) {
+                    const u64 *Pil = P + ((i64)i * m + l) * len;
+                    const u64 *Flj = F + ((i64)l * n + j) * lenF;
+                    i64 amax = degP < k ? degP : k;
+                    for (i64 a = 0; a <= amax; a++) {
+                        i64 b = k - a;
+                        if (b < lenF) acc_add(&acc, Pil[a], Flj[b], p);
+                    }
+                }
+                R[(i64)i * n + j] = (u64)(acc % p);
+            }
+        /* b. Q = M-Basis-1(R, t) */
+        orc_mbasis1(p, m, n, R, t, Q);
+        /* c. P <- Q.P (Q has degree <= 1) */
+        i64 degN = degP + 1 < d ? degP + 1 : d;
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int i = 0; i < m; i++)
+            for (int j = 0; j < m; j++) {
+                u64 *out = Pn + ((i64)i * m + j) * len;
+                for (i64 a = 0; a <= degN; a++) {
+                    u128 acc = 0;
+                    for (int l = 0; l < m; l++) {
+                        u64 q0 = Q[((i64)i * m + l) * 2 + 0], q1 = Q[((i64)i * m + l) * 2 + 1];
+                        const u64 *Plj = P + ((i64)l * m + j) * len;
+                        if (q0 && a <= degP) acc_add(&acc, q0, Plj[a], p);
+                        if (q1 && a >= 1 && a - 1 <= degP) acc_add(&acc, q1, Plj[a - 1], p);
+                    }
+                    out[a] = (u64)(acc % p);
+                }
+            }
+        degP = degN;
+        memcpy(P, Pn, sizeof(u64) * (size_t)m * m * len);
+        /* ... and t <- rdeg_s(P) */
+        orc_rdeg(m, m, P, len, s, t);
+    }
+    for (int i = 0; i < m; i++) rdeg[i] = t[i];
+    free(R); free(Q); free(Pn); free(t);
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 3, PM-Basis(F, d, s) with threshold T (M-Basis if d <= T). */
+/* ------------------------------------------------------------------ */
+
+void orc_pmbasis(u64 p, int m, int n, const u64 *F, i64 lenF, i64 d, const i64 *s, i64 T,
+                 u64 *P, i64 *rdeg)
+{
+    if (d <= T) { orc_mbasis(p, m, n, F, lenF, d, s, P, rdeg); return; }
+    const i64 d1 = (d + 1) / 2, d2 = d / 2;
+    /* F mod x^d as a dense m x n matrix of length d */
+    u64 *Fd = (u64 *)calloc((size_t)m * n * d, sizeof(u64));
+    for (i64 e = 0; e < (i64)m * n; e++)
+        for (i64 a = 0; a < d && a < lenF; a++) Fd[e * d + a] = F[e * lenF + a];
+    /* step 2: P1 = PM-Basis(F mod x^d1, d1, s) */
+    u64 *P1 = (u64 *)malloc(sizeof(u64) * (size_t)m * m * (d1 + 1));
+    i64 *t1 = (i64 *)malloc(sizeof(i64) * m);
+    orc_pmbasis(p, m, n, Fd, d, d1, s, T, P1, t1);
+    /* step 3: R = MiddleProduct(P1, F, d1, d2): coefficients d1..d-1 of P1.F */
+    u64 *Rm = (u64 *)malloc(sizeof(u64) * (size_t)m * n * (d2 > 0 ? d2 : 1));
+    orc_pmat_middle_product(p, m, m, n, P1, d1 + 1, Fd, d, d1, d2, Rm);
+    /* step 4: t = rdeg_s(P1) (returned above); step 5: P2 = PM-Basis(R, d2, t) */
+    u64 *P2 = (u64 *)malloc(sizeof(u64) * (size_t)m * m * (d2 + 1));
+    i64 *t2 = (i64 *)malloc(sizeof(i64) * m);
+    orc_pmbasis(p, m, n, Rm, d2, d2, t1, T, P2, t2);
+    /* step 6: P = P2.P1, degree <= d */
+    orc_pmat_slice(p, m, m, m, P2, d2 + 1, P1, d1 + 1, 0, d + 1, P);
+    orc_rdeg(m, m, P, d + 1, s, rdeg);
+    free(Fd); free(P1); free(t1); free(Rm); free(P2); free(t2);
+}
+
+/* ------------------------------------------------------------------ */
+/* Resultants                                                           */
+/* ------------------------------------------------------------------ */
+
+static i64 poly_deg(const u64 *a, i64 len)
+{
+    for (i64 i = len - 1; i >= 0; i--) if (a[i]) return i;
+    return -1;
+}
+
+/* Res(A, B) for A of degree a and B of degree b (actual degrees, both >= 0)
+ * by the Euclidean algorithm: with R = A mod B of degree r,
+ *   Res(A, B) = (-1)^(a b) lc(B)^(a - r) Res(B, R),
+ * Res(A, c) = c^a for a nonzero constant c, and Res = 0 when a remainder
+ * vanishes before a constant is reached.  Res(A,B) = lc(A)^b lc(B)^a
+ * prod (alpha_i - beta_j) over the roots. */
+u64 orc_univ_resultant(u64 p, const u64 *A0, i64 a, const u64 *B0, i64 b)
+{
+    u64 *A = (u64 *)malloc(sizeof(u64) * (a + 1));
+    u64 *B = (u64 *)malloc(sizeof(u64) * (b + 1));
+    memcpy(A, A0, sizeof(u64) * (a + 1));
+    memcpy(B, B0, sizeof(u64) * (b + 1));
+    u64 acc = 1 % p;
+    for (;;) {
+        if (b == 0) { acc = f_mul(acc, orc_powmod(B[0], (u64)a, p), p); break; }
+        if (a == 0) { acc = f_mul(acc, orc_powmod(A[0], (u64)b, p), p); break; }
+        /* A <- A mod B, by long division from the top coefficient down */
+        u64 ilc = orc_invmod(B[b], p);
+        for (i64 da = a; da >= b; da--) {
+            u64 f = f_mul(A[da], ilc, p);
+            if (!f) continue;
+            for (i64 i = 0; i <= b; i++)
+                A[da - b + i] = f_sub(A[da - b + i], f_mul(f, B[i], p), p);
+        }
+        i64 r = poly_deg(A, a < b ? a + 1 : b);
+        if (r < 0) { acc = 0; break; }
+        if ((a & 1) && (b & 1)) acc = f_neg(acc, p);
+        acc = f_mul(acc, orc_powmod(B[b], (u64)(a - r), p), p);
+        /* (A, B) <- (B, R) */
+        u64 *tmp = A; A = B; B = tmp;
+        a = b; b = r;
+    }
+    free(A); free(B);
+    return acc;
+}
+
+/* Res_y(f, g) in F_p[x] with formal y-degrees dyf, dyg.
+ * f[j*(dxf+1) + i] = coefficient of x^i y^j (likewise g).
+ * R receives D+1 coefficients, D = dxf*dyg + dxg*dyf (the degree bound).
+ * Points x = 0, 1, 2, ... where lc_y(f)(x) lc_y(g)(x) = 0 are skipped, so at
+ * the points used the univariate degrees equal the formal ones and the
+ * resultant specialises.  Returns 0 on success, -1 if p has too few points. */
+int orc_bivariate_resultant(u64 p, int dxf, int dyf, const u64 *f, int dxg, int dyg,
+                            const u64 *g, u64 *R)
+{
+    const i64 D = (i64)dxf * dyg + (i64)dxg * dyf;
+    const i64 N = D + 1;
+    u64 *xs = (u64 *)malloc(sizeof(u64) * N);
+    u64 *vs = (u64 *)malloc(sizeof(u64) * N);
+    /* choose the points */
+    i64 cnt = 0;
+    for (u64 x = 0; cnt < N; x++) {
+        if (x >= p) { free(xs); free(vs); return -1; }
+        u64 lf = 0, lg = 0;
+        for (int i = dxf; i >= 0; i--) lf = f_add(f_mul(lf, x, p), f[(i64)dyf * (dxf + 1) + i], p);
+        for (int i = dxg; i >= 0; i--) lg = f_add(f_mul(lg, x, p), g[(i64)dyg * (dxg + 1) + i], p);
+        if (lf && lg) xs[cnt++] = x;
+    }
+    /* values: univariate resultants of the specialisations */
+#pragma omp parallel
+    {
+        u64 *fa = (u64 *)malloc(sizeof(u64) * (dyf + 1));
+        u64 *ga = (u64 *)malloc(sizeof(u64) * (dyg + 1));
+#pragma omp for schedule(dynamic, 16)
+        for (i64 t = 0; t < N; t++) {
+            u64 x = xs[t];
+            for (int j = 0; j <= dyf; j++) {
+                u64 v = 0;
+                for (int i = dxf; i >= 0; i--) v = f_add(f_mul(v, x, p), f[(i64)j * (dxf + 1) + i], p);
+                fa[j] = v;
+            }
+            for (int j = 0; j <= dyg; j++) {
+                u64 v = 0;
+                for (int i = dxg; i >= 0; i--) v = f_add(f_mul(v, x, p), g[(i64)j * (dxg + 1) + i], p);
+                ga[j] = v;
+            }
+            vs[t] = orc_univ_resultant(p, fa, dyf, ga, dyg);
+        }
+        free(fa); free(ga);
+    }
+    /* Newton divided differences; x_i - x_{i-j} is a positive integer at most
+     * xs[N-1], so a table of inverses of 1..xs[N-1] serves every level.
+     * Level j: c_i <- (c_i - c_{i-1}) / (x_i - x_{i-j}) for i >= j. */
+    u64 xmax = xs[N - 1];
+    u64 *inv = (u64 *)malloc(sizeof(u64) * (xmax + 2));
+    u64 *c = vs, *c2 = (u64 *)malloc(sizeof(u64) * N);
+    inv[0] = 0;
+#pragma omp parallel for schedule(static)
+    for (i64 e = 1; e <= (i64)xmax; e++) inv[e] = orc_invmod((u64)e, p);
+    for (i64 j = 1; j < N; j++) {
+#pragma omp parallel for schedule(static) if (N - j > 4096)
+        for (i64 i = j; i < N; i++)
+            c2[i] = f_mul(f_sub(c[i], c[i - 1], p), inv[xs[i] - xs[i - j]], p);
+        memcpy(c + j, c2 + j, sizeof(u64) * (N - j));
+    }
+    /* Newton form -> monomial form, from the innermost factor out:
+     * R <- R.(x - x_i) + c_i for i = N-2 .. 0, starting from R = c_{N-1}. */
+    u64 *Rn = c2;
+    memset(R, 0, sizeof(u64) * N);
+    R[0] = c[N - 1];
+    for (i64 i = N - 2, deg = 0; i >= 0; i--, deg++) {
+        u64 xi = xs[i];
+        Rn[deg + 1] = R[deg];
+#pragma omp parallel for schedule(static) if (deg > 4096)
+        for (i64 e = 1; e <= deg; e++) Rn[e] = f_sub(R[e - 1], f_mul(xi, R[e], p), p);
+        Rn[0] = f_sub(c[i], f_mul(xi, R[0], p), p);
+        memcpy(R, Rn, sizeof(u64) * (deg + 2));
+    }
+    free(c2);
+    free(xs); free(vs); free(inv);
+    return 0;
+}
