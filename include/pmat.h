@@ -1,0 +1,161 @@
+/*
+ * pmat.h -- C ABI of libpmat: exact univariate polynomial-matrix arithmetic
+ * over F_p on one GB300 GPU (sm_103a).
+ *
+ * Operations (Hyun, Neiger, Schost, "Implementations of efficient univariate
+ * polynomial matrix algorithms and application to bivariate resultants",
+ * ISSAC 2019):
+ *   pmat_mul, pmat_mul_trunc      Sec. 2, "Polynomial matrix multiplication"
+ *   pmat_middle_product           Sec. 2, "Polynomial multiplication":
+ *                                 MiddleProduct(F, G, c, d)
+ *   pmat_mul_batched              many independent products in one call
+ *   pm_basis                      Sec. 3, Algorithm 3 (PM-Basis) over
+ *                                 Algorithms 1-2 (M-Basis-1, M-Basis)
+ *   bivariate_resultant           Sec. 5.2, resultant of bivariate
+ *                                 polynomials (the direct method)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * * A polynomial matrix X with r x c entries of length len is one contiguous
+ *   array in DEVICE memory, entry-major and row-major: coefficient t of entry
+ *   (i, j) is X[(i*c + j)*len + t].
+ * * Element width w is 4 (uint32_t, requires p < 2^32) or 8 (uint64_t,
+ *   requires p < 2^62).  Inputs must be reduced into [0, p); outputs are.
+ * * p >= 2.  Products are ring operations and accept any such p; pm_basis and
+ *   bivariate_resultant need p prime (not checked, as for a field type) and
+ *   odd (checked).
+ * * The caller owns every input and output buffer; outputs must not alias
+ *   inputs.  The context owns its workspace, twiddle tables and plans.
+ * * All calls are asynchronous and ordered on the context's stream.  A
+ *   status returned by a call covers argument checking and launch errors;
+ *   pm_sync() waits for the stream and returns the first deferred error.
+ * * Every function returns an int status (PM_OK = 0 or a PM_E* code below)
+ *   and never throws.  pm_last_error() gives a message for the last failure.
+ * * Maximum transform length is 2^20 points: a product whose result needs
+ *   more returns PM_EINVAL.
+ */
+#ifndef PMAT_H
+#define PMAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PM_OK = 0,
+    PM_EINVAL = 1,       /* bad argument (dimension, length, modulus, width) */
+    PM_EDOMAIN = 2,      /* an input coefficient is not in [0, p) (debug check) */
+    PM_ENOMEM = 3,       /* device workspace allocation failed */
+    PM_ECUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+    PM_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
+    PM_EUNSUPPORTED = 6  /* valid request outside what this build handles */
+};
+
+typedef struct pm_ctx pm_ctx;
+
+/* Option keys for pm_set_option. */
+enum {
+    PM_OPT_POINTWISE = 1,   /* 0 = auto, 1 = CUDA-core 64-bit, 2 = tensor-core limbs */
+    PM_OPT_THRESHOLD = 2,   /* PM-Basis threshold T (>= 1): M-Basis when order <= T;
+                               default 32 (Sec. 3, "Interpolant bases") */
+    PM_OPT_DEBUG_CHECKS = 3 /* 1 = check inputs are in [0, p) (PM_EDOMAIN) */
+};
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * owned by the caller (kept, not destroyed), or NULL for a context-owned
+ * non-blocking stream.  *ctx receives the handle.  Returns PM_EINVAL on a bad
+ * device, PM_ECUDA on a runtime failure. */
+int pm_create(pm_ctx **ctx, int device, void *cuda_stream);
+
+/* Destroy a context: synchronises its stream, frees its device memory. */
+int pm_destroy(pm_ctx *ctx);
+
+/* Set an option (keys above).  PM_EINVAL on an unknown key or bad value. */
+int pm_set_option(pm_ctx *ctx, int key, int64_t value);
+
+/* Replace the stream used by later calls (NULL = the context's own). */
+int pm_set_stream(pm_ctx *ctx, void *cuda_stream);
+
+/* Wait for all work queued on the context's stream; return the first
+ * deferred error (kernel fault, device-side timeout) or PM_OK. */
+int pm_sync(pm_ctx *ctx);
+
+/* Message for the last non-OK status on this context (never NULL). */
+const char *pm_last_error(pm_ctx *ctx);
+
+/* Number of CUDA kernel launches issued by this context since creation
+ * (a diagnostic counter; it includes set-up kernels). */
+int64_t pm_kernel_launches(pm_ctx *ctx);
+
+/* C (m x k, length dA+dB-1) = A (m x n, length dA) . B (n x k, length dB)
+ * mod p.  Sec. 2, "Polynomial matrix multiplication": evaluation and
+ * interpolation at roots of unity; for moduli without suitable roots the
+ * product is lifted to Z[x] and taken modulo several NTT primes, then
+ * recombined (the "3-primes" approach, with as many primes as the integer
+ * coefficients need).  Requires m, n, k, dA, dB >= 1. */
+int pmat_mul(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k,
+             const void *A, int64_t dA, const void *B, int64_t dB, void *C);
+
+/* C (m x k, length t) = A . B mod x^t (Sec. 2; the truncated product used by
+ * Newton iteration in Sec. 4.3).  Requires t >= 1; coefficients of degree
+ * >= dA+dB-1 are zero. */
+int pmat_mul_trunc(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k,
+                   const void *A, int64_t dA, const void *B, int64_t dB, int64_t t, void *C);
+
+/* C (m x k, length d) = MiddleProduct(A, B, c, d): the coefficients of
+ * degrees c .. c+d-1 of A . B (Sec. 2, "Polynomial multiplication").
+ * The paper states it for A of length c and B of length c+d; this entry
+ * point also accepts A of length c+1, the case of the PM-Basis residual
+ * (Algorithm 3, step 3).  Requires 1 <= dA <= c+1, 1 <= dB <= c+d, d >= 1. */
+int pmat_middle_product(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k,
+                        const void *A, int64_t dA, const void *B, int64_t dB,
+                        int64_t c, int64_t d, void *C);
+
+/* One product of a batch: C_i = A_i . B_i mod p_i, full length dA+dB-1.
+ * Descriptors live in HOST memory; the matrices in device memory. */
+typedef struct {
+    uint64_t p;
+    int w, m, n, k;
+    const void *A;
+    int64_t dA;
+    const void *B;
+    int64_t dB;
+    void *C;
+} pmat_desc;
+
+/* `count` independent products (each as pmat_mul) in one call: work of all
+ * products is binned by transform length and run by shared launches.  On a
+ * bad descriptor returns PM_EINVAL and runs nothing. */
+int pmat_mul_batched(pm_ctx *ctx, int count, const pmat_desc *descs);
+
+/* PM-Basis (Sec. 3, Algorithm 3; leaves: Algorithm 2 with Algorithm 1).
+ * F: m x n matrix of uint64_t (w = 8) with entries of length lenF in device
+ * memory; only F mod x^d is read (requires lenF >= 1; missing coefficients are
+ * zero).  shift: HOST int64_t[m].  P: DEVICE output, m x m entries of length
+ * d+1, an s-ordered weak Popov approximant basis of (F, d).  rdeg_out: HOST
+ * int64_t[m] receiving rdeg_s(P) (this call therefore synchronises the
+ * stream).  Requires p odd, 1 <= n, 1 <= m, d >= 1. */
+int pm_basis(pm_ctx *ctx, uint64_t p, int m, int n, const void *F, int64_t lenF,
+             int64_t d, const int64_t *shift, void *P, int64_t *rdeg_out);
+
+/* Res_y(f, g) in F_p[x] for f, g in F_p[x, y] with formal y-degrees dyf,
+ * dyg and x-degrees <= dxf, dxg (Sec. 5.2, the direct evaluation /
+ * interpolation method).  f: DEVICE uint64_t[(dyf+1)*(dxf+1)] with
+ * f[j*(dxf+1) + i] = coefficient of x^i y^j (likewise g).  R: DEVICE
+ * uint64_t[nprimes][D+1], D = dxf*dyg + dxg*dyf; instance i is computed
+ * modulo primes[i] (HOST array) from f + i*(dyf+1)*(dxf+1) and
+ * g + i*(dyg+1)*(dxg+1).  Requires every prime odd and larger than 2(D+1),
+ * the leading y-coefficients not identically zero.  Returns PM_EUNSUPPORTED
+ * when no usable geometric progression is found. */
+int bivariate_resultant(pm_ctx *ctx, int nprimes, const uint64_t *primes,
+                        int dxf, int dyf, const void *f, int dxg, int dyg, const void *g,
+                        void *R);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMAT_H */

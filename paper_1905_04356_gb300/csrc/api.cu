@@ -1,0 +1,575 @@
+// api.cu -- context management and the product entry points of the C ABI.
+//
+// Products (Sec. 2, "Polynomial matrix multiplication"): forward transforms
+// of every entry of A and B, pointwise m x n . n x k products at every point,
+// inverse transforms with the requested slice, and -- when p itself has no
+// suitable roots of unity -- the same modulo K NTT primes followed by CRT.
+// Transform lengths: full product L >= dA + dB - 1; truncated product mod x^t
+// L >= min(dA,t) + min(dB,t) - 1; middle product of degrees c..c+d-1
+// L >= c + d, since every aliased coefficient then lands below c.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "host.h"
+
+// ------------------------------------------------------------------ errors
+int pm_fail(pm_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int pm_cuda(pm_ctx *ctx, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return PM_OK;
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return pm_fail(ctx, PM_ENOMEM, m);
+    return pm_fail(ctx, PM_ECUDA, m);
+}
+
+#define CK(call)                                                        \
+    do {                                                                \
+        int _rc = pm_cuda(ctx, (call), #call);                          \
+        if (_rc) return _rc;                                            \
+    } while (0)
+#define CKI(call)                                                       \
+    do {                                                                \
+        int _rc = (call);                                               \
+        if (_rc) return _rc;                                            \
+    } while (0)
+
+// ------------------------------------------------------------------ host arithmetic
+uint64_t host_mulmod(uint64_t a, uint64_t b, uint64_t p) { return (uint64_t)((unsigned __int128)a * b % p); }
+uint64_t host_powmod(uint64_t a, uint64_t e, uint64_t p)
+{
+    uint64_t r = 1 % p;
+    a %= p;
+    while (e) {
+        if (e & 1) r = host_mulmod(r, a, p);
+        a = host_mulmod(a, a, p);
+        e >>= 1;
+    }
+    return r;
+}
+
+// Deterministic Miller-Rabin for n < 2^32 (bases 2, 7, 61 suffice below 4.76e9).
+static bool is_prime32(uint64_t n)
+{
+    if (n < 2) return false;
+    for (uint64_t s : {2ull, 3ull, 5ull, 7ull, 11ull, 13ull, 61ull})
+        if (n % s == 0) return n == s;
+    uint64_t d = n - 1;
+    int r = 0;
+    while (!(d & 1)) { d >>= 1; r++; }
+    for (uint64_t a : {2ull, 7ull, 61ull}) {
+        uint64_t x = host_powmod(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool comp = true;
+        for (int i = 1; i < r && comp; i++) {
+            x = host_mulmod(x, x, n);
+            if (x == n - 1) comp = false;
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+
+int ceil_log2(int64_t x)
+{
+    int l = 0;
+    while ((int64_t(1) << l) < x) l++;
+    return l;
+}
+
+// Primitive root of F_q (q prime < 2^32): trial-factor q - 1.
+static uint32_t primitive_root(uint32_t q)
+{
+    std::vector<uint64_t> f;
+    uint64_t m = q - 1;
+    for (uint64_t d = 2; d * d <= m; d++)
+        if (m % d == 0) {
+            f.push_back(d);
+            while (m % d == 0) m /= d;
+        }
+    if (m > 1) f.push_back(m);
+    for (uint64_t g = 2;; g++) {
+        bool ok = true;
+        for (uint64_t d : f)
+            if (host_powmod(g, (q - 1) / d, q) == 1) { ok = false; break; }
+        if (ok) return (uint32_t)g;
+    }
+}
+
+static void slot_init(PrimeSlot &s, uint32_t q)
+{
+    s.q = q;
+    uint64_t g = primitive_root(q);
+    for (int l = 0; l <= PM_MAX_LOG2L; l++) {
+        if (((uint64_t)(q - 1) % (1ull << l)) != 0) { s.rf[l] = s.ri[l] = 0; continue; }
+        uint64_t w = host_powmod(g, (q - 1) >> l, q);
+        s.rf[l] = (u32)w;
+        s.ri[l] = (u32)host_powmod(w, q - 2, q);
+    }
+}
+
+static int slot_tables(pm_ctx *ctx, PrimeSlot &s, int lg)
+{
+    if (s.maxlog >= lg && s.twf) return PM_OK;
+    int want = lg < PM_LB_LOG2 ? PM_LB_LOG2 : lg;
+    if (s.rf[want] == 0) want = lg;
+    size_t bytes = (size_t(1) << want) * sizeof(uint2);
+    if (s.twf) { CK(cudaFreeAsync(s.twf, ctx->stream)); CK(cudaFreeAsync(s.twi, ctx->stream)); }
+    s.twf = s.twi = nullptr;
+    CK(cudaMallocAsync((void **)&s.twf, bytes, ctx->stream));
+    CK(cudaMallocAsync((void **)&s.twi, bytes, ctx->stream));
+    CK(launch_twiddles(s.twf, s.twi, s.q, s.rf, s.ri, want, ctx->stream, &ctx->launches));
+    s.maxlog = want;
+    return PM_OK;
+}
+
+static PrimeDev prime_dev(const PrimeSlot &s, int lg)
+{
+    PrimeDev P;
+    const uint64_t q = s.q;
+    P.q = s.q;
+    P.q2 = 2 * s.q;
+    P.r32 = (u32)((1ull << 32) % q);
+    P.r32s = (u32)(((uint64_t)P.r32 << 32) / q);
+    P.ones = (u32)((1ull << 32) / q);
+    uint64_t L = 1ull << lg;
+    P.linv = (u32)host_powmod(L % q, q - 2, q);
+    P.linvs = (u32)(((uint64_t)P.linv << 32) / q);
+    P.twf = s.twf;
+    P.twi = s.twi;
+    return P;
+}
+
+// ------------------------------------------------------------------ memory
+int ws_reserve(pm_ctx *ctx, size_t bytes, void **out)
+{
+    if (bytes > ctx->ws_size) {
+        size_t want = bytes + (bytes >> 3);
+        if (ctx->ws) CK(cudaFreeAsync(ctx->ws, ctx->stream));
+        ctx->ws = nullptr;
+        ctx->ws_size = 0;
+        cudaError_t e = cudaMallocAsync(&ctx->ws, want, ctx->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->ws = nullptr;
+            return pm_fail(ctx, PM_ENOMEM, "workspace allocation failed");
+        }
+        ctx->ws_size = want;
+    }
+    *out = ctx->ws;
+    return PM_OK;
+}
+
+int arena_reserve(pm_ctx *ctx, size_t bytes)
+{
+    Arena &a = ctx->arena;
+    a.used = 0;
+    if (bytes <= a.size) return PM_OK;
+    if (a.base) CK(cudaFreeAsync(a.base, ctx->stream));
+    a.base = nullptr;
+    a.size = 0;
+    cudaError_t e = cudaMallocAsync((void **)&a.base, bytes, ctx->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        a.base = nullptr;
+        return pm_fail(ctx, PM_ENOMEM, "driver arena allocation failed");
+    }
+    a.size = bytes;
+    return PM_OK;
+}
+
+void *arena_alloc(pm_ctx *ctx, size_t bytes)
+{
+    Arena &a = ctx->arena;
+    size_t off = (a.used + 255) & ~size_t(255);
+    if (off + bytes > a.size) return nullptr;
+    a.used = off + bytes;
+    return a.base + off;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ------------------------------------------------------------------ primes per product
+// The product is exact over Z when prod q_i exceeds the largest integer
+// coefficient n . min(dA, dB) . (p-1)^2.
+static int choose_primes(pm_ctx *ctx, uint64_t p, int n, int64_t dmin, int lg, std::vector<PrimeSlot *> &out,
+                         bool &direct)
+{
+    out.clear();
+    direct = false;
+    if (p < (1ull << 30) && p > 2 && ((p - 1) % (1ull << lg)) == 0 && is_prime32(p)) {
+        for (auto &s : ctx->direct)
+            if (s.q == p) { out.push_back(&s); direct = true; break; }
+        if (!direct) {
+            ctx->direct.emplace_back();
+            slot_init(ctx->direct.back(), (u32)p);
+            // pointers into `direct` may move: rebuild after emplace
+            out.push_back(&ctx->direct.back());
+            direct = true;
+        }
+        return slot_tables(ctx, *out[0], lg);
+    }
+    const double need = std::log2((double)n) + std::log2((double)dmin) + 2.0 * std::log2((double)(p - 1 ? p - 1 : 1));
+    double have = 0;
+    for (auto &s : ctx->table) {
+        out.push_back(&s);
+        have += std::log2((double)s.q);
+        if (have > need + 0.01) break;
+    }
+    if (have <= need + 0.01) return pm_fail(ctx, PM_EUNSUPPORTED, "product needs more CRT primes than the table holds");
+    for (auto *s : out) CKI(slot_tables(ctx, *s, lg));
+    return PM_OK;
+}
+
+static void fill_crt(CrtJob &J, const std::vector<PrimeSlot *> &pr, uint64_t p)
+{
+    const int K = (int)pr.size();
+    J.K = K;
+    J.p = p;
+    J.mu = (uint64_t)(((unsigned __int128)1 << 64) / p);
+    J.small_p = p <= (1ull << 30);
+    for (int i = 0; i < K; i++) {
+        const uint64_t qi = pr[i]->q;
+        J.q[i] = (u32)qi;
+        for (int j = 0; j < i; j++) {
+            uint64_t c = host_powmod(pr[j]->q % qi, qi - 2, qi);
+            J.c[i][j] = (u32)c;
+            J.cs[i][j] = (u32)((c << 32) / qi);
+        }
+        uint64_t qm = qi % p;
+        J.qm[i] = qm;
+        J.qms[i] = (uint64_t)(((unsigned __int128)qm << 64) / p);
+    }
+}
+
+// ------------------------------------------------------------------ checks
+__global__ void k_check_range(const void *x, int64_t count, int w, uint64_t p, int *status)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t v = w == 8 ? ((const uint64_t *)x)[i] : ((const uint32_t *)x)[i];
+        if (v >= p) atomicCAS(status, 0, PM_EDOMAIN);
+    }
+}
+
+static int debug_check(pm_ctx *ctx, const void *x, int64_t count, int w, uint64_t p)
+{
+    if (!ctx->opt_debug) return PM_OK;
+    k_check_range<<<256, 256, 0, ctx->stream>>>(x, count, w, p, ctx->d_status);
+    ctx->launches++;
+    CK(cudaGetLastError());
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (st == PM_EDOMAIN) {
+        CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+        return pm_fail(ctx, PM_EDOMAIN, "input coefficient not in [0, p)");
+    }
+    return PM_OK;
+}
+
+// ------------------------------------------------------------------ product core
+template <typename J>
+static void pack_add(JobPack<J> &pk, const J &job, int blocks)
+{
+    const int n = pk.njobs;
+    pk.jobs[n] = job;
+    pk.blk_start[n + 1] = pk.blk_start[n] + blocks;
+    pk.njobs = n + 1;
+}
+
+template <typename J>
+static void pack_reset(JobPack<J> &pk)
+{
+    pk.njobs = 0;
+    pk.blk_start[0] = 0;
+}
+
+static int fwd_entries_per_block(int lg)
+{
+    const int tpt = (1 << lg) >> 4, th = fwd_block_threads(lg);
+    return th / tpt;
+}
+
+static int run_forward(pm_ctx *ctx, const PrimeDev &P, const void *src, int mode, int64_t src_stride, int64_t src_len,
+                       int entries, u32 *dst, int lg, JobPack<FwdJob> &pk, JobPack<ColJob> &pc)
+{
+    const int64_t L = int64_t(1) << lg;
+    if (lg <= PM_LB_LOG2) {
+        FwdJob j;
+        j.src = src; j.dst = dst; j.src_stride = src_stride; j.dst_stride = L;
+        j.src_len = (int)src_len; j.src_mode = mode; j.count = entries; j._pad = 0; j.P = P;
+        const int epb = fwd_entries_per_block(lg);
+        pack_add(pk, j, (entries + epb - 1) / epb);
+    } else {
+        ColJob c;
+        c.src = src; c.dst = dst; c.src_stride = src_stride; c.dst_stride = L;
+        c.src_len = (int)src_len; c.mode = mode; c.count = entries; c.out_off = 0; c.out_len = 0; c._pad = 0; c.P = P;
+        pack_add(pc, c, entries * blocks_per_entry_cols(lg));
+        FwdJob j;
+        const int64_t nb = L >> PM_LB_LOG2;
+        j.src = dst; j.dst = dst; j.src_stride = 1 << PM_LB_LOG2; j.dst_stride = 1 << PM_LB_LOG2;
+        j.src_len = 1 << PM_LB_LOG2; j.src_mode = 0; j.count = (int)(entries * nb); j._pad = 0; j.P = P;
+        const int epb = fwd_entries_per_block(PM_LB_LOG2);
+        pack_add(pk, j, (int)((entries * nb + epb - 1) / epb));
+    }
+    return PM_OK;
+}
+
+int prod_slice(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA, int64_t sA,
+               const void *B, int64_t dB, int64_t sB, int64_t off, int64_t len, int lg, void *C, int64_t sC)
+{
+    if (lg < 4) lg = 4;
+    if (lg > PM_MAX_LOG2L) return pm_fail(ctx, PM_EINVAL, "transform longer than 2^20 points");
+    const int64_t L = int64_t(1) << lg;
+    std::vector<PrimeSlot *> pr;
+    bool direct = false;
+    CKI(choose_primes(ctx, p, n, dA < dB ? dA : dB, lg, pr, direct));
+    const int K = (int)pr.size();
+    const size_t eA = (size_t)m * n, eB = (size_t)n * k, eC = (size_t)m * k;
+    const size_t bA = align256(eA * L * 4), bB = align256(eB * L * 4), bC = align256(eC * L * 4);
+    const int64_t out_len = off + len <= L ? len : (off < L ? L - off : 0);
+    const size_t bR = direct ? 0 : eC * (size_t)len * 4;   // residue planes packed: CRT indexes by count
+    void *ws = nullptr;
+    CKI(ws_reserve(ctx, K * (bA + bB + bC) + K * bR + 256, &ws));
+    char *base = (char *)ws;
+    u32 *Ah = (u32 *)base, *Bh = (u32 *)(base + K * bA), *Ch = (u32 *)(base + K * (bA + bB));
+    u32 *Rs = (u32 *)(base + K * (bA + bB + bC));
+
+    // 1. forward transforms of A and B modulo every prime (reduction fused)
+    {
+        JobPack<FwdJob> pk; pack_reset(pk);
+        JobPack<ColJob> pc; pack_reset(pc);
+        for (int i = 0; i < K; i++) {
+            PrimeDev P = prime_dev(*pr[i], lg);
+            run_forward(ctx, P, A, w, sA, dA, (int)eA, (u32 *)((char *)Ah + i * bA), lg, pk, pc);
+            run_forward(ctx, P, B, w, sB, dB, (int)eB, (u32 *)((char *)Bh + i * bB), lg, pk, pc);
+        }
+        if (pc.njobs) CK(launch_ntt_fwd_cols(pc, lg, ctx->stream, &ctx->launches));
+        CK(launch_ntt_fwd_block(pk, lg > PM_LB_LOG2 ? PM_LB_LOG2 : lg, ctx->stream, &ctx->launches));
+    }
+    // 2. pointwise products at every point
+    {
+        JobPack<PwJob> pk; pack_reset(pk);
+        for (int i = 0; i < K; i++) {
+            PwJob j;
+            j.A = (u32 *)((char *)Ah + i * bA); j.B = (u32 *)((char *)Bh + i * bB); j.C = (u32 *)((char *)Ch + i * bC);
+            j.m = m; j.n = n; j.k = k; j.L = (int)L; j.P = prime_dev(*pr[i], lg);
+            pack_add(pk, j, pw_blocks(j));
+        }
+        CK(launch_pointwise(pk, ctx->stream, &ctx->launches));
+    }
+    // 3. inverse transforms, scaled, writing the slice [off, off + len)
+    {
+        const int mode = direct ? w : 1;
+        JobPack<InvJob> pk; pack_reset(pk);
+        JobPack<ColJob> pc; pack_reset(pc);
+        for (int i = 0; i < K; i++) {
+            PrimeDev P = prime_dev(*pr[i], lg);
+            u32 *src = (u32 *)((char *)Ch + i * bC);
+            void *dst = direct ? C : (void *)((char *)Rs + i * bR);
+            const int64_t dstride = direct ? sC : len;
+            if (lg <= PM_LB_LOG2) {
+                InvJob j;
+                j.src = src; j.dst = dst; j.src_stride = L; j.dst_stride = dstride;
+                j.out_off = (int)off; j.out_len = (int)out_len; j.dst_mode = mode; j.count = (int)eC; j.P = P;
+                const int epb = fwd_entries_per_block(lg);
+                pack_add(pk, j, (int)((eC + epb - 1) / epb));
+            } else {
+                const int64_t nb = L >> PM_LB_LOG2;
+                InvJob j;
+                j.src = src; j.dst = src; j.src_stride = 1 << PM_LB_LOG2; j.dst_stride = 1 << PM_LB_LOG2;
+                j.out_off = 0; j.out_len = 0; j.dst_mode = 0; j.count = (int)(eC * nb); j.P = P;
+                const int epb = fwd_entries_per_block(PM_LB_LOG2);
+                pack_add(pk, j, (int)((eC * nb + epb - 1) / epb));
+                ColJob c;
+                c.src = src; c.dst = dst; c.src_stride = L; c.dst_stride = dstride;
+                c.src_len = 0; c.mode = mode; c.count = (int)eC; c.out_off = (int)off; c.out_len = (int)out_len; c._pad = 0;
+                c.P = P;
+                pack_add(pc, c, (int)eC * blocks_per_entry_cols(lg));
+            }
+        }
+        CK(launch_ntt_inv_block(pk, lg > PM_LB_LOG2 ? PM_LB_LOG2 : lg, ctx->stream, &ctx->launches));
+        if (pc.njobs) CK(launch_ntt_inv_cols(pc, lg, ctx->stream, &ctx->launches));
+    }
+    // 4. CRT recombination into values mod p
+    if (!direct) {
+        JobPack<CrtJob> pk; pack_reset(pk);
+        CrtJob j;
+        memset(&j, 0, sizeof(j));
+        fill_crt(j, pr, p);
+        j.res = Rs; j.dst = C; j.count = (int64_t)eC * len; j.len = len; j.dst_stride = sC; j.w = w;
+        pack_add(pk, j, crt_blocks(j));
+        CK(launch_crt(pk, ctx->stream, &ctx->launches));
+    }
+    // 5. slice positions beyond the transform length are zero
+    if (out_len < len) {
+        const int64_t z0 = out_len > 0 ? out_len : 0;
+        CK(cudaMemset2DAsync((char *)C + z0 * w, (size_t)sC * w, 0, (size_t)(len - z0) * w, eC, ctx->stream));
+    }
+    return PM_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+int pm_create(pm_ctx **out, int device, void *cuda_stream)
+{
+    if (!out) return PM_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return PM_EINVAL;
+    }
+    pm_ctx *ctx = new (std::nothrow) pm_ctx();
+    if (!ctx) return PM_ENOMEM;
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return PM_ECUDA; }
+    if (cuda_stream) ctx->stream = (cudaStream_t)cuda_stream;
+    else {
+        if (cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking) != cudaSuccess) { delete ctx; return PM_ECUDA; }
+        ctx->stream = ctx->own;
+    }
+    if (cudaMalloc((void **)&ctx->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->own) cudaStreamDestroy(ctx->own);
+        delete ctx;
+        return PM_ECUDA;
+    }
+    // CRT primes: q = c 2^20 + 1 < 2^30, largest first (all in (2^29, 2^30))
+    for (uint64_t c = 1023; c >= 512 && ctx->table.size() < PM_MAXK; c--) {
+        uint64_t q = (c << 20) + 1;
+        if (is_prime32(q)) {
+            ctx->table.emplace_back();
+            slot_init(ctx->table.back(), (u32)q);
+        }
+    }
+    ctx->direct.reserve(16);
+    *out = ctx;
+    return PM_OK;
+}
+
+int pm_destroy(pm_ctx *ctx)
+{
+    if (!ctx) return PM_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &s : ctx->table) { cudaFree(s.twf); cudaFree(s.twi); }
+    for (auto &s : ctx->direct) { cudaFree(s.twf); cudaFree(s.twi); }
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->arena.base) cudaFree(ctx->arena.base);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->own) cudaStreamDestroy(ctx->own);
+    delete ctx;
+    return PM_OK;
+}
+
+int pm_set_option(pm_ctx *ctx, int key, int64_t value)
+{
+    if (!ctx) return PM_EINVAL;
+    switch (key) {
+    case PM_OPT_POINTWISE:
+        if (value < 0 || value > 2) return pm_fail(ctx, PM_EINVAL, "pointwise path must be 0, 1 or 2");
+        ctx->opt_pointwise = (int)value;
+        return PM_OK;
+    case PM_OPT_THRESHOLD:
+        if (value < 1) return pm_fail(ctx, PM_EINVAL, "threshold must be >= 1");
+        ctx->opt_T = value;
+        return PM_OK;
+    case PM_OPT_DEBUG_CHECKS:
+        ctx->opt_debug = value ? 1 : 0;
+        return PM_OK;
+    default:
+        return pm_fail(ctx, PM_EINVAL, "unknown option key");
+    }
+}
+
+int pm_set_stream(pm_ctx *ctx, void *cuda_stream)
+{
+    if (!ctx) return PM_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own;
+    if (!ctx->stream) {
+        CK(cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking));
+        ctx->stream = ctx->own;
+    }
+    return PM_OK;
+}
+
+int pm_sync(pm_ctx *ctx)
+{
+    if (!ctx) return PM_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    int st = 0;
+    CK(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) {
+        CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
+        return pm_fail(ctx, st, st == PM_ETIMEOUT ? "device-side wait timed out" : "device status error");
+    }
+    return PM_OK;
+}
+
+const char *pm_last_error(pm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t pm_kernel_launches(pm_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+static int check_common(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA,
+                        const void *B, int64_t dB, const void *C)
+{
+    if (!ctx) return PM_EINVAL;
+    if (m < 1 || n < 1 || k < 1) return pm_fail(ctx, PM_EINVAL, "dimensions must be >= 1");
+    if (dA < 1 || dB < 1) return pm_fail(ctx, PM_EINVAL, "lengths must be >= 1");
+    if (p < 2) return pm_fail(ctx, PM_EINVAL, "modulus must be >= 2");
+    if (w != 4 && w != 8) return pm_fail(ctx, PM_EINVAL, "element width must be 4 or 8");
+    if (w == 4 && p > (1ull << 32)) return pm_fail(ctx, PM_EINVAL, "w = 4 needs p <= 2^32");
+    if (p >= (1ull << 62)) return pm_fail(ctx, PM_EINVAL, "p must be below 2^62");
+    if (!A || !B || !C) return pm_fail(ctx, PM_EINVAL, "null buffer");
+    if (dA > (1 << PM_MAX_LOG2L) || dB > (1 << PM_MAX_LOG2L)) return pm_fail(ctx, PM_EINVAL, "length exceeds 2^20");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return pm_fail(ctx, PM_ECUDA, "cudaSetDevice failed");
+    CKI(debug_check(ctx, A, (int64_t)m * n * dA, w, p));
+    CKI(debug_check(ctx, B, (int64_t)n * k * dB, w, p));
+    return PM_OK;
+}
+
+int pmat_mul(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA, const void *B,
+             int64_t dB, void *C)
+{
+    CKI(check_common(ctx, p, w, m, n, k, A, dA, B, dB, C));
+    const int64_t len = dA + dB - 1;
+    const int lg = ceil_log2(len);
+    if (lg > PM_MAX_LOG2L) return pm_fail(ctx, PM_EINVAL, "product longer than 2^20");
+    return prod_slice(ctx, p, w, m, n, k, A, dA, dA, B, dB, dB, 0, len, lg, C, len);
+}
+
+int pmat_mul_trunc(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA, const void *B,
+                   int64_t dB, int64_t t, void *C)
+{
+    CKI(check_common(ctx, p, w, m, n, k, A, dA, B, dB, C));
+    if (t < 1) return pm_fail(ctx, PM_EINVAL, "t must be >= 1");
+    const int64_t a = dA < t ? dA : t, b = dB < t ? dB : t;
+    const int lg = ceil_log2(a + b - 1);
+    if (lg > PM_MAX_LOG2L) return pm_fail(ctx, PM_EINVAL, "product longer than 2^20");
+    return prod_slice(ctx, p, w, m, n, k, A, a, dA, B, b, dB, 0, t, lg, C, t);
+}
+
+int pmat_middle_product(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA,
+                        const void *B, int64_t dB, int64_t c, int64_t d, void *C)
+{
+    CKI(check_common(ctx, p, w, m, n, k, A, dA, B, dB, C));
+    if (c < 0 || d < 1) return pm_fail(ctx, PM_EINVAL, "need c >= 0, d >= 1");
+    if (dA > c + 1) return pm_fail(ctx, PM_EINVAL, "middle product needs dA <= c + 1");
+    if (dB > c + d) return pm_fail(ctx, PM_EINVAL, "middle product needs dB <= c + d");
+    const int lg = ceil_log2(c + d);
+    if (lg > PM_MAX_LOG2L) return pm_fail(ctx, PM_EINVAL, "product longer than 2^20");
+    return prod_slice(ctx, p, w, m, n, k, A, dA, dA, B, dB, dB, c, d, lg, C, d);
+}
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+// common.cuh -- shared device arithmetic and job descriptors of libpmat.
+//
+// Modular arithmetic is written from the published methods:
+//  * Shoup's precomputed-quotient multiplication (V. Shoup, NTL; "Harvey,
+//    Faster arithmetic for number-theoretic transforms", 2014, Sec. 2): for a
+//    constant w < q and w' = floor(w 2^32 / q), x w mod q lies in [0, 2q).
+//  * Harvey's lazy butterflies (same paper, Algorithms 4 and 5): values are
+//    kept in [0, 2q) (Gentleman-Sande, forward) or [0, 4q) (Cooley-Tukey,
+//    inverse), which needs q < 2^30.
+//  * Barrett reduction (P. Barrett, CRYPTO 1986) with mu = floor(2^64 / p).
+//  * Montgomery multiplication (P. L. Montgomery, Math. Comp. 1985) with
+//    R = 2^64 for odd p < 2^63.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+typedef uint32_t u32;
+typedef uint64_t u64;
+typedef int64_t i64;
+
+#define PM_MAX_LOG2L 20      // largest transform: 2^20 points
+#define PM_LB_LOG2 13        // transforms up to 2^13 points run in one CTA
+#define PM_MAXJ 32           // job descriptors per launch
+#define PM_MAXK 6            // CRT primes per product
+
+// ---------------------------------------------------------------- 32-bit
+__device__ __forceinline__ u32 shoup_mul(u32 x, u32 w, u32 ws, u32 q)
+{
+    return x * w - __umulhi(x, ws) * q;   // in [0, 2q) for any x < 2^32
+}
+__device__ __forceinline__ u32 csub(u32 x, u32 m) { return min(x, x - m); }  // x < 2m -> [0,m)
+
+// Gentleman-Sande (DIF) butterfly, inputs and outputs in [0, 2q):
+// (X, Y) -> (X + Y, (X - Y) w)
+__device__ __forceinline__ void bfly_dif(u32 &X, u32 &Y, uint2 w, u32 q, u32 q2)
+{
+    u32 s = X + Y;
+    u32 d = X - Y + q2;
+    X = csub(s, q2);
+    Y = shoup_mul(d, w.x, w.y, q);
+}
+// Cooley-Tukey (DIT) butterfly, inputs and outputs in [0, 4q):
+// (X, Y) -> (X + Y w, X - Y w)
+__device__ __forceinline__ void bfly_dit(u32 &X, u32 &Y, uint2 w, u32 q, u32 q2)
+{
+    u32 x = csub(X, q2);
+    u32 t = shoup_mul(Y, w.x, w.y, q);
+    X = x + t;
+    Y = x - t + q2;
+}
+
+// Per-prime constants carried by every job.
+struct PrimeDev {
+    u32 q, q2;         // q, 2q
+    u32 r32, r32s;     // 2^32 mod q, Shoup companion
+    u32 ones;          // floor(2^32 / q): Shoup companion of 1
+    u32 linv, linvs;   // L^-1 mod q for the job's transform length, companion
+    const uint2 *twf;  // twf[h + r] = (omega_{2h}^r, companion), h = 1, 2, 4, ...
+    const uint2 *twi;  // inverse roots
+};
+
+// x mod q in [0, q) for x < 2^64 (x = hi 2^32 + lo, both folded by Shoup)
+__device__ __forceinline__ u32 reduce64(u64 x, const PrimeDev &P)
+{
+    u32 hi = (u32)(x >> 32), lo = (u32)x;
+    u32 s = shoup_mul(hi, P.r32, P.r32s, P.q) + shoup_mul(lo, 1u, P.ones, P.q);  // < 4q
+    return csub(csub(s, P.q2), P.q);
+}
+
+// ---------------------------------------------------------------- 64-bit
+__device__ __forceinline__ u64 shoup_mul64(u64 x, u64 w, u64 ws, u64 p)
+{
+    return x * w - __umul64hi(x, ws) * p;  // in [0, 2p), p < 2^63
+}
+__device__ __forceinline__ u64 csub64(u64 x, u64 m) { return x >= m ? x - m : x; }
+__device__ __forceinline__ u64 barrett64(u64 x, u64 p, u64 mu)
+{
+    u64 r = x - __umul64hi(x, mu) * p;     // in [0, 2p)
+    return csub64(r, p);
+}
+// Montgomery product a b R^-1 mod p for a, b < p, p odd < 2^63, pn = -p^-1 mod 2^64
+__device__ __forceinline__ u64 mont_mul(u64 a, u64 b, u64 p, u64 pn)
+{
+    u64 lo = a * b, hi = __umul64hi(a, b);
+    u64 m = lo * pn;
+    u64 r = hi + __umul64hi(m, p) + (lo != 0);
+    return csub64(r, p);
+}
+__device__ __forceinline__ u64 add64(u64 a, u64 b, u64 p) { u64 s = a + b; return s >= p ? s - p : s; }
+__device__ __forceinline__ u64 sub64(u64 a, u64 b, u64 p) { return a >= b ? a - b : a + (p - b); }
+
+// ---------------------------------------------------------------- jobs
+// Forward transform of `count` blocks of 2^lg points.  Block e reads
+// src + e*src_stride (src_len values, zero beyond) and writes dst + e*dst_stride.
+// src_mode: 0 = u32 already in [0, 2q), 4 = user u32 in [0,p), 8 = user u64.
+struct FwdJob {
+    const void *src;
+    u32 *dst;
+    i64 src_stride, dst_stride;
+    int src_len, src_mode, count, _pad;
+    PrimeDev P;
+};
+// Inverse transform.  dst_mode: 0 = u32 staging (unscaled, all points),
+// 1 = u32 residues (scaled, [0,q)), 4 / 8 = final u32 / u64 values (p = q).
+// Points x in [out_off, out_off + out_len) are written to dst + e*dst_stride + (x - out_off).
+struct InvJob {
+    const u32 *src;
+    void *dst;
+    i64 src_stride, dst_stride;
+    int out_off, out_len, dst_mode, count;
+    PrimeDev P;
+};
+// Column pass for transforms longer than 2^PM_LB_LOG2: the top stages act on
+// columns c + j 2^PM_LB_LOG2 of each entry.
+struct ColJob {
+    const void *src;   // fwd: user/u32 source (mode as FwdJob); inv: u32
+    void *dst;         // fwd: u32 [entry][L]; inv: as InvJob
+    i64 src_stride, dst_stride;
+    int src_len, mode, count, out_off, out_len, _pad;
+    PrimeDev P;
+};
+// Pointwise products at every transform point: C_j = A_j B_j mod q.
+struct PwJob {
+    const u32 *A, *B;
+    u32 *C;
+    int m, n, k, L;
+    PrimeDev P;
+};
+// Garner CRT of K residue planes into values mod p.
+struct CrtJob {
+    const u32 *res;     // [K][count], count = entries * len
+    void *dst;          // entry e, position t -> dst[e * dst_stride + t], u32 or u64
+    i64 count, len, dst_stride;
+    int K, w;
+    u64 p, mu;          // p and floor(2^64/p)
+    u32 q[PM_MAXK];
+    u32 c[PM_MAXK][PM_MAXK], cs[PM_MAXK][PM_MAXK];   // q_j^-1 mod q_i, companions
+    u64 qm[PM_MAXK], qms[PM_MAXK];                   // q_i mod p, Shoup-64 companions
+    int small_p;        // p <= 2^30: residues need a reduction mod p
+};
+
+template <typename J>
+struct JobPack {
+    int njobs;
+    int blk_start[PM_MAXJ + 1];
+    J jobs[PM_MAXJ];
+};
+
+// ---------------------------------------------------------------- launchers
+// All return cudaError_t of the launch; `launches` is incremented per launch.
+cudaError_t launch_twiddles(uint2 *twf, uint2 *twi, u32 q, const u32 *roots_f, const u32 *roots_i,
+                            int maxlog, cudaStream_t st, long long *launches);
+cudaError_t launch_ntt_fwd_block(const JobPack<FwdJob> &pk, int lg, cudaStream_t st, long long *launches);
+cudaError_t launch_ntt_inv_block(const JobPack<InvJob> &pk, int lg, cudaStream_t st, long long *launches);
+cudaError_t launch_ntt_fwd_cols(const JobPack<ColJob> &pk, int lg, cudaStream_t st, long long *launches);
+cudaError_t launch_ntt_inv_cols(const JobPack<ColJob> &pk, int lg, cudaStream_t st, long long *launches);
+cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
+cudaError_t launch_crt(const JobPack<CrtJob> &pk, cudaStream_t st, long long *launches);
+int fwd_block_threads(int lg);
+int blocks_per_entry_cols(int lg);
+int pw_blocks(const PwJob &j);
+int crt_blocks(const CrtJob &j);

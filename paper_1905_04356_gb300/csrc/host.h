@@ -1,0 +1,58 @@
+// host.h -- host-side context and the internal product entry shared by the
+// C-ABI products, PM-Basis and the resultant driver.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "pmat.h"
+
+struct PrimeSlot {
+    u32 q = 0;
+    int maxlog = 0;               // tables cover transforms up to 2^maxlog points
+    uint2 *twf = nullptr, *twi = nullptr;
+    u32 rf[PM_MAX_LOG2L + 1], ri[PM_MAX_LOG2L + 1];
+};
+
+struct Arena {                    // bump allocator over one device buffer
+    char *base = nullptr;
+    size_t size = 0, used = 0;
+};
+
+struct pm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own = nullptr;
+    std::string err = "no error";
+    int opt_pointwise = 0, opt_debug = 0;
+    int64_t opt_T = 32;
+    std::vector<PrimeSlot> table;     // CRT primes, largest first
+    std::vector<PrimeSlot> direct;    // NTT-friendly moduli used directly (p = q)
+    void *ws = nullptr;
+    size_t ws_size = 0;
+    long long launches = 0;
+    int *d_status = nullptr;          // deferred device status (0 = OK)
+    Arena arena;                      // driver buffers (PM-Basis, resultant)
+};
+
+int pm_fail(pm_ctx *ctx, int code, const std::string &msg);
+int pm_cuda(pm_ctx *ctx, cudaError_t e, const char *what);
+
+// Device workspace of at least `bytes` (grows stream-ordered).
+int ws_reserve(pm_ctx *ctx, size_t bytes, void **out);
+// Arena: reset / reserve-grow / allocate (256-byte aligned).
+int arena_reserve(pm_ctx *ctx, size_t bytes);
+void *arena_alloc(pm_ctx *ctx, size_t bytes);
+
+// C (m x k, entry stride sC) = coefficients off .. off+len-1 of A . B mod p,
+// A: m x n, length dA, entry stride sA; B: n x k, length dB, stride sB.
+// L is the cyclic transform length (power of 2, >= 16) chosen by the caller
+// so that no aliased coefficient lands in [off, off+len) except beyond L
+// (positions >= L of the slice are set to zero).
+int prod_slice(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA, int64_t sA,
+               const void *B, int64_t dB, int64_t sB, int64_t off, int64_t len, int lg, void *C, int64_t sC);
+
+int ceil_log2(int64_t x);
+uint64_t host_mulmod(uint64_t a, uint64_t b, uint64_t p);
+uint64_t host_powmod(uint64_t a, uint64_t e, uint64_t p);

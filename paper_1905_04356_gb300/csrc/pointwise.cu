@@ -1,0 +1,151 @@
+// pointwise.cu -- pointwise matrix products in the transform domain and the
+// multi-prime CRT recombination.
+//
+// Pointwise: at every evaluation point j, C_j = A_j B_j mod q (Sec. 2,
+// "Polynomial matrix multiplication": the n^omega d term of the cost).  This
+// is the CUDA-core form: each thread owns one point and a 4 x 4 tile of
+// outputs; 30-bit residues multiply into 64-bit lazy accumulators (16 terms
+// below 2^64), folded mod q every 16 terms.  Loads are coalesced across the
+// points of a warp (the transform domain is entry-major, point-minor).
+//
+// CRT: for moduli without suitable roots of unity the product is lifted to
+// Z[x] and computed modulo K NTT primes (Sec. 2, "3-primes multiplication";
+// here K is the least count whose product bounds the integer coefficients).
+// Garner's mixed-radix algorithm recovers the integer coefficient, and a
+// Horner pass in F_p reduces it mod p.
+#include "common.cuh"
+
+#define PW_T 4
+#define PW_PTS 128
+
+__device__ __forceinline__ int find_job_pw(const int *blk_start, int b)
+{
+    int j = 0;
+    while (b >= blk_start[j + 1]) j++;
+    return j;
+}
+
+int pw_blocks(const PwJob &j)
+{
+    const int npb = (j.L + PW_PTS - 1) / PW_PTS;
+    return npb * ((j.m + PW_T - 1) / PW_T) * ((j.k + PW_T - 1) / PW_T);
+}
+
+__global__ void __launch_bounds__(PW_PTS) k_pointwise(const __grid_constant__ JobPack<PwJob> pk)
+{
+    const int b = blockIdx.x;
+    const int jb = find_job_pw(pk.blk_start, b);
+    const PwJob &J = pk.jobs[jb];
+    int rel = b - pk.blk_start[jb];
+    const int npb = (J.L + PW_PTS - 1) / PW_PTS, ntk = (J.k + PW_T - 1) / PW_T;
+    const int pb = rel % npb;
+    rel /= npb;
+    const int tk = rel % ntk, ti = rel / ntk;
+    const int pt = pb * PW_PTS + threadIdx.x;
+    if (pt >= J.L) return;
+    const int i0 = ti * PW_T, k0 = tk * PW_T;
+    const int m = J.m, n = J.n, k = J.k;
+    const i64 L = J.L;
+
+    u64 acc[PW_T][PW_T];
+    u32 part[PW_T][PW_T];
+#pragma unroll
+    for (int a = 0; a < PW_T; a++)
+#pragma unroll
+        for (int c = 0; c < PW_T; c++) { acc[a][c] = 0; part[a][c] = 0; }
+
+    for (int l = 0; l < n; l++) {
+        u32 av[PW_T], bv[PW_T];
+#pragma unroll
+        for (int a = 0; a < PW_T; a++)
+            av[a] = (i0 + a < m) ? __ldg(J.A + ((i64)(i0 + a) * n + l) * L + pt) : 0u;
+#pragma unroll
+        for (int c = 0; c < PW_T; c++)
+            bv[c] = (k0 + c < k) ? __ldg(J.B + ((i64)l * k + k0 + c) * L + pt) : 0u;
+#pragma unroll
+        for (int a = 0; a < PW_T; a++)
+#pragma unroll
+            for (int c = 0; c < PW_T; c++) acc[a][c] += (u64)av[a] * bv[c];
+        if ((l & 15) == 15 || l == n - 1) {
+#pragma unroll
+            for (int a = 0; a < PW_T; a++)
+#pragma unroll
+                for (int c = 0; c < PW_T; c++) {
+                    part[a][c] = csub(part[a][c] + reduce64(acc[a][c], J.P), J.P.q);
+                    acc[a][c] = 0;
+                }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < PW_T; a++)
+#pragma unroll
+        for (int c = 0; c < PW_T; c++)
+            if (i0 + a < m && k0 + c < k) J.C[((i64)(i0 + a) * k + k0 + c) * L + pt] = part[a][c];
+}
+
+cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches)
+{
+    k_pointwise<<<pk.blk_start[pk.njobs], PW_PTS, 0, st>>>(pk);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ CRT
+#define CRT_THREADS 256
+#define CRT_PER_THREAD 4
+
+int crt_blocks(const CrtJob &j)
+{
+    const i64 per = (i64)CRT_THREADS * CRT_PER_THREAD;
+    return (int)((j.count + per - 1) / per);
+}
+
+__global__ void __launch_bounds__(CRT_THREADS) k_crt(const __grid_constant__ JobPack<CrtJob> pk)
+{
+    const int b = blockIdx.x;
+    const int jb = find_job_pw(pk.blk_start, b);
+    const CrtJob &J = pk.jobs[jb];
+    const i64 start = (i64)(b - pk.blk_start[jb]) * CRT_THREADS * CRT_PER_THREAD + threadIdx.x;
+    const int K = J.K;
+#pragma unroll 1
+    for (int it = 0; it < CRT_PER_THREAD; it++) {
+        const i64 idx = start + (i64)it * CRT_THREADS;
+        if (idx >= J.count) return;
+        u32 v[PM_MAXK];
+        // Garner: v_i = (...((r_i - v_0) c_i0 - v_1) c_i1 ... - v_{i-1}) c_i,i-1 mod q_i
+#pragma unroll
+        for (int i = 0; i < PM_MAXK; i++) {
+            if (i >= K) break;
+            const u32 qi = J.q[i];
+            u32 t = __ldg(J.res + (i64)i * J.count + idx);
+#pragma unroll
+            for (int j = 0; j < PM_MAXK; j++) {
+                if (j >= i) break;
+                const u32 vj = csub(v[j], qi);          // v_j < q_j < 2 q_i
+                t = shoup_mul(t + qi - vj, J.c[i][j], J.cs[i][j], qi);
+                t = csub(t, qi);
+            }
+            v[i] = t;
+        }
+        // X = v_0 + q_0 (v_1 + q_1 (v_2 + ...)) reduced mod p by Horner
+        u64 y = J.small_p ? barrett64(v[K - 1], J.p, J.mu) : v[K - 1];
+#pragma unroll
+        for (int i = PM_MAXK - 2; i >= 0; i--) {
+            if (i > K - 2) continue;
+            u64 z = shoup_mul64(y, J.qm[i], J.qms[i], J.p);              // [0, 2p)
+            z += J.small_p ? barrett64(v[i], J.p, J.mu) : v[i];         // [0, 3p)
+            z = csub64(csub64(z, J.p), J.p);
+            y = z;
+        }
+        const i64 e = idx / J.len, o = e * J.dst_stride + (idx - e * J.len);
+        if (J.w == 8) ((u64 *)J.dst)[o] = y;
+        else ((u32 *)J.dst)[o] = (u32)y;
+    }
+}
+
+cudaError_t launch_crt(const JobPack<CrtJob> &pk, cudaStream_t st, long long *launches)
+{
+    k_crt<<<pk.blk_start[pk.njobs], CRT_THREADS, 0, st>>>(pk);
+    ++*launches;
+    return cudaGetLastError();
+}

@@ -1,0 +1,248 @@
+"""Thin ctypes binding of libpmat (include/pmat.h): argument marshalling only.
+
+Every step of every operation runs in the library's CUDA kernels; this module
+only passes device pointers, sizes and the CUDA stream.  PyTorch provides
+device memory and streams.  There is no CPU fallback: when libpmat.so is
+missing or no GPU is present, calls raise.
+
+Polynomial matrices are torch CUDA tensors of shape (rows, cols, length),
+contiguous, with dtype uint32/int32 (w = 4) or uint64/int64 (w = 8); the
+bits are read as unsigned residues in [0, p).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpmat.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "pmat.h")
+
+PM_OK, PM_EINVAL, PM_EDOMAIN, PM_ENOMEM, PM_ECUDA, PM_ETIMEOUT, PM_EUNSUPPORTED = range(7)
+PM_OPT_POINTWISE, PM_OPT_THRESHOLD, PM_OPT_DEBUG_CHECKS = 1, 2, 3
+STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_EDOMAIN", 3: "PM_ENOMEM", 4: "PM_ECUDA",
+                5: "PM_ETIMEOUT", 6: "PM_EUNSUPPORTED"}
+
+
+class PmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class pmat_desc(C.Structure):
+    _fields_ = [("p", C.c_uint64), ("w", C.c_int), ("m", C.c_int), ("n", C.c_int), ("k", C.c_int),
+                ("A", C.c_void_p), ("dA", C.c_int64), ("B", C.c_void_p), ("dB", C.c_int64), ("C", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libpmat.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        P, i32, i64, u64 = C.c_void_p, C.c_int, C.c_int64, C.c_uint64
+        sig = {
+            "pm_create": ([C.POINTER(C.c_void_p), i32, P], i32),
+            "pm_destroy": ([P], i32),
+            "pm_set_option": ([P, i32, i64], i32),
+            "pm_set_stream": ([P, P], i32),
+            "pm_sync": ([P], i32),
+            "pm_last_error": ([P], C.c_char_p),
+            "pm_kernel_launches": ([P], i64),
+            "pmat_mul": ([P, u64, i32, i32, i32, i32, P, i64, P, i64, P], i32),
+            "pmat_mul_trunc": ([P, u64, i32, i32, i32, i32, P, i64, P, i64, i64, P], i32),
+            "pmat_middle_product": ([P, u64, i32, i32, i32, i32, P, i64, P, i64, i64, i64, P], i32),
+            "pmat_mul_batched": ([P, i32, C.POINTER(pmat_desc)], i32),
+            "pm_basis": ([P, u64, i32, i32, P, i64, i64, P, P, P], i32),
+            "bivariate_resultant": ([P, i32, P, i32, i32, P, i32, i32, P, P], i32),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def header_functions():
+    """Names of the functions declared in include/pmat.h."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(\w+)\s*\(", src, flags=re.M)) - {"if"})
+
+
+# ------------------------------------------------------------------ helpers
+def width(t: torch.Tensor) -> int:
+    if t.dtype in (torch.int32, torch.uint32):
+        return 4
+    if t.dtype in (torch.int64, torch.uint64):
+        return 8
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _dev(t: torch.Tensor) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t
+
+
+def to_device(a: np.ndarray, device="cuda") -> torch.Tensor:
+    """Copy a uint32/uint64 NumPy array to the device (stored as int32/int64 bits)."""
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint64:
+        return torch.from_numpy(a.view(np.int64)).to(device)
+    if a.dtype == np.uint32:
+        return torch.from_numpy(a.view(np.int32)).to(device)
+    raise TypeError(f"unsupported dtype {a.dtype}")
+
+
+def to_host(t: torch.Tensor) -> np.ndarray:
+    a = t.detach().cpu().contiguous().numpy()
+    if a.dtype in (np.int64, np.uint64):
+        return a.view(np.uint64)
+    return a.view(np.uint32)
+
+
+class Context:
+    """One pm_ctx bound to a CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        L = lib()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = C.c_void_p()
+        rc = L.pm_create(C.byref(h), device, C.c_void_p(stream.cuda_stream))
+        if rc != PM_OK:
+            raise PmError(rc, "pm_create failed")
+        self.h = h
+
+    def _ck(self, rc: int):
+        if rc != PM_OK:
+            raise PmError(rc, lib().pm_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, key: int, value: int):
+        self._ck(lib().pm_set_option(self.h, key, value))
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        self._ck(lib().pm_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
+
+    def sync(self):
+        self._ck(lib().pm_sync(self.h))
+
+    def launches(self) -> int:
+        return int(lib().pm_kernel_launches(self.h))
+
+
+def _out(out, shape, like):
+    if out is None:
+        return torch.empty(shape, dtype=like.dtype, device=like.device)
+    if tuple(out.shape) != tuple(shape) or out.dtype != like.dtype:
+        raise ValueError(f"out must be {shape} of {like.dtype}")
+    return _dev(out)
+
+
+def pmat_mul(ctx: Context, p: int, A: torch.Tensor, B: torch.Tensor, out=None) -> torch.Tensor:
+    """C = A . B mod p (A: m x n x dA, B: n x k x dB) -> m x k x (dA + dB - 1)."""
+    A, B = _dev(A), _dev(B)
+    m, n, dA = A.shape
+    n2, k, dB = B.shape
+    if n != n2 or A.dtype != B.dtype:
+        raise ValueError("shape/dtype mismatch")
+    Cout = _out(out, (m, k, dA + dB - 1), A)
+    ctx._ck(lib().pmat_mul(ctx.h, p, width(A), m, n, k, A.data_ptr(), dA, B.data_ptr(), dB, Cout.data_ptr()))
+    return Cout
+
+
+def pmat_mul_trunc(ctx: Context, p: int, A, B, t: int, out=None) -> torch.Tensor:
+    """C = A . B mod x^t -> m x k x t."""
+    A, B = _dev(A), _dev(B)
+    m, n, dA = A.shape
+    _, k, dB = B.shape
+    Cout = _out(out, (m, k, t), A)
+    ctx._ck(lib().pmat_mul_trunc(ctx.h, p, width(A), m, n, k, A.data_ptr(), dA, B.data_ptr(), dB, t,
+                                 Cout.data_ptr()))
+    return Cout
+
+
+def pmat_middle_product(ctx: Context, p: int, A, B, c: int, d: int, out=None) -> torch.Tensor:
+    """Coefficients c .. c+d-1 of A . B -> m x k x d."""
+    A, B = _dev(A), _dev(B)
+    m, n, dA = A.shape
+    _, k, dB = B.shape
+    Cout = _out(out, (m, k, d), A)
+    ctx._ck(lib().pmat_middle_product(ctx.h, p, width(A), m, n, k, A.data_ptr(), dA, B.data_ptr(), dB, c, d,
+                                      Cout.data_ptr()))
+    return Cout
+
+
+def pmat_mul_batched(ctx: Context, items, outs=None):
+    """items: list of (p, A, B); returns the list of products (each as pmat_mul)."""
+    n = len(items)
+    arr = (pmat_desc * max(n, 1))()
+    res = []
+    for i, (p, A, B) in enumerate(items):
+        A, B = _dev(A), _dev(B)
+        m, nn, dA = A.shape
+        _, k, dB = B.shape
+        Cout = _out(outs[i] if outs else None, (m, k, dA + dB - 1), A)
+        arr[i] = pmat_desc(p, width(A), m, nn, k, A.data_ptr(), dA, B.data_ptr(), dB, Cout.data_ptr())
+        res.append(Cout)
+    ctx._ck(lib().pmat_mul_batched(ctx.h, n, arr))
+    return res
+
+
+def pm_basis(ctx: Context, p: int, F: torch.Tensor, d: int, shift, out=None):
+    """PM-Basis (Algorithm 3): returns (P as m x m x (d+1) uint64 bits, rdeg_s(P) as int64 array)."""
+    F = _dev(F)
+    if width(F) != 8:
+        raise TypeError("pm_basis takes 64-bit coefficients")
+    m, n, lenF = F.shape
+    s = np.ascontiguousarray(np.asarray(shift, dtype=np.int64))
+    if s.shape != (m,):
+        raise ValueError("shift must have m entries")
+    P = _out(out, (m, m, d + 1), F)
+    rd = np.zeros(m, dtype=np.int64)
+    ctx._ck(lib().pm_basis(ctx.h, p, m, n, F.data_ptr(), lenF, d, s.ctypes.data, P.data_ptr(), rd.ctypes.data))
+    return P, rd
+
+
+def bivariate_resultant(ctx: Context, primes, f: torch.Tensor, g: torch.Tensor, out=None) -> torch.Tensor:
+    """Res_y(f, g) modulo each prime.  f: (nprimes, dyf+1, dxf+1) 64-bit, f[., j, i] = coeff of x^i y^j."""
+    f, g = _dev(f), _dev(g)
+    if f.dim() == 2:
+        f, g = f.unsqueeze(0), g.unsqueeze(0)
+    npr, dyf1, dxf1 = f.shape
+    _, dyg1, dxg1 = g.shape
+    pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint64).reshape(-1))
+    if len(pr) != npr:
+        raise ValueError("one prime per instance")
+    D = (dxf1 - 1) * (dyg1 - 1) + (dxg1 - 1) * (dyf1 - 1)
+    R = _out(out, (npr, D + 1), f)
+    ctx._ck(lib().bivariate_resultant(ctx.h, npr, pr.ctypes.data, dxf1 - 1, dyf1 - 1, f.data_ptr(), dxg1 - 1,
+                                      dyg1 - 1, g.data_ptr(), R.data_ptr()))
+    return R

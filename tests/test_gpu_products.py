@@ -1,0 +1,174 @@
+"""GPU parity of the product path (C-ABI -> CUDA) against the CPU oracle.
+
+Bit-exact: every residue of every tested output must match (the products
+are exact; there is no tolerance).  Sizes span several transform tiles, the
+column path (transforms longer than 2^13 points) and ragged lengths; the
+full-size workloads are checked on sampled coefficients the oracle computes
+one by one.
+"""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+P60 = 1152921504606846883          # 2^60 - 93
+P62 = 4611686018427387847          # 2^62 - 57
+P32 = 4294967291                   # 2^32 - 5: word-size, no 2-power roots of unity
+COMPOSITE = 1000000000             # products are ring operations: any p >= 2
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_04356_gb300 import Context, build
+    build.build()
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def _dt(p, w):
+    return np.uint32 if w == 4 else np.uint64
+
+
+def _rand(g, p, shape, w):
+    return synth.uniform(g, shape, p, _dt(p, w))
+
+
+def _gpu(ctx, fn, p, A, B, *args):
+    from paper_1905_04356_gb300 import pmat
+    dA, dB = pmat.to_device(A), pmat.to_device(B)
+    out = getattr(pmat, fn)(ctx, p, dA, dB, *args)
+    ctx.sync()
+    return pmat.to_host(out)
+
+
+CASES = [
+    # p, w, m, n, k, dA, dB
+    (synth.P998, 4, 1, 1, 1, 1, 1),
+    (synth.P998, 4, 4, 4, 4, 256, 256),
+    (synth.P998, 8, 3, 5, 2, 17, 33),
+    (synth.P998, 4, 7, 3, 9, 300, 1000),
+    (P60, 8, 1, 1, 1, 1, 1),
+    (P60, 8, 3, 5, 2, 17, 33),
+    (P60, 8, 5, 17, 6, 700, 513),
+    (P62, 8, 2, 9, 3, 129, 64),
+    (P32, 4, 4, 6, 5, 200, 77),
+    (97, 4, 6, 6, 6, 40, 41),
+    (2, 4, 3, 3, 3, 50, 20),
+    (COMPOSITE, 4, 3, 4, 2, 90, 45),
+    (P60, 8, 2, 3, 2, 4000, 4500),        # L = 2^13, one CTA per transform
+    (synth.P998, 4, 2, 2, 3, 5000, 4000),  # L = 2^14: column path
+    (P60, 8, 2, 2, 1, 9000, 7000),         # L = 2^14, 5 primes
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"p{c[0]}_w{c[1]}_{c[2]}x{c[3]}x{c[4]}_{c[5]}_{c[6]}" for c in CASES])
+def test_full_product_matches_oracle(ctx, case):
+    p, w, m, n, k, dA, dB = case
+    g = synth.rng(hash(case) & 0xffffffff)
+    A = _rand(g, p, (m, n, dA), w)
+    B = _rand(g, p, (n, k, dB), w)
+    got = _gpu(ctx, "pmat_mul", p, A, B)
+    exp = oracle.pmat_mul(p, A, B)
+    assert got.shape == exp.shape
+    assert np.array_equal(got.astype(np.uint64), exp)
+
+
+@pytest.mark.parametrize("case", [(P60, 8, 3, 4, 5, 100, 60), (synth.P998, 4, 4, 2, 3, 333, 222),
+                                  (P32, 4, 2, 3, 2, 3000, 3100)])
+def test_truncated_product_matches_oracle(ctx, case):
+    p, w, m, n, k, dA, dB = case
+    g = synth.rng(7)
+    A = _rand(g, p, (m, n, dA), w)
+    B = _rand(g, p, (n, k, dB), w)
+    for t in (1, 17, min(dA, dB), dA + dB - 1, dA + dB + 40):
+        got = _gpu(ctx, "pmat_mul_trunc", p, A, B, t)
+        exp = oracle.pmat_mul_trunc(p, A, B, t)
+        assert np.array_equal(got.astype(np.uint64), exp), t
+
+
+@pytest.mark.parametrize("p,w", [(P60, 8), (synth.P998, 4)])
+def test_middle_product_matches_oracle(ctx, p, w):
+    g = synth.rng(11)
+    m, n, k = 3, 4, 2
+    # (c, d, dA, dB): the paper's c = d case, the PM-Basis residual shape
+    # (dA = c + 1, dB = c + d), and shorter operands
+    for c, d, dA, dB in ((64, 64, 64, 128), (33, 32, 34, 65), (500, 300, 501, 800), (10, 5, 3, 9),
+                         (4096, 4096, 4097, 8192), (0, 7, 1, 7)):
+        A = _rand(g, p, (m, n, dA), w)
+        B = _rand(g, p, (n, k, dB), w)
+        got = _gpu(ctx, "pmat_middle_product", p, A, B, c, d)
+        exp = oracle.pmat_middle_product(p, A, B, c, d)
+        assert np.array_equal(got.astype(np.uint64), exp), (c, d, dA, dB)
+
+
+def test_long_transform_sampled(ctx):
+    """1 x 2 . 2 x 1 with lengths 40000 / 30000: L = 2^17 (column path, 7 top stages)."""
+    p = P60
+    g = synth.rng(3)
+    A = _rand(g, p, (1, 2, 40000), 8)
+    B = _rand(g, p, (2, 1, 30000), 8)
+    got = _gpu(ctx, "pmat_mul", p, A, B)
+    rnd = random.Random(1)
+    for t in [0, 1, 29999, 39999, 69998] + [rnd.randrange(69999) for _ in range(40)]:
+        assert int(got[0, 0, t]) == oracle.pmat_coeff(p, A, B, 0, 0, t), t
+
+
+@pytest.mark.parametrize("ntt_prime", [False, True], ids=["p60", "p998"])
+def test_c2_full_size_sampled(ctx, ntt_prime):
+    """32x32 . 32x32, degree < 4096: sampled coefficients vs the oracle."""
+    W = synth.product_c2(0, ntt_prime=ntt_prime)
+    p, A, B = W["p"], W["A"], W["B"]
+    got = _gpu(ctx, "pmat_mul", p, A, B)
+    assert got.shape == (32, 32, 8191)
+    rnd = random.Random(5)
+    picks = [(0, 0, 0), (31, 31, 8190), (5, 7, 4095)] + \
+        [(rnd.randrange(32), rnd.randrange(32), rnd.randrange(8191)) for _ in range(150)]
+    for (i, kk, t) in picks:
+        assert int(got[i, kk, t]) == oracle.pmat_coeff(p, A, B, i, kk, t), (i, kk, t)
+
+
+def test_c1_full(ctx):
+    W = synth.product_c1(0)
+    got = _gpu(ctx, "pmat_mul", W["p"], W["A"], W["B"])
+    exp = oracle.pmat_mul(W["p"], W["A"], W["B"])
+    assert got.dtype == np.uint32 and np.array_equal(got.astype(np.uint64), exp)
+
+
+def test_argument_errors(ctx):
+    import torch
+    from paper_1905_04356_gb300 import PmError, pmat
+    A = torch.zeros((2, 3, 5), dtype=torch.int64, device="cuda")
+    B = torch.zeros((3, 2, 5), dtype=torch.int64, device="cuda")
+    with pytest.raises(PmError) as e:
+        pmat.pmat_middle_product(ctx, P60, A, B, 2, 3)       # dA = 5 > c + 1
+    assert e.value.code == pmat.PM_EINVAL
+    with pytest.raises(PmError) as e:
+        pmat.pmat_mul(ctx, 1, A, B)                           # p < 2
+    assert e.value.code == pmat.PM_EINVAL
+    A4 = torch.zeros((2, 3, 5), dtype=torch.int32, device="cuda")
+    B4 = torch.zeros((3, 2, 5), dtype=torch.int32, device="cuda")
+    with pytest.raises(PmError) as e:
+        pmat.pmat_mul(ctx, P60, A4, B4)                       # w = 4 with p >= 2^32
+    assert e.value.code == pmat.PM_EINVAL
+
+
+def test_debug_check_rejects_unreduced_input(ctx):
+    from paper_1905_04356_gb300 import PmError, pmat
+    A = np.full((2, 2, 4), 200, dtype=np.uint32)          # >= p = 97
+    B = np.ones((2, 2, 4), dtype=np.uint32)
+    ctx.set_option(pmat.PM_OPT_DEBUG_CHECKS, 1)
+    try:
+        with pytest.raises(PmError) as e:
+            _gpu(ctx, "pmat_mul", 97, A, B)
+        assert e.value.code == pmat.PM_EDOMAIN
+    finally:
+        ctx.set_option(pmat.PM_OPT_DEBUG_CHECKS, 0)
