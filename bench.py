@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark: exact polynomial-matrix product over F_p on GB300.
+
+Step = one pmat_mul of 32 x 32 . 32 x 32 polynomial matrices of degree < 4096
+modulo a random 60-bit prime drawn from seed 0 (uint64 storage; the library
+takes it through 5 NTT primes and CRT): forward transforms, pointwise
+products, inverse transforms, recombination.  The same sizes modulo
+998244353 (uint32, one NTT prime) are reported under "extra".
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  --impl reference times the CPU oracle (plain C,
+OpenMP) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pmat-mul & PM-Basis ms, % of HBM/int8 roofline; TC-batched vs plain NTT"
+WORKLOAD = "pmat_mul 32x32 . 32x32, degree < 4096, random 60-bit p (seed 0), uint64"
+CONFIG = {"workload": WORKLOAD, "m": 32, "n": 32, "k": 32, "deg_bound": 4096, "p_bits": 60, "seed": 0,
+          "crt_primes": 5, "transform_len": 8192}
+PAPER_CONTEXT = {"ms": 2000.0, "hardware": "Intel i7-4790, 1 thread, NTL 11.3.1",
+                 "workload": "m = 32, degree 4096, random 60-bit prime (product table of Sec. 2)"}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def sha(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def traffic_for(kernel: str, src_file: str):
+    """dram bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        e = t.get(kernel)
+        if e and e.get("source_sha") == sha(os.path.join(ROOT, "paper_1905_04356_gb300", "csrc", src_file)):
+            return e.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
+def oracle_sample(W, rows: int):
+    """Time the oracle on the first `rows` rows of A (rows x 32 of the 32 x 32 output entries)."""
+    import oracle
+    A = W["A"][:rows]
+    t0 = time.perf_counter()
+    oracle.pmat_mul(W["p"], A, W["B"])
+    dt = time.perf_counter() - t0
+    return dt * 1000.0 * (W["A"].shape[0] / rows), dt, oracle.max_threads()
+
+
+def cpu_baseline(W, budget_s=15.0):
+    ms1, dt1, cores = oracle_sample(W, 1)
+    rows = max(1, min(32, int(budget_s / max(dt1, 1e-3))))
+    if rows > 1:
+        ms, dt, cores = oracle_sample(W, rows)
+    else:
+        ms, dt = ms1, dt1
+    return {"value": round(ms, 1), "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": f"{rows} of 32 output rows ({rows * 32} of 1024 entries, all 8191 coefficients), "
+                      f"{dt:.1f} s of CPU time, scaled to the full product"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import synth
+    W = synth.product_c2(0)
+    for _ in range(args.warmup):
+        oracle_sample(W, 1)
+    vals, cores = [], 1
+    for _ in range(args.steps):
+        ms, _, cores = oracle_sample(W, 1)
+        vals.append(ms)
+    v = statistics.median(vals)
+    sample = "1 of 32 output rows (32 of 1024 entries, all coefficients) per step, scaled to the full product"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 2), "unit": "ms", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 2), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": CONFIG,
+        "cpu_baseline": {"value": round(v, 2), "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(v, 2), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+    import synth
+    from paper_1905_04356_gb300 import Context, build, pmat
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+
+    W = synth.product_c2(0)
+    W998 = synth.product_c2(0, ntt_prime=True)
+    p, Ah, Bh = W["p"], W["A"], W["B"]
+    m, n, dA = Ah.shape
+    k, dB = Bh.shape[1], Bh.shape[2]
+    lenC = dA + dB - 1
+    s = torch.cuda.Stream()
+    ctx = Context(local, stream=s)
+    with torch.cuda.stream(s):
+        A, B = pmat.to_device(Ah), pmat.to_device(Bh)
+        Cd = torch.empty((m, k, lenC), dtype=torch.int64, device="cuda")
+        A2, B2 = pmat.to_device(W998["A"]), pmat.to_device(W998["B"])
+        C2 = torch.empty((m, k, lenC), dtype=torch.int32, device="cuda")
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+
+    def step(i):
+        pmat.pmat_mul(ctx, p, A, B, out=Cd)
+
+    def timed(fn, K, events=True):
+        ts = []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for i in range(K):
+            flush.add_(1)                      # L2 flush, outside the per-step events
+            ev[i][0].record(s)
+            fn(i)
+            ev[i][1].record(s)
+        torch.cuda.synchronize()
+        for a, b in ev:
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    with torch.cuda.stream(s):
+        for i in range(args.warmup):
+            step(i)
+        torch.cuda.synchronize()
+        # ---- timed region
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        n0 = ctx.launches()
+        t_wall = time.perf_counter()
+        ts = timed(step, args.steps)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+        launches = ctx.launches() - n0
+        if dist:
+            dist.barrier()
+        ck = clocks.stop()
+        ms_step = sum(ts) / len(ts)
+        if dist:
+            t = torch.tensor([ms_step], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_step = float(t.item())
+
+        # ---- per-stage times (events on the launching stream) for the roofline
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
+        ctx.stage_times()
+        timed(step, max(5, args.steps // 2))
+        st = ctx.stage_times()
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
+
+        # ---- same sizes modulo 998244353 (one NTT prime, uint32)
+        for _ in range(3):
+            pmat.pmat_mul(ctx, W998["p"], A2, B2, out=C2)
+        ts998 = timed(lambda i: pmat.pmat_mul(ctx, W998["p"], A2, B2, out=C2), args.steps)
+
+        # ---- end to end: pinned host buffers, copies inside the timed region
+        Ap = torch.from_numpy(Ah.view(np.int64)).pin_memory()
+        Bp = torch.from_numpy(Bh.view(np.int64)).pin_memory()
+        Cp = torch.empty((m, k, lenC), dtype=torch.int64).pin_memory()
+
+        def e2e_step(i):
+            A.copy_(Ap, non_blocking=True)
+            B.copy_(Bp, non_blocking=True)
+            pmat.pmat_mul(ctx, p, A, B, out=Cd)
+            Cp.copy_(Cd, non_blocking=True)
+
+        for i in range(2):
+            e2e_step(i)
+        torch.cuda.synchronize()
+        ts_e2e = timed(e2e_step, args.steps)
+        h2d = Ah.nbytes + Bh.nbytes
+        d2h = m * k * lenC * 8
+
+    # ---- roofline of the dominant kernel (algorithmic bytes per launch / measured launch time)
+    K, L = 5, 8192
+    eA, eB, eC = m * n, n * k, m * k
+    alg = {   # minimum bytes each stage's kernel must read + write (one launch per stage here)
+        "fwd_ntt": (eA * dA + eB * dB) * 8 + K * (eA + eB) * L * 4,
+        "pointwise": K * (eA + eB) * L * 4 + K * eC * L * 4,
+        "inv_ntt": K * eC * L * 4 + K * eC * lenC * 4,
+        "crt": K * eC * lenC * 4 + eC * lenC * 8,
+    }
+    kname = {"fwd_ntt": ("k_ntt_fwd_block", "ntt.cu"), "pointwise": ("k_pointwise", "pointwise.cu"),
+             "inv_ntt": ("k_ntt_inv_block", "ntt.cu"), "crt": ("k_crt", "pointwise.cu")}
+    stages = {k2: v for k2, v in st.items() if v[1] > 0}
+    dom = max(stages, key=lambda x: stages[x][0])
+    dom_ms = stages[dom][0] / stages[dom][1]
+    pk = peaks()
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    achieved = alg[dom] / (dom_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": kname[dom][0], "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic_for(*kname[dom]),
+            "algorithmic_bytes_per_launch": alg[dom], "launch_ms": round(dom_ms, 4),
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback"}
+    compulsory = (eA * dA + eB * dB) * 8 + eC * lenC * 8
+    value = ms_step / world
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": dict(CONFIG, l2="256 MiB buffer written between steps, outside the per-step events",
+                       replicas=world),
+        "roofline": roof,
+        "e2e": {"value": round(sum(ts_e2e) / len(ts_e2e) / world, 4), "unit": "ms", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": ck,
+        "extra": {
+            "stage_ms_per_step": {k2: round(v[0] / max(5, args.steps // 2), 4) for k2, v in stages.items()},
+            "step_compulsory_bytes": compulsory,
+            "step_compulsory_GBps": round(compulsory / (ms_step * 1e-3) / 1e9, 1),
+            "step_compulsory_frac_hbm": round(compulsory / (ms_step * 1e-3) / 1e9 / peak, 4),
+            "c2_p998_ms": round(sum(ts998) / len(ts998), 4),
+            "wall_s_timed_region": round(t_wall, 3),
+            "paper_context": PAPER_CONTEXT,
+        },
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(W)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -61,12 +61,24 @@ enum {
     PM_OPT_POINTWISE = 1,   /* 0 = auto, 1 = CUDA-core 64-bit, 2 = tensor-core limbs */
     PM_OPT_THRESHOLD = 2,   /* PM-Basis threshold T (>= 1): M-Basis when order <= T;
                                default 32 (Sec. 3, "Interpolant bases") */
-    PM_OPT_DEBUG_CHECKS = 3 /* 1 = check inputs are in [0, p) (PM_EDOMAIN) */
+    PM_OPT_DEBUG_CHECKS = 3, /* 1 = check inputs are in [0, p) (PM_EDOMAIN) */
+    PM_OPT_STAGE_TIMING = 4  /* 1 = record CUDA events around every stage (see pm_stage_times) */
+};
+
+/* Stages reported by pm_stage_times. */
+enum {
+    PM_STAGE_FWD = 0,        /* forward transforms (reduction mod q fused) */
+    PM_STAGE_POINTWISE = 1,  /* pointwise products at the transform points */
+    PM_STAGE_INV = 2,        /* inverse transforms (scaling and slice fused) */
+    PM_STAGE_CRT = 3,        /* multi-prime recombination */
+    PM_STAGE_LEAF = 4,       /* PM-Basis leaves (Algorithm 2 on the device) */
+    PM_STAGE_OTHER = 5,      /* driver kernels: shifts, scalings, Euclid */
+    PM_NSTAGES = 8
 };
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
- * owned by the caller (kept, not destroyed), or NULL for a context-owned
- * non-blocking stream.  *ctx receives the handle.  Returns PM_EINVAL on a bad
+ * owned by the caller (kept, not destroyed; cudaStreamLegacy selects the
+ * legacy default stream), or NULL for a context-owned non-blocking stream.  *ctx receives the handle.  Returns PM_EINVAL on a bad
  * device, PM_ECUDA on a runtime failure. */
 int pm_create(pm_ctx **ctx, int device, void *cuda_stream);
 
@@ -89,6 +101,13 @@ const char *pm_last_error(pm_ctx *ctx);
 /* Number of CUDA kernel launches issued by this context since creation
  * (a diagnostic counter; it includes set-up kernels). */
 int64_t pm_kernel_launches(pm_ctx *ctx);
+
+/* With PM_OPT_STAGE_TIMING on, every stage of every call is bracketed by
+ * CUDA events on the context's stream.  This call synchronises the stream,
+ * adds the elapsed times of all stages recorded since the previous call into
+ * ms[PM_NSTAGES] and their launch counts into launches[PM_NSTAGES] (host
+ * arrays, overwritten), and clears the record.  Either pointer may be NULL. */
+int pm_stage_times(pm_ctx *ctx, double *ms, int64_t *launches);
 
 /* C (m x k, length dA+dB-1) = A (m x n, length dA) . B (n x k, length dB)
  * mod p.  Sec. 2, "Polynomial matrix multiplication": evaluation and

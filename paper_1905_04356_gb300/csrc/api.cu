@@ -195,6 +195,36 @@ void *arena_alloc(pm_ctx *ctx, size_t bytes)
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// ------------------------------------------------------------------ stage timing
+static cudaEvent_t take_event(pm_ctx *ctx)
+{
+    cudaEvent_t e = nullptr;
+    if (!ctx->spare.empty()) { e = ctx->spare.back(); ctx->spare.pop_back(); }
+    else cudaEventCreate(&e);
+    return e;
+}
+
+int stage_begin(pm_ctx *ctx, int stage)
+{
+    if (!ctx->opt_timing) return -1;
+    pm_ctx::Mark mk;
+    mk.stage = stage;
+    mk.a = take_event(ctx);
+    mk.b = take_event(ctx);
+    mk.launches = ctx->launches;
+    cudaEventRecord(mk.a, ctx->stream);
+    ctx->marks.push_back(mk);
+    return (int)ctx->marks.size() - 1;
+}
+
+void stage_end(pm_ctx *ctx, int token)
+{
+    if (token < 0 || token >= (int)ctx->marks.size()) return;
+    pm_ctx::Mark &mk = ctx->marks[token];
+    mk.launches = ctx->launches - mk.launches;
+    cudaEventRecord(mk.b, ctx->stream);
+}
+
 // ------------------------------------------------------------------ primes per product
 // The product is exact over Z when prod q_i exceeds the largest integer
 // coefficient n . min(dA, dB) . (p-1)^2.
@@ -342,6 +372,7 @@ int prod_slice(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *
     u32 *Rs = (u32 *)(base + K * (bA + bB + bC));
 
     // 1. forward transforms of A and B modulo every prime (reduction fused)
+    int tok = stage_begin(ctx, PM_STAGE_FWD);
     {
         JobPack<FwdJob> pk; pack_reset(pk);
         JobPack<ColJob> pc; pack_reset(pc);
@@ -353,7 +384,9 @@ int prod_slice(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *
         if (pc.njobs) CK(launch_ntt_fwd_cols(pc, lg, ctx->stream, &ctx->launches));
         CK(launch_ntt_fwd_block(pk, lg > PM_LB_LOG2 ? PM_LB_LOG2 : lg, ctx->stream, &ctx->launches));
     }
+    stage_end(ctx, tok);
     // 2. pointwise products at every point
+    tok = stage_begin(ctx, PM_STAGE_POINTWISE);
     {
         JobPack<PwJob> pk; pack_reset(pk);
         for (int i = 0; i < K; i++) {
@@ -364,7 +397,9 @@ int prod_slice(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *
         }
         CK(launch_pointwise(pk, ctx->stream, &ctx->launches));
     }
+    stage_end(ctx, tok);
     // 3. inverse transforms, scaled, writing the slice [off, off + len)
+    tok = stage_begin(ctx, PM_STAGE_INV);
     {
         const int mode = direct ? w : 1;
         JobPack<InvJob> pk; pack_reset(pk);
@@ -397,8 +432,10 @@ int prod_slice(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *
         CK(launch_ntt_inv_block(pk, lg > PM_LB_LOG2 ? PM_LB_LOG2 : lg, ctx->stream, &ctx->launches));
         if (pc.njobs) CK(launch_ntt_inv_cols(pc, lg, ctx->stream, &ctx->launches));
     }
+    stage_end(ctx, tok);
     // 4. CRT recombination into values mod p
     if (!direct) {
+        tok = stage_begin(ctx, PM_STAGE_CRT);
         JobPack<CrtJob> pk; pack_reset(pk);
         CrtJob j;
         memset(&j, 0, sizeof(j));
@@ -406,6 +443,7 @@ int prod_slice(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *
         j.res = Rs; j.dst = C; j.count = (int64_t)eC * len; j.len = len; j.dst_stride = sC; j.w = w;
         pack_add(pk, j, crt_blocks(j));
         CK(launch_crt(pk, ctx->stream, &ctx->launches));
+        stage_end(ctx, tok);
     }
     // 5. slice positions beyond the transform length are zero
     if (out_len < len) {
@@ -466,6 +504,8 @@ int pm_destroy(pm_ctx *ctx)
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->arena.base) cudaFree(ctx->arena.base);
     if (ctx->d_status) cudaFree(ctx->d_status);
+    for (auto &mk : ctx->marks) { cudaEventDestroy(mk.a); cudaEventDestroy(mk.b); }
+    for (auto e : ctx->spare) cudaEventDestroy(e);
     if (ctx->own) cudaStreamDestroy(ctx->own);
     delete ctx;
     return PM_OK;
@@ -485,6 +525,9 @@ int pm_set_option(pm_ctx *ctx, int key, int64_t value)
         return PM_OK;
     case PM_OPT_DEBUG_CHECKS:
         ctx->opt_debug = value ? 1 : 0;
+        return PM_OK;
+    case PM_OPT_STAGE_TIMING:
+        ctx->opt_timing = value ? 1 : 0;
         return PM_OK;
     default:
         return pm_fail(ctx, PM_EINVAL, "unknown option key");
@@ -520,6 +563,25 @@ int pm_sync(pm_ctx *ctx)
 const char *pm_last_error(pm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int64_t pm_kernel_launches(pm_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int pm_stage_times(pm_ctx *ctx, double *ms, int64_t *launches)
+{
+    if (!ctx) return PM_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ms) for (int i = 0; i < PM_NSTAGES; i++) ms[i] = 0;
+    if (launches) for (int i = 0; i < PM_NSTAGES; i++) launches[i] = 0;
+    for (auto &mk : ctx->marks) {
+        float t = 0;
+        CK(cudaEventElapsedTime(&t, mk.a, mk.b));
+        if (ms) ms[mk.stage] += t;
+        if (launches) launches[mk.stage] += mk.launches;
+        ctx->spare.push_back(mk.a);
+        ctx->spare.push_back(mk.b);
+    }
+    ctx->marks.clear();
+    return PM_OK;
+}
 
 static int check_common(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA,
                         const void *B, int64_t dB, const void *C)

@@ -34,7 +34,15 @@ struct pm_ctx {
     long long launches = 0;
     int *d_status = nullptr;          // deferred device status (0 = OK)
     Arena arena;                      // driver buffers (PM-Basis, resultant)
+    int opt_timing = 0;
+    struct Mark { int stage; cudaEvent_t a, b; long long launches; };
+    std::vector<Mark> marks;          // recorded stage intervals
+    std::vector<cudaEvent_t> spare;   // reusable events
 };
+
+// Stage timing: stage_begin returns a token; stage_end closes it.
+int stage_begin(pm_ctx *ctx, int stage);
+void stage_end(pm_ctx *ctx, int token);
 
 int pm_fail(pm_ctx *ctx, int code, const std::string &msg);
 int pm_cuda(pm_ctx *ctx, cudaError_t e, const char *what);

@@ -23,7 +23,9 @@ LIB_PATH = os.path.join(HERE, "libpmat.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pmat.h")
 
 PM_OK, PM_EINVAL, PM_EDOMAIN, PM_ENOMEM, PM_ECUDA, PM_ETIMEOUT, PM_EUNSUPPORTED = range(7)
-PM_OPT_POINTWISE, PM_OPT_THRESHOLD, PM_OPT_DEBUG_CHECKS = 1, 2, 3
+PM_OPT_POINTWISE, PM_OPT_THRESHOLD, PM_OPT_DEBUG_CHECKS, PM_OPT_STAGE_TIMING = 1, 2, 3, 4
+PM_NSTAGES = 8
+STAGES = ["fwd_ntt", "pointwise", "inv_ntt", "crt", "leaf", "other"]
 STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_EDOMAIN", 3: "PM_ENOMEM", 4: "PM_ECUDA",
                 5: "PM_ETIMEOUT", 6: "PM_EUNSUPPORTED"}
 
@@ -58,6 +60,7 @@ def lib():
             "pm_sync": ([P], i32),
             "pm_last_error": ([P], C.c_char_p),
             "pm_kernel_launches": ([P], i64),
+            "pm_stage_times": ([P, P, P], i32),
             "pmat_mul": ([P, u64, i32, i32, i32, i32, P, i64, P, i64, P], i32),
             "pmat_mul_trunc": ([P, u64, i32, i32, i32, i32, P, i64, P, i64, i64, P], i32),
             "pmat_middle_product": ([P, u64, i32, i32, i32, i32, P, i64, P, i64, i64, i64, P], i32),
@@ -124,7 +127,9 @@ class Context:
             stream = torch.cuda.current_stream(device)
         self.stream = stream
         h = C.c_void_p()
-        rc = L.pm_create(C.byref(h), device, C.c_void_p(stream.cuda_stream))
+        # handle 0 is torch's legacy default stream: pass cudaStreamLegacy (0x1),
+        # since NULL asks the library for a stream of its own
+        rc = L.pm_create(C.byref(h), device, C.c_void_p(stream.cuda_stream or 1))
         if rc != PM_OK:
             raise PmError(rc, "pm_create failed")
         self.h = h
@@ -149,13 +154,20 @@ class Context:
 
     def set_stream(self, stream: torch.cuda.Stream):
         self.stream = stream
-        self._ck(lib().pm_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
+        self._ck(lib().pm_set_stream(self.h, C.c_void_p(stream.cuda_stream or 1)))
 
     def sync(self):
         self._ck(lib().pm_sync(self.h))
 
     def launches(self) -> int:
         return int(lib().pm_kernel_launches(self.h))
+
+    def stage_times(self):
+        """{stage: (ms, launches)} recorded since the last call (needs PM_OPT_STAGE_TIMING)."""
+        ms = np.zeros(PM_NSTAGES, dtype=np.float64)
+        nl = np.zeros(PM_NSTAGES, dtype=np.int64)
+        self._ck(lib().pm_stage_times(self.h, ms.ctypes.data, nl.ctypes.data))
+        return {name: (float(ms[i]), int(nl[i])) for i, name in enumerate(STAGES)}
 
 
 def _out(out, shape, like):
