@@ -51,7 +51,8 @@ enum {
     PM_ENOMEM = 3,       /* device workspace allocation failed */
     PM_ECUDA = 4,        /* a CUDA runtime call or kernel launch failed */
     PM_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
-    PM_EUNSUPPORTED = 6  /* valid request outside what this build handles */
+    PM_EUNSUPPORTED = 6, /* valid request outside what this build handles */
+    PM_ESCRATCH = 7      /* request needs more than the fixed scratch array of pmat_mul_noalloc */
 };
 
 typedef struct pm_ctx pm_ctx;
@@ -149,6 +150,31 @@ typedef struct {
  * products is binned by transform length and run by shared launches.  On a
  * bad descriptor returns PM_EINVAL and runs nothing. */
 int pmat_mul_batched(pm_ctx *ctx, int count, const pmat_desc *descs);
+
+/* pmat_mul without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory --
+ * code being captured into a CUDA graph that must hold no allocation nodes,
+ * code running under a framework whose pool owns all device memory, or a
+ * process with a device-memory budget fixed at start-up.  It computes what
+ * pmat_mul computes (same arguments, same result) on the CUDA stream
+ * `cuda_stream` (NULL = the legacy default stream) of the CURRENT device, and
+ * takes no context.
+ * Scratch: one file-scope device array of 64 MiB, held by every GPU that
+ * loads the library until the process exits.  A product whose scratch need
+ *   K * (2 * al(2^lg * 8) + al(m n 2^lg 4) + al(n k 2^lg 4) + al(m k 2^lg 4))
+ *   + (K > 1 or p not an NTT prime ? K * m k (dA+dB-1) * 4 : 0)
+ * (2^lg = the transform length >= dA+dB-1, K = the number of NTT primes,
+ * al = round up to 256 bytes) exceeds 64 MiB is rejected with PM_ESCRATCH
+ * before anything runs.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current), so make
+ * that first call before any stream capture.  Every call overwrites the
+ * array: calls that overlap on the GPU (several streams or host threads)
+ * race and must be serialised by the caller.  Calls no cudaMalloc, cudaFree
+ * or other allocating routine.  Returns PM_EINVAL on bad arguments, PM_ECUDA
+ * on a runtime or launch failure. */
+int pmat_mul_noalloc(uint64_t p, int w, int m, int n, int k,
+                     const void *A, int64_t dA, const void *B, int64_t dB, void *C,
+                     void *cuda_stream);
 
 /* PM-Basis (Sec. 3, Algorithm 3; leaves: Algorithm 2 with Algorithm 1).
  * F: m x n matrix of uint64_t (w = 8) with entries of length lenF in device

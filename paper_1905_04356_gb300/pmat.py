@@ -22,12 +22,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpmat.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pmat.h")
 
-PM_OK, PM_EINVAL, PM_EDOMAIN, PM_ENOMEM, PM_ECUDA, PM_ETIMEOUT, PM_EUNSUPPORTED = range(7)
+PM_OK, PM_EINVAL, PM_EDOMAIN, PM_ENOMEM, PM_ECUDA, PM_ETIMEOUT, PM_EUNSUPPORTED, PM_ESCRATCH = range(8)
 PM_OPT_POINTWISE, PM_OPT_THRESHOLD, PM_OPT_DEBUG_CHECKS, PM_OPT_STAGE_TIMING = 1, 2, 3, 4
 PM_NSTAGES = 8
 STAGES = ["fwd_ntt", "pointwise", "inv_ntt", "crt", "leaf", "other"]
 STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_EDOMAIN", 3: "PM_ENOMEM", 4: "PM_ECUDA",
-                5: "PM_ETIMEOUT", 6: "PM_EUNSUPPORTED"}
+                5: "PM_ETIMEOUT", 6: "PM_EUNSUPPORTED", 7: "PM_ESCRATCH"}
 
 
 class PmError(RuntimeError):
@@ -65,6 +65,7 @@ def lib():
             "pmat_mul_trunc": ([P, u64, i32, i32, i32, i32, P, i64, P, i64, i64, P], i32),
             "pmat_middle_product": ([P, u64, i32, i32, i32, i32, P, i64, P, i64, i64, i64, P], i32),
             "pmat_mul_batched": ([P, i32, C.POINTER(pmat_desc)], i32),
+            "pmat_mul_noalloc": ([u64, i32, i32, i32, i32, P, i64, P, i64, P, P], i32),
             "pm_basis": ([P, u64, i32, i32, P, i64, i64, P, P, P], i32),
             "bivariate_resultant": ([P, i32, P, i32, i32, P, i32, i32, P, P], i32),
         }
