@@ -32,14 +32,6 @@ int pmat_mul_batched(pm_ctx *ctx, int count, const pmat_desc *d)
     return PM_OK;
 }
 
-int pm_basis(pm_ctx *ctx, uint64_t p, int m, int n, const void *F, int64_t lenF, int64_t d, const int64_t *shift,
-             void *P, int64_t *rdeg_out)
-{
-    (void)p; (void)m; (void)n; (void)F; (void)lenF; (void)d; (void)shift; (void)P; (void)rdeg_out;
-    if (!ctx) return PM_EINVAL;
-    return pm_fail(ctx, PM_EUNSUPPORTED, "pm_basis not built yet");
-}
-
 int bivariate_resultant(pm_ctx *ctx, int nprimes, const uint64_t *primes, int dxf, int dyf, const void *f, int dxg,
                         int dyg, const void *g, void *R)
 {

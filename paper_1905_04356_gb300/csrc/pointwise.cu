@@ -3,9 +3,9 @@
 //
 // Pointwise: at every evaluation point j, C_j = A_j B_j mod q (Sec. 2,
 // "Polynomial matrix multiplication": the n^omega d term of the cost).  This
-// is the CUDA-core form: each thread owns one point and a 4 x 4 tile of
+// is the CUDA-core form: each thread owns one point and a 4 x 8 tile of
 // outputs; 30-bit residues multiply into 64-bit lazy accumulators (16 terms
-// below 2^64), folded mod q every 16 terms.  Loads are coalesced across the
+// below 2^64, one mad.wide.u32 each), folded mod q every 16 terms.  Loads are coalesced across the
 // points of a warp (the transform domain is entry-major, point-minor).
 //
 // CRT: for moduli without suitable roots of unity the product is lifted to
@@ -15,8 +15,9 @@
 // Horner pass in F_p reduces it mod p.
 #include "common.cuh"
 
-#define PW_T 4
-#define PW_PTS 128
+#define PW_TI 4      // output rows per thread
+#define PW_TK 8      // output columns per thread
+#define PW_PTS 128   // points (threads) per block
 
 __device__ __forceinline__ int find_job_pw(const int *blk_start, int b)
 {
@@ -28,58 +29,80 @@ __device__ __forceinline__ int find_job_pw(const int *blk_start, int b)
 int pw_blocks(const PwJob &j)
 {
     const int npb = (j.L + PW_PTS - 1) / PW_PTS;
-    return npb * ((j.m + PW_T - 1) / PW_T) * ((j.k + PW_T - 1) / PW_T);
+    return npb * ((j.m + PW_TI - 1) / PW_TI) * ((j.k + PW_TK - 1) / PW_TK);
 }
 
+__device__ __forceinline__ void mad_wide(u64 &acc, u32 a, u32 b)
+{
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
+// One thread: one point, a PW_TI x PW_TK tile of outputs.  Rows / columns past
+// the matrix edge read a valid row (the last one) and are not stored, so the
+// inner loop carries no predicates.
 __global__ void __launch_bounds__(PW_PTS) k_pointwise(const __grid_constant__ JobPack<PwJob> pk)
 {
     const int b = blockIdx.x;
     const int jb = find_job_pw(pk.blk_start, b);
     const PwJob &J = pk.jobs[jb];
+    const int m = J.m, n = J.n, k = J.k, Li = J.L;
+    const u32 q = J.P.q, q2 = J.P.q2, r32 = J.P.r32, r32s = J.P.r32s, ones = J.P.ones;
     int rel = b - pk.blk_start[jb];
-    const int npb = (J.L + PW_PTS - 1) / PW_PTS, ntk = (J.k + PW_T - 1) / PW_T;
+    const int npb = (Li + PW_PTS - 1) / PW_PTS, ntk = (k + PW_TK - 1) / PW_TK;
     const int pb = rel % npb;
     rel /= npb;
     const int tk = rel % ntk, ti = rel / ntk;
     const int pt = pb * PW_PTS + threadIdx.x;
-    if (pt >= J.L) return;
-    const int i0 = ti * PW_T, k0 = tk * PW_T;
-    const int m = J.m, n = J.n, k = J.k;
-    const i64 L = J.L;
+    if (pt >= Li) return;
+    const int i0 = ti * PW_TI, k0 = tk * PW_TK;
+    const i64 L = Li;
 
-    u64 acc[PW_T][PW_T];
-    u32 part[PW_T][PW_T];
+    const u32 *pa[PW_TI], *pbp[PW_TK];
 #pragma unroll
-    for (int a = 0; a < PW_T; a++)
+    for (int a = 0; a < PW_TI; a++) pa[a] = J.A + (i64)min(i0 + a, m - 1) * n * L + pt;
 #pragma unroll
-        for (int c = 0; c < PW_T; c++) { acc[a][c] = 0; part[a][c] = 0; }
+    for (int c = 0; c < PW_TK; c++) pbp[c] = J.B + (i64)min(k0 + c, k - 1) * L + pt;
+    const i64 sb = (i64)k * L;   // B stride between consecutive l
 
-    for (int l = 0; l < n; l++) {
-        u32 av[PW_T], bv[PW_T];
+    u32 part[PW_TI][PW_TK];
 #pragma unroll
-        for (int a = 0; a < PW_T; a++)
-            av[a] = (i0 + a < m) ? __ldg(J.A + ((i64)(i0 + a) * n + l) * L + pt) : 0u;
+    for (int a = 0; a < PW_TI; a++)
 #pragma unroll
-        for (int c = 0; c < PW_T; c++)
-            bv[c] = (k0 + c < k) ? __ldg(J.B + ((i64)l * k + k0 + c) * L + pt) : 0u;
+        for (int c = 0; c < PW_TK; c++) part[a][c] = 0;
+
+    for (int l0 = 0; l0 < n; l0 += 16) {
+        const int lend = min(n, l0 + 16);
+        u64 acc[PW_TI][PW_TK];
 #pragma unroll
-        for (int a = 0; a < PW_T; a++)
+        for (int a = 0; a < PW_TI; a++)
 #pragma unroll
-            for (int c = 0; c < PW_T; c++) acc[a][c] += (u64)av[a] * bv[c];
-        if ((l & 15) == 15 || l == n - 1) {
+            for (int c = 0; c < PW_TK; c++) acc[a][c] = 0;
+        for (int l = l0; l < lend; l++) {
+            u32 av[PW_TI], bv[PW_TK];
 #pragma unroll
-            for (int a = 0; a < PW_T; a++)
+            for (int a = 0; a < PW_TI; a++) av[a] = __ldg(pa[a] + (i64)l * L);
 #pragma unroll
-                for (int c = 0; c < PW_T; c++) {
-                    part[a][c] = csub(part[a][c] + reduce64(acc[a][c], J.P), J.P.q);
-                    acc[a][c] = 0;
-                }
+            for (int c = 0; c < PW_TK; c++) bv[c] = __ldg(pbp[c] + (i64)l * sb);
+#pragma unroll
+            for (int a = 0; a < PW_TI; a++)
+#pragma unroll
+                for (int c = 0; c < PW_TK; c++) mad_wide(acc[a][c], av[a], bv[c]);
         }
+        // fold: acc < 16 q^2 < 2^64; acc = hi 2^32 + lo -> [0, q)
+#pragma unroll
+        for (int a = 0; a < PW_TI; a++)
+#pragma unroll
+            for (int c = 0; c < PW_TK; c++) {
+                const u32 hi = (u32)(acc[a][c] >> 32), lo = (u32)acc[a][c];
+                u32 s2 = shoup_mul(hi, r32, r32s, q) + shoup_mul(lo, 1u, ones, q);    // < 4q
+                s2 = csub(csub(s2, q2), q);
+                part[a][c] = csub(part[a][c] + s2, q);
+            }
     }
 #pragma unroll
-    for (int a = 0; a < PW_T; a++)
+    for (int a = 0; a < PW_TI; a++)
 #pragma unroll
-        for (int c = 0; c < PW_T; c++)
+        for (int c = 0; c < PW_TK; c++)
             if (i0 + a < m && k0 + c < k) J.C[((i64)(i0 + a) * k + k0 + c) * L + pt] = part[a][c];
 }
 
