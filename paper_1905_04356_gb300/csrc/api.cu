@@ -235,15 +235,12 @@ static int choose_primes(pm_ctx *ctx, uint64_t p, int n, int64_t dmin, int lg, s
     direct = false;
     if (p < (1ull << 30) && p > 2 && ((p - 1) % (1ull << lg)) == 0 && is_prime32(p)) {
         for (auto &s : ctx->direct)
-            if (s.q == p) { out.push_back(&s); direct = true; break; }
-        if (!direct) {
-            ctx->direct.emplace_back();
-            slot_init(ctx->direct.back(), (u32)p);
-            // pointers into `direct` may move: rebuild after emplace
-            out.push_back(&ctx->direct.back());
-            direct = true;
-        }
-        return slot_tables(ctx, *out[0], lg);
+            if (s.q == p) { out.push_back(&s); direct = true; return PM_OK; }
+        ctx->direct.emplace_back();
+        slot_init(ctx->direct.back(), (u32)p);
+        out.push_back(&ctx->direct.back());
+        direct = true;
+        return PM_OK;
     }
     const double need = std::log2((double)n) + std::log2((double)dmin) + 2.0 * std::log2((double)(p - 1 ? p - 1 : 1));
     double have = 0;
@@ -253,7 +250,6 @@ static int choose_primes(pm_ctx *ctx, uint64_t p, int n, int64_t dmin, int lg, s
         if (have > need + 0.01) break;
     }
     if (have <= need + 0.01) return pm_fail(ctx, PM_EUNSUPPORTED, "product needs more CRT primes than the table holds");
-    for (auto *s : out) CKI(slot_tables(ctx, *s, lg));
     return PM_OK;
 }
 
@@ -326,8 +322,10 @@ static int fwd_entries_per_block(int lg)
     return th / tpt;
 }
 
-static int run_forward(pm_ctx *ctx, const PrimeDev &P, const void *src, int mode, int64_t src_stride, int64_t src_len,
-                       int entries, u32 *dst, int lg, JobPack<FwdJob> &pk, JobPack<ColJob> &pc)
+// Forward jobs of one operand modulo one prime (a column pass first when L > 2^13).
+static void add_forward(const PrimeDev &P, const void *src, int mode, int64_t src_stride, int64_t src_len,
+                        int entries, u32 *dst, int lg, std::vector<FwdJob> &blk, std::vector<int> &blk_n,
+                        std::vector<ColJob> &col, std::vector<int> &col_n)
 {
     const int64_t L = int64_t(1) << lg;
     if (lg <= PM_LB_LOG2) {
@@ -335,18 +333,220 @@ static int run_forward(pm_ctx *ctx, const PrimeDev &P, const void *src, int mode
         j.src = src; j.dst = dst; j.src_stride = src_stride; j.dst_stride = L;
         j.src_len = (int)src_len; j.src_mode = mode; j.count = entries; j._pad = 0; j.P = P;
         const int epb = fwd_entries_per_block(lg);
-        pack_add(pk, j, (entries + epb - 1) / epb);
+        blk.push_back(j);
+        blk_n.push_back((entries + epb - 1) / epb);
     } else {
         ColJob c;
         c.src = src; c.dst = dst; c.src_stride = src_stride; c.dst_stride = L;
         c.src_len = (int)src_len; c.mode = mode; c.count = entries; c.out_off = 0; c.out_len = 0; c._pad = 0; c.P = P;
-        pack_add(pc, c, entries * blocks_per_entry_cols(lg));
+        col.push_back(c);
+        col_n.push_back(entries * blocks_per_entry_cols(lg));
         FwdJob j;
         const int64_t nb = L >> PM_LB_LOG2;
         j.src = dst; j.dst = dst; j.src_stride = 1 << PM_LB_LOG2; j.dst_stride = 1 << PM_LB_LOG2;
         j.src_len = 1 << PM_LB_LOG2; j.src_mode = 0; j.count = (int)(entries * nb); j._pad = 0; j.P = P;
         const int epb = fwd_entries_per_block(PM_LB_LOG2);
-        pack_add(pk, j, (int)((entries * nb + epb - 1) / epb));
+        blk.push_back(j);
+        blk_n.push_back((int)((entries * nb + epb - 1) / epb));
+    }
+}
+
+// Launch a list of jobs in packs of PM_MAXJ.
+template <typename J, typename F>
+static int launch_packs(pm_ctx *ctx, const std::vector<J> &jobs, const std::vector<int> &nblk, F launch)
+{
+    size_t i = 0;
+    while (i < jobs.size()) {
+        JobPack<J> pk;
+        pack_reset(pk);
+        while (i < jobs.size() && pk.njobs < PM_MAXJ) { pack_add(pk, jobs[i], nblk[i]); i++; }
+        CK(launch(pk));
+    }
+    return PM_OK;
+}
+
+namespace {
+struct Plan {
+    std::vector<PrimeSlot *> pr;
+    bool direct;
+    size_t bA, bB, bC, bR, total;
+    int64_t out_len;
+};
+}  // namespace
+
+#define PM_BATCH_WS_CAP (16ull << 30)   // workspace bytes per chunk of a batch
+
+int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
+{
+    // ---- plan every request; size the twiddle tables before any job takes their addresses
+    std::vector<Plan> plan(count);
+    for (int r = 0; r < count; r++) {
+        const ProdReq &q = reqs[r];
+        if (q.lg > PM_MAX_LOG2L) return pm_fail(ctx, PM_EINVAL, "transform longer than 2^20 points");
+        Plan &P = plan[r];
+        CKI(choose_primes(ctx, q.p, q.n, q.dA < q.dB ? q.dA : q.dB, q.lg, P.pr, P.direct));
+        const int64_t L = int64_t(1) << q.lg;
+        const size_t eA = (size_t)q.m * q.n, eB = (size_t)q.n * q.k, eC = (size_t)q.m * q.k;
+        P.bA = align256(eA * L * 4);
+        P.bB = align256(eB * L * 4);
+        P.bC = align256(eC * L * 4);
+        P.bR = P.direct ? 0 : eC * (size_t)q.len * 4;     // packed planes: the CRT kernel reads res + i * count
+        P.total = P.pr.size() * (P.bA + P.bB + P.bC) + align256(P.pr.size() * P.bR);
+        P.out_len = q.off + q.len <= L ? q.len : (q.off < L ? L - q.off : 0);
+    }
+    for (int r = 0; r < count; r++)
+        for (auto *s : plan[r].pr) CKI(slot_tables(ctx, *s, reqs[r].lg));
+
+    // ---- chunks under the workspace cap
+    int r0 = 0;
+    while (r0 < count) {
+        size_t tot = plan[r0].total;
+        int r1 = r0 + 1;
+        while (r1 < count && tot + plan[r1].total <= PM_BATCH_WS_CAP) tot += plan[r1].total, r1++;
+        void *ws = nullptr;
+        CKI(ws_reserve(ctx, tot + 256, &ws));
+        struct Bufs { char *A, *B, *C, *R; };
+        std::vector<Bufs> buf(r1 - r0);
+        char *cur = (char *)ws;
+        for (int r = r0; r < r1; r++) {
+            const Plan &P = plan[r];
+            const size_t K = P.pr.size();
+            Bufs &b = buf[r - r0];
+            b.A = cur; cur += K * P.bA;
+            b.B = cur; cur += K * P.bB;
+            b.C = cur; cur += K * P.bC;
+            b.R = cur; cur += align256(K * P.bR);
+        }
+        // 1. forward transforms, binned by transform length
+        int tok = stage_begin(ctx, PM_STAGE_FWD);
+        for (int lg = 4; lg <= PM_MAX_LOG2L; lg++) {
+            std::vector<FwdJob> blk; std::vector<int> bn;
+            std::vector<ColJob> col; std::vector<int> cn;
+            for (int r = r0; r < r1; r++) {
+                const ProdReq &q = reqs[r];
+                if (q.lg != lg) continue;
+                const Plan &P = plan[r];
+                const Bufs &b = buf[r - r0];
+                for (size_t i = 0; i < P.pr.size(); i++) {
+                    PrimeDev D = prime_dev(*P.pr[i], lg);
+                    add_forward(D, q.A, q.w, q.sA, q.dA, q.m * q.n, (u32 *)(b.A + i * P.bA), lg, blk, bn, col, cn);
+                    add_forward(D, q.B, q.w, q.sB, q.dB, q.n * q.k, (u32 *)(b.B + i * P.bB), lg, blk, bn, col, cn);
+                }
+            }
+            if (!col.empty())
+                CKI(launch_packs(ctx, col, cn, [&](const JobPack<ColJob> &pk) {
+                    return launch_ntt_fwd_cols(pk, lg, ctx->stream, &ctx->launches); }));
+            if (!blk.empty()) {
+                const int blg = lg > PM_LB_LOG2 ? PM_LB_LOG2 : lg;
+                CKI(launch_packs(ctx, blk, bn, [&](const JobPack<FwdJob> &pk) {
+                    return launch_ntt_fwd_block(pk, blg, ctx->stream, &ctx->launches); }));
+            }
+        }
+        stage_end(ctx, tok);
+        // 2. pointwise products (jobs of any length share launches)
+        tok = stage_begin(ctx, PM_STAGE_POINTWISE);
+        {
+            std::vector<PwJob> jobs; std::vector<int> nb;
+            for (int r = r0; r < r1; r++) {
+                const ProdReq &q = reqs[r];
+                const Plan &P = plan[r];
+                const Bufs &b = buf[r - r0];
+                for (size_t i = 0; i < P.pr.size(); i++) {
+                    PwJob j;
+                    j.A = (u32 *)(b.A + i * P.bA); j.B = (u32 *)(b.B + i * P.bB); j.C = (u32 *)(b.C + i * P.bC);
+                    j.m = q.m; j.n = q.n; j.k = q.k; j.L = 1 << q.lg; j.P = prime_dev(*P.pr[i], q.lg);
+                    jobs.push_back(j);
+                    nb.push_back(pw_blocks(j));
+                }
+            }
+            CKI(launch_packs(ctx, jobs, nb, [&](const JobPack<PwJob> &pk) {
+                return launch_pointwise(pk, ctx->stream, &ctx->launches); }));
+        }
+        stage_end(ctx, tok);
+        // 3. inverse transforms, scaled, writing each slice, binned by length
+        tok = stage_begin(ctx, PM_STAGE_INV);
+        for (int lg = 4; lg <= PM_MAX_LOG2L; lg++) {
+            std::vector<InvJob> blk; std::vector<int> bn;
+            std::vector<ColJob> col; std::vector<int> cn;
+            const int64_t L = int64_t(1) << lg;
+            for (int r = r0; r < r1; r++) {
+                const ProdReq &q = reqs[r];
+                if (q.lg != lg) continue;
+                const Plan &P = plan[r];
+                const Bufs &b = buf[r - r0];
+                const int mode = P.direct ? q.w : 1;
+                const int64_t eC = (int64_t)q.m * q.k;
+                for (size_t i = 0; i < P.pr.size(); i++) {
+                    PrimeDev D = prime_dev(*P.pr[i], lg);
+                    u32 *src = (u32 *)(b.C + i * P.bC);
+                    void *dst = P.direct ? q.C : (void *)(b.R + i * P.bR);
+                    const int64_t dstride = P.direct ? q.sC : q.len;
+                    if (lg <= PM_LB_LOG2) {
+                        InvJob j;
+                        j.src = src; j.dst = dst; j.src_stride = L; j.dst_stride = dstride;
+                        j.out_off = (int)q.off; j.out_len = (int)P.out_len; j.dst_mode = mode; j.count = (int)eC; j.P = D;
+                        const int epb = fwd_entries_per_block(lg);
+                        blk.push_back(j);
+                        bn.push_back((int)((eC + epb - 1) / epb));
+                    } else {
+                        const int64_t nbk = L >> PM_LB_LOG2;
+                        InvJob j;
+                        j.src = src; j.dst = src; j.src_stride = 1 << PM_LB_LOG2; j.dst_stride = 1 << PM_LB_LOG2;
+                        j.out_off = 0; j.out_len = 0; j.dst_mode = 0; j.count = (int)(eC * nbk); j.P = D;
+                        const int epb = fwd_entries_per_block(PM_LB_LOG2);
+                        blk.push_back(j);
+                        bn.push_back((int)((eC * nbk + epb - 1) / epb));
+                        ColJob c;
+                        c.src = src; c.dst = dst; c.src_stride = L; c.dst_stride = dstride;
+                        c.src_len = 0; c.mode = mode; c.count = (int)eC; c.out_off = (int)q.off;
+                        c.out_len = (int)P.out_len; c._pad = 0; c.P = D;
+                        col.push_back(c);
+                        cn.push_back((int)eC * blocks_per_entry_cols(lg));
+                    }
+                }
+            }
+            if (!blk.empty()) {
+                const int blg = lg > PM_LB_LOG2 ? PM_LB_LOG2 : lg;
+                CKI(launch_packs(ctx, blk, bn, [&](const JobPack<InvJob> &pk) {
+                    return launch_ntt_inv_block(pk, blg, ctx->stream, &ctx->launches); }));
+            }
+            if (!col.empty())
+                CKI(launch_packs(ctx, col, cn, [&](const JobPack<ColJob> &pk) {
+                    return launch_ntt_inv_cols(pk, lg, ctx->stream, &ctx->launches); }));
+        }
+        stage_end(ctx, tok);
+        // 4. CRT recombination into values mod p
+        tok = stage_begin(ctx, PM_STAGE_CRT);
+        {
+            std::vector<CrtJob> jobs; std::vector<int> nb;
+            for (int r = r0; r < r1; r++) {
+                const Plan &P = plan[r];
+                if (P.direct) continue;
+                const ProdReq &q = reqs[r];
+                CrtJob j;
+                memset(&j, 0, sizeof(j));
+                fill_crt(j, P.pr, q.p);
+                j.res = (const u32 *)buf[r - r0].R; j.dst = q.C; j.count = (int64_t)q.m * q.k * q.len;
+                j.len = q.len; j.dst_stride = q.sC; j.w = q.w;
+                jobs.push_back(j);
+                nb.push_back(crt_blocks(j));
+            }
+            if (!jobs.empty())
+                CKI(launch_packs(ctx, jobs, nb, [&](const JobPack<CrtJob> &pk) {
+                    return launch_crt(pk, ctx->stream, &ctx->launches); }));
+        }
+        stage_end(ctx, tok);
+        // 5. slice positions beyond the transform length are zero
+        for (int r = r0; r < r1; r++) {
+            const ProdReq &q = reqs[r];
+            const Plan &P = plan[r];
+            if (P.out_len < q.len) {
+                const int64_t z0 = P.out_len > 0 ? P.out_len : 0;
+                CK(cudaMemset2DAsync((char *)q.C + z0 * q.w, (size_t)q.sC * q.w, 0, (size_t)(q.len - z0) * q.w,
+                                     (size_t)q.m * q.k, ctx->stream));
+            }
+        }
+        r0 = r1;
     }
     return PM_OK;
 }
@@ -354,103 +554,10 @@ static int run_forward(pm_ctx *ctx, const PrimeDev &P, const void *src, int mode
 int prod_slice(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA, int64_t sA,
                const void *B, int64_t dB, int64_t sB, int64_t off, int64_t len, int lg, void *C, int64_t sC)
 {
-    if (lg < 4) lg = 4;
-    if (lg > PM_MAX_LOG2L) return pm_fail(ctx, PM_EINVAL, "transform longer than 2^20 points");
-    const int64_t L = int64_t(1) << lg;
-    std::vector<PrimeSlot *> pr;
-    bool direct = false;
-    CKI(choose_primes(ctx, p, n, dA < dB ? dA : dB, lg, pr, direct));
-    const int K = (int)pr.size();
-    const size_t eA = (size_t)m * n, eB = (size_t)n * k, eC = (size_t)m * k;
-    const size_t bA = align256(eA * L * 4), bB = align256(eB * L * 4), bC = align256(eC * L * 4);
-    const int64_t out_len = off + len <= L ? len : (off < L ? L - off : 0);
-    const size_t bR = direct ? 0 : eC * (size_t)len * 4;   // residue planes packed: CRT indexes by count
-    void *ws = nullptr;
-    CKI(ws_reserve(ctx, K * (bA + bB + bC) + K * bR + 256, &ws));
-    char *base = (char *)ws;
-    u32 *Ah = (u32 *)base, *Bh = (u32 *)(base + K * bA), *Ch = (u32 *)(base + K * (bA + bB));
-    u32 *Rs = (u32 *)(base + K * (bA + bB + bC));
-
-    // 1. forward transforms of A and B modulo every prime (reduction fused)
-    int tok = stage_begin(ctx, PM_STAGE_FWD);
-    {
-        JobPack<FwdJob> pk; pack_reset(pk);
-        JobPack<ColJob> pc; pack_reset(pc);
-        for (int i = 0; i < K; i++) {
-            PrimeDev P = prime_dev(*pr[i], lg);
-            run_forward(ctx, P, A, w, sA, dA, (int)eA, (u32 *)((char *)Ah + i * bA), lg, pk, pc);
-            run_forward(ctx, P, B, w, sB, dB, (int)eB, (u32 *)((char *)Bh + i * bB), lg, pk, pc);
-        }
-        if (pc.njobs) CK(launch_ntt_fwd_cols(pc, lg, ctx->stream, &ctx->launches));
-        CK(launch_ntt_fwd_block(pk, lg > PM_LB_LOG2 ? PM_LB_LOG2 : lg, ctx->stream, &ctx->launches));
-    }
-    stage_end(ctx, tok);
-    // 2. pointwise products at every point
-    tok = stage_begin(ctx, PM_STAGE_POINTWISE);
-    {
-        JobPack<PwJob> pk; pack_reset(pk);
-        for (int i = 0; i < K; i++) {
-            PwJob j;
-            j.A = (u32 *)((char *)Ah + i * bA); j.B = (u32 *)((char *)Bh + i * bB); j.C = (u32 *)((char *)Ch + i * bC);
-            j.m = m; j.n = n; j.k = k; j.L = (int)L; j.P = prime_dev(*pr[i], lg);
-            pack_add(pk, j, pw_blocks(j));
-        }
-        CK(launch_pointwise(pk, ctx->stream, &ctx->launches));
-    }
-    stage_end(ctx, tok);
-    // 3. inverse transforms, scaled, writing the slice [off, off + len)
-    tok = stage_begin(ctx, PM_STAGE_INV);
-    {
-        const int mode = direct ? w : 1;
-        JobPack<InvJob> pk; pack_reset(pk);
-        JobPack<ColJob> pc; pack_reset(pc);
-        for (int i = 0; i < K; i++) {
-            PrimeDev P = prime_dev(*pr[i], lg);
-            u32 *src = (u32 *)((char *)Ch + i * bC);
-            void *dst = direct ? C : (void *)((char *)Rs + i * bR);
-            const int64_t dstride = direct ? sC : len;
-            if (lg <= PM_LB_LOG2) {
-                InvJob j;
-                j.src = src; j.dst = dst; j.src_stride = L; j.dst_stride = dstride;
-                j.out_off = (int)off; j.out_len = (int)out_len; j.dst_mode = mode; j.count = (int)eC; j.P = P;
-                const int epb = fwd_entries_per_block(lg);
-                pack_add(pk, j, (int)((eC + epb - 1) / epb));
-            } else {
-                const int64_t nb = L >> PM_LB_LOG2;
-                InvJob j;
-                j.src = src; j.dst = src; j.src_stride = 1 << PM_LB_LOG2; j.dst_stride = 1 << PM_LB_LOG2;
-                j.out_off = 0; j.out_len = 0; j.dst_mode = 0; j.count = (int)(eC * nb); j.P = P;
-                const int epb = fwd_entries_per_block(PM_LB_LOG2);
-                pack_add(pk, j, (int)((eC * nb + epb - 1) / epb));
-                ColJob c;
-                c.src = src; c.dst = dst; c.src_stride = L; c.dst_stride = dstride;
-                c.src_len = 0; c.mode = mode; c.count = (int)eC; c.out_off = (int)off; c.out_len = (int)out_len; c._pad = 0;
-                c.P = P;
-                pack_add(pc, c, (int)eC * blocks_per_entry_cols(lg));
-            }
-        }
-        CK(launch_ntt_inv_block(pk, lg > PM_LB_LOG2 ? PM_LB_LOG2 : lg, ctx->stream, &ctx->launches));
-        if (pc.njobs) CK(launch_ntt_inv_cols(pc, lg, ctx->stream, &ctx->launches));
-    }
-    stage_end(ctx, tok);
-    // 4. CRT recombination into values mod p
-    if (!direct) {
-        tok = stage_begin(ctx, PM_STAGE_CRT);
-        JobPack<CrtJob> pk; pack_reset(pk);
-        CrtJob j;
-        memset(&j, 0, sizeof(j));
-        fill_crt(j, pr, p);
-        j.res = Rs; j.dst = C; j.count = (int64_t)eC * len; j.len = len; j.dst_stride = sC; j.w = w;
-        pack_add(pk, j, crt_blocks(j));
-        CK(launch_crt(pk, ctx->stream, &ctx->launches));
-        stage_end(ctx, tok);
-    }
-    // 5. slice positions beyond the transform length are zero
-    if (out_len < len) {
-        const int64_t z0 = out_len > 0 ? out_len : 0;
-        CK(cudaMemset2DAsync((char *)C + z0 * w, (size_t)sC * w, 0, (size_t)(len - z0) * w, eC, ctx->stream));
-    }
-    return PM_OK;
+    ProdReq q;
+    q.p = p; q.w = w; q.m = m; q.n = n; q.k = k; q.lg = lg < 4 ? 4 : lg;
+    q.A = A; q.B = B; q.C = C; q.dA = dA; q.sA = sA; q.dB = dB; q.sB = sB; q.off = off; q.len = len; q.sC = sC;
+    return prod_batch(ctx, &q, 1);
 }
 
 // ------------------------------------------------------------------ C ABI
@@ -489,7 +596,6 @@ int pm_create(pm_ctx **out, int device, void *cuda_stream)
             slot_init(ctx->table.back(), (u32)q);
         }
     }
-    ctx->direct.reserve(16);
     *out = ctx;
     return PM_OK;
 }

@@ -1,6 +1,7 @@
-// drivers.cu -- entry points built on the product core: batched products,
-// PM-Basis (Algorithm 3) and the bivariate resultant (Sec. 5.2).
+// drivers.cu -- pmat_mul_batched: many independent products through one
+// planned batch (jobs binned by transform length into shared launches).
 #include <cstring>
+#include <vector>
 
 #include "host.h"
 
@@ -23,21 +24,19 @@ int pmat_mul_batched(pm_ctx *ctx, int count, const pmat_desc *d)
             ceil_log2(x.dA + x.dB - 1) > PM_MAX_LOG2L)
             return pm_fail(ctx, PM_EINVAL, "bad descriptor " + std::to_string(i));
     }
+    std::vector<ProdReq> reqs(count);
     for (int i = 0; i < count; i++) {
         const pmat_desc &x = d[i];
-        const int64_t len = x.dA + x.dB - 1;
-        CKI(prod_slice(ctx, x.p, x.w, x.m, x.n, x.k, x.A, x.dA, x.dA, x.B, x.dB, x.dB, 0, len, ceil_log2(len), x.C,
-                       len));
+        ProdReq &q = reqs[i];
+        q.p = x.p; q.w = x.w; q.m = x.m; q.n = x.n; q.k = x.k;
+        q.A = x.A; q.B = x.B; q.C = x.C;
+        q.dA = x.dA; q.sA = x.dA; q.dB = x.dB; q.sB = x.dB;
+        q.off = 0; q.len = x.dA + x.dB - 1; q.sC = q.len;
+        const int lg = ceil_log2(q.len);
+        q.lg = lg < 4 ? 4 : lg;
     }
-    return PM_OK;
-}
-
-int bivariate_resultant(pm_ctx *ctx, int nprimes, const uint64_t *primes, int dxf, int dyf, const void *f, int dxg,
-                        int dyg, const void *g, void *R)
-{
-    (void)nprimes; (void)primes; (void)dxf; (void)dyf; (void)f; (void)dxg; (void)dyg; (void)g; (void)R;
-    if (!ctx) return PM_EINVAL;
-    return pm_fail(ctx, PM_EUNSUPPORTED, "bivariate_resultant not built yet");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return pm_fail(ctx, PM_ECUDA, "cudaSetDevice failed");
+    return prod_batch(ctx, reqs.data(), count);
 }
 
 }  // extern "C"

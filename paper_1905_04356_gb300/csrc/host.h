@@ -2,6 +2,7 @@
 // C-ABI products, PM-Basis and the resultant driver.
 #pragma once
 #include <cstdint>
+#include <deque>
 #include <string>
 #include <vector>
 
@@ -28,7 +29,7 @@ struct pm_ctx {
     int opt_pointwise = 0, opt_debug = 0;
     int64_t opt_T = 32;
     std::vector<PrimeSlot> table;     // CRT primes, largest first
-    std::vector<PrimeSlot> direct;    // NTT-friendly moduli used directly (p = q)
+    std::deque<PrimeSlot> direct;     // NTT-friendly moduli used directly (p = q); stable addresses
     void *ws = nullptr;
     size_t ws_size = 0;
     long long launches = 0;
@@ -60,6 +61,18 @@ void *arena_alloc(pm_ctx *ctx, size_t bytes);
 // (positions >= L of the slice are set to zero).
 int prod_slice(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA, int64_t sA,
                const void *B, int64_t dB, int64_t sB, int64_t off, int64_t len, int lg, void *C, int64_t sC);
+
+// One product request (the arguments of prod_slice).
+struct ProdReq {
+    uint64_t p;
+    int w, m, n, k, lg;
+    const void *A, *B;
+    void *C;
+    int64_t dA, sA, dB, sB, off, len, sC;
+};
+// Run many independent product requests: planned together, their jobs binned by
+// transform length into shared launches, the workspace chunked under a cap.
+int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count);
 
 int ceil_log2(int64_t x);
 uint64_t host_mulmod(uint64_t a, uint64_t b, uint64_t p);

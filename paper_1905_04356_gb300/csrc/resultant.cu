@@ -1,0 +1,409 @@
+// resultant.cu -- bivariate resultant Res_y(f, g) in F_p[x] (Sec. 5.2, the
+// direct evaluation / interpolation method), on the device.
+//
+// With N = D + 1 points (D = dxf dyg + dxg dyf bounds deg Res), q = alpha:
+//  1. Evaluation of every x-coefficient polynomial of f and g at the geometric
+//     progression 1, q, ..., q^(N-1) (Sec. 2: evaluation at geometric
+//     progressions in O(M(d))): with C(t) = t (t - 1) / 2, i e = C(i+e) - C(i)
+//     - C(e), so F(q^i) = q^-C(i) sum_e (F_e q^-C(e)) q^C(i+e): a middle product
+//     of the scaled, reversed coefficients with the chirp h_t = q^C(t), run on
+//     the product hot path (pmat_middle_product of a J x 1 by a 1 x 1 matrix).
+//  2. At each point, the univariate resultant by the Euclidean algorithm
+//     (Res(A,B) = (-1)^(ab) lc(B)^(a-r) Res(B, A mod B)), one warp per point,
+//     pseudo-remainders so that no inversion is needed until the end.
+//  3. Interpolation at the geometric progression: with w_t = prod_{l=1..t}
+//     (q^l - 1), the Newton coefficients c_k satisfy sum_i (v_i / w_i) x^i =
+//     (sum_k c_k q^C(k) x^k)(sum_t x^t / w_t), and the series of 1 / w_t has
+//     the inverse sum_t (-1)^t q^C(t) x^t / w_t (q-exponential identity); the
+//     Newton-to-monomial change of basis is, by the q-binomial theorem,
+//     R_m w_m = sum_t c_{m+t} w_{m+t} (-1)^t q^C(t) / w_t.  Both are
+//     truncated products of length N on the hot path.
+// The points are c q^i (the substitution x -> c x, undone on the result's
+// coefficients): they must be distinct (q^l != 1 for 0 < l < N) and keep the
+// leading y-coefficients nonzero; a pair (c, q) that fails either is replaced
+// by the next candidate.  By uniqueness of the resultant the output does not
+// depend on the points.
+#include <cstring>
+#include <vector>
+
+#include "host.h"
+
+#define CKI(call)                                                       \
+    do {                                                                \
+        int _rc = (call);                                               \
+        if (_rc) return _rc;                                            \
+    } while (0)
+
+#define RES_MAXI 16   // instances per launch
+
+struct ResInst {
+    u64 p, pn, one, r2;     // Montgomery constants (R = 2^64)
+    u64 qm, qim;            // q and q^-1, Montgomery form
+    u64 cm, cim;            // point scale c and c^-1, Montgomery form (points are c q^i)
+    const u64 *f, *g;       // inputs (plain), f[j*(dxf+1) + i]
+    u64 *R;                 // output (plain), N values
+    u64 *qp, *h, *hinv;     // q^t, q^C(t), q^-C(t) (Montgomery), t < NE
+    u64 *Ua, *Hb;           // evaluation operands (plain): J x E and NE
+    u64 *S;                 // evaluation output J x N (plain)
+    u64 *Vt;                // values, point-major N x J (Montgomery)
+    u64 *v;                 // resultant values (plain), N
+    u64 *w, *winv;          // w_t and 1 / w_t (Montgomery), N
+    u64 *Va, *Eb, *Cp, *Ur, *Y;   // interpolation operands / outputs (plain), N
+};
+
+struct ResPack {
+    int count;
+    int dxf, dyf, dxg, dyg;
+    int E, J, N, NE;        // E = max(dxf, dxg) + 1, J = dyf + dyg + 2, NE = N + E - 1
+    int *flag;              // bit 1: q^l = 1 for some 0 < l < N; bit 2: a leading coefficient vanishes
+    ResInst in[RES_MAXI];
+};
+
+__device__ __forceinline__ u64 mm(u64 a, u64 b, const ResInst &I) { return mont_mul(a, b, I.p, I.pn); }
+__device__ u64 mpw(u64 a, u64 e, const ResInst &I)
+{
+    u64 r = I.one;
+    while (e) {
+        if (e & 1) r = mm(r, a, I);
+        a = mm(a, a, I);
+        e >>= 1;
+    }
+    return r;
+}
+
+// ------------------------------------------------------------------ 1. powers, evaluation operands
+__global__ void k_res_powers(const __grid_constant__ ResPack P)
+{
+    const ResInst &I = P.in[blockIdx.y];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < P.NE; t += gridDim.x * blockDim.x) {
+        const u64 c2 = (u64)t * (u64)(t > 0 ? t - 1 : 0) / 2;
+        const u64 qt = mpw(I.qm, (u64)t, I);
+        I.qp[t] = qt;
+        I.h[t] = mpw(I.qm, c2, I);
+        I.hinv[t] = mpw(I.qim, c2, I);
+        I.Hb[t] = mm(I.h[t], 1, I);
+        if (t >= 1 && t < P.N && qt == I.one) atomicOr(P.flag, 1);
+    }
+}
+
+// Ua[j][E-1-e] = coefficient e of row j times q^-C(e); rows 0..dyf from f, then g.
+__global__ void k_res_prep_eval(const __grid_constant__ ResPack P)
+{
+    const ResInst &I = P.in[blockIdx.y];
+    const int total = P.J * P.E;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < total; x += gridDim.x * blockDim.x) {
+        const int j = x / P.E, e = x % P.E;
+        u64 c = 0;
+        if (j <= P.dyf) { if (e <= P.dxf) c = I.f[(i64)j * (P.dxf + 1) + e]; }
+        else { const int jg = j - P.dyf - 1; if (e <= P.dxg) c = I.g[(i64)jg * (P.dxg + 1) + e]; }
+        c = mm(c, mpw(I.cm, (u64)e, I), I);                         // x -> c x: coefficient e times c^e
+        I.Ua[(i64)j * P.E + (P.E - 1 - e)] = mm(c, I.hinv[e], I);   // plain x Montgomery = plain
+    }
+}
+
+// values F_j(q^i) = q^-C(i) S[j][i], stored point-major in Montgomery form; leading
+// y-coefficients must not vanish.
+__global__ void k_res_eval_finish(const __grid_constant__ ResPack P)
+{
+    const ResInst &I = P.in[blockIdx.y];
+    const i64 total = (i64)P.J * P.N;
+    for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < total; x += (i64)gridDim.x * blockDim.x) {
+        const int j = (int)(x / P.N), i = (int)(x % P.N);
+        const u64 val = mm(I.S[x], I.hinv[i], I);
+        if ((j == P.dyf || j == P.J - 1) && val == 0) atomicOr(P.flag, 2);
+        I.Vt[(i64)i * P.J + j] = mm(val, I.r2, I);
+    }
+}
+
+// ------------------------------------------------------------------ 2. Euclid, one warp per point
+__device__ __forceinline__ int warp_deg(const u64 *A, int start)
+{
+    const int lane = threadIdx.x & 31;
+    for (int base = start & ~31; base >= 0; base -= 32) {
+        const int c = base + lane;
+        const unsigned b = __ballot_sync(0xffffffffu, c <= start && A[c] != 0);
+        if (b) return base + 31 - __clz(b);
+    }
+    return -1;
+}
+
+__global__ void __launch_bounds__(256) k_res_euclid(const __grid_constant__ ResPack P, int dmax)
+{
+    extern __shared__ u64 sme[];
+    const ResInst &I = P.in[blockIdx.y];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int pt = blockIdx.x * (blockDim.x >> 5) + wid;
+    if (pt >= P.N) return;
+    u64 *A = sme + (size_t)wid * 2 * (dmax + 1);
+    u64 *B = A + (dmax + 1);
+    const u64 *val = I.Vt + (i64)pt * P.J;
+    int a = P.dyf, b = P.dyg;
+    for (int c = lane; c <= a; c += 32) A[c] = val[c];
+    for (int c = lane; c <= b; c += 32) B[c] = val[P.dyf + 1 + c];
+    __syncwarp();
+    u64 num = I.one, den = I.one;
+    bool neg = false;
+    for (;;) {
+        if (b == 0) { num = mm(num, mpw(B[0], (u64)a, I), I); break; }
+        if (a == 0) { num = mm(num, mpw(A[0], (u64)b, I), I); break; }
+        if (a < b) {                                // Res(A, B) = (-1)^(ab) Res(B, A)
+            u64 *s = A; A = B; B = s;
+            int t = a; a = b; b = t;
+            neg ^= (a & b & 1);
+        }
+        // A <- lc(B)^s A mod B by s pseudo-division steps
+        const u64 lcB = B[b];
+        const u64 pb = mpw(lcB, (u64)b, I);
+        int da = a;
+        while (da >= b) {
+            const u64 lcA = A[da];
+            const int sh = da - b;
+            __syncwarp();                               // every lane has read lc(A) before A[da] changes
+            for (int c = lane; c <= da; c += 32) {
+                u64 x = mm(lcB, A[c], I);
+                if (c >= sh) x = sub64(x, mm(lcA, B[c - sh], I), I.p);
+                A[c] = x;
+            }
+            __syncwarp();
+            den = mm(den, pb, I);                   // Res(B, lc(B)^s R) = lc(B)^(s b) Res(B, R)
+            da = warp_deg(A, da - 1);
+            __syncwarp();
+        }
+        const int r = da;
+        if (r < 0) { num = 0; break; }
+        neg ^= (a & b & 1);
+        num = mm(num, mpw(lcB, (u64)(a - r), I), I);
+        u64 *s = A; A = B; B = s;                   // (A, B) <- (B, R)
+        a = b;
+        b = r;
+    }
+    if (lane == 0) {
+        u64 res = mm(num, mpw(den, I.p - 2, I), I);
+        res = mm(res, 1, I);
+        if (neg && res) res = I.p - res;
+        I.v[pt] = res;
+    }
+}
+
+// ------------------------------------------------------------------ 3. interpolation
+// w_t = prod_{l=1..t} (q^l - 1) and 1 / w_t, one block of 1024 threads per instance:
+// chunked prefix / suffix products, one inversion.
+__global__ void __launch_bounds__(1024) k_res_wscan(const __grid_constant__ ResPack P)
+{
+    __shared__ u64 pre[1024], suf[1024];
+    const ResInst &I = P.in[blockIdx.x];
+    const int N = P.N, tid = threadIdx.x;
+    const int per = (N + 1023) / 1024;
+    const int lo = tid * per, hi = min(N, lo + per);
+    auto fac = [&](int t) -> u64 { return t >= 1 ? sub64(I.qp[t], I.one, I.p) : I.one; };
+    u64 a = I.one;
+    for (int t = lo; t < hi; t++) a = mm(a, fac(t), I);
+    pre[tid] = a;
+    suf[tid] = a;
+    __syncthreads();
+    // inclusive scans (Hillis-Steele), forward for prefixes and backward for suffixes
+    for (int o = 1; o < 1024; o <<= 1) {
+        u64 x = tid >= o ? pre[tid - o] : I.one;
+        u64 y = tid + o < 1024 ? suf[tid + o] : I.one;
+        __syncthreads();
+        pre[tid] = mm(pre[tid], x, I);
+        suf[tid] = mm(suf[tid], y, I);
+        __syncthreads();
+    }
+    const u64 total = pre[1023];
+    const u64 tinv = mpw(total, I.p - 2, I);       // 1 / w_{N-1}
+    u64 run = tid ? pre[tid - 1] : I.one;           // product of the factors before this chunk
+    for (int t = lo; t < hi; t++) { run = mm(run, fac(t), I); I.w[t] = run; }
+    // 1 / w_t = (1 / w_{N-1}) prod_{l = t+1 .. N-1} (q^l - 1)
+    u64 after = tid + 1 < 1024 ? suf[tid + 1] : I.one;
+    for (int t = hi - 1; t >= lo; t--) { I.winv[t] = mm(tinv, after, I); after = mm(after, fac(t), I); }
+}
+
+// V_i = v_i / w_i and E_t = (-1)^t q^C(t) / w_t (plain)
+__global__ void k_res_interp1(const __grid_constant__ ResPack P)
+{
+    const ResInst &I = P.in[blockIdx.y];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < P.N; t += gridDim.x * blockDim.x) {
+        I.Va[t] = mm(I.v[t], I.winv[t], I);
+        u64 e = mm(mm(I.h[t], I.winv[t], I), 1, I);
+        if ((t & 1) && e) e = I.p - e;
+        I.Eb[t] = e;
+    }
+}
+
+// c_k = C'_k q^-C(k); u_k = c_k w_k; Ur[N-1-k] = u_k (plain)
+__global__ void k_res_interp2(const __grid_constant__ ResPack P)
+{
+    const ResInst &I = P.in[blockIdx.y];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P.N; k += gridDim.x * blockDim.x) {
+        const u64 c = mm(I.Cp[k], I.hinv[k], I);
+        I.Ur[P.N - 1 - k] = mm(c, I.w[k], I);
+    }
+}
+
+// R_m = Y_{N-1-m} / w_m (plain)
+__global__ void k_res_interp3(const __grid_constant__ ResPack P)
+{
+    const ResInst &I = P.in[blockIdx.y];
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < P.N; m += gridDim.x * blockDim.x)
+        I.R[m] = mm(mm(I.Y[P.N - 1 - m], I.winv[m], I), mpw(I.cim, (u64)m, I), I);   // undo x -> c x
+}
+
+// ------------------------------------------------------------------ host driver
+static uint64_t mont_pn(uint64_t p)
+{
+    uint64_t inv = 1;
+    for (int i = 0; i < 7; i++) inv *= 2 - p * inv;
+    return (uint64_t)0 - inv;
+}
+
+static int res_batch(pm_ctx *ctx, int cnt, const uint64_t *primes, const uint64_t *alphas, const uint64_t *scales,
+                     int dxf, int dyf,
+                     const u64 *f, int dxg, int dyg, const u64 *g, u64 *R, int *h_flag)
+{
+    const int64_t D = (int64_t)dxf * dyg + (int64_t)dxg * dyf;
+    const int N = (int)(D + 1), E = (dxf > dxg ? dxf : dxg) + 1, J = dyf + dyg + 2, NE = N + E - 1;
+    const size_t nf = (size_t)(dyf + 1) * (dxf + 1), ng = (size_t)(dyg + 1) * (dxg + 1);
+    ResPack pk;
+    memset(&pk, 0, sizeof(pk));
+    pk.count = cnt; pk.dxf = dxf; pk.dyf = dyf; pk.dxg = dxg; pk.dyg = dyg;
+    pk.E = E; pk.J = J; pk.N = N; pk.NE = NE;
+    const size_t per = (size_t)NE * 8 * 4 + (size_t)J * E * 8 + (size_t)J * N * 8 * 2 + (size_t)N * 8 * 8 + 16 * 256;
+    CKI(arena_reserve(ctx, per * cnt + 256));
+    pk.flag = (int *)arena_alloc(ctx, 256);
+    for (int i = 0; i < cnt; i++) {
+        ResInst &I = pk.in[i];
+        const uint64_t p = primes[i];
+        I.p = p;
+        I.pn = mont_pn(p);
+        I.one = (uint64_t)(((unsigned __int128)1 << 64) % p);
+        I.r2 = (uint64_t)((unsigned __int128)I.one * I.one % p);
+        I.qm = (uint64_t)((unsigned __int128)(alphas[i] % p) * I.one % p);
+        I.qim = (uint64_t)((unsigned __int128)host_powmod(alphas[i] % p, p - 2, p) * I.one % p);
+        I.cm = (uint64_t)((unsigned __int128)(scales[i] % p) * I.one % p);
+        I.cim = (uint64_t)((unsigned __int128)host_powmod(scales[i] % p, p - 2, p) * I.one % p);
+        I.f = f + i * nf;
+        I.g = g + i * ng;
+        I.R = R + (size_t)i * N;
+        auto A = [&](size_t n) { return (u64 *)arena_alloc(ctx, n * 8); };
+        I.qp = A(NE); I.h = A(NE); I.hinv = A(NE); I.Hb = A(NE);
+        I.Ua = A((size_t)J * E); I.S = A((size_t)J * N); I.Vt = A((size_t)J * N);
+        I.v = A(N); I.w = A(N); I.winv = A(N); I.Va = A(N); I.Eb = A(N); I.Cp = A(N); I.Ur = A(N); I.Y = A(N);
+        if (!I.Y) return pm_fail(ctx, PM_ENOMEM, "resultant arena exhausted");
+    }
+    CKI(pm_cuda(ctx, cudaMemsetAsync(pk.flag, 0, sizeof(int), ctx->stream), "flag"));
+    const dim3 grid((NE + 255) / 256 < 1024 ? (NE + 255) / 256 : 1024, cnt);
+    int tok = stage_begin(ctx, PM_STAGE_OTHER);
+    k_res_powers<<<grid, 256, 0, ctx->stream>>>(pk);
+    k_res_prep_eval<<<dim3((J * E + 255) / 256, cnt), 256, 0, ctx->stream>>>(pk);
+    ctx->launches += 2;
+    CKI(pm_cuda(ctx, cudaGetLastError(), "resultant prep"));
+    stage_end(ctx, tok);
+    // 1. evaluation: one middle product per instance (J x 1 times 1 x 1)
+    {
+        std::vector<ProdReq> rq(cnt);
+        for (int i = 0; i < cnt; i++) {
+            ProdReq &q = rq[i];
+            q.p = primes[i]; q.w = 8; q.m = J; q.n = 1; q.k = 1;
+            q.A = pk.in[i].Ua; q.dA = E; q.sA = E;
+            q.B = pk.in[i].Hb; q.dB = NE; q.sB = NE;
+            q.off = E - 1; q.len = N; q.C = pk.in[i].S; q.sC = N;
+            q.lg = ceil_log2((int64_t)E - 1 + N);
+            if (q.lg < 4) q.lg = 4;
+        }
+        CKI(prod_batch(ctx, rq.data(), cnt));
+    }
+    tok = stage_begin(ctx, PM_STAGE_OTHER);
+    k_res_eval_finish<<<dim3(1024, cnt), 256, 0, ctx->stream>>>(pk);
+    ctx->launches++;
+    CKI(pm_cuda(ctx, cudaGetLastError(), "resultant eval"));
+    // the flag decides whether this q is usable
+    CKI(pm_cuda(ctx, cudaMemcpyAsync(h_flag, pk.flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "flag"));
+    CKI(pm_cuda(ctx, cudaStreamSynchronize(ctx->stream), "flag sync"));
+    stage_end(ctx, tok);
+    if (*h_flag) return PM_OK;
+    // 2. univariate resultants, one warp per point
+    tok = stage_begin(ctx, PM_STAGE_OTHER);
+    {
+        const int dmax = dyf > dyg ? dyf : dyg;
+        const size_t sm = (size_t)8 * 2 * (dmax + 1) * 8;
+        if (sm > 48 * 1024) cudaFuncSetAttribute(k_res_euclid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_res_euclid<<<dim3((N + 7) / 8, cnt), 256, sm, ctx->stream>>>(pk, dmax);
+        k_res_wscan<<<cnt, 1024, 0, ctx->stream>>>(pk);
+        k_res_interp1<<<dim3((N + 255) / 256, cnt), 256, 0, ctx->stream>>>(pk);
+        ctx->launches += 3;
+        CKI(pm_cuda(ctx, cudaGetLastError(), "resultant euclid"));
+    }
+    stage_end(ctx, tok);
+    // 3. interpolation: two truncated products of length N
+    std::vector<ProdReq> rq(cnt);
+    auto trunc_req = [&](int i, const u64 *Aop, const u64 *Bop, u64 *Cout) {
+        ProdReq &q = rq[i];
+        q.p = primes[i]; q.w = 8; q.m = 1; q.n = 1; q.k = 1;
+        q.A = Aop; q.dA = N; q.sA = N; q.B = Bop; q.dB = N; q.sB = N;
+        q.off = 0; q.len = N; q.C = Cout; q.sC = N;
+        q.lg = ceil_log2(2 * (int64_t)N - 1);
+        if (q.lg < 4) q.lg = 4;
+    };
+    for (int i = 0; i < cnt; i++) trunc_req(i, pk.in[i].Va, pk.in[i].Eb, pk.in[i].Cp);
+    CKI(prod_batch(ctx, rq.data(), cnt));
+    tok = stage_begin(ctx, PM_STAGE_OTHER);
+    k_res_interp2<<<dim3((N + 255) / 256, cnt), 256, 0, ctx->stream>>>(pk);
+    ctx->launches++;
+    CKI(pm_cuda(ctx, cudaGetLastError(), "resultant interp"));
+    stage_end(ctx, tok);
+    for (int i = 0; i < cnt; i++) trunc_req(i, pk.in[i].Ur, pk.in[i].Eb, pk.in[i].Y);
+    CKI(prod_batch(ctx, rq.data(), cnt));
+    tok = stage_begin(ctx, PM_STAGE_OTHER);
+    k_res_interp3<<<dim3((N + 255) / 256, cnt), 256, 0, ctx->stream>>>(pk);
+    ctx->launches++;
+    CKI(pm_cuda(ctx, cudaGetLastError(), "resultant interp"));
+    stage_end(ctx, tok);
+    return PM_OK;
+}
+
+extern "C" int bivariate_resultant(pm_ctx *ctx, int nprimes, const uint64_t *primes, int dxf, int dyf, const void *f,
+                                   int dxg, int dyg, const void *g, void *R)
+{
+    if (!ctx) return PM_EINVAL;
+    if (nprimes < 1 || !primes || !f || !g || !R) return pm_fail(ctx, PM_EINVAL, "bad arguments");
+    if (dxf < 0 || dyf < 0 || dxg < 0 || dyg < 0) return pm_fail(ctx, PM_EINVAL, "negative degree");
+    if (dyf > 2047 || dyg > 2047) return pm_fail(ctx, PM_EUNSUPPORTED, "y-degree above 2047");
+    const int64_t D = (int64_t)dxf * dyg + (int64_t)dxg * dyf;
+    const int E = (dxf > dxg ? dxf : dxg) + 1;
+    if (2 * (D + 1) - 1 > (1 << PM_MAX_LOG2L) || D + E > (1 << PM_MAX_LOG2L))
+        return pm_fail(ctx, PM_EINVAL, "resultant degree too large for the transforms");
+    for (int i = 0; i < nprimes; i++)
+        if (!(primes[i] & 1) || primes[i] < 3 || primes[i] >= (1ull << 62) || primes[i] <= (uint64_t)(2 * (D + 1)))
+            return pm_fail(ctx, PM_EINVAL, "each prime must be odd, below 2^62 and above 2(D+1)");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return pm_fail(ctx, PM_ECUDA, "cudaSetDevice failed");
+    const size_t nf = (size_t)(dyf + 1) * (dxf + 1), ng = (size_t)(dyg + 1) * (dxg + 1);
+    const size_t N = (size_t)D + 1;
+    for (int i0 = 0; i0 < nprimes; i0 += RES_MAXI) {
+        const int cnt = nprimes - i0 < RES_MAXI ? nprimes - i0 : RES_MAXI;
+        std::vector<uint64_t> alpha(cnt, 3), scale(cnt, 1);
+        // candidates (c, q) = (1, 3), (2, 5), (3, 7), ...: a batch is retried with the
+        // next candidate of each failing instance (the flag is per batch)
+        for (int attempt = 0;; attempt++) {
+            if (attempt >= 64) return pm_fail(ctx, PM_EUNSUPPORTED, "no usable geometric progression found");
+            int flag = 0;
+            CKI(res_batch(ctx, cnt, primes + i0, alpha.data(), scale.data(), dxf, dyf, (const u64 *)f + i0 * nf, dxg, dyg,
+                          (const u64 *)g + i0 * ng, (u64 *)R + i0 * N, &flag));
+            if (!flag) break;
+            if (cnt > 1) {   // find which instances fail by running them alone
+                bool any = false;
+                for (int i = 0; i < cnt; i++) {
+                    int fl = 0;
+                    CKI(res_batch(ctx, 1, primes + i0 + i, &alpha[i], &scale[i], dxf, dyf, (const u64 *)f + (i0 + i) * nf, dxg,
+                                  dyg, (const u64 *)g + (i0 + i) * ng, (u64 *)R + (i0 + i) * N, &fl));
+                    if (fl) { alpha[i] += 2; scale[i] += 1; any = true; }
+                }
+                if (!any) break;
+            } else {
+                alpha[0] += 2;
+                scale[0] += 1;
+            }
+        }
+    }
+    return PM_OK;
+}
