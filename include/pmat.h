@@ -63,7 +63,9 @@ enum {
     PM_OPT_THRESHOLD = 2,   /* PM-Basis threshold T (>= 1): M-Basis when order <= T;
                                default 32 (Sec. 3, "Interpolant bases") */
     PM_OPT_DEBUG_CHECKS = 3, /* 1 = check inputs are in [0, p) (PM_EDOMAIN) */
-    PM_OPT_STAGE_TIMING = 4  /* 1 = record CUDA events around every stage (see pm_stage_times) */
+    PM_OPT_STAGE_TIMING = 4, /* 1 = record CUDA events around every stage (see pm_stage_times) */
+    PM_OPT_LEAF_CLUSTER = 5  /* PM-Basis leaves: 1 = a cluster of 8 CTAs with the basis in shared
+                                memory (default), 0 = one CTA with the basis in global memory */
 };
 
 /* Stages reported by pm_stage_times. */

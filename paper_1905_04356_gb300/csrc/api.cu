@@ -635,6 +635,9 @@ int pm_set_option(pm_ctx *ctx, int key, int64_t value)
     case PM_OPT_STAGE_TIMING:
         ctx->opt_timing = value ? 1 : 0;
         return PM_OK;
+    case PM_OPT_LEAF_CLUSTER:
+        ctx->opt_leaf_cluster = value ? 1 : 0;
+        return PM_OK;
     default:
         return pm_fail(ctx, PM_EINVAL, "unknown option key");
     }

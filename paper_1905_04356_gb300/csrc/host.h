@@ -36,6 +36,7 @@ struct pm_ctx {
     int *d_status = nullptr;          // deferred device status (0 = OK)
     Arena arena;                      // driver buffers (PM-Basis, resultant)
     int opt_timing = 0;
+    int opt_leaf_cluster = 1;         // PM-Basis leaves on a CTA cluster (0 = one CTA)
     struct Mark { int stage; cudaEvent_t a, b; long long launches; };
     std::vector<Mark> marks;          // recorded stage intervals
     std::vector<cudaEvent_t> spare;   // reusable events

@@ -331,12 +331,19 @@ cudaError_t launch_ntt_inv_block(const JobPack<InvJob> &pk, int lg, cudaStream_t
 }
 
 // ------------------------------------------------------------------ column passes
-// Transform length L = 2^lg > 2^13: R1 = L / 2^13 rows per column, columns in
-// tiles of 32 consecutive c.  Block b of a job covers entry b / 256, tile b % 256.
-#define COLS_TILE 32
-#define COLS_PER_ENTRY ((1 << PM_LB_LOG2) / COLS_TILE)
+// Transform length L = 2^lg > 2^13: R1 = L / 2^13 rows per column.  A block takes
+// a tile of TC = 4096 / R1 consecutive columns (at least 32) and all R1 rows, so
+// every tile holds 4096 points; rows of a tile are contiguous runs of TC words.
+#define COLS_POINTS 4096
 
-int blocks_per_entry_cols(int lg) { (void)lg; return COLS_PER_ENTRY; }
+__host__ __device__ __forceinline__ int cols_tile(int lg)
+{
+    const int r1 = 1 << (lg - PM_LB_LOG2);
+    const int tc = COLS_POINTS / r1;
+    return tc < 32 ? 32 : tc;
+}
+
+int blocks_per_entry_cols(int lg) { return (1 << PM_LB_LOG2) / cols_tile(lg); }
 
 __global__ void __launch_bounds__(256) k_ntt_fwd_cols(const __grid_constant__ JobPack<ColJob> pk, int lg)
 {
@@ -344,33 +351,34 @@ __global__ void __launch_bounds__(256) k_ntt_fwd_cols(const __grid_constant__ Jo
     const int b = blockIdx.x;
     const int jb = find_job(pk.blk_start, b);
     const ColJob &J = pk.jobs[jb];
+    const int TC = cols_tile(lg), tiles = (1 << PM_LB_LOG2) / TC;
     const int rel = b - pk.blk_start[jb];
-    const i64 e = rel / COLS_PER_ENTRY;
-    const int c0 = (rel % COLS_PER_ENTRY) * COLS_TILE;
+    const i64 e = rel / tiles;
+    const int c0 = (rel % tiles) * TC;
     const int R1 = 1 << (lg - PM_LB_LOG2), LB = 1 << PM_LB_LOG2;
     const u32 q = J.P.q, q2 = J.P.q2;
     const char *src = (const char *)J.src;
     const i64 sb = e * J.src_stride;
 
-    for (int idx = threadIdx.x; idx < R1 * COLS_TILE; idx += blockDim.x) {
-        const int row = idx / COLS_TILE, cc = idx % COLS_TILE;
+    for (int idx = threadIdx.x; idx < R1 * TC; idx += blockDim.x) {
+        const int row = idx / TC, cc = idx % TC;
         const int x = c0 + cc + row * LB;
         sm[idx] = x < J.src_len ? load_coeff(src, J.mode, sb + x, J.P) : 0u;
     }
     __syncthreads();
     for (int hr = R1 >> 1; hr >= 1; hr >>= 1) {
         const int h = hr * LB;
-        for (int bi = threadIdx.x; bi < (R1 >> 1) * COLS_TILE; bi += blockDim.x) {
-            const int cc = bi % COLS_TILE, pj = bi / COLS_TILE;
+        for (int bi = threadIdx.x; bi < (R1 >> 1) * TC; bi += blockDim.x) {
+            const int cc = bi % TC, pj = bi / TC;
             const int jj = pj & (hr - 1), j0 = ((pj / hr) * 2 * hr) + jj;
             const uint2 w = __ldg(J.P.twf + h + c0 + cc + jj * LB);
-            bfly_dif(sm[j0 * COLS_TILE + cc], sm[(j0 + hr) * COLS_TILE + cc], w, q, q2);
+            bfly_dif(sm[j0 * TC + cc], sm[(j0 + hr) * TC + cc], w, q, q2);
         }
         __syncthreads();
     }
     u32 *d = (u32 *)J.dst + e * J.dst_stride;
-    for (int idx = threadIdx.x; idx < R1 * COLS_TILE; idx += blockDim.x) {
-        const int row = idx / COLS_TILE, cc = idx % COLS_TILE;
+    for (int idx = threadIdx.x; idx < R1 * TC; idx += blockDim.x) {
+        const int row = idx / TC, cc = idx % TC;
         d[c0 + cc + row * LB] = sm[idx];
     }
 }
@@ -381,30 +389,31 @@ __global__ void __launch_bounds__(256) k_ntt_inv_cols(const __grid_constant__ Jo
     const int b = blockIdx.x;
     const int jb = find_job(pk.blk_start, b);
     const ColJob &J = pk.jobs[jb];
+    const int TC = cols_tile(lg), tiles = (1 << PM_LB_LOG2) / TC;
     const int rel = b - pk.blk_start[jb];
-    const i64 e = rel / COLS_PER_ENTRY;
-    const int c0 = (rel % COLS_PER_ENTRY) * COLS_TILE;
+    const i64 e = rel / tiles;
+    const int c0 = (rel % tiles) * TC;
     const int R1 = 1 << (lg - PM_LB_LOG2), LB = 1 << PM_LB_LOG2;
     const u32 q = J.P.q, q2 = J.P.q2;
     const u32 *s = (const u32 *)J.src + e * J.src_stride;
 
-    for (int idx = threadIdx.x; idx < R1 * COLS_TILE; idx += blockDim.x) {
-        const int row = idx / COLS_TILE, cc = idx % COLS_TILE;
+    for (int idx = threadIdx.x; idx < R1 * TC; idx += blockDim.x) {
+        const int row = idx / TC, cc = idx % TC;
         sm[idx] = s[c0 + cc + row * LB];
     }
     __syncthreads();
     for (int hr = 1; hr < R1; hr <<= 1) {
         const int h = hr * LB;
-        for (int bi = threadIdx.x; bi < (R1 >> 1) * COLS_TILE; bi += blockDim.x) {
-            const int cc = bi % COLS_TILE, pj = bi / COLS_TILE;
+        for (int bi = threadIdx.x; bi < (R1 >> 1) * TC; bi += blockDim.x) {
+            const int cc = bi % TC, pj = bi / TC;
             const int jj = pj & (hr - 1), j0 = ((pj / hr) * 2 * hr) + jj;
             const uint2 w = __ldg(J.P.twi + h + c0 + cc + jj * LB);
-            bfly_dit(sm[j0 * COLS_TILE + cc], sm[(j0 + hr) * COLS_TILE + cc], w, q, q2);
+            bfly_dit(sm[j0 * TC + cc], sm[(j0 + hr) * TC + cc], w, q, q2);
         }
         __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < R1 * COLS_TILE; idx += blockDim.x) {
-        const int row = idx / COLS_TILE, cc = idx % COLS_TILE;
+    for (int idx = threadIdx.x; idx < R1 * TC; idx += blockDim.x) {
+        const int row = idx / TC, cc = idx % TC;
         const int x = c0 + cc + row * LB;
         const int t = x - J.out_off;
         if (t < 0 || t >= J.out_len) continue;
@@ -416,7 +425,7 @@ __global__ void __launch_bounds__(256) k_ntt_inv_cols(const __grid_constant__ Jo
 
 cudaError_t launch_ntt_fwd_cols(const JobPack<ColJob> &pk, int lg, cudaStream_t st, long long *launches)
 {
-    const int sm = (1 << (lg - PM_LB_LOG2)) * COLS_TILE * (int)sizeof(u32);
+    const int sm = (1 << (lg - PM_LB_LOG2)) * cols_tile(lg) * (int)sizeof(u32);
     k_ntt_fwd_cols<<<pack_blocks(pk), 256, sm, st>>>(pk, lg);
     ++*launches;
     return cudaGetLastError();
@@ -424,7 +433,7 @@ cudaError_t launch_ntt_fwd_cols(const JobPack<ColJob> &pk, int lg, cudaStream_t 
 
 cudaError_t launch_ntt_inv_cols(const JobPack<ColJob> &pk, int lg, cudaStream_t st, long long *launches)
 {
-    const int sm = (1 << (lg - PM_LB_LOG2)) * COLS_TILE * (int)sizeof(u32);
+    const int sm = (1 << (lg - PM_LB_LOG2)) * cols_tile(lg) * (int)sizeof(u32);
     k_ntt_inv_cols<<<pack_blocks(pk), 256, sm, st>>>(pk, lg);
     ++*launches;
     return cudaGetLastError();

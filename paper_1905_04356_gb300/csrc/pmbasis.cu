@@ -20,6 +20,7 @@
 // case (the first n rows in that order are independent) is solved by
 // fraction-free Gauss-Jordan, any other case by a fraction-free elimination in
 // row order; rows are normalised once when the leaf ends.
+#include <cooperative_groups.h>
 #include <cstring>
 #include <vector>
 
@@ -70,31 +71,337 @@ __device__ u64 mpow(u64 a, u64 e, const LeafArgs &A)
     return r;
 }
 
-// ------------------------------------------------------------------ leaf kernel
-// Shared memory (dynamic): t[m] i64, lam[m], kap[m], W[m][m], R[m][n], M[n][m],
-// piv[n], ord[m], ind[m], misc.
+// ------------------------------------------------------------------ Algorithm 1 with scaled rows
+// Shared-memory scratch of the elimination (all pointers into shared memory).
+struct ElimSm {
+    u64 *kap, *W, *M, *fac, *dpr, *bas, *tb, *vv, *tv;
+    int *ord, *ind, *pcs, *misc, *perm;
+    u64 *Wc;     // compact relation: Wc[j * n + b] = W[j][ilist[b]], b < nind
+    int *ilist;  // independent rows, misc[4] = their count
+};
+
+__device__ __forceinline__ size_t elim_words(int m, int n)
+{
+    const int mx = m > n ? m : n;
+    return (size_t)m + (size_t)m * m + (size_t)n * m + mx + (n + 1) + (size_t)n * n + (size_t)n * m + n + m +
+           (size_t)m * (mx);
+}
+
+__device__ ElimSm elim_carve(u64 *w, int *ip, int m, int n)
+{
+    ElimSm E;
+    const int mx = m > n ? m : n;
+    E.kap = w; w += m;
+    E.W = w; w += (size_t)m * m;
+    E.M = w; w += (size_t)n * m;
+    E.fac = w; w += mx;
+    E.dpr = w; w += n + 1;
+    E.bas = w; w += (size_t)n * n;
+    E.tb = w; w += (size_t)n * m;
+    E.vv = w; w += n;
+    E.tv = w; w += m;
+    E.Wc = w;
+    E.ord = ip; ip += m;
+    E.ind = ip; ip += m;
+    E.pcs = ip; ip += n;
+    E.perm = ip; ip += n;
+    E.misc = ip; ip += 8;
+    E.ilist = ip;
+    return E;
+}
+
+// Fraction-free Gauss-Jordan of the n x m matrix E.M (n <= 64, m <= 128) by the
+// first GJ_WARPS warps of the block: lanes own columns, warps own rows (row c in
+// warp c % GJ_WARPS), values stay in registers; per pivot step only the pivot
+// candidates and the pivot row go through shared memory, between two named
+// barriers of the group.  Pivot of column s: the lowest row not yet used with a
+// nonzero entry.  Returns true (uniformly) when every column had a pivot; E.M then
+// holds the result and E.perm[s] the pivot row of column s.
+#define GJ_WARPS 8
+
+template <int GJ_RPW, int GJ_CPL>
+__device__ bool gj_regs(const LeafArgs &A, ElimSm &E, int *cand, u64 *prow, int *failp)
+{
+    int &fail = *failp;
+    const int m = A.m, n = A.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const u64 p = A.p, pn = A.pn;
+    const bool grp = warp < GJ_WARPS;
+    u64 v[GJ_RPW][GJ_CPL];
+    if (tid == 0) fail = 0;
+    if (grp) {
+#pragma unroll
+        for (int i = 0; i < GJ_RPW; i++)
+#pragma unroll
+            for (int t = 0; t < GJ_CPL; t++) {
+                const int c = warp + GJ_WARPS * i, col = lane + 32 * t;
+                v[i][t] = (c < n && col < m) ? E.M[c * m + col] : 0;
+            }
+        asm volatile("bar.sync 1, %0;" ::"r"(GJ_WARPS * 32));
+        unsigned long long used = 0;
+        for (int s = 0; s < n; s++) {
+            const int ls = s & 31, ts = s >> 5;
+            // this warp's candidate: lowest unused own row with a nonzero entry in column s
+            int mine = 0x7fffffff;
+#pragma unroll
+            for (int i = GJ_RPW - 1; i >= 0; i--) {
+                const int c = warp + GJ_WARPS * i;
+                u64 x = 0;
+#pragma unroll
+                for (int t = 0; t < GJ_CPL; t++) x = (t == ts) ? v[i][t] : x;
+                if (c < n && !((used >> c) & 1ull) && x) mine = c;
+            }
+            mine = __shfl_sync(0xffffffffu, mine, ls);
+            if (lane == 0) cand[warp] = mine;
+            asm volatile("bar.sync 1, %0;" ::"r"(GJ_WARPS * 32));
+            int r = 0x7fffffff;
+#pragma unroll
+            for (int w = 0; w < GJ_WARPS; w++) r = min(r, cand[w]);
+            if (r == 0x7fffffff) break;                 // uniform over the group
+            used |= 1ull << r;
+            if (warp == r % GJ_WARPS) {
+                const int slot = r / GJ_WARPS;
+#pragma unroll
+                for (int t = 0; t < GJ_CPL; t++) {
+                    u64 x = 0;
+#pragma unroll
+                    for (int i = 0; i < GJ_RPW; i++) x = (i == slot) ? v[i][t] : x;
+                    prow[lane + 32 * t] = x;
+                }
+            }
+            if (tid == 0) E.perm[s] = r;
+            asm volatile("bar.sync 1, %0;" ::"r"(GJ_WARPS * 32));
+            const u64 pv = prow[s];
+#pragma unroll
+            for (int i = 0; i < GJ_RPW; i++) {
+                const int c = warp + GJ_WARPS * i;
+                if (c >= n || c == r) continue;         // uniform within the warp
+                u64 x = 0;
+#pragma unroll
+                for (int t = 0; t < GJ_CPL; t++) x = (t == ts) ? v[i][t] : x;
+                const u64 f = __shfl_sync(0xffffffffu, x, ls);
+#pragma unroll
+                for (int t = 0; t < GJ_CPL; t++)
+                    v[i][t] = sub64(mont_mul(pv, v[i][t], p, pn), mont_mul(f, prow[lane + 32 * t], p, pn), p);
+            }
+            if (s == n - 1) break;
+        }
+        if (tid == 0 && __popcll(used) != n) fail = 1;
+#pragma unroll
+        for (int i = 0; i < GJ_RPW; i++)
+#pragma unroll
+            for (int t = 0; t < GJ_CPL; t++) {
+                const int c = warp + GJ_WARPS * i, col = lane + 32 * t;
+                if (c < n && col < m) E.M[c * m + col] = v[i][t];
+            }
+    }
+    __syncthreads();
+    return fail == 0;
+}
+
+// Register tile: GJ_RPW rows per warp (n <= 8 GJ_RPW), GJ_CPL columns per lane (m <= 32 GJ_CPL).
+__device__ bool gj_dispatch(const LeafArgs &A, ElimSm &E)
+{
+    __shared__ int cand[GJ_WARPS];
+    __shared__ u64 prow[32 * 4];
+    __shared__ int fail;
+    const int rpw = (A.n + GJ_WARPS - 1) / GJ_WARPS, cpl = (A.m + 31) / 32;
+    if (cpl == 1) {
+        if (rpw <= 1) return gj_regs<1, 1>(A, E, cand, prow, &fail);
+        if (rpw <= 2) return gj_regs<2, 1>(A, E, cand, prow, &fail);
+        if (rpw <= 4) return gj_regs<4, 1>(A, E, cand, prow, &fail);
+    } else if (cpl == 2) {
+        if (rpw <= 2) return gj_regs<2, 2>(A, E, cand, prow, &fail);
+        if (rpw <= 4) return gj_regs<4, 2>(A, E, cand, prow, &fail);
+        if (rpw <= 8) return gj_regs<8, 2>(A, E, cand, prow, &fail);
+    } else if (cpl <= 4) {
+        if (rpw <= 4) return gj_regs<4, 4>(A, E, cand, prow, &fail);
+        if (rpw <= 8) return gj_regs<8, 4>(A, E, cand, prow, &fail);
+    }
+    return false;   // shapes beyond the register tile take the row-order elimination
+}
+
+// Algorithm 1 on the residual R (m x n, Montgomery) with shift t: rows visited in
+// increasing (t_i, i) order.  Output: ind[i] = 1 for rows that become x e_i; for the
+// other rows j, the scaled relation kap_j R_j = -sum_i W[j][i] R_i (W stored
+// negated), i.e. the row of Q is kap_j e_j + sum_i W[j][i] e_i.  All threads of the
+// block call it; it ends with a barrier.
+__device__ void mbasis1_scaled(const LeafArgs &A, const u64 *R, const i64 *t, ElimSm &E)
+{
+    const int m = A.m, n = A.n, tid = threadIdx.x, nth = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
+    const u64 p = A.p;
+    for (int i = tid; i < m; i += nth) {
+        int r = 0;
+        const i64 ti = t[i];
+        for (int j = 0; j < m; j++) r += (t[j] < ti) || (t[j] == ti && j < i);
+        E.ord[r] = i;
+        E.ind[i] = 0;
+        E.kap[i] = A.one;
+    }
+    for (int x = tid; x < m * m; x += nth) E.W[x] = 0;
+    __syncthreads();
+    bool ok = false;
+    if (m > n) {
+        // fast path: Gauss-Jordan on [R_I^T | R_D^T] (n x m), I = the first n rows in order
+        for (int x = tid; x < n * m; x += nth) {
+            const int c = x / m, pos = x % m;
+            E.M[x] = R[E.ord[pos] * n + c];
+        }
+        __syncthreads();
+        ok = gj_dispatch(A, E);
+        if (ok) {
+            // pivots d_s = M[perm[s]][s]: fac[s] = prod_{s' != s} d_s', dpr[n] = prod d
+            if (n <= 32) {
+                if (warp == 0) {
+                    const u64 d = lane < n ? E.M[E.perm[lane] * m + lane] : A.one;
+                    u64 pre = d, suf = d;                       // inclusive scans, both directions
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const u64 a1 = __shfl_up_sync(0xffffffffu, pre, o);
+                        const u64 b1 = __shfl_down_sync(0xffffffffu, suf, o);
+                        if (lane >= o) pre = mont_mul(pre, a1, p, A.pn);
+                        if (lane + o < 32) suf = mont_mul(suf, b1, p, A.pn);
+                    }
+                    u64 pex = __shfl_up_sync(0xffffffffu, pre, 1), sex = __shfl_down_sync(0xffffffffu, suf, 1);
+                    if (lane == 0) pex = A.one;
+                    if (lane == 31) sex = A.one;
+                    if (lane < n) E.fac[lane] = mont_mul(pex, sex, p, A.pn);
+                    const u64 tot = __shfl_sync(0xffffffffu, pre, 31);
+                    if (lane == 0) E.dpr[n] = tot;
+                }
+            } else if (tid == 0) {
+                u64 acc = A.one;
+                for (int s2 = 0; s2 < n; s2++) { E.dpr[s2] = acc; acc = mont_mul(acc, E.M[E.perm[s2] * m + s2], p, A.pn); }
+                E.dpr[n] = acc;
+                u64 suf = A.one;
+                for (int s2 = n - 1; s2 >= 0; s2--) {
+                    E.fac[s2] = mont_mul(E.dpr[s2], suf, p, A.pn);
+                    suf = mont_mul(suf, E.M[E.perm[s2] * m + s2], p, A.pn);
+                }
+            }
+            __syncthreads();
+            for (int x = tid; x < (m - n) * n; x += nth) {
+                const int jp = n + x / n, s2 = x % n;
+                const int j = E.ord[jp], i = E.ord[s2];
+                const u64 w = mont_mul(E.M[E.perm[s2] * m + jp], E.fac[s2], p, A.pn);
+                E.W[j * m + i] = w ? p - w : 0;
+            }
+            for (int pos = tid; pos < m; pos += nth) {
+                const int i = E.ord[pos];
+                if (pos < n) E.ind[i] = 1;
+                else E.kap[i] = E.dpr[n];
+            }
+        }
+        __syncthreads();
+    }
+    if (!ok) {
+        // general path: rows in order, fraction-free common-denominator elimination
+        for (int x = tid; x < m * m; x += nth) E.W[x] = 0;
+        if (tid == 0) { E.misc[2] = 0; E.dpr[0] = A.one; }
+        __syncthreads();
+        for (int pos = 0; pos < m; pos++) {
+            const int r = E.ord[pos];
+            const int rank = E.misc[2];
+            const u64 D = E.dpr[0];
+            for (int x = tid; x < n + m; x += nth) {
+                u64 acc;
+                if (x < n) {
+                    acc = mont_mul(D, R[r * n + x], p, A.pn);
+                    for (int b = 0; b < rank; b++)
+                        acc = sub64(acc, mont_mul(R[r * n + E.pcs[b]], E.bas[b * n + x], p, A.pn), p);
+                    E.vv[x] = acc;
+                } else {
+                    const int i = x - n;
+                    acc = (i == r) ? D : 0;
+                    for (int b = 0; b < rank; b++)
+                        acc = sub64(acc, mont_mul(R[r * n + E.pcs[b]], E.tb[b * m + i], p, A.pn), p);
+                    E.tv[i] = acc;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int pc = -1;
+                for (int c = 0; c < n; c++) if (E.vv[c]) { pc = c; break; }
+                E.misc[3] = pc;
+            }
+            __syncthreads();
+            const int pc = E.misc[3];
+            if (pc >= 0) {
+                const u64 pv = E.vv[pc];
+                for (int b = tid; b < rank; b += nth) E.fac[b] = E.bas[b * n + pc];
+                __syncthreads();
+                for (int x = tid; x < rank * (n + m); x += nth) {
+                    const int b = x / (n + m), c = x % (n + m);
+                    if (c < n) E.bas[b * n + c] = sub64(mont_mul(pv, E.bas[b * n + c], p, A.pn), mont_mul(E.fac[b], E.vv[c], p, A.pn), p);
+                    else E.tb[b * m + (c - n)] = sub64(mont_mul(pv, E.tb[b * m + (c - n)], p, A.pn),
+                                                      mont_mul(E.fac[b], E.tv[c - n], p, A.pn), p);
+                }
+                for (int c = tid; c < n + m; c += nth) {
+                    if (c < n) E.bas[rank * n + c] = mont_mul(D, E.vv[c], p, A.pn);
+                    else E.tb[rank * m + (c - n)] = mont_mul(D, E.tv[c - n], p, A.pn);
+                }
+                __syncthreads();
+                if (tid == 0) { E.pcs[rank] = pc; E.misc[2] = rank + 1; E.dpr[0] = mont_mul(pv, D, p, A.pn); E.ind[r] = 1; }
+            } else {
+                // dependent: the row of Q is tv (tv[r] = D): kap_r = D, W[r][i] = tv[i]
+                for (int i = tid; i < m; i += nth)
+                    if (i != r) E.W[r * m + i] = E.tv[i];
+                if (tid == 0) E.kap[r] = D;
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    // compact form of the relations: the independent rows in index order, and for
+    // every dependent row its coefficients on them
+    if (tid == 0) {
+        int c = 0;
+        for (int i = 0; i < m; i++) if (E.ind[i]) E.ilist[c++] = i;
+        E.misc[4] = c;
+    }
+    __syncthreads();
+    const int nind = E.misc[4];
+    for (int x = tid; x < m * nind; x += nth) {
+        const int j = x / nind, b = x % nind;
+        E.Wc[j * n + b] = E.W[j * m + E.ilist[b]];
+    }
+    __syncthreads();
+}
+
+// New value of one coefficient of a dependent row j: kap_j X[j] + sum_i W[j][i] X[i],
+// X[i] at stride `rs` between rows, lazy 128-bit sums reduced every `chunk` terms.
+__device__ __forceinline__ u64 dep_combine(const LeafArgs &A, const ElimSm &E, int j, const u64 *X, i64 rs)
+{
+    const int n = A.n, nind = E.misc[4];
+    const u64 *wc = E.Wc + (size_t)j * n;
+    u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0, accm = 0;   // two independent chains (even / odd terms)
+    int c0 = 1, c1 = 0;
+    mac128(h0, l0, E.kap[j], X[(i64)j * rs]);
+    int b = 0;
+    for (; b + 1 < nind; b += 2) {
+        mac128(h1, l1, wc[b], X[(i64)E.ilist[b] * rs]);
+        mac128(h0, l0, wc[b + 1], X[(i64)E.ilist[b + 1] * rs]);
+        if (++c1 == A.chunk) { accm = add64(accm, redc128(h1, l1, A.p, A.pn), A.p); h1 = l1 = 0; c1 = 0; }
+        if (++c0 == A.chunk) { accm = add64(accm, redc128(h0, l0, A.p, A.pn), A.p); h0 = l0 = 0; c0 = 0; }
+    }
+    if (b < nind) mac128(h1, l1, wc[b], X[(i64)E.ilist[b] * rs]);   // c1 < chunk here
+    accm = add64(accm, redc128(h0, l0, A.p, A.pn), A.p);
+    return add64(accm, redc128(h1, l1, A.p, A.pn), A.p);
+}
+
+// ------------------------------------------------------------------ leaf kernel, one CTA
+// G and P in global memory (double-buffered); for shapes whose slices do not fit
+// the cluster kernel's shared memory.
 __global__ void __launch_bounds__(512) k_mbasis_leaf(const LeafArgs A)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int m = A.m, n = A.n, T = A.T;
-    const u64 p = A.p;
     const int tid = threadIdx.x, nth = blockDim.x;
     i64 *t = (i64 *)smraw;
     u64 *lam = (u64 *)(t + m);
-    u64 *kap = lam + m;
-    u64 *W = kap + m;               // W[j*m + i]: -(coefficient of e_i) in the scaled row j of Q
-    u64 *R = W + m * m;             // R[i*n + c]
-    u64 *M = R + m * n;             // M[c*m + pos]  (Gauss-Jordan on [R_I^T | R_D^T])
-    u64 *fac = M + n * m;           // column snapshot, n
-    u64 *dpr = fac + (m > n ? m : n);   // pivots / prefix products, n + 1
-    u64 *bas = dpr + n + 1;         // general path: basis vectors [n][n]
-    u64 *tb = bas + n * n;          // general path: transformations [n][m]
-    u64 *vv = tb + n * m;           // general path: v[n], tv[m]
-    u64 *tv = vv + n;
-    int *ord = (int *)(tv + m);
-    int *ind = ord + m;             // 1 = independent at this step
-    int *pcs = ind + m;             // general path: pivot columns [n]
-    int *misc = pcs + n;            // misc[0] = fast path ok, misc[1] = pivot row, misc[2] = rank, misc[3] = pc
+    u64 *R = lam + m;
+    u64 *ew = R + (size_t)m * n;
+    int *ei = (int *)(ew + elim_words(m, n));
+    ElimSm E = elim_carve(ew, ei, m, n);
 
     u64 *G = A.G0, *Gn = A.G1, *P = A.P0, *Pn = A.P1;
     for (int i = tid; i < m; i += nth) { t[i] = A.s_in[i]; lam[i] = A.one; }
@@ -108,213 +415,146 @@ __global__ void __launch_bounds__(512) k_mbasis_leaf(const LeafArgs A)
         P[x] = (a == 0 && (e / m) == (e % m)) ? A.one : 0;
     }
     __syncthreads();
-
     for (int k = 0; k < T; k++) {
-        // ---- order rows by (t_i, i); gather the residual R = G[:, :, k]
-        for (int i = tid; i < m; i += nth) {
-            int r = 0;
-            const i64 ti = t[i];
-            for (int j = 0; j < m; j++) r += (t[j] < ti) || (t[j] == ti && j < i);
-            ord[r] = i;
-            ind[i] = 0;
-            kap[i] = A.one;
-        }
         for (int x = tid; x < m * n; x += nth) R[x] = G[(i64)x * T + k];
-        for (int x = tid; x < m * m; x += nth) W[x] = 0;
-        if (tid == 0) misc[0] = 0;
         __syncthreads();
-
-        // ---- fast path: the first n rows in order are independent (needs m > n)
-        if (m > n) {
-            for (int x = tid; x < n * m; x += nth) {
-                const int c = x / m, pos = x % m;
-                M[x] = R[ord[pos] * n + c];
-            }
-            if (tid == 0) misc[0] = 1;
-            __syncthreads();
-            for (int s = 0; s < n; s++) {
-                if (tid == 0) {
-                    int r = -1;
-                    for (int c = s; c < n; c++) if (M[c * m + s]) { r = c; break; }
-                    misc[1] = r;
-                    if (r < 0) misc[0] = 0;
-                }
-                __syncthreads();
-                const int r = misc[1];
-                if (r < 0) break;
-                if (r != s)
-                    for (int col = tid; col < m; col += nth) {
-                        u64 a = M[s * m + col];
-                        M[s * m + col] = M[r * m + col];
-                        M[r * m + col] = a;
-                    }
-                __syncthreads();
-                for (int c = tid; c < n; c += nth) fac[c] = M[c * m + s];
-                __syncthreads();
-                const u64 pv = M[s * m + s];
-                for (int x = tid; x < n * m; x += nth) {
-                    const int c = x / m, col = x % m;
-                    if (c == s) continue;
-                    const u64 f = fac[c];
-                    M[x] = sub64(mmul(pv, M[x], A), mmul(f, M[s * m + col], A), p);
-                }
-                __syncthreads();
-            }
-            if (misc[0]) {
-                // prefix / suffix products of the pivots d_r = M[r][r]:
-                // W[j][ord[r]] = -Y[r][j] prod_{r' != r} d_r', kap_j = prod d
-                if (tid == 0) {
-                    u64 acc = A.one;
-                    for (int r = 0; r < n; r++) { dpr[r] = acc; acc = mmul(acc, M[r * m + r], A); }
-                    dpr[n] = acc;   // product of all pivots
-                    u64 suf = A.one;
-                    for (int r = n - 1; r >= 0; r--) { fac[r] = mmul(dpr[r], suf, A); suf = mmul(suf, M[r * m + r], A); }
-                }
-                __syncthreads();
-                for (int x = tid; x < (m - n) * n; x += nth) {
-                    const int jp = n + x / n, r = x % n;
-                    const int j = ord[jp], i = ord[r];
-                    const u64 w = mmul(M[r * m + jp], fac[r], A);   // the relation's coefficient of R_i
-                    W[j * m + i] = w ? p - w : 0;                   // stored negated: Q'_j = kap_j e_j - w e_i
-                }
-                for (int pos = tid; pos < m; pos += nth) {
-                    const int i = ord[pos];
-                    if (pos < n) ind[i] = 1;
-                    else kap[i] = dpr[n];
-                }
-            }
-            __syncthreads();
-        }
-
-        // ---- general path: rows in order, fraction-free common-denominator elimination
-        if (!misc[0]) {
-            for (int x = tid; x < m * m; x += nth) W[x] = 0;
-            if (tid == 0) { misc[2] = 0; dpr[0] = A.one; }
-            __syncthreads();
-            for (int pos = 0; pos < m; pos++) {
-                const int r = ord[pos];
-                const int rank = misc[2];
-                const u64 D = dpr[0];
-                // v = D R_r - sum_b R_r[pc_b] bas_b ; tv = D e_r - sum_b R_r[pc_b] tb_b
-                for (int x = tid; x < n + m; x += nth) {
-                    u64 acc;
-                    if (x < n) {
-                        acc = mmul(D, R[r * n + x], A);
-                        for (int b = 0; b < rank; b++)
-                            acc = sub64(acc, mmul(R[r * n + pcs[b]], bas[b * n + x], A), p);
-                        vv[x] = acc;
-                    } else {
-                        const int i = x - n;
-                        acc = (i == r) ? D : 0;
-                        for (int b = 0; b < rank; b++)
-                            acc = sub64(acc, mmul(R[r * n + pcs[b]], tb[b * m + i], A), p);
-                        tv[i] = acc;
-                    }
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    int pc = -1;
-                    for (int c = 0; c < n; c++) if (vv[c]) { pc = c; break; }
-                    misc[3] = pc;
-                }
-                __syncthreads();
-                const int pc = misc[3];
-                if (pc >= 0) {
-                    const u64 pv = vv[pc];
-                    for (int b = tid; b < rank; b += nth) fac[b] = bas[b * n + pc];
-                    __syncthreads();
-                    for (int x = tid; x < rank * (n + m); x += nth) {
-                        const int b = x / (n + m), c = x % (n + m);
-                        if (c < n) bas[b * n + c] = sub64(mmul(pv, bas[b * n + c], A), mmul(fac[b], vv[c], A), p);
-                        else tb[b * m + (c - n)] = sub64(mmul(pv, tb[b * m + (c - n)], A), mmul(fac[b], tv[c - n], A), p);
-                    }
-                    for (int c = tid; c < n + m; c += nth) {
-                        if (c < n) bas[rank * n + c] = mmul(D, vv[c], A);
-                        else tb[rank * m + (c - n)] = mmul(D, tv[c - n], A);
-                    }
-                    __syncthreads();
-                    if (tid == 0) { pcs[rank] = pc; misc[2] = rank + 1; dpr[0] = mmul(pv, D, A); ind[r] = 1; }
-                } else {
-                    // dependent: Q'_r = tv (tv[r] = D), i.e. kap_r = D, W[r][i] = tv[i] for i != r
-                    for (int i = tid; i < m; i += nth)
-                        if (i != r) W[r * m + i] = tv[i];
-                    if (tid == 0) kap[r] = D;
-                }
-                __syncthreads();
-            }
-        }
-        __syncthreads();
-
-        // ---- updates: G <- Q' G (coefficients k+1 .. T-1), P <- Q' P, lam, t
-        // independent rows: x . row (shift by one coefficient); dependent j: kap_j row_j + sum_i W[j][i] row_i
-        const int chunk = A.chunk;
+        mbasis1_scaled(A, R, t, E);
         const int ngl = T - k - 1;
         for (int x = tid; x < m * n * ngl; x += nth) {
             const int a = k + 1 + x % ngl, e = x / ngl, j = e / n, c = e % n;
-            u64 val;
-            if (ind[j]) val = G[(i64)e * T + a - 1];
-            else {
-                u64 hi = 0, lo = 0, accm = 0;
-                int cnt = 1;
-                mac128(hi, lo, kap[j], G[(i64)e * T + a]);
-                for (int i = 0; i < m; i++) {
-                    const u64 w = W[j * m + i];
-                    if (!w) continue;
-                    mac128(hi, lo, w, G[((i64)i * n + c) * T + a]);
-                    if (++cnt == chunk) { accm = add64(accm, redc128(hi, lo, p, A.pn), p); hi = lo = 0; cnt = 0; }
-                }
-                val = add64(accm, redc128(hi, lo, p, A.pn), p);
-            }
-            Gn[(i64)e * T + a] = val;
+            Gn[(i64)e * T + a] = E.ind[j] ? G[(i64)e * T + a - 1] : dep_combine(A, E, j, G + (i64)c * T + a, (i64)n * T);
         }
-        const int np = k + 2;   // P has degree <= k before the step, <= k + 1 after
+        const int np = k + 2;
         for (int x = tid; x < m * m * np; x += nth) {
             const int a = x % np, e = x / np, j = e / m, c = e % m;
             u64 val;
-            if (ind[j]) val = a ? P[(i64)e * LP + a - 1] : 0;
+            if (E.ind[j]) val = a ? P[(i64)e * LP + a - 1] : 0;
             else if (a == k + 1) val = 0;
-            else {
-                u64 hi = 0, lo = 0, accm = 0;
-                int cnt = 1;
-                mac128(hi, lo, kap[j], P[(i64)e * LP + a]);
-                for (int i = 0; i < m; i++) {
-                    const u64 w = W[j * m + i];
-                    if (!w) continue;
-                    mac128(hi, lo, w, P[((i64)i * m + c) * LP + a]);
-                    if (++cnt == chunk) { accm = add64(accm, redc128(hi, lo, p, A.pn), p); hi = lo = 0; cnt = 0; }
-                }
-                val = add64(accm, redc128(hi, lo, p, A.pn), p);
-            }
+            else val = dep_combine(A, E, j, P + (i64)c * LP + a, (i64)m * LP);
             Pn[(i64)e * LP + a] = val;
         }
         __syncthreads();
         for (int i = tid; i < m; i += nth) {
-            if (ind[i]) t[i] += 1;
-            else lam[i] = mmul(kap[i], lam[i], A);
+            if (E.ind[i]) t[i] += 1;
+            else lam[i] = mmul(E.kap[i], lam[i], A);
         }
-        { u64 *s = G; G = Gn; Gn = s; s = P; P = Pn; Pn = s; }
+        { u64 *s2 = G; G = Gn; Gn = s2; s2 = P; P = Pn; Pn = s2; }
         __syncthreads();
     }
-
-    // ---- normalise rows (P_true = lam^-1 P) and leave Montgomery form
     for (int i = tid; i < m; i += nth) {
-        const u64 inv = mpow(lam[i], p - 2, A);     // Montgomery form of lam_i^-1
-        kap[i] = mmul(inv, 1, A);                   // plain lam_i^-1
+        E.kap[i] = mmul(mpow(lam[i], A.p - 2, A), 1, A);   // plain lam_i^-1
         A.s_out[i] = t[i];
     }
     __syncthreads();
     for (int x = tid; x < m * m * LP; x += nth) {
         const int a = x % LP, e = x / LP, i = e / m;
-        A.P[(i64)e * A.sP + a] = mmul(P[x], kap[i], A);
+        A.P[(i64)e * A.sP + a] = mmul(P[x], E.kap[i], A);
     }
+}
+
+// ------------------------------------------------------------------ leaf kernel, CTA cluster
+// LEAF_CL CTAs; CTA r owns the G columns [r n / CL, (r+1) n / CL) and the P columns
+// [r m / CL, (r+1) m / CL), both in its shared memory (double-buffered).  Each step,
+// every CTA writes its part of the residual into every CTA's residual buffer
+// (distributed shared memory, double-buffered by step parity), one cluster barrier,
+// then every CTA runs the same elimination and updates its own slices.
+#define LEAF_CL_MAX 16
+
+__global__ void __launch_bounds__(512) k_mbasis_leaf_cl(const LeafArgs A)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int LEAF_CL = (int)cl.num_blocks();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int m = A.m, n = A.n, T = A.T, LP = T + 1;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int rk = (int)cl.block_rank();
+    const int g0 = rk * n / LEAF_CL, g1 = (rk + 1) * n / LEAF_CL, ng = g1 - g0;
+    const int p0 = rk * m / LEAF_CL, p1 = (rk + 1) * m / LEAF_CL, np_ = p1 - p0;
+    const int ngm = (n + LEAF_CL - 1) / LEAF_CL, npm = (m + LEAF_CL - 1) / LEAF_CL;
+    i64 *t = (i64 *)smraw;
+    u64 *lam = (u64 *)(t + m);
+    u64 *Rb = lam + m;                                  // 2 x m x n
+    u64 *G = Rb + 2 * (size_t)m * n, *Gn = G + (size_t)m * ngm * T;
+    u64 *P = Gn + (size_t)m * ngm * T, *Pn = P + (size_t)m * npm * LP;
+    u64 *ew = Pn + (size_t)m * npm * LP;
+    int *ei = (int *)(ew + elim_words(m, n));
+    ElimSm E = elim_carve(ew, ei, m, n);
+
+    // G slice: G[(i*ngm + cl)*T + a] = F[i][g0 + cl][a]; P slice: identity columns
+    for (int i = tid; i < m; i += nth) { t[i] = A.s_in[i]; lam[i] = A.one; }
+    for (int x = tid; x < m * ng * T; x += nth) {
+        const int a = x % T, e = x / T, i = e / ng, c = e % ng;
+        G[((i64)i * ngm + c) * T + a] = mmul(A.F[((i64)i * n + g0 + c) * A.sF + a], A.r2, A);
+    }
+    for (int x = tid; x < m * np_ * LP; x += nth) {
+        const int a = x % LP, e = x / LP, i = e / np_, c = e % np_;
+        P[((i64)i * npm + c) * LP + a] = (a == 0 && i == p0 + c) ? A.one : 0;
+    }
+    __syncthreads();
+    for (int k = 0; k < T; k++) {
+        u64 *R = Rb + (size_t)(k & 1) * m * n;
+        // scatter this CTA's residual columns to every CTA of the cluster
+        for (int x = tid; x < LEAF_CL * m * ng; x += nth) {
+            const int dst = x / (m * ng), e = x % (m * ng), i = e / ng, c = e % ng;
+            u64 *rR = cl.map_shared_rank(R, dst);
+            rR[i * n + g0 + c] = G[((i64)i * ngm + c) * T + k];
+        }
+        cl.sync();
+        mbasis1_scaled(A, R, t, E);
+        const int ngl = T - k - 1;
+        for (int x = tid; x < m * ng * ngl; x += nth) {
+            const int a = k + 1 + x % ngl, e = x / ngl, j = e / ng, c = e % ng;
+            const i64 o = ((i64)j * ngm + c) * T + a;
+            Gn[o] = E.ind[j] ? G[o - 1] : dep_combine(A, E, j, G + (i64)c * T + a, (i64)ngm * T);
+        }
+        const int npc = k + 2;
+        for (int x = tid; x < m * np_ * npc; x += nth) {
+            const int a = x % npc, e = x / npc, j = e / np_, c = e % np_;
+            const i64 o = ((i64)j * npm + c) * LP + a;
+            u64 val;
+            if (E.ind[j]) val = a ? P[o - 1] : 0;
+            else if (a == k + 1) val = 0;
+            else val = dep_combine(A, E, j, P + (i64)c * LP + a, (i64)npm * LP);
+            Pn[o] = val;
+        }
+        __syncthreads();
+        for (int i = tid; i < m; i += nth) {
+            if (E.ind[i]) t[i] += 1;
+            else lam[i] = mmul(E.kap[i], lam[i], A);
+        }
+        { u64 *s2 = G; G = Gn; Gn = s2; s2 = P; P = Pn; Pn = s2; }
+        __syncthreads();
+    }
+    for (int i = tid; i < m; i += nth) E.kap[i] = mmul(mpow(lam[i], A.p - 2, A), 1, A);   // plain lam_i^-1
+    if (rk == 0)
+        for (int i = tid; i < m; i += nth) A.s_out[i] = t[i];
+    __syncthreads();
+    for (int x = tid; x < m * np_ * LP; x += nth) {
+        const int a = x % LP, e = x / LP, i = e / np_, c = e % np_;
+        A.P[((i64)i * m + p0 + c) * A.sP + a] = mmul(P[((i64)i * npm + c) * LP + a], E.kap[i], A);
+    }
+    cl.sync();   // no CTA leaves while others may still write into its residual buffers
+}
+
+static size_t elim_bytes(int m, int n)
+{
+    const int mx = m > n ? m : n;
+    const size_t words = (size_t)m + (size_t)m * m + (size_t)n * m + mx + (n + 1) + (size_t)n * n + (size_t)n * m + n + m +
+                         (size_t)m * mx;
+    return words * 8 + ((size_t)3 * m + 2 * n + 8) * 4;
 }
 
 static size_t leaf_smem(int m, int n)
 {
-    const int mx = m > n ? m : n;
-    size_t words = (size_t)m * 3 + (size_t)m * m + (size_t)m * n + (size_t)n * m + mx + (n + 1) + (size_t)n * n +
-                   (size_t)n * m + n + m;
-    return words * 8 + (size_t)(3 * m + n + 8) * 4 + 64;
+    return (size_t)2 * m * 8 + (size_t)m * n * 8 + elim_bytes(m, n) + 64;
+}
+
+static size_t leaf_cl_smem(int m, int n, int T, int LEAF_CL)
+{
+    const int ngm = (n + LEAF_CL - 1) / LEAF_CL, npm = (m + LEAF_CL - 1) / LEAF_CL;
+    return (size_t)2 * m * 8 + (size_t)2 * m * n * 8 + (size_t)2 * m * ngm * T * 8 + (size_t)2 * m * npm * (T + 1) * 8 +
+           elim_bytes(m, n) + 64;
 }
 
 // ------------------------------------------------------------------ host recursion
@@ -322,6 +562,7 @@ namespace {
 
 struct PmbCtx {
     pm_ctx *ctx;
+    bool use_cluster;
     LeafArgs base;     // p-dependent constants + leaf scratch
     int m, n;
     int64_t T;
@@ -346,10 +587,40 @@ int leaf(PmbCtx &C, const u64 *F, int64_t sF, int64_t e, const i64 *s_in, u64 *P
     LeafArgs A = C.base;
     A.T = (int)e;
     A.F = F; A.sF = sF; A.s_in = s_in; A.s_out = s_out; A.P = P; A.sP = sP;
-    const size_t sm = leaf_smem(C.m, C.n);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_mbasis_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int tok = stage_begin(ctx, PM_STAGE_LEAF);
-    k_mbasis_leaf<<<1, 512, sm, ctx->stream>>>(A);
+    bool done = false;
+    if (C.use_cluster) {
+        for (int clsz = LEAF_CL_MAX; clsz >= 8 && !done; clsz /= 2) {
+            const size_t smc = leaf_cl_smem(C.m, C.n, (int)e, clsz);
+            if (smc > 200 * 1024) continue;
+            cudaFuncSetAttribute(k_mbasis_leaf_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+            if (clsz > 8) cudaFuncSetAttribute(k_mbasis_leaf_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(clsz);
+            cfg.blockDim = dim3(512);
+            cfg.dynamicSmemBytes = smc;
+            cfg.stream = ctx->stream;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = clsz;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int ncl = 0;
+            if (cudaOccupancyMaxActiveClusters(&ncl, k_mbasis_leaf_cl, &cfg) != cudaSuccess || ncl < 1) {
+                cudaGetLastError();
+                continue;
+            }
+            if (cudaLaunchKernelEx(&cfg, k_mbasis_leaf_cl, A) == cudaSuccess) done = true;
+            else cudaGetLastError();
+        }
+    }
+    if (!done) {
+        const size_t sm = leaf_smem(C.m, C.n);
+        if (sm > 48 * 1024) cudaFuncSetAttribute(k_mbasis_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_mbasis_leaf<<<1, 512, sm, ctx->stream>>>(A);
+    }
     ctx->launches++;
     cudaError_t err = cudaGetLastError();
     stage_end(ctx, tok);
@@ -398,6 +669,7 @@ extern "C" int pm_basis(pm_ctx *ctx, uint64_t p, int m, int n, const void *F, in
 
     PmbCtx C;
     C.ctx = ctx;
+    C.use_cluster = ctx->opt_leaf_cluster != 0;
     C.m = m;
     C.n = n;
     C.T = ctx->opt_T;

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "libpmat.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pmat.h")
 
 PM_OK, PM_EINVAL, PM_EDOMAIN, PM_ENOMEM, PM_ECUDA, PM_ETIMEOUT, PM_EUNSUPPORTED, PM_ESCRATCH = range(8)
-PM_OPT_POINTWISE, PM_OPT_THRESHOLD, PM_OPT_DEBUG_CHECKS, PM_OPT_STAGE_TIMING = 1, 2, 3, 4
+PM_OPT_POINTWISE, PM_OPT_THRESHOLD, PM_OPT_DEBUG_CHECKS, PM_OPT_STAGE_TIMING, PM_OPT_LEAF_CLUSTER = 1, 2, 3, 4, 5
 PM_NSTAGES = 8
 STAGES = ["fwd_ntt", "pointwise", "inv_ntt", "crt", "leaf", "other"]
 STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_EDOMAIN", 3: "PM_ENOMEM", 4: "PM_ECUDA",

@@ -93,3 +93,20 @@ def test_pm_basis_rejects_even_modulus(ctx):
     with pytest.raises(PmError) as e:
         pmat.pm_basis(ctx, 1 << 20, F, 4, [0, 0])
     assert e.value.code == pmat.PM_EINVAL
+
+
+@pytest.mark.parametrize("case", [(P60, 6, 2, 40, 8), (97, 5, 3, 30, 32), (P60, 32, 16, 96, 32)])
+def test_single_cta_leaf_matches_oracle(ctx, case):
+    """The one-CTA leaf kernel (basis in global memory) gives the same bases."""
+    from paper_1905_04356_gb300 import pmat
+    p, m, n, d, T = case
+    g = synth.rng(77 + d)
+    F = synth.uniform(g, (m, n, d), p, np.uint64)
+    s = [(i * 7) % 5 - 2 for i in range(m)]
+    ctx.set_option(pmat.PM_OPT_LEAF_CLUSTER, 0)
+    try:
+        P, rd = _run(ctx, p, F, d, s, T)
+    finally:
+        ctx.set_option(pmat.PM_OPT_LEAF_CLUSTER, 1)
+    Pexp, rdexp = oracle.mbasis(p, F, d, s)
+    assert np.array_equal(P, Pexp) and np.array_equal(rd, rdexp)
