@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the PM-Basis / batched / resultant timings")
     return ap.parse_args()
 
 
@@ -159,6 +160,57 @@ def run_reference(args, rank):
         "cpu_baseline": {"value": round(v, 2), "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(v, 2), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+# ---------------------------------------------------------------- other workloads (reported under "extra")
+def extra_workloads(ctx, s, reps=3):
+    """PM-Basis (F 32x16, order 8192, 60-bit p), 512 batched uneven products, resultants
+    (deg_x = deg_y = 150, 1 prime and 16 primes): ms per call, CUDA events on the stream."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1905_04356_gb300 import pmat
+
+    def ev_ms(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for _ in range(n):
+            fn()
+        b.record(s)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    out = {}
+    with torch.cuda.stream(s):
+        W = synth.pmbasis_c3(0)
+        F = pmat.to_device(W["F"])
+        out["pm_basis_32x16_d8192_ms"] = round(ev_ms(lambda: pmat.pm_basis(ctx, W["p"], F, W["d"], W["shift"]), reps), 2)
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
+        ctx.stage_times()
+        pmat.pm_basis(ctx, W["p"], F, W["d"], W["shift"])
+        st = ctx.stage_times()
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
+        out["pm_basis_stage_ms"] = {k: round(v[0], 2) for k, v in st.items() if v[1]}
+        out["pm_basis_leaf_us_per_order_step"] = round(st["leaf"][0] * 1000 / W["d"], 2)
+        del F
+        R = synth.resultant_c5(0, nprimes=16)
+        f1, g1 = pmat.to_device(np.stack(R["f"][:1])), pmat.to_device(np.stack(R["g"][:1]))
+        out["resultant_150_1prime_ms"] = round(
+            ev_ms(lambda: pmat.bivariate_resultant(ctx, R["primes"][:1], f1, g1), reps), 2)
+        f16, g16 = pmat.to_device(np.stack(R["f"])), pmat.to_device(np.stack(R["g"]))
+        out["resultant_150_16primes_ms"] = round(
+            ev_ms(lambda: pmat.bivariate_resultant(ctx, R["primes"], f16, g16), 2), 2)
+        items = synth.batch_c4(0)
+        dev = [(it["p"], pmat.to_device(it["A"]), pmat.to_device(it["B"])) for it in items]
+        outs = [torch.empty((it["m"], it["k"], 2 * it["d"] - 1), dtype=dev[i][1].dtype, device="cuda")
+                for i, it in enumerate(items)]
+        n0 = ctx.launches()
+        out["batched_512_ms"] = round(ev_ms(lambda: pmat.pmat_mul_batched(ctx, dev, outs), 2), 2)
+        out["batched_512_launches_per_call"] = (ctx.launches() - n0) // 3
+        del dev, outs
+    return out
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -313,6 +365,8 @@ def main():
             "paper_context": PAPER_CONTEXT,
         },
     }
+    if not args.no_extra:
+        out["extra"].update(extra_workloads(ctx, s))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(W)
     if rank == 0:

@@ -110,3 +110,22 @@ def test_single_cta_leaf_matches_oracle(ctx, case):
         ctx.set_option(pmat.PM_OPT_LEAF_CLUSTER, 1)
     Pexp, rdexp = oracle.mbasis(p, F, d, s)
     assert np.array_equal(P, Pexp) and np.array_equal(rd, rdexp)
+
+
+def test_pm_basis_32x16_order_8192_matches_oracle_fingerprint(ctx):
+    """F 32 x 16, order 8192, 60-bit prime, shift 0: the whole basis against the SHA-256 of
+    the oracle's M-Basis output (and its row degrees)."""
+    import hashlib
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "golden.json")))["pmbasis_32x16_d8192"]
+    W = synth.pmbasis_c3(0)
+    assert W["p"] == gold["p"]
+    P, rd = _run(ctx, W["p"], W["F"], W["d"], W["shift"], 32)
+    assert list(P.shape) == gold["shape"]
+    assert [int(v) for v in rd] == gold["rdeg"]
+    assert sum(gold["rdeg"]) == 16 * 8192
+    flat = P.reshape(-1)
+    for i, v in gold["samples"]:
+        assert int(flat[i]) == v
+    assert hashlib.sha256(np.ascontiguousarray(P).tobytes()).hexdigest() == gold["sha256"]

@@ -172,3 +172,20 @@ def test_debug_check_rejects_unreduced_input(ctx):
         assert e.value.code == pmat.PM_EDOMAIN
     finally:
         ctx.set_option(pmat.PM_OPT_DEBUG_CHECKS, 0)
+
+
+@pytest.mark.parametrize("name,ntt_prime", [("product_32x32_p60", False), ("product_32x32_p998", True)])
+def test_c2_full_output_matches_oracle_fingerprint(ctx, name, ntt_prime):
+    """The whole 32x32 . 32x32, length-4096 product against the SHA-256 of the oracle's output."""
+    import hashlib
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "golden.json")))[name]
+    W = synth.product_c2(0, ntt_prime=ntt_prime)
+    assert W["p"] == gold["p"]
+    got = _gpu(ctx, "pmat_mul", W["p"], W["A"], W["B"]).astype(np.uint64)
+    assert list(got.shape) == gold["shape"]
+    flat = got.reshape(-1)
+    for i, v in gold["samples"]:
+        assert int(flat[i]) == v
+    assert hashlib.sha256(np.ascontiguousarray(got).tobytes()).hexdigest() == gold["sha256"]
