@@ -59,7 +59,9 @@ typedef struct pm_ctx pm_ctx;
 
 /* Option keys for pm_set_option. */
 enum {
-    PM_OPT_POINTWISE = 1,   /* 0 = auto, 1 = CUDA-core 64-bit, 2 = tensor-core limbs */
+    PM_OPT_POINTWISE = 1,   /* 0 = auto (the faster form measured on GB300: CUDA cores),
+                               1 = CUDA-core 64-bit products, 2 = tensor-core 8-bit limb
+                               products where m, n, k <= 32 (CUDA cores elsewhere) */
     PM_OPT_THRESHOLD = 2,   /* PM-Basis threshold T (>= 1): M-Basis when order <= T;
                                default 32 (Sec. 3, "Interpolant bases") */
     PM_OPT_DEBUG_CHECKS = 3, /* 1 = check inputs are in [0, p) (PM_EDOMAIN) */

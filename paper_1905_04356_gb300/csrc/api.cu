@@ -443,10 +443,13 @@ int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
             }
         }
         stage_end(ctx, tok);
-        // 2. pointwise products (jobs of any length share launches)
+        // 2. pointwise products (jobs of any length share launches): tensor-core limb
+        //    products where the shape allows (m, n, k <= 32) when that form is requested,
+        //    the CUDA-core 64-bit form otherwise
+        stage_end(ctx, tok);
         tok = stage_begin(ctx, PM_STAGE_POINTWISE);
         {
-            std::vector<PwJob> jobs; std::vector<int> nb;
+            std::vector<PwJob> jobs, tjobs; std::vector<int> nb, tnb;
             for (int r = r0; r < r1; r++) {
                 const ProdReq &q = reqs[r];
                 const Plan &P = plan[r];
@@ -455,12 +458,16 @@ int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
                     PwJob j;
                     j.A = (u32 *)(b.A + i * P.bA); j.B = (u32 *)(b.B + i * P.bB); j.C = (u32 *)(b.C + i * P.bC);
                     j.m = q.m; j.n = q.n; j.k = q.k; j.L = 1 << q.lg; j.P = prime_dev(*P.pr[i], q.lg);
-                    jobs.push_back(j);
-                    nb.push_back(pw_blocks(j));
+                    if (ctx->opt_pointwise == 2 && tc_supported(j)) { tjobs.push_back(j); tnb.push_back(tc_blocks(j)); }
+                    else { jobs.push_back(j); nb.push_back(pw_blocks(j)); }
                 }
             }
-            CKI(launch_packs(ctx, jobs, nb, [&](const JobPack<PwJob> &pk) {
-                return launch_pointwise(pk, ctx->stream, &ctx->launches); }));
+            if (!jobs.empty())
+                CKI(launch_packs(ctx, jobs, nb, [&](const JobPack<PwJob> &pk) {
+                    return launch_pointwise(pk, ctx->stream, &ctx->launches); }));
+            if (!tjobs.empty())
+                CKI(launch_packs(ctx, tjobs, tnb, [&](const JobPack<PwJob> &pk) {
+                    return launch_pointwise_tc(pk, ctx->d_status, ctx->stream, &ctx->launches); }));
         }
         stage_end(ctx, tok);
         // 3. inverse transforms, scaled, writing each slice, binned by length

@@ -189,3 +189,24 @@ def test_c2_full_output_matches_oracle_fingerprint(ctx, name, ntt_prime):
     for i, v in gold["samples"]:
         assert int(flat[i]) == v
     assert hashlib.sha256(np.ascontiguousarray(got).tobytes()).hexdigest() == gold["sha256"]
+
+
+@pytest.mark.parametrize("case", [(P60, 8, 32, 32, 32, 300, 200), (synth.P998, 4, 5, 7, 3, 100, 90),
+                                  (P60, 8, 32, 32, 16, 64, 130), (97, 4, 17, 9, 31, 40, 33),
+                                  (P62, 8, 32, 1, 32, 20, 20)])
+def test_tensor_core_and_cuda_core_pointwise_agree_with_oracle(ctx, case):
+    """Both pointwise forms (8-bit limbs on tcgen05, 64-bit lazy sums on CUDA cores) give the
+    oracle's product bit for bit."""
+    from paper_1905_04356_gb300 import pmat
+    p, w, m, n, k, dA, dB = case
+    g = synth.rng(31 + m * n * k)
+    A = _rand(g, p, (m, n, dA), w)
+    B = _rand(g, p, (n, k, dB), w)
+    exp = oracle.pmat_mul(p, A, B)
+    try:
+        for mode in (1, 2):
+            ctx.set_option(pmat.PM_OPT_POINTWISE, mode)
+            got = _gpu(ctx, "pmat_mul", p, A, B)
+            assert np.array_equal(got.astype(np.uint64), exp), mode
+    finally:
+        ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
