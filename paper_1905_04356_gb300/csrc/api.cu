@@ -449,7 +449,7 @@ int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
         stage_end(ctx, tok);
         tok = stage_begin(ctx, PM_STAGE_POINTWISE);
         {
-            std::vector<PwJob> jobs, tjobs; std::vector<int> nb, tnb;
+            std::vector<PwJob> jobs, tjobs, sjobs; std::vector<int> nb, tnb, snb;
             for (int r = r0; r < r1; r++) {
                 const ProdReq &q = reqs[r];
                 const Plan &P = plan[r];
@@ -459,12 +459,16 @@ int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
                     j.A = (u32 *)(b.A + i * P.bA); j.B = (u32 *)(b.B + i * P.bB); j.C = (u32 *)(b.C + i * P.bC);
                     j.m = q.m; j.n = q.n; j.k = q.k; j.L = 1 << q.lg; j.P = prime_dev(*P.pr[i], q.lg);
                     if (ctx->opt_pointwise == 2 && tc_supported(j)) { tjobs.push_back(j); tnb.push_back(tc_blocks(j)); }
+                    else if (pws_supported(j)) { sjobs.push_back(j); snb.push_back(pws_blocks(j)); }
                     else { jobs.push_back(j); nb.push_back(pw_blocks(j)); }
                 }
             }
             if (!jobs.empty())
                 CKI(launch_packs(ctx, jobs, nb, [&](const JobPack<PwJob> &pk) {
                     return launch_pointwise(pk, ctx->stream, &ctx->launches); }));
+            if (!sjobs.empty())
+                CKI(launch_packs(ctx, sjobs, snb, [&](const JobPack<PwJob> &pk) {
+                    return launch_pointwise_s(pk, ctx->stream, &ctx->launches); }));
             if (!tjobs.empty())
                 CKI(launch_packs(ctx, tjobs, tnb, [&](const JobPack<PwJob> &pk) {
                     return launch_pointwise_tc(pk, ctx->d_status, ctx->stream, &ctx->launches); }));

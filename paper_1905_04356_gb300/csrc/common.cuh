@@ -158,6 +158,9 @@ cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long lon
 cudaError_t launch_crt(const JobPack<CrtJob> &pk, cudaStream_t st, long long *launches);
 cudaError_t launch_pointwise_tc(const JobPack<PwJob> &pk, int *status, cudaStream_t st, long long *launches);
 bool tc_supported(const PwJob &j);
+cudaError_t launch_pointwise_s(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
+bool pws_supported(const PwJob &j);
+int pws_blocks(const PwJob &j);
 int tc_blocks(const PwJob &j);
 int fwd_block_threads(int lg);
 int blocks_per_entry_cols(int lg);

@@ -113,6 +113,118 @@ cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long lon
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ staged CUDA-core form
+// A block takes 8 consecutive points of one prime.  The residues of every entry at
+// those points are staged in shared memory (32-byte coalesced reads; rows padded to
+// 9 words), then each thread computes a 4 x 8 output tile at one point: warp w owns
+// output rows 4w.., lane = 8 * (column tile) + point.  Within a warp the A reads are
+// broadcasts and the B reads fall in distinct banks.  Outputs are staged and
+// written back 32 bytes per entry.  Needs m n, n k, m k <= 1024 (else k_pointwise).
+#define PS_PTS 8
+#define PS_ROW 9
+#define PS_THREADS 256
+
+int pws_blocks(const PwJob &j) { return (j.L + PS_PTS - 1) / PS_PTS; }
+bool pws_supported(const PwJob &j) { return j.m * j.n <= 1024 && j.n * j.k <= 1024 && j.m * j.k <= 1024 && j.L >= 16; }
+
+__global__ void __launch_bounds__(PS_THREADS, 2) k_pointwise_s(const __grid_constant__ JobPack<PwJob> pk)
+{
+    extern __shared__ __align__(16) u32 sms[];
+    const int b = blockIdx.x;
+    const int jb = find_job_pw(pk.blk_start, b);
+    const PwJob &J = pk.jobs[jb];
+    const int m = J.m, n = J.n, k = J.k, L = J.L;
+    const u32 q = J.P.q, q2 = J.P.q2, r32 = J.P.r32, r32s = J.P.r32s, ones = J.P.ones;
+    const int j0 = (b - pk.blk_start[jb]) * PS_PTS;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int eA = m * n, eB = n * k, eC = m * k;
+    u32 *rA = sms, *rB = sms + eA * PS_ROW, *rC = rB + eB * PS_ROW;
+
+    for (int x = tid; x < (eA + eB) * 2; x += PS_THREADS) {
+        const int e = x >> 1, h = x & 1;
+        const u32 *src = e < eA ? J.A + (i64)e * L : J.B + (i64)(e - eA) * L;
+        const uint4 v = *(const uint4 *)(src + j0 + 4 * h);
+        u32 *dst = (e < eA ? rA + e * PS_ROW : rB + (e - eA) * PS_ROW) + 4 * h;
+        dst[0] = v.x; dst[1] = v.y; dst[2] = v.z; dst[3] = v.w;
+    }
+    __syncthreads();
+
+    const int pp = lane & 7, tkl = lane >> 3;                 // point, column tile within the warp
+    const int nti = (m + PW_TI - 1) / PW_TI, ntk = (k + PW_TK - 1) / PW_TK;
+    // work items: (row tile ti, column-tile group tg); a warp takes 4 column tiles of one row tile
+    const int ngroups = (ntk + 3) / 4;
+    for (int item = warp; item < nti * ngroups; item += PS_THREADS / 32) {
+        const int ti = item / ngroups, tk = (item % ngroups) * 4 + tkl;
+        const int i0 = ti * PW_TI, k0 = tk * PW_TK;
+        const bool live = tk < ntk;
+        int oa[PW_TI], ob[PW_TK];                              // 32-bit shared-memory offsets
+#pragma unroll
+        for (int a = 0; a < PW_TI; a++) oa[a] = min(i0 + a, m - 1) * n * PS_ROW + pp;
+#pragma unroll
+        for (int c = 0; c < PW_TK; c++) ob[c] = min(k0 + c, k - 1) * PS_ROW + pp;
+        const int sbk = k * PS_ROW;
+        // 64-bit accumulators as (hi, lo) words with a carry chain per product;
+        // acc < q + 15 (q - 1)^2 < 2^64: fold to [0, q) every 15 products
+        u32 alo[PW_TI][PW_TK], ahi[PW_TI][PW_TK];
+#pragma unroll
+        for (int a = 0; a < PW_TI; a++)
+#pragma unroll
+            for (int c = 0; c < PW_TK; c++) { alo[a][c] = 0; ahi[a][c] = 0; }
+        for (int l0 = 0; l0 < n; l0 += 15) {
+            const int lend = min(n, l0 + 15);
+#pragma unroll 3
+            for (int l = l0; l < lend; l++) {
+                u32 av[PW_TI], bv[PW_TK];
+#pragma unroll
+                for (int a = 0; a < PW_TI; a++) av[a] = rA[oa[a] + l * PS_ROW];
+#pragma unroll
+                for (int c = 0; c < PW_TK; c++) bv[c] = rB[ob[c] + l * sbk];
+#pragma unroll
+                for (int a = 0; a < PW_TI; a++)
+#pragma unroll
+                    for (int c = 0; c < PW_TK; c++)
+                        asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;"
+                            : "+r"(alo[a][c]), "+r"(ahi[a][c]) : "r"(av[a]), "r"(bv[c]));
+            }
+#pragma unroll
+            for (int a = 0; a < PW_TI; a++)
+#pragma unroll
+                for (int c = 0; c < PW_TK; c++) {
+                    u32 s2 = shoup_mul(ahi[a][c], r32, r32s, q) + shoup_mul(alo[a][c], 1u, ones, q);
+                    alo[a][c] = csub(csub(s2, q2), q);
+                    ahi[a][c] = 0;
+                }
+        }
+        if (live) {
+#pragma unroll
+            for (int a = 0; a < PW_TI; a++)
+#pragma unroll
+                for (int c = 0; c < PW_TK; c++)
+                    if (i0 + a < m && k0 + c < k) rC[((i0 + a) * k + k0 + c) * PS_ROW + pp] = alo[a][c];
+        }
+    }
+    __syncthreads();
+    for (int x = tid; x < eC * 2; x += PS_THREADS) {
+        const int e = x >> 1, h = x & 1;
+        const u32 *s4 = rC + e * PS_ROW + 4 * h;
+        *(uint4 *)(J.C + (i64)e * L + j0 + 4 * h) = make_uint4(s4[0], s4[1], s4[2], s4[3]);
+    }
+}
+
+cudaError_t launch_pointwise_s(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches)
+{
+    int mx = 0;
+    for (int i = 0; i < pk.njobs; i++) {
+        const PwJob &j = pk.jobs[i];
+        const int t = (j.m * j.n + j.n * j.k + j.m * j.k) * PS_ROW * 4;
+        mx = t > mx ? t : mx;
+    }
+    if (mx > 48 * 1024) cudaFuncSetAttribute(k_pointwise_s, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    k_pointwise_s<<<pk.blk_start[pk.njobs], PS_THREADS, mx, st>>>(pk);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ CRT
 #define CRT_THREADS 256
 #define CRT_PER_THREAD 4
