@@ -159,7 +159,7 @@ __device__ __forceinline__ void fwd_first(u32 (&v)[16], u32 *X, const FwdJob &J,
     }
 }
 
-__global__ void __launch_bounds__(512) k_ntt_fwd_block(const __grid_constant__ JobPack<FwdJob> pk, int lg)
+__global__ void __launch_bounds__(512, 3) k_ntt_fwd_block(const __grid_constant__ JobPack<FwdJob> pk, int lg)
 {
     extern __shared__ u32 sm[];
     const int b = blockIdx.x;
@@ -241,7 +241,7 @@ __device__ __forceinline__ void inv_last(u32 (&v)[16], const u32 *X, const InvJo
     }
 }
 
-__global__ void __launch_bounds__(512) k_ntt_inv_block(const __grid_constant__ JobPack<InvJob> pk, int lg)
+__global__ void __launch_bounds__(512, 3) k_ntt_inv_block(const __grid_constant__ JobPack<InvJob> pk, int lg)
 {
     extern __shared__ u32 sm[];
     const int b = blockIdx.x;
