@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the PM-Basis / batched / resultant timings")
+    ap.add_argument("--extra", default="pm_basis,resultant,batched",
+                    help="comma-separated subset of pm_basis, resultant, batched")
     return ap.parse_args()
 
 
@@ -163,7 +165,7 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------- other workloads (reported under "extra")
-def extra_workloads(ctx, s, reps=3):
+def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched"), reps=3):
     """PM-Basis (F 32x16, order 8192, 60-bit p), 512 batched uneven products, resultants
     (deg_x = deg_y = 150, 1 prime and 16 primes): ms per call, CUDA events on the stream."""
     import numpy as np
@@ -182,34 +184,43 @@ def extra_workloads(ctx, s, reps=3):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / n
 
-    out = {}
-    with torch.cuda.stream(s):
+    def pm_basis():
         W = synth.pmbasis_c3(0)
         F = pmat.to_device(W["F"])
-        out["pm_basis_32x16_d8192_ms"] = round(ev_ms(lambda: pmat.pm_basis(ctx, W["p"], F, W["d"], W["shift"]), reps), 2)
+        run = lambda: pmat.pm_basis(ctx, W["p"], F, W["d"], W["shift"])  # noqa: E731
+        out = {"pm_basis_32x16_d8192_ms": round(ev_ms(run, reps), 2)}
         ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
         ctx.stage_times()
-        pmat.pm_basis(ctx, W["p"], F, W["d"], W["shift"])
+        run()
         st = ctx.stage_times()
         ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
         out["pm_basis_stage_ms"] = {k: round(v[0], 2) for k, v in st.items() if v[1]}
         out["pm_basis_leaf_us_per_order_step"] = round(st["leaf"][0] * 1000 / W["d"], 2)
-        del F
+        return out
+
+    def resultant():
         R = synth.resultant_c5(0, nprimes=16)
         f1, g1 = pmat.to_device(np.stack(R["f"][:1])), pmat.to_device(np.stack(R["g"][:1]))
-        out["resultant_150_1prime_ms"] = round(
-            ev_ms(lambda: pmat.bivariate_resultant(ctx, R["primes"][:1], f1, g1), reps), 2)
         f16, g16 = pmat.to_device(np.stack(R["f"])), pmat.to_device(np.stack(R["g"]))
-        out["resultant_150_16primes_ms"] = round(
-            ev_ms(lambda: pmat.bivariate_resultant(ctx, R["primes"], f16, g16), 2), 2)
+        return {"resultant_150_1prime_ms": round(
+                    ev_ms(lambda: pmat.bivariate_resultant(ctx, R["primes"][:1], f1, g1), reps), 2),
+                "resultant_150_16primes_ms": round(
+                    ev_ms(lambda: pmat.bivariate_resultant(ctx, R["primes"], f16, g16), 2), 2)}
+
+    def batched():
         items = synth.batch_c4(0)
         dev = [(it["p"], pmat.to_device(it["A"]), pmat.to_device(it["B"])) for it in items]
         outs = [torch.empty((it["m"], it["k"], 2 * it["d"] - 1), dtype=dev[i][1].dtype, device="cuda")
                 for i, it in enumerate(items)]
         n0 = ctx.launches()
-        out["batched_512_ms"] = round(ev_ms(lambda: pmat.pmat_mul_batched(ctx, dev, outs), 2), 2)
-        out["batched_512_launches_per_call"] = (ctx.launches() - n0) // 3
-        del dev, outs
+        ms = ev_ms(lambda: pmat.pmat_mul_batched(ctx, dev, outs), 2)
+        return {"batched_512_ms": round(ms, 2), "batched_512_launches_per_call": (ctx.launches() - n0) // 3}
+
+    out = {}
+    with torch.cuda.stream(s):
+        for name, fn in (("pm_basis", pm_basis), ("resultant", resultant), ("batched", batched)):
+            if name in which:
+                out.update(fn())
     return out
 
 
@@ -330,7 +341,7 @@ def main():
         "inv_ntt": K * eC * L * 4 + K * eC * lenC * 4,
         "crt": K * eC * lenC * 4 + eC * lenC * 8,
     }
-    kname = {"fwd_ntt": ("k_ntt_fwd_block", "ntt.cu"), "pointwise": ("k_pointwise", "pointwise.cu"),
+    kname = {"fwd_ntt": ("k_ntt_fwd_block", "ntt.cu"), "pointwise": ("k_pointwise_s", "pointwise.cu"),
              "inv_ntt": ("k_ntt_inv_block", "ntt.cu"), "crt": ("k_crt", "pointwise.cu")}
     stages = {k2: v for k2, v in st.items() if v[1] > 0}
     dom = max(stages, key=lambda x: stages[x][0])
@@ -366,7 +377,7 @@ def main():
         },
     }
     if not args.no_extra:
-        out["extra"].update(extra_workloads(ctx, s))
+        out["extra"].update(extra_workloads(ctx, s, tuple(args.extra.split(","))))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(W)
     if rank == 0:
