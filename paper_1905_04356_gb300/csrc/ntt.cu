@@ -121,29 +121,31 @@ __device__ __forceinline__ int find_job(const int *blk_start, int b)
 }
 
 // ------------------------------------------------------------------ forward, block
-// First pass of radix 2^r (r = 1..4): groups g + j*lo with lo = L >> r; each
-// thread takes 16 >> r groups.  Reads the source, writes shared memory (or
-// the destination when this pass is also the last one, L = 16).
-template <int r>
-__device__ __forceinline__ void fwd_first(u32 (&v)[16], u32 *X, const FwdJob &J, i64 e, bool act, int lg,
-                                          int tid, int tpt)
+// Kernels are instantiated per transform length 2^LG (LG = 4..13), so every pass's
+// stride lo is a compile-time constant: with the padded index spad(x) = x + x/32
+// and a group base b (b mod lo = gl < lo, b / lo a multiple of 16),
+// spad(b + j lo) = spad(b) + j lo + (j lo) / 32, i.e. immediate offsets.
+template <int LO>
+__device__ __forceinline__ constexpr int poff(int j) { return j * LO + ((j * LO) >> 5); }
+
+template <int LG, int R0>
+__device__ __forceinline__ void fwd_first_t(u32 (&v)[16], u32 *X, const FwdJob &J, i64 e, bool act, int tid)
 {
-    constexpr int R = 1 << r;
-    const int L = 1 << lg, lo = L >> r;
+    constexpr int L = 1 << LG, TPT = L >> 4, R = 1 << R0, LO = L >> R0;
     const u32 q = J.P.q, q2 = J.P.q2;
     const char *src = (const char *)J.src;
     const i64 sb = e * J.src_stride;
 #pragma unroll
-    for (int it = 0; it < (16 >> r); it++) {
-        const int g = tid + it * tpt;
+    for (int it = 0; it < (16 >> R0); it++) {
+        const int g = tid + it * TPT;
 #pragma unroll
         for (int j = 0; j < R; j++) {
-            const int x = g + j * lo;
+            const int x = g + j * LO;
             v[it * R + j] = (act && x < J.src_len) ? load_coeff(src, J.src_mode, sb + x, J.P) : 0u;
         }
-        grp_dif<r>(v, it * R, g & (lo - 1), lo, J.P.twf, q, q2);
+        grp_dif<R0>(v, it * R, g & (LO - 1), LO, J.P.twf, q, q2);
     }
-    if (lg == r) {   // single pass (L = 16): final values, contiguous
+    if (LG == R0) {
         if (act) {
             u32 *d = J.dst + e * J.dst_stride;
 #pragma unroll
@@ -152,57 +154,61 @@ __device__ __forceinline__ void fwd_first(u32 (&v)[16], u32 *X, const FwdJob &J,
         return;
     }
 #pragma unroll
-    for (int it = 0; it < (16 >> r); it++) {
-        const int g = tid + it * tpt;
+    for (int it = 0; it < (16 >> R0); it++) {
+        const int g = tid + it * TPT;
+        u32 *xb = X + spad(g);
 #pragma unroll
-        for (int j = 0; j < R; j++) X[spad(g + j * lo)] = v[it * R + j];
+        for (int j = 0; j < R; j++) xb[poff<LO>(j)] = v[it * R + j];
     }
 }
 
-__global__ void __launch_bounds__(512, 3) k_ntt_fwd_block(const __grid_constant__ JobPack<FwdJob> pk, int lg)
+// one radix-16 pass of the forward transform with constant stride LO
+template <int LG, int LO, bool LAST>
+__device__ __forceinline__ void fwd_pass16(u32 (&v)[16], u32 *X, const FwdJob &J, i64 e, bool act, int tid)
+{
+    constexpr int LLO = (LO == 1) ? 0 : (LO == 2) ? 1 : (LO == 4) ? 2 : (LO == 8) ? 3 : (LO == 16) ? 4 : (LO == 32) ? 5 :
+                        (LO == 64) ? 6 : (LO == 128) ? 7 : (LO == 256) ? 8 : 9;
+    const u32 q = J.P.q, q2 = J.P.q2;
+    const int g = tid, gl = g & (LO - 1);
+    const int base = ((g >> LLO) << (LLO + 4)) + gl;
+    __syncthreads();
+    const u32 *xb = X + spad(base);
+#pragma unroll
+    for (int j = 0; j < 16; j++) v[j] = xb[poff<LO>(j)];
+    grp_dif<4>(v, 0, gl, LO, J.P.twf, q, q2);
+    if (LAST) {
+        if (act) {
+            uint4 *d = (uint4 *)(J.dst + e * J.dst_stride + base);
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                d[j] = make_uint4(csub(v[4 * j], q), csub(v[4 * j + 1], q), csub(v[4 * j + 2], q), csub(v[4 * j + 3], q));
+        }
+    } else {
+        u32 *xw = X + spad(base);   // each thread writes back exactly the points it read
+#pragma unroll
+        for (int j = 0; j < 16; j++) xw[poff<LO>(j)] = v[j];
+    }
+}
+
+template <int LG>
+__global__ void __launch_bounds__(512, 3) k_ntt_fwd_block(const __grid_constant__ JobPack<FwdJob> pk)
 {
     extern __shared__ u32 sm[];
+    constexpr int L = 1 << LG, TPT = L >> 4, B0 = ((LG - 1) & 3) + 1;
     const int b = blockIdx.x;
     const int jb = find_job(pk.blk_start, b);
     const FwdJob &J = pk.jobs[jb];
-    const int L = 1 << lg, tpt = L >> 4, tpb = blockDim.x / tpt;
-    const int lt = threadIdx.x / tpt, tid = threadIdx.x - lt * tpt;
+    const int tpb = blockDim.x / TPT;
+    const int lt = threadIdx.x / TPT, tid = threadIdx.x - lt * TPT;
     const i64 e = (i64)(b - pk.blk_start[jb]) * tpb + lt;
     const bool act = e < J.count;
     u32 *X = sm + lt * (L + (L >> 5));
-    const u32 q = J.P.q, q2 = J.P.q2;
     u32 v[16];
-
-    const int b0 = ((lg - 1) & 3) + 1;
-    switch (b0) {
-    case 1: fwd_first<1>(v, X, J, e, act, lg, tid, tpt); break;
-    case 2: fwd_first<2>(v, X, J, e, act, lg, tid, tpt); break;
-    case 3: fwd_first<3>(v, X, J, e, act, lg, tid, tpt); break;
-    default: fwd_first<4>(v, X, J, e, act, lg, tid, tpt); break;
-    }
-    if (lg == b0) return;
-    for (int s0 = b0; s0 < lg; s0 += 4) {
-        __syncthreads();
-        const int llo = lg - s0 - 4, lo = 1 << llo;
-        const int g = tid, gl = g & (lo - 1);
-        const int base = ((g >> llo) << (llo + 4)) + gl;
-#pragma unroll
-        for (int j = 0; j < 16; j++) v[j] = X[spad(base + j * lo)];
-        grp_dif<4>(v, 0, gl, lo, J.P.twf, q, q2);
-        if (llo == 0) {
-            if (act) {
-                uint4 *d = (uint4 *)(J.dst + e * J.dst_stride + base);
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    d[j] = make_uint4(csub(v[4 * j], q), csub(v[4 * j + 1], q), csub(v[4 * j + 2], q),
-                                      csub(v[4 * j + 3], q));
-            }
-        } else {
-            // each thread writes back exactly the points it read: no barrier needed here
-#pragma unroll
-            for (int j = 0; j < 16; j++) X[spad(base + j * lo)] = v[j];
-        }
-    }
+    fwd_first_t<LG, B0>(v, X, J, e, act, tid);
+    // radix-16 passes: stride L >> (B0 + 4), L >> (B0 + 8), ..., 1
+    if constexpr (LG - B0 >= 4) fwd_pass16<LG, (L >> (B0 + 4)), (LG - B0 == 4)>(v, X, J, e, act, tid);
+    if constexpr (LG - B0 >= 8) fwd_pass16<LG, (L >> (B0 + 8)), (LG - B0 == 8)>(v, X, J, e, act, tid);
+    if constexpr (LG - B0 >= 12) fwd_pass16<LG, (L >> (B0 + 12)), (LG - B0 == 12)>(v, X, J, e, act, tid);
 }
 
 // ------------------------------------------------------------------ inverse, block
@@ -219,81 +225,87 @@ __device__ __forceinline__ void store_out(const InvJob &J, i64 e, int x, u32 val
     else ((u32 *)J.dst)[e * J.dst_stride + t] = y;
 }
 
-template <int r>
-__device__ __forceinline__ void inv_last(u32 (&v)[16], const u32 *X, const InvJob &J, i64 e, bool act, int lg,
-                                         int tid, int tpt, bool from_regs)
+template <int LG, int R0>
+__device__ __forceinline__ void inv_last_t(u32 (&v)[16], const u32 *X, const InvJob &J, i64 e, bool act, int tid,
+                                           bool from_regs)
 {
-    constexpr int R = 1 << r;
-    const int L = 1 << lg, lo = L >> r;
+    constexpr int L = 1 << LG, TPT = L >> 4, R = 1 << R0, LO = L >> R0;
     const u32 q = J.P.q, q2 = J.P.q2;
 #pragma unroll
-    for (int it = 0; it < (16 >> r); it++) {
-        const int g = tid + it * tpt;
+    for (int it = 0; it < (16 >> R0); it++) {
+        const int g = tid + it * TPT;
         if (!from_regs) {
+            const u32 *xb = X + spad(g);
 #pragma unroll
-            for (int j = 0; j < R; j++) v[it * R + j] = X[spad(g + j * lo)];
+            for (int j = 0; j < R; j++) v[it * R + j] = xb[poff<LO>(j)];
         }
-        grp_dit<r>(v, it * R, g & (lo - 1), lo, J.P.twi, q, q2);
+        grp_dit<R0>(v, it * R, g & (LO - 1), LO, J.P.twi, q, q2);
         if (act) {
 #pragma unroll
-            for (int j = 0; j < R; j++) store_out(J, e, g + j * lo, v[it * R + j]);
+            for (int j = 0; j < R; j++) store_out(J, e, g + j * LO, v[it * R + j]);
         }
     }
 }
 
-__global__ void __launch_bounds__(512, 3) k_ntt_inv_block(const __grid_constant__ JobPack<InvJob> pk, int lg)
+// one radix-16 pass of the inverse transform with constant stride LO
+template <int LG, int LO, bool FIRST>
+__device__ __forceinline__ void inv_pass16(u32 (&v)[16], u32 *X, const InvJob &J, i64 e, bool act, int tid)
 {
-    extern __shared__ u32 sm[];
-    const int b = blockIdx.x;
-    const int jb = find_job(pk.blk_start, b);
-    const InvJob &J = pk.jobs[jb];
-    const int L = 1 << lg, tpt = L >> 4, tpb = blockDim.x / tpt;
-    const int lt = threadIdx.x / tpt, tid = threadIdx.x - lt * tpt;
-    const i64 e = (i64)(b - pk.blk_start[jb]) * tpb + lt;
-    const bool act = e < J.count;
-    u32 *X = sm + lt * (L + (L >> 5));
+    constexpr int LLO = (LO == 1) ? 0 : (LO == 2) ? 1 : (LO == 4) ? 2 : (LO == 8) ? 3 : (LO == 16) ? 4 : (LO == 32) ? 5 :
+                        (LO == 64) ? 6 : (LO == 128) ? 7 : (LO == 256) ? 8 : 9;
     const u32 q = J.P.q, q2 = J.P.q2;
-    u32 v[16];
-    const int b0 = ((lg - 1) & 3) + 1;
-
-    if (lg == b0) {   // L = 16: one radix-16 pass straight from the source
-        const u32 *s = J.src + e * J.src_stride;
+    const int g = tid, gl = g & (LO - 1);
+    const int base = ((g >> LLO) << (LLO + 4)) + gl;
+    if (FIRST) {
+        if (act) {
+            const uint4 *s4 = (const uint4 *)(J.src + e * J.src_stride + base);
 #pragma unroll
-        for (int j = 0; j < 16; j++) v[j] = act ? s[j] : 0u;
-        inv_last<4>(v, X, J, e, act, lg, tid, tpt, true);
-        return;
-    }
-    // radix-16 passes, lo = 1, 16, 256, ... over the low lg - b0 stages
-    for (int s0 = 0; s0 < lg - b0; s0 += 4) {
-        const int llo = s0, lo = 1 << llo;
-        const int g = tid, gl = g & (lo - 1);
-        const int base = ((g >> llo) << (llo + 4)) + gl;
-        if (s0 == 0) {
-            if (act) {
-                const uint4 *s = (const uint4 *)(J.src + e * J.src_stride + base);
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    uint4 t = s[j];
-                    v[4 * j] = t.x; v[4 * j + 1] = t.y; v[4 * j + 2] = t.z; v[4 * j + 3] = t.w;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 16; j++) v[j] = 0u;
+            for (int j = 0; j < 4; j++) {
+                uint4 t = s4[j];
+                v[4 * j] = t.x; v[4 * j + 1] = t.y; v[4 * j + 2] = t.z; v[4 * j + 3] = t.w;
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < 16; j++) v[j] = X[spad(base + j * lo)];
+            for (int j = 0; j < 16; j++) v[j] = 0u;
         }
-        grp_dit<4>(v, 0, gl, lo, J.P.twi, q, q2);
+    } else {
+        const u32 *xb = X + spad(base);
 #pragma unroll
-        for (int j = 0; j < 16; j++) X[spad(base + j * lo)] = v[j];
-        __syncthreads();
+        for (int j = 0; j < 16; j++) v[j] = xb[poff<LO>(j)];
     }
-    switch (b0) {
-    case 1: inv_last<1>(v, X, J, e, act, lg, tid, tpt, false); break;
-    case 2: inv_last<2>(v, X, J, e, act, lg, tid, tpt, false); break;
-    case 3: inv_last<3>(v, X, J, e, act, lg, tid, tpt, false); break;
-    default: inv_last<4>(v, X, J, e, act, lg, tid, tpt, false); break;
+    grp_dit<4>(v, 0, gl, LO, J.P.twi, q, q2);
+    u32 *xw = X + spad(base);
+#pragma unroll
+    for (int j = 0; j < 16; j++) xw[poff<LO>(j)] = v[j];
+    __syncthreads();
+}
+
+template <int LG>
+__global__ void __launch_bounds__(512, 3) k_ntt_inv_block(const __grid_constant__ JobPack<InvJob> pk)
+{
+    extern __shared__ u32 sm[];
+    constexpr int L = 1 << LG, TPT = L >> 4, B0 = ((LG - 1) & 3) + 1;
+    const int b = blockIdx.x;
+    const int jb = find_job(pk.blk_start, b);
+    const InvJob &J = pk.jobs[jb];
+    const int tpb = blockDim.x / TPT;
+    const int lt = threadIdx.x / TPT, tid = threadIdx.x - lt * TPT;
+    const i64 e = (i64)(b - pk.blk_start[jb]) * tpb + lt;
+    const bool act = e < J.count;
+    u32 *X = sm + lt * (L + (L >> 5));
+    u32 v[16];
+    if constexpr (LG == B0) {   // L = 16: one radix-16 pass straight from the source
+        const u32 *s = J.src + e * J.src_stride;
+#pragma unroll
+        for (int j = 0; j < 16; j++) v[j] = act ? s[j] : 0u;
+        inv_last_t<LG, 4>(v, X, J, e, act, tid, true);
+        return;
+    } else {
+        // radix-16 passes, stride 1, 16, 256 over the low LG - B0 stages
+        inv_pass16<LG, 1, true>(v, X, J, e, act, tid);
+        if constexpr (LG - B0 >= 8) inv_pass16<LG, 16, false>(v, X, J, e, act, tid);
+        if constexpr (LG - B0 >= 12) inv_pass16<LG, 256, false>(v, X, J, e, act, tid);
+        inv_last_t<LG, B0>(v, X, J, e, act, tid, false);
     }
 }
 
@@ -312,22 +324,58 @@ static int block_smem(int lg, int threads)
 template <typename Pack>
 static int pack_blocks(const Pack &pk) { return pk.blk_start[pk.njobs]; }
 
+template <int LG>
+static cudaError_t fwd_lg(const JobPack<FwdJob> &pk, cudaStream_t st)
+{
+    const int th = fwd_block_threads(LG), sm = block_smem(LG, th);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_ntt_fwd_block<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    k_ntt_fwd_block<LG><<<pack_blocks(pk), th, sm, st>>>(pk);
+    return cudaGetLastError();
+}
+
+template <int LG>
+static cudaError_t inv_lg(const JobPack<InvJob> &pk, cudaStream_t st)
+{
+    const int th = fwd_block_threads(LG), sm = block_smem(LG, th);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_ntt_inv_block<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    k_ntt_inv_block<LG><<<pack_blocks(pk), th, sm, st>>>(pk);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ntt_fwd_block(const JobPack<FwdJob> &pk, int lg, cudaStream_t st, long long *launches)
 {
-    const int th = fwd_block_threads(lg), sm = block_smem(lg, th);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_ntt_fwd_block, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    k_ntt_fwd_block<<<pack_blocks(pk), th, sm, st>>>(pk, lg);
     ++*launches;
-    return cudaGetLastError();
+    switch (lg) {
+    case 4: return fwd_lg<4>(pk, st);
+    case 5: return fwd_lg<5>(pk, st);
+    case 6: return fwd_lg<6>(pk, st);
+    case 7: return fwd_lg<7>(pk, st);
+    case 8: return fwd_lg<8>(pk, st);
+    case 9: return fwd_lg<9>(pk, st);
+    case 10: return fwd_lg<10>(pk, st);
+    case 11: return fwd_lg<11>(pk, st);
+    case 12: return fwd_lg<12>(pk, st);
+    case 13: return fwd_lg<13>(pk, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_ntt_inv_block(const JobPack<InvJob> &pk, int lg, cudaStream_t st, long long *launches)
 {
-    const int th = fwd_block_threads(lg), sm = block_smem(lg, th);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_ntt_inv_block, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    k_ntt_inv_block<<<pack_blocks(pk), th, sm, st>>>(pk, lg);
     ++*launches;
-    return cudaGetLastError();
+    switch (lg) {
+    case 4: return inv_lg<4>(pk, st);
+    case 5: return inv_lg<5>(pk, st);
+    case 6: return inv_lg<6>(pk, st);
+    case 7: return inv_lg<7>(pk, st);
+    case 8: return inv_lg<8>(pk, st);
+    case 9: return inv_lg<9>(pk, st);
+    case 10: return inv_lg<10>(pk, st);
+    case 11: return inv_lg<11>(pk, st);
+    case 12: return inv_lg<12>(pk, st);
+    case 13: return inv_lg<13>(pk, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // ------------------------------------------------------------------ column passes
