@@ -191,7 +191,7 @@ __device__ __forceinline__ void fwd_pass16(u32 (&v)[16], u32 *X, const FwdJob &J
 }
 
 template <int LG>
-__global__ void __launch_bounds__(512, 3) k_ntt_fwd_block(const __grid_constant__ JobPack<FwdJob> pk)
+__global__ void __launch_bounds__(512, 4) k_ntt_fwd_block(const __grid_constant__ JobPack<FwdJob> pk)
 {
     extern __shared__ u32 sm[];
     constexpr int L = 1 << LG, TPT = L >> 4, B0 = ((LG - 1) & 3) + 1;
@@ -281,7 +281,7 @@ __device__ __forceinline__ void inv_pass16(u32 (&v)[16], u32 *X, const InvJob &J
 }
 
 template <int LG>
-__global__ void __launch_bounds__(512, 3) k_ntt_inv_block(const __grid_constant__ JobPack<InvJob> pk)
+__global__ void __launch_bounds__(512, 4) k_ntt_inv_block(const __grid_constant__ JobPack<InvJob> pk)
 {
     extern __shared__ u32 sm[];
     constexpr int L = 1 << LG, TPT = L >> 4, B0 = ((LG - 1) & 3) + 1;

@@ -235,46 +235,53 @@ int crt_blocks(const CrtJob &j)
     return (int)((j.count + per - 1) / per);
 }
 
+template <int K>
+__device__ __forceinline__ void crt_one(const CrtJob &J, i64 idx)
+{
+    u32 v[K];
+    // Garner: v_i = (...((r_i - v_0) c_i0 - v_1) c_i1 ... - v_{i-1}) c_i,i-1 mod q_i
+#pragma unroll
+    for (int i = 0; i < K; i++) {
+        const u32 qi = J.q[i];
+        u32 t = __ldg(J.res + (i64)i * J.count + idx);
+#pragma unroll
+        for (int j = 0; j < i; j++) {
+            const u32 vj = csub(v[j], qi);              // v_j < q_j < 2 q_i
+            t = csub(shoup_mul(t + qi - vj, J.c[i][j], J.cs[i][j], qi), qi);
+        }
+        v[i] = t;
+    }
+    // X = v_0 + q_0 (v_1 + q_1 (v_2 + ...)) reduced mod p by Horner
+    u64 y = J.small_p ? barrett64(v[K - 1], J.p, J.mu) : v[K - 1];
+#pragma unroll
+    for (int i = K - 2; i >= 0; i--) {
+        u64 z = shoup_mul64(y, J.qm[i], J.qms[i], J.p);              // [0, 2p)
+        z += J.small_p ? barrett64(v[i], J.p, J.mu) : v[i];         // [0, 3p)
+        y = csub64(csub64(z, J.p), J.p);
+    }
+    const i64 e = idx / J.len, o = e * J.dst_stride + (idx - e * J.len);
+    if (J.w == 8) ((u64 *)J.dst)[o] = y;
+    else ((u32 *)J.dst)[o] = (u32)y;
+}
+
 __global__ void __launch_bounds__(CRT_THREADS) k_crt(const __grid_constant__ JobPack<CrtJob> pk)
 {
     const int b = blockIdx.x;
     const int jb = find_job_pw(pk.blk_start, b);
     const CrtJob &J = pk.jobs[jb];
     const i64 start = (i64)(b - pk.blk_start[jb]) * CRT_THREADS * CRT_PER_THREAD + threadIdx.x;
-    const int K = J.K;
-#pragma unroll 1
+#pragma unroll
     for (int it = 0; it < CRT_PER_THREAD; it++) {
         const i64 idx = start + (i64)it * CRT_THREADS;
         if (idx >= J.count) return;
-        u32 v[PM_MAXK];
-        // Garner: v_i = (...((r_i - v_0) c_i0 - v_1) c_i1 ... - v_{i-1}) c_i,i-1 mod q_i
-#pragma unroll
-        for (int i = 0; i < PM_MAXK; i++) {
-            if (i >= K) break;
-            const u32 qi = J.q[i];
-            u32 t = __ldg(J.res + (i64)i * J.count + idx);
-#pragma unroll
-            for (int j = 0; j < PM_MAXK; j++) {
-                if (j >= i) break;
-                const u32 vj = csub(v[j], qi);          // v_j < q_j < 2 q_i
-                t = shoup_mul(t + qi - vj, J.c[i][j], J.cs[i][j], qi);
-                t = csub(t, qi);
-            }
-            v[i] = t;
+        switch (J.K) {
+        case 1: crt_one<1>(J, idx); break;
+        case 2: crt_one<2>(J, idx); break;
+        case 3: crt_one<3>(J, idx); break;
+        case 4: crt_one<4>(J, idx); break;
+        case 5: crt_one<5>(J, idx); break;
+        default: crt_one<6>(J, idx); break;
         }
-        // X = v_0 + q_0 (v_1 + q_1 (v_2 + ...)) reduced mod p by Horner
-        u64 y = J.small_p ? barrett64(v[K - 1], J.p, J.mu) : v[K - 1];
-#pragma unroll
-        for (int i = PM_MAXK - 2; i >= 0; i--) {
-            if (i > K - 2) continue;
-            u64 z = shoup_mul64(y, J.qm[i], J.qms[i], J.p);              // [0, 2p)
-            z += J.small_p ? barrett64(v[i], J.p, J.mu) : v[i];         // [0, 3p)
-            z = csub64(csub64(z, J.p), J.p);
-            y = z;
-        }
-        const i64 e = idx / J.len, o = e * J.dst_stride + (idx - e * J.len);
-        if (J.w == 8) ((u64 *)J.dst)[o] = y;
-        else ((u32 *)J.dst)[o] = (u32)y;
     }
 }
 
