@@ -127,6 +127,12 @@ __device__ __forceinline__ int warp_deg(const u64 *A, int start)
     return -1;
 }
 
+// Res(A, B) = (-1)^(ab) lc(B)^(a-r) Res(B, A mod B); with s pseudo-division steps
+// A_s = lc(B)^s A mod B, Res(B, A_s) = lc(B)^(s b) Res(B, A mod B).  Each remainder
+// step records (lc(B), a - r, s b) in shared memory; the powers are taken at the end,
+// 32 records at a time across the lanes.  Two steps with shifts sh and sh - 1 are
+// fused: A <- lc(B)^2 A - lc(B) lc(A) x^sh B - t x^(sh-1) B, t = lc(B) A[da-1] -
+// lc(A) B[b-1] (t = 0 only means the degree fell further; the relation still holds).
 __global__ void __launch_bounds__(256) k_res_euclid(const __grid_constant__ ResPack P, int dmax)
 {
     extern __shared__ u64 sme[];
@@ -134,51 +140,82 @@ __global__ void __launch_bounds__(256) k_res_euclid(const __grid_constant__ ResP
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int pt = blockIdx.x * (blockDim.x >> 5) + wid;
     if (pt >= P.N) return;
-    u64 *A = sme + (size_t)wid * 2 * (dmax + 1);
+    const int nrec = dmax + 2;
+    u64 *A = sme + (size_t)wid * (2 * (dmax + 1) + 3 * nrec);
     u64 *B = A + (dmax + 1);
+    u64 *rl = B + (dmax + 1);            // lc(B) per remainder step
+    u64 *rn = rl + nrec;                 // exponent a - r
+    u64 *rd = rn + nrec;                 // exponent s b
     const u64 *val = I.Vt + (i64)pt * P.J;
     int a = P.dyf, b = P.dyg;
     for (int c = lane; c <= a; c += 32) A[c] = val[c];
     for (int c = lane; c <= b; c += 32) B[c] = val[P.dyf + 1 + c];
     __syncwarp();
-    u64 num = I.one, den = I.one;
-    bool neg = false;
+    u64 tail = I.one;                    // lc^deg factor of the last step
+    bool neg = false, zero = false;
+    int nr = 0;
     for (;;) {
-        if (b == 0) { num = mm(num, mpw(B[0], (u64)a, I), I); break; }
-        if (a == 0) { num = mm(num, mpw(A[0], (u64)b, I), I); break; }
+        if (b == 0) { tail = mpw(B[0], (u64)a, I); break; }
+        if (a == 0) { tail = mpw(A[0], (u64)b, I); break; }
         if (a < b) {                                // Res(A, B) = (-1)^(ab) Res(B, A)
-            u64 *s = A; A = B; B = s;
+            u64 *sw = A; A = B; B = sw;
             int t = a; a = b; b = t;
             neg ^= (a & b & 1);
         }
-        // A <- lc(B)^s A mod B by s pseudo-division steps
         const u64 lcB = B[b];
-        const u64 pb = mpw(lcB, (u64)b, I);
-        int da = a;
+        const u64 lcB2 = mm(lcB, lcB, I);
+        int da = a, s = 0;
         while (da >= b) {
             const u64 lcA = A[da];
             const int sh = da - b;
-            __syncwarp();                               // every lane has read lc(A) before A[da] changes
-            for (int c = lane; c <= da; c += 32) {
-                u64 x = mm(lcB, A[c], I);
-                if (c >= sh) x = sub64(x, mm(lcA, B[c - sh], I), I.p);
-                A[c] = x;
+            if (sh >= 1) {
+                const u64 t = sub64(mm(lcB, A[da - 1], I), mm(lcA, B[b - 1], I), I.p);
+                const u64 f1 = mm(lcB, lcA, I);
+                __syncwarp();                       // every lane has read A[da], A[da - 1]
+                for (int c = lane; c <= da - 2; c += 32) {
+                    u64 x = mm(lcB2, A[c], I);
+                    if (c >= sh) x = sub64(x, mm(f1, B[c - sh], I), I.p);
+                    if (c >= sh - 1) x = sub64(x, mm(t, B[c - sh + 1], I), I.p);
+                    A[c] = x;
+                }
+                s += 2;
+                __syncwarp();                       // the new coefficients are visible to the whole warp
+                da = warp_deg(A, da - 2);
+            } else {
+                __syncwarp();
+                for (int c = lane; c <= da - 1; c += 32) A[c] = sub64(mm(lcB, A[c], I), mm(lcA, B[c], I), I.p);
+                s += 1;
+                __syncwarp();
+                da = warp_deg(A, da - 1);
             }
-            __syncwarp();
-            den = mm(den, pb, I);                   // Res(B, lc(B)^s R) = lc(B)^(s b) Res(B, R)
-            da = warp_deg(A, da - 1);
             __syncwarp();
         }
         const int r = da;
-        if (r < 0) { num = 0; break; }
+        if (r < 0) { zero = true; break; }
         neg ^= (a & b & 1);
-        num = mm(num, mpw(lcB, (u64)(a - r), I), I);
-        u64 *s = A; A = B; B = s;                   // (A, B) <- (B, R)
+        if (lane == 0) { rl[nr] = lcB; rn[nr] = (u64)(a - r); rd[nr] = (u64)s * (u64)b; }
+        nr++;
+        u64 *sw = A; A = B; B = sw;                // (A, B) <- (B, R)
         a = b;
         b = r;
     }
+    __syncwarp();
+    if (zero) {
+        if (lane == 0) I.v[pt] = 0;
+        return;
+    }
+    // num = prod lc^(a-r), den = prod lc^(s b): 32 records at a time
+    u64 num = I.one, den = I.one;
+    for (int i = lane; i < nr; i += 32) {
+        num = mm(num, mpw(rl[i], rn[i], I), I);
+        den = mm(den, mpw(rl[i], rd[i], I), I);
+    }
+    for (int o = 16; o >= 1; o >>= 1) {
+        num = mm(num, __shfl_xor_sync(0xffffffffu, num, o), I);
+        den = mm(den, __shfl_xor_sync(0xffffffffu, den, o), I);
+    }
     if (lane == 0) {
-        u64 res = mm(num, mpw(den, I.p - 2, I), I);
+        u64 res = mm(mm(num, tail, I), mpw(den, I.p - 2, I), I);
         res = mm(res, 1, I);
         if (neg && res) res = I.p - res;
         I.v[pt] = res;
@@ -326,7 +363,7 @@ static int res_batch(pm_ctx *ctx, int cnt, const uint64_t *primes, const uint64_
     tok = stage_begin(ctx, PM_STAGE_OTHER);
     {
         const int dmax = dyf > dyg ? dyf : dyg;
-        const size_t sm = (size_t)8 * 2 * (dmax + 1) * 8;
+        const size_t sm = (size_t)8 * (2 * (dmax + 1) + 3 * (dmax + 2)) * 8;
         if (sm > 48 * 1024) cudaFuncSetAttribute(k_res_euclid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_res_euclid<<<dim3((N + 7) / 8, cnt), 256, sm, ctx->stream>>>(pk, dmax);
         k_res_wscan<<<cnt, 1024, 0, ctx->stream>>>(pk);
