@@ -341,7 +341,7 @@ def main():
         "inv_ntt": K * eC * L * 4 + K * eC * lenC * 4,
         "crt": K * eC * lenC * 4 + eC * lenC * 8,
     }
-    kname = {"fwd_ntt": ("k_ntt_fwd_block", "ntt.cu"), "pointwise": ("k_pointwise_s", "pointwise.cu"),
+    kname = {"fwd_ntt": ("k_ntt_fwd_block", "ntt.cu"), "pointwise": ("k_pointwise", "pointwise.cu"),
              "inv_ntt": ("k_ntt_inv_block", "ntt.cu"), "crt": ("k_crt", "pointwise.cu")}
     stages = {k2: v for k2, v in st.items() if v[1] > 0}
     dom = max(stages, key=lambda x: stages[x][0])

@@ -445,30 +445,26 @@ int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
         stage_end(ctx, tok);
         // 2. pointwise products (jobs of any length share launches): tensor-core limb
         //    products where the shape allows (m, n, k <= 32) when that form is requested,
-        //    the CUDA-core 64-bit form otherwise
-        stage_end(ctx, tok);
+        //    the staged CUDA-core 64-bit form otherwise
         tok = stage_begin(ctx, PM_STAGE_POINTWISE);
         {
-            std::vector<PwJob> jobs, tjobs, sjobs; std::vector<int> nb, tnb, snb;
+            std::vector<PwJob> jobs, tjobs; std::vector<int> nb, tnb;
             for (int r = r0; r < r1; r++) {
                 const ProdReq &q = reqs[r];
                 const Plan &P = plan[r];
                 const Bufs &b = buf[r - r0];
                 for (size_t i = 0; i < P.pr.size(); i++) {
                     PwJob j;
+                    memset(&j, 0, sizeof(j));
                     j.A = (u32 *)(b.A + i * P.bA); j.B = (u32 *)(b.B + i * P.bB); j.C = (u32 *)(b.C + i * P.bC);
                     j.m = q.m; j.n = q.n; j.k = q.k; j.L = 1 << q.lg; j.P = prime_dev(*P.pr[i], q.lg);
                     if (ctx->opt_pointwise == 2 && tc_supported(j)) { tjobs.push_back(j); tnb.push_back(tc_blocks(j)); }
-                    else if (pws_supported(j)) { sjobs.push_back(j); snb.push_back(pws_blocks(j)); }
-                    else { jobs.push_back(j); nb.push_back(pw_blocks(j)); }
+                    else { const int nbk = pw_plan(j); jobs.push_back(j); nb.push_back(nbk); }
                 }
             }
             if (!jobs.empty())
                 CKI(launch_packs(ctx, jobs, nb, [&](const JobPack<PwJob> &pk) {
                     return launch_pointwise(pk, ctx->stream, &ctx->launches); }));
-            if (!sjobs.empty())
-                CKI(launch_packs(ctx, sjobs, snb, [&](const JobPack<PwJob> &pk) {
-                    return launch_pointwise_s(pk, ctx->stream, &ctx->launches); }));
             if (!tjobs.empty())
                 CKI(launch_packs(ctx, tjobs, tnb, [&](const JobPack<PwJob> &pk) {
                     return launch_pointwise_tc(pk, ctx->d_status, ctx->stream, &ctx->launches); }));

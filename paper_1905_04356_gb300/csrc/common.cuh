@@ -120,10 +120,17 @@ struct ColJob {
     PrimeDev P;
 };
 // Pointwise products at every transform point: C_j = A_j B_j mod q.
+// The CUDA-core kernel's block plan (pw_plan): block tiles of bi x bk thread tiles of
+// 4 x 8 outputs (nbk tiles across k, ntile per transform point group), the inner
+// dimension staged lc <= 32 at a time and split into ns contiguous slices; mg_* are
+// division magics ceil(2^31 / d) for d = lc, the last chunk, the tile width and the
+// last tile's width; smem = dynamic shared memory in bytes.
 struct PwJob {
     const u32 *A, *B;
     u32 *C;
     int m, n, k, L;
+    int bi, bk, ns, lc, nbk, ntile, smem;
+    u32 mg_lc, mg_lt, mg_cb, mg_ct;
     PrimeDev P;
 };
 // Garner CRT of K residue planes into values mod p.
@@ -155,14 +162,11 @@ cudaError_t launch_ntt_inv_block(const JobPack<InvJob> &pk, int lg, cudaStream_t
 cudaError_t launch_ntt_fwd_cols(const JobPack<ColJob> &pk, int lg, cudaStream_t st, long long *launches);
 cudaError_t launch_ntt_inv_cols(const JobPack<ColJob> &pk, int lg, cudaStream_t st, long long *launches);
 cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
+int pw_plan(PwJob &j);
 cudaError_t launch_crt(const JobPack<CrtJob> &pk, cudaStream_t st, long long *launches);
 cudaError_t launch_pointwise_tc(const JobPack<PwJob> &pk, int *status, cudaStream_t st, long long *launches);
 bool tc_supported(const PwJob &j);
-cudaError_t launch_pointwise_s(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
-bool pws_supported(const PwJob &j);
-int pws_blocks(const PwJob &j);
 int tc_blocks(const PwJob &j);
 int fwd_block_threads(int lg);
 int blocks_per_entry_cols(int lg);
-int pw_blocks(const PwJob &j);
 int crt_blocks(const CrtJob &j);

@@ -238,9 +238,11 @@ extern "C" int pmat_mul_noalloc(uint64_t p, int w, int m, int n, int k, const vo
         JobPack<PwJob> pk; pk.njobs = 0; pk.blk_start[0] = 0;
         for (int i = 0; i < K; i++) {
             PwJob j;
+            memset(&j, 0, sizeof(j));
             j.A = (u32 *)((char *)Ah + i * bA); j.B = (u32 *)((char *)Bh + i * bB); j.C = (u32 *)((char *)Ch + i * bC);
             j.m = m; j.n = n; j.k = k; j.L = (int)L; j.P = P[i];
-            add(pk, j, pw_blocks(j));
+            const int nb = pw_plan(j);
+            add(pk, j, nb);
         }
         if (launch_pointwise(pk, st, &launches) != cudaSuccess) return PM_ECUDA;
     }

@@ -3,10 +3,11 @@
 //
 // Pointwise: at every evaluation point j, C_j = A_j B_j mod q (Sec. 2,
 // "Polynomial matrix multiplication": the n^omega d term of the cost).  This
-// is the CUDA-core form: each thread owns one point and a 4 x 8 tile of
-// outputs; 30-bit residues multiply into 64-bit lazy accumulators (16 terms
-// below 2^64, one mad.wide.u32 each), folded mod q every 16 terms.  Loads are coalesced across the
-// points of a warp (the transform domain is entry-major, point-minor).
+// is the CUDA-core form: a block takes 8 consecutive points and stages the
+// residues it needs in shared memory; each thread owns one point and a 4 x 8
+// tile of outputs, multiplying 30-bit residues into 64-bit lazy accumulators
+// (a carry chain of two 32-bit multiply-adds per product) folded mod q every
+// 15 products.
 //
 // CRT: for moduli without suitable roots of unity the product is lifted to
 // Z[x] and computed modulo K NTT primes (Sec. 2, "3-primes multiplication";
@@ -15,9 +16,15 @@
 // Horner pass in F_p reduces it mod p.
 #include "common.cuh"
 
-#define PW_TI 4      // output rows per thread
-#define PW_TK 8      // output columns per thread
-#define PW_PTS 128   // points (threads) per block
+#define PS_PTS 8        // points per block
+#define PS_ROW 9        // shared-memory words per staged entry: 8 points + 1 pad
+#define PS_THREADS 256  // 8 warps = 32 slots of 8 lanes (one lane per point)
+#define PS_LC 32        // inner-dimension entries staged per chunk
+#define PS_PA 290       // A-row pitch (words): >= 32 * 9 and = 2 mod 8, so thread tiles
+                        // 4 rows apart start 8 banks apart
+#define PS_PB 289       // B-column pitch (words, B staged column-major): odd, so thread
+                        // tiles 8 columns apart start 8 banks apart
+#define PS_WORDS 28160  // shared-memory budget per block (110 KB: 2 blocks per SM)
 
 __device__ __forceinline__ int find_job_pw(const int *blk_start, int b)
 {
@@ -26,201 +33,241 @@ __device__ __forceinline__ int find_job_pw(const int *blk_start, int b)
     return j;
 }
 
-int pw_blocks(const PwJob &j)
+static u32 magic31(int d) { return (u32)(((1ull << 31) + d - 1) / d); }
+
+// Block plan.  The m x k output is cut into block tiles of bi x bk thread tiles
+// (4 x 8 outputs each, bi bk <= 32 slots), chosen to minimise the lanes spent on
+// thread tiles plus the entries staged, within the shared-memory budget; the inner
+// dimension n is staged PS_LC entries at a time and, when a block tile leaves slots
+// free, each chunk is split into ns contiguous slices whose partial sums are added
+// at the end.  Returns the block count.
+int pw_plan(PwJob &j)
 {
-    const int npb = (j.L + PW_PTS - 1) / PW_PTS;
-    return npb * ((j.m + PW_TI - 1) / PW_TI) * ((j.k + PW_TK - 1) / PW_TK);
-}
-
-__device__ __forceinline__ void mad_wide(u64 &acc, u32 a, u32 b)
-{
-    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
-}
-
-// One thread: one point, a PW_TI x PW_TK tile of outputs.  Rows / columns past
-// the matrix edge read a valid row (the last one) and are not stored, so the
-// inner loop carries no predicates.
-__global__ void __launch_bounds__(PW_PTS) k_pointwise(const __grid_constant__ JobPack<PwJob> pk)
-{
-    const int b = blockIdx.x;
-    const int jb = find_job_pw(pk.blk_start, b);
-    const PwJob &J = pk.jobs[jb];
-    const int m = J.m, n = J.n, k = J.k, Li = J.L;
-    const u32 q = J.P.q, q2 = J.P.q2, r32 = J.P.r32, r32s = J.P.r32s, ones = J.P.ones;
-    int rel = b - pk.blk_start[jb];
-    const int npb = (Li + PW_PTS - 1) / PW_PTS, ntk = (k + PW_TK - 1) / PW_TK;
-    const int pb = rel % npb;
-    rel /= npb;
-    const int tk = rel % ntk, ti = rel / ntk;
-    const int pt = pb * PW_PTS + threadIdx.x;
-    if (pt >= Li) return;
-    const int i0 = ti * PW_TI, k0 = tk * PW_TK;
-    const i64 L = Li;
-
-    const u32 *pa[PW_TI], *pbp[PW_TK];
-#pragma unroll
-    for (int a = 0; a < PW_TI; a++) pa[a] = J.A + (i64)min(i0 + a, m - 1) * n * L + pt;
-#pragma unroll
-    for (int c = 0; c < PW_TK; c++) pbp[c] = J.B + (i64)min(k0 + c, k - 1) * L + pt;
-    const i64 sb = (i64)k * L;   // B stride between consecutive l
-
-    u32 part[PW_TI][PW_TK];
-#pragma unroll
-    for (int a = 0; a < PW_TI; a++)
-#pragma unroll
-        for (int c = 0; c < PW_TK; c++) part[a][c] = 0;
-
-    for (int l0 = 0; l0 < n; l0 += 16) {
-        const int lend = min(n, l0 + 16);
-        u64 acc[PW_TI][PW_TK];
-#pragma unroll
-        for (int a = 0; a < PW_TI; a++)
-#pragma unroll
-            for (int c = 0; c < PW_TK; c++) acc[a][c] = 0;
-        for (int l = l0; l < lend; l++) {
-            u32 av[PW_TI], bv[PW_TK];
-#pragma unroll
-            for (int a = 0; a < PW_TI; a++) av[a] = __ldg(pa[a] + (i64)l * L);
-#pragma unroll
-            for (int c = 0; c < PW_TK; c++) bv[c] = __ldg(pbp[c] + (i64)l * sb);
-#pragma unroll
-            for (int a = 0; a < PW_TI; a++)
-#pragma unroll
-                for (int c = 0; c < PW_TK; c++) mad_wide(acc[a][c], av[a], bv[c]);
+    const int nti = (j.m + 3) / 4, ntk = (j.k + 7) / 8;
+    long long best = -1;
+    for (int bi = 1; bi <= nti && bi <= 32; bi++)
+        for (int bk = 1; bk <= ntk && bi * bk <= 32; bk++) {
+            if (bi * 4 * PS_PA + bk * 8 * PS_PB > PS_WORDS) continue;
+            const long long nb = (long long)((nti + bi - 1) / bi) * ((ntk + bk - 1) / bk);
+            const long long cost = nb * (((bi * bk + 3) / 4) * 4 * 64 + (bi * 4 + bk * 8) * 16 + 64);
+            if (best < 0 || cost < best) { best = cost; j.bi = bi; j.bk = bk; }
         }
-        // fold: acc < 16 q^2 < 2^64; acc = hi 2^32 + lo -> [0, q)
-#pragma unroll
-        for (int a = 0; a < PW_TI; a++)
-#pragma unroll
-            for (int c = 0; c < PW_TK; c++) {
-                const u32 hi = (u32)(acc[a][c] >> 32), lo = (u32)acc[a][c];
-                u32 s2 = shoup_mul(hi, r32, r32s, q) + shoup_mul(lo, 1u, ones, q);    // < 4q
-                s2 = csub(csub(s2, q2), q);
-                part[a][c] = csub(part[a][c] + s2, q);
-            }
-    }
-#pragma unroll
-    for (int a = 0; a < PW_TI; a++)
-#pragma unroll
-        for (int c = 0; c < PW_TK; c++)
-            if (i0 + a < m && k0 + c < k) J.C[((i64)(i0 + a) * k + k0 + c) * L + pt] = part[a][c];
+    const int items = j.bi * j.bk, rb = j.bi * 4, cb = j.bk * 8;
+    j.lc = j.n < PS_LC ? j.n : PS_LC;
+    j.ns = 1;                                                  // slices of >= 8 products per chunk
+    while (items * j.ns * 2 <= 32 && j.ns * 2 * 8 <= j.lc) j.ns *= 2;
+    const int stage = rb * PS_PA + cb * PS_PB, red = j.ns * rb * cb * PS_ROW;
+    j.smem = (stage > red ? stage : red) * 4;
+    j.nbk = (ntk + j.bk - 1) / j.bk;
+    j.ntile = ((nti + j.bi - 1) / j.bi) * j.nbk;
+    const int nch = (j.n + j.lc - 1) / j.lc;
+    j.mg_lc = magic31(j.lc);
+    j.mg_lt = magic31(j.n - (nch - 1) * j.lc);
+    j.mg_cb = magic31(cb);
+    j.mg_ct = magic31(j.k - (j.nbk - 1) * cb);
+    return (j.L / PS_PTS) * j.ntile;
 }
 
-cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches)
+template <int OFF>
+__device__ __forceinline__ u32 lds(u32 addr)
 {
-    k_pointwise<<<pk.blk_start[pk.njobs], PW_PTS, 0, st>>>(pk);
-    ++*launches;
-    return cudaGetLastError();
+    u32 v;
+    asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(addr), "n"(OFF));
+    return v;
 }
 
-// ------------------------------------------------------------------ staged CUDA-core form
-// A block takes 8 consecutive points of one prime.  The residues of every entry at
-// those points are staged in shared memory (32-byte coalesced reads; rows padded to
-// 9 words), then each thread computes a 4 x 8 output tile at one point: warp w owns
-// output rows 4w.., lane = 8 * (column tile) + point.  Within a warp the A reads are
-// broadcasts and the B reads fall in distinct banks.  Outputs are staged and
-// written back 32 bytes per entry.  Needs m n, n k, m k <= 1024 (else k_pointwise).
-#define PS_PTS 8
-#define PS_ROW 9
-#define PS_THREADS 256
+// One inner-dimension step l + U of a 4 x 8 thread tile: A rows at fa + a PS_PA words,
+// B columns at fb + c PS_PB words, consecutive l 9 words apart; each product goes into
+// a 64-bit (hi, lo) accumulator through a carry chain.
+template <int U>
+__device__ __forceinline__ void pw_step(u32 (&alo)[4][8], u32 (&ahi)[4][8], u32 fa, u32 fb)
+{
+    u32 av[4], bv[8];
+    av[0] = lds<U * 36>(fa);
+    av[1] = lds<U * 36 + 4 * PS_PA>(fa);
+    av[2] = lds<U * 36 + 8 * PS_PA>(fa);
+    av[3] = lds<U * 36 + 12 * PS_PA>(fa);
+    bv[0] = lds<U * 36>(fb);
+    bv[1] = lds<U * 36 + 4 * PS_PB>(fb);
+    bv[2] = lds<U * 36 + 8 * PS_PB>(fb);
+    bv[3] = lds<U * 36 + 12 * PS_PB>(fb);
+    bv[4] = lds<U * 36 + 16 * PS_PB>(fb);
+    bv[5] = lds<U * 36 + 20 * PS_PB>(fb);
+    bv[6] = lds<U * 36 + 24 * PS_PB>(fb);
+    bv[7] = lds<U * 36 + 28 * PS_PB>(fb);
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int c = 0; c < 8; c++)
+            asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;"
+                : "+r"(alo[a][c]), "+r"(ahi[a][c]) : "r"(av[a]), "r"(bv[c]));
+}
 
-int pws_blocks(const PwJob &j) { return (j.L + PS_PTS - 1) / PS_PTS; }
-bool pws_supported(const PwJob &j) { return j.m * j.n <= 1024 && j.n * j.k <= 1024 && j.m * j.k <= 1024 && j.L >= 16; }
-
-__global__ void __launch_bounds__(PS_THREADS, 2) k_pointwise_s(const __grid_constant__ JobPack<PwJob> pk)
+// One block: 8 consecutive points of one transform and one block tile of the output.
+// Thread (warp w, lane) has slot 4 w + lane / 8 -> (slice, thread tile) and point
+// lane % 8.  Per chunk of <= 32 inner entries, the A rows and B columns of the block
+// tile are staged (32-byte coalesced reads: the 8 points of an entry, four 16-byte
+// loads in flight per thread), then every live slot accumulates its 4 x 8 tile over
+// its slice of the chunk.  Thread-tile rows / columns past the matrix edge read
+// unused staging words and are never stored, so the inner loop carries no
+// predicates.  Partial tiles go through shared memory, slices are summed, and each
+// entry's 8 points are written back as two 16-byte stores.
+//
+// Accumulation: acc < 2^32 + 2q + 16 (q - 1)^2 < 2^64 for q < 2^30, so after every 16
+// products acc is folded lazily to lo + (hi 2^32 mod q) < 2^32 + 2q, and reduced to
+// [0, q) once at the end.
+__global__ void __launch_bounds__(PS_THREADS, 2) k_pointwise(const __grid_constant__ JobPack<PwJob> pk)
 {
     extern __shared__ __align__(16) u32 sms[];
     const int b = blockIdx.x;
     const int jb = find_job_pw(pk.blk_start, b);
     const PwJob &J = pk.jobs[jb];
-    const int m = J.m, n = J.n, k = J.k, L = J.L;
+    const int n = J.n, k = J.k, L = J.L, ns = J.ns, lc = J.lc, bk = J.bk;
     const u32 q = J.P.q, q2 = J.P.q2, r32 = J.P.r32, r32s = J.P.r32s, ones = J.P.ones;
-    const int j0 = (b - pk.blk_start[jb]) * PS_PTS;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int eA = m * n, eB = n * k, eC = m * k;
-    u32 *rA = sms, *rB = sms + eA * PS_ROW, *rC = rB + eB * PS_ROW;
+    const int rel = b - pk.blk_start[jb];
+    const int tile = rel % J.ntile, j0 = (rel / J.ntile) * PS_PTS;
+    const int rb = J.bi * 4, cb = bk * 8;
+    const int r0 = (tile / J.nbk) * rb, c0 = (tile % J.nbk) * cb;
+    const int rows = min(J.m - r0, rb), cols = min(k - c0, cb);
+    const int tid = threadIdx.x, lane = tid & 31, pp = lane & 7;
+    const int slot = (tid >> 5) * 4 + (lane >> 3), items = J.bi * bk;
+    const int item = slot % items, slice = slot / items;
+    const bool live = slice < ns;
+    const int ti = item / bk, tk = item % bk;
+    u32 *rA = sms, *rB = sms + rb * PS_PA;
+    const u32 sA = (u32)__cvta_generic_to_shared(rA) + (ti * 4 * PS_PA + pp) * 4;
+    const u32 sB = (u32)__cvta_generic_to_shared(rB) + (tk * 8 * PS_PB + pp) * 4;
 
-    for (int x = tid; x < (eA + eB) * 2; x += PS_THREADS) {
-        const int e = x >> 1, h = x & 1;
-        const u32 *src = e < eA ? J.A + (i64)e * L : J.B + (i64)(e - eA) * L;
-        const uint4 v = *(const uint4 *)(src + j0 + 4 * h);
-        u32 *dst = (e < eA ? rA + e * PS_ROW : rB + (e - eA) * PS_ROW) + 4 * h;
-        dst[0] = v.x; dst[1] = v.y; dst[2] = v.z; dst[3] = v.w;
-    }
-    __syncthreads();
+    u32 alo[4][8], ahi[4][8];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int c = 0; c < 8; c++) { alo[a][c] = 0; ahi[a][c] = 0; }
+    bool lazy = false;                                         // accumulators not yet in [0, q)
 
-    const int pp = lane & 7, tkl = lane >> 3;                 // point, column tile within the warp
-    const int nti = (m + PW_TI - 1) / PW_TI, ntk = (k + PW_TK - 1) / PW_TK;
-    // work items: (row tile ti, column-tile group tg); a warp takes 4 column tiles of one row tile
-    const int ngroups = (ntk + 3) / 4;
-    for (int item = warp; item < nti * ngroups; item += PS_THREADS / 32) {
-        const int ti = item / ngroups, tk = (item % ngroups) * 4 + tkl;
-        const int i0 = ti * PW_TI, k0 = tk * PW_TK;
-        const bool live = tk < ntk;
-        int oa[PW_TI], ob[PW_TK];                              // 32-bit shared-memory offsets
+    for (int l0 = 0; l0 < n; l0 += lc) {
+        const int lcv = min(lc, n - l0);
+        if (l0) __syncthreads();                               // the previous chunk is consumed
+        // stage: entry e < nA is A (row, l) = divmod(e, lcv), else B (l, col) = divmod(e - nA, cols)
+        {
+            const int nA = rows * lcv, tot = (nA + lcv * cols) * 2;
+            const u32 mA = lcv == lc ? J.mg_lc : J.mg_lt, mB = cols == cb ? J.mg_cb : J.mg_ct;
+            for (int x0 = tid; x0 < tot; x0 += 4 * PS_THREADS) {
+                uint4 v[4];
+                u32 *d[4];
 #pragma unroll
-        for (int a = 0; a < PW_TI; a++) oa[a] = min(i0 + a, m - 1) * n * PS_ROW + pp;
-#pragma unroll
-        for (int c = 0; c < PW_TK; c++) ob[c] = min(k0 + c, k - 1) * PS_ROW + pp;
-        const int sbk = k * PS_ROW;
-        // 64-bit accumulators as (hi, lo) words with a carry chain per product;
-        // acc < q + 15 (q - 1)^2 < 2^64: fold to [0, q) every 15 products
-        u32 alo[PW_TI][PW_TK], ahi[PW_TI][PW_TK];
-#pragma unroll
-        for (int a = 0; a < PW_TI; a++)
-#pragma unroll
-            for (int c = 0; c < PW_TK; c++) { alo[a][c] = 0; ahi[a][c] = 0; }
-        for (int l0 = 0; l0 < n; l0 += 15) {
-            const int lend = min(n, l0 + 15);
-#pragma unroll 3
-            for (int l = l0; l < lend; l++) {
-                u32 av[PW_TI], bv[PW_TK];
-#pragma unroll
-                for (int a = 0; a < PW_TI; a++) av[a] = rA[oa[a] + l * PS_ROW];
-#pragma unroll
-                for (int c = 0; c < PW_TK; c++) bv[c] = rB[ob[c] + l * sbk];
-#pragma unroll
-                for (int a = 0; a < PW_TI; a++)
-#pragma unroll
-                    for (int c = 0; c < PW_TK; c++)
-                        asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;"
-                            : "+r"(alo[a][c]), "+r"(ahi[a][c]) : "r"(av[a]), "r"(bv[c]));
-            }
-#pragma unroll
-            for (int a = 0; a < PW_TI; a++)
-#pragma unroll
-                for (int c = 0; c < PW_TK; c++) {
-                    u32 s2 = shoup_mul(ahi[a][c], r32, r32s, q) + shoup_mul(alo[a][c], 1u, ones, q);
-                    alo[a][c] = csub(csub(s2, q2), q);
-                    ahi[a][c] = 0;
+                for (int i = 0; i < 4; i++) {
+                    const int x = min(x0 + i * PS_THREADS, tot - 1);
+                    const int e = x >> 1, h = x & 1;
+                    const bool isA = e < nA;
+                    const int f = isA ? e : e - nA, dv = isA ? lcv : cols;
+                    const int qt = (int)__umulhi((u32)f << 1, isA ? mA : mB), rm = f - qt * dv;
+                    const u32 *src = isA ? J.A + (i64)((r0 + qt) * n + l0 + rm) * L
+                                         : J.B + (i64)((l0 + qt) * k + c0 + rm) * L;
+                    d[i] = (isA ? rA + qt * PS_PA + rm * PS_ROW : rB + rm * PS_PB + qt * PS_ROW) + 4 * h;
+                    v[i] = __ldg((const uint4 *)(src + j0 + 4 * h));
                 }
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                    if (x0 + i * PS_THREADS < tot) { d[i][0] = v[i].x; d[i][1] = v[i].y; d[i][2] = v[i].z; d[i][3] = v[i].w; }
+            }
         }
+        __syncthreads();
         if (live) {
+            // this slice's contiguous share of the chunk, in groups of 16 products
+            const int per = (lcv + ns - 1) / ns, lb = slice * per, le = min(lcv, lb + per);
+            u32 fa = sA + lb * PS_ROW * 4, fb = sB + lb * PS_ROW * 4;
+            for (int g = lb; g < le; g += 16) {
+                int cnt = min(le, g + 16) - g;
+                for (; cnt >= 8; cnt -= 8) {
+                    pw_step<0>(alo, ahi, fa, fb); pw_step<1>(alo, ahi, fa, fb);
+                    pw_step<2>(alo, ahi, fa, fb); pw_step<3>(alo, ahi, fa, fb);
+                    pw_step<4>(alo, ahi, fa, fb); pw_step<5>(alo, ahi, fa, fb);
+                    pw_step<6>(alo, ahi, fa, fb); pw_step<7>(alo, ahi, fa, fb);
+                    fa += 8 * PS_ROW * 4; fb += 8 * PS_ROW * 4;
+                }
+                for (; cnt > 0; cnt--) {
+                    pw_step<0>(alo, ahi, fa, fb);
+                    fa += PS_ROW * 4; fb += PS_ROW * 4;
+                }
+                if (g + 16 < le || l0 + lc < n) {
+                    // more products follow: acc <- lo + (hi 2^32 mod q), the carry into hi kept
 #pragma unroll
-            for (int a = 0; a < PW_TI; a++)
+                    for (int a = 0; a < 4; a++)
 #pragma unroll
-                for (int c = 0; c < PW_TK; c++)
-                    if (i0 + a < m && k0 + c < k) rC[((i0 + a) * k + k0 + c) * PS_ROW + pp] = alo[a][c];
+                        for (int c = 0; c < 8; c++) {
+                            const u32 t = shoup_mul(ahi[a][c], r32, r32s, q);
+                            asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, 0, 0;" : "+r"(alo[a][c]), "=r"(ahi[a][c]) : "r"(t));
+                        }
+                    lazy = true;
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 4; a++)
+#pragma unroll
+                        for (int c = 0; c < 8; c++) {
+                            const u32 s2 = shoup_mul(ahi[a][c], r32, r32s, q) + shoup_mul(alo[a][c], 1u, ones, q);
+                            alo[a][c] = csub(csub(s2, q2), q);
+                            ahi[a][c] = 0;
+                        }
+                    lazy = false;
+                }
+            }
         }
     }
+    if (lazy) {                                                // a slice empty in the last chunk
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                const u32 s2 = shoup_mul(ahi[a][c], r32, r32s, q) + shoup_mul(alo[a][c], 1u, ones, q);
+                alo[a][c] = csub(csub(s2, q2), q);
+            }
+    }
     __syncthreads();
-    for (int x = tid; x < eC * 2; x += PS_THREADS) {
+    // partial tiles: red[slice][row][col][point]
+    u32 *red = sms;
+    if (live) {
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                const int r = ti * 4 + a, cc = tk * 8 + c;
+                if (r < rows && cc < cols) red[((slice * rb + r) * cb + cc) * PS_ROW + pp] = alo[a][c];
+            }
+    }
+    __syncthreads();
+    const u32 mC = cols == cb ? J.mg_cb : J.mg_ct;
+    for (int x = tid; x < rows * cols * 2; x += PS_THREADS) {
         const int e = x >> 1, h = x & 1;
-        const u32 *s4 = rC + e * PS_ROW + 4 * h;
-        *(uint4 *)(J.C + (i64)e * L + j0 + 4 * h) = make_uint4(s4[0], s4[1], s4[2], s4[3]);
+        const int r = (int)__umulhi((u32)e << 1, mC), c = e - r * cols;
+        uint4 o;
+        if (ns == 1) {
+            const u32 *s4 = red + (r * cb + c) * PS_ROW + 4 * h;
+            o = make_uint4(s4[0], s4[1], s4[2], s4[3]);
+        } else {
+            u32 w[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                u64 s = 0;                                     // ns <= 32 terms < q: s < 2^35
+                for (int sl = 0; sl < ns; sl++) s += red[((sl * rb + r) * cb + c) * PS_ROW + 4 * h + t];
+                const u32 s2 = shoup_mul((u32)(s >> 32), r32, r32s, q) + shoup_mul((u32)s, 1u, ones, q);
+                w[t] = csub(csub(s2, q2), q);
+            }
+            o = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        *(uint4 *)(J.C + (i64)((r0 + r) * k + c0 + c) * L + j0 + 4 * h) = o;
     }
 }
 
-cudaError_t launch_pointwise_s(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches)
+cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches)
 {
     int mx = 0;
-    for (int i = 0; i < pk.njobs; i++) {
-        const PwJob &j = pk.jobs[i];
-        const int t = (j.m * j.n + j.n * j.k + j.m * j.k) * PS_ROW * 4;
-        mx = t > mx ? t : mx;
+    for (int i = 0; i < pk.njobs; i++) mx = pk.jobs[i].smem > mx ? pk.jobs[i].smem : mx;
+    if (mx > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_pointwise, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e != cudaSuccess) return e;
     }
-    if (mx > 48 * 1024) cudaFuncSetAttribute(k_pointwise_s, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    k_pointwise_s<<<pk.blk_start[pk.njobs], PS_THREADS, mx, st>>>(pk);
+    k_pointwise<<<pk.blk_start[pk.njobs], PS_THREADS, mx, st>>>(pk);
     ++*launches;
     return cudaGetLastError();
 }

@@ -67,6 +67,13 @@ CASES = [
     (P60, 8, 2, 3, 2, 4000, 4500),        # L = 2^13, one CTA per transform
     (synth.P998, 4, 2, 2, 3, 5000, 4000),  # L = 2^14: column path
     (P60, 8, 2, 2, 1, 9000, 7000),         # L = 2^14, 5 primes
+    # pointwise block plans: a slice left empty in the last inner chunk (n = 32 + 5),
+    # 2 x 2 block tiles with two chunks, uneven tiles, several column tiles, 4 slices
+    (P60, 8, 4, 37, 8, 50, 40),
+    (synth.P998, 4, 64, 64, 64, 40, 30),
+    (P60, 8, 36, 57, 51, 70, 50),
+    (P62, 8, 33, 2, 70, 25, 25),
+    (97, 4, 2, 300, 2, 30, 20),
 ]
 
 
