@@ -13,6 +13,9 @@ of the paper its C function follows:
 * ``mbasis1``: Algorithm 1.  ``mbasis``: Algorithm 2.  ``pmbasis``: Algorithm 3.
 * ``univ_resultant`` / ``bivariate_resultant``: Sec. 5.2, the direct
   evaluation / Euclid / interpolation method.
+* ``matinv`` / ``inv_trunc``: Sec. 4 (linear system solving by lifting): the
+  inverse of a constant matrix and the truncated inverse A^-1 mod x^t, by
+  definition.
 """
 from __future__ import annotations
 
@@ -56,6 +59,10 @@ def lib():
         L.orc_powmod.argtypes = [u64, u64, u64]
         L.orc_invmod.restype = u64
         L.orc_invmod.argtypes = [u64, u64]
+        L.orc_matinv.restype = i32
+        L.orc_matinv.argtypes = [u64, i32, P, P]
+        L.orc_inv_trunc.restype = i32
+        L.orc_inv_trunc.argtypes = [u64, i32, P, i64, i64, P]
         _lib = L
     return _lib
 
@@ -161,6 +168,33 @@ def bivariate_resultant(p, f, g, threads=None):
     if rc[0] != 0:
         raise ValueError("too few evaluation points in F_p")
     return R
+
+
+class SingularError(ValueError):
+    """A constant matrix (or A(0)) is not invertible modulo p."""
+
+
+def matinv(p, M):
+    """Inverse of the n x n matrix M over F_p (p prime)."""
+    M = _u64(M)
+    n = M.shape[0]
+    out = np.zeros((n, n), dtype=np.uint64)
+    if lib().orc_matinv(p, n, _ptr(M), _ptr(out)):
+        raise SingularError("singular matrix mod p")
+    return out
+
+
+def inv_trunc(p, A, t, threads=None):
+    """A^-1 mod x^t (A: n x n x dA with A(0) invertible mod the prime p): n x n x t."""
+    A = _u64(A)
+    n, n2, dA = A.shape
+    assert n == n2
+    X = np.zeros((n, n, t), dtype=np.uint64)
+    rc = []
+    _with_threads(threads, lambda: rc.append(lib().orc_inv_trunc(p, n, _ptr(A), dA, t, _ptr(X))))
+    if rc[0]:
+        raise SingularError("A(0) is singular mod p")
+    return X
 
 
 def powmod(a, e, p):

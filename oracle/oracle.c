@@ -33,6 +33,12 @@
  *                    Sec. 5.2, the "Direct" method: evaluate in x, take
  *                    univariate resultants in y by the Euclidean algorithm,
  *                    interpolate (Newton divided differences).
+ *   orc_matinv / orc_inv_trunc
+ *                    Sec. 4, "Linear system solving": the truncated inverse
+ *                    S = A^-1 mod x^t of a polynomial matrix with A(0)
+ *                    invertible, taken by its definition -- the power series
+ *                    X with A.X = I mod x^t, coefficient by coefficient:
+ *                    X_0 = A_0^-1, X_j = -A_0^-1 (A_1 X_{j-1} + ... + A_j X_0).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -430,5 +436,85 @@ int orc_bivariate_resultant(u64 p, int dxf, int dyf, const u64 *f, int dxg, int 
     }
     free(c2);
     free(xs); free(vs); free(inv);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Truncated inverse (Sec. 4, linear system solving by lifting)         */
+/* ------------------------------------------------------------------ */
+
+/* Inverse of the n x n constant matrix M (row-major) by Gauss-Jordan
+ * elimination over F_p (p prime) on [M | I]: pivot = the first row at or
+ * below the current one with a nonzero entry in the column.  Returns 0 and
+ * writes Minv, or 1 if M is singular. */
+int orc_matinv(u64 p, int n, const u64 *M, u64 *Minv)
+{
+    int w = 2 * n;
+    u64 *T = (u64 *)malloc(sizeof(u64) * (size_t)n * w);
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < w; j++)
+            T[(size_t)i * w + j] = j < n ? M[(size_t)i * n + j] % p : (j - n == i ? 1 % p : 0);
+    for (int c = 0; c < n; c++) {
+        int r = -1;
+        for (int i = c; i < n; i++) if (T[(size_t)i * w + c]) { r = i; break; }
+        if (r < 0) { free(T); return 1; }
+        if (r != c)
+            for (int j = 0; j < w; j++) {
+                u64 t = T[(size_t)r * w + j];
+                T[(size_t)r * w + j] = T[(size_t)c * w + j];
+                T[(size_t)c * w + j] = t;
+            }
+        u64 iv = orc_invmod(T[(size_t)c * w + c], p);
+        for (int j = 0; j < w; j++) T[(size_t)c * w + j] = f_mul(T[(size_t)c * w + j], iv, p);
+        for (int i = 0; i < n; i++) {
+            if (i == c) continue;
+            u64 f = T[(size_t)i * w + c];
+            if (!f) continue;
+            for (int j = 0; j < w; j++)
+                T[(size_t)i * w + j] = f_sub(T[(size_t)i * w + j], f_mul(f, T[(size_t)c * w + j], p), p);
+        }
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) Minv[(size_t)i * n + j] = T[(size_t)i * w + n + j];
+    free(T);
+    return 0;
+}
+
+/* X (n x n, length t) = A^-1 mod x^t for A (n x n, length dA), by the
+ * recurrence X_j = -A_0^-1 sum_{i=1..min(j, dA-1)} A_i X_{j-i}.  Returns 0, or
+ * 1 if A(0) is singular (X untouched). */
+int orc_inv_trunc(u64 p, int n, const u64 *A, i64 dA, i64 t, u64 *X)
+{
+    size_t nn = (size_t)n * n;
+    u64 *A0 = (u64 *)calloc(nn, sizeof(u64)), *A0i = (u64 *)calloc(nn, sizeof(u64));
+    u64 *Sj = (u64 *)malloc(sizeof(u64) * nn);
+    for (size_t e = 0; e < nn; e++) A0[e] = A[e * dA];
+    if (orc_matinv(p, n, A0, A0i)) { free(A0); free(A0i); free(Sj); return 1; }
+    memset(X, 0, sizeof(u64) * nn * t);
+    for (size_t e = 0; e < nn; e++) X[e * t] = A0i[e];
+    for (i64 j = 1; j < t; j++) {
+        /* S_j = sum_{i=1..min(j, dA-1)} A_i X_{j-i} */
+#pragma omp parallel for schedule(static) if (nn >= 64)
+        for (size_t e = 0; e < nn; e++) {
+            int r = (int)(e / n), c = (int)(e % n);
+            u128 acc = 0;
+            int cnt = 0;
+            u64 s = 0;
+            for (i64 i = 1; i <= j && i < dA; i++)
+                for (int l = 0; l < n; l++) {
+                    acc += (u128)A[((size_t)r * n + l) * dA + i] * X[((size_t)l * n + c) * t + (j - i)];
+                    if (++cnt == 256) { s = f_add(s, (u64)(acc % p), p); acc = 0; cnt = 0; }
+                }
+            Sj[e] = f_add(s, (u64)(acc % p), p);
+        }
+        /* X_j = -A_0^-1 S_j */
+        for (int r = 0; r < n; r++)
+            for (int c = 0; c < n; c++) {
+                u64 v = 0;
+                for (int l = 0; l < n; l++) v = f_add(v, f_mul(A0i[(size_t)r * n + l], Sj[(size_t)l * n + c], p), p);
+                X[((size_t)r * n + c) * t + j] = f_neg(v, p);
+            }
+    }
+    free(A0); free(A0i); free(Sj);
     return 0;
 }
