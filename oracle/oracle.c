@@ -498,14 +498,10 @@ int orc_inv_trunc(u64 p, int n, const u64 *A, i64 dA, i64 t, u64 *X)
         for (size_t e = 0; e < nn; e++) {
             int r = (int)(e / n), c = (int)(e % n);
             u128 acc = 0;
-            int cnt = 0;
-            u64 s = 0;
             for (i64 i = 1; i <= j && i < dA; i++)
-                for (int l = 0; l < n; l++) {
-                    acc += (u128)A[((size_t)r * n + l) * dA + i] * X[((size_t)l * n + c) * t + (j - i)];
-                    if (++cnt == 256) { s = f_add(s, (u64)(acc % p), p); acc = 0; cnt = 0; }
-                }
-            Sj[e] = f_add(s, (u64)(acc % p), p);
+                for (int l = 0; l < n; l++)
+                    acc_add(&acc, A[((size_t)r * n + l) * dA + i], X[((size_t)l * n + c) * t + (j - i)], p);
+            Sj[e] = (u64)(acc % p);
         }
         /* X_j = -A_0^-1 S_j */
         for (int r = 0; r < n; r++)

@@ -16,7 +16,8 @@ import synth
 from tests import pyref
 
 P60 = 1152921504606846883
-PRIMES = [2, 3, 97, synth.P998, P60]
+P62 = 4611686018427387847
+PRIMES = [2, 3, 97, synth.P998, P60, P62]
 
 
 def _rand(rnd, p, r, c, length):
@@ -54,7 +55,7 @@ def test_matinv_against_determinant_and_product(p):
 
 
 @pytest.mark.parametrize("p", PRIMES)
-@pytest.mark.parametrize("n,dA,t", [(1, 1, 1), (1, 4, 9), (2, 3, 7), (3, 5, 12), (4, 9, 6)])
+@pytest.mark.parametrize("n,dA,t", [(1, 1, 1), (1, 4, 9), (2, 3, 7), (3, 5, 12), (4, 9, 6), (2, 40, 33)])
 def test_inverse_defining_identity_both_sides(p, n, dA, t):
     rnd = random.Random(hash((p, n, dA, t)) & 0xffff)
     A = _rand(rnd, p, n, n, dA)
@@ -68,7 +69,7 @@ def test_inverse_defining_identity_both_sides(p, n, dA, t):
     assert np.array_equal(pad(AX), I) and np.array_equal(pad(XA), I)
 
 
-@pytest.mark.parametrize("p", [97, synth.P998, P60])
+@pytest.mark.parametrize("p", [97, synth.P998, P60, P62])
 def test_scalar_geometric_series(p):
     a = 123456789 % p
     A = np.array([[[1, (p - a) % p]]], dtype=np.uint64)       # 1 - a x
