@@ -43,9 +43,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the PM-Basis / batched / resultant timings")
-    ap.add_argument("--extra", default="pm_basis,resultant,batched",
-                    help="comma-separated subset of pm_basis, resultant, batched")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the PM-Basis / batched / resultant / inverse timings")
+    ap.add_argument("--extra", default="pm_basis,resultant,batched,inverse",
+                    help="comma-separated subset of pm_basis, resultant, batched, inverse")
     return ap.parse_args()
 
 
@@ -165,9 +166,10 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------- other workloads (reported under "extra")
-def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched"), reps=3):
+def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"), reps=3):
     """PM-Basis (F 32x16, order 8192, 60-bit p), 512 batched uneven products, resultants
-    (deg_x = deg_y = 150, 1 prime and 16 primes): ms per call, CUDA events on the stream."""
+    (deg_x = deg_y = 150, 1 prime and 16 primes), the truncated inverse of a 32x32 matrix of
+    degree < 4096 mod x^4096 (60-bit p): ms per call, CUDA events on the stream."""
     import numpy as np
     import torch
     import synth
@@ -216,9 +218,25 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched"), reps=3):
         ms = ev_ms(lambda: pmat.pmat_mul_batched(ctx, dev, outs), 2)
         return {"batched_512_ms": round(ms, 2), "batched_512_launches_per_call": (ctx.launches() - n0) // 3}
 
+    def inverse():
+        W = synth.inverse_w(0)
+        A = pmat.to_device(W["A"])
+        X = torch.empty((32, 32, W["t"]), dtype=A.dtype, device="cuda")
+        run = lambda: pmat.pmat_inv_trunc(ctx, W["p"], A, W["t"], out=X)  # noqa: E731
+        out = {"inv_trunc_32x32_t4096_ms": round(ev_ms(run, reps), 3)}
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
+        ctx.stage_times()
+        run()
+        st = ctx.stage_times()
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
+        ctx.sync()
+        out["inv_trunc_stage_ms"] = {k: round(v[0], 3) for k, v in st.items() if v[1]}
+        return out
+
     out = {}
     with torch.cuda.stream(s):
-        for name, fn in (("pm_basis", pm_basis), ("resultant", resultant), ("batched", batched)):
+        for name, fn in (("pm_basis", pm_basis), ("resultant", resultant), ("batched", batched),
+                         ("inverse", inverse)):
             if name in which:
                 out.update(fn())
     return out

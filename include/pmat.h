@@ -13,6 +13,9 @@
  *                                 Algorithms 1-2 (M-Basis-1, M-Basis)
  *   bivariate_resultant           Sec. 5.2, resultant of bivariate
  *                                 polynomials (the direct method)
+ *   pmat_inv_trunc                Sec. 4, "Linear system solving": the
+ *                                 truncated inverse A^-1 mod x^t by matrix
+ *                                 Newton iteration
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -23,7 +26,7 @@
  *   requires p < 2^62).  Inputs must be reduced into [0, p); outputs are.
  * * p >= 2.  Products are ring operations and accept any such p; pm_basis and
  *   bivariate_resultant need p prime (not checked, as for a field type) and
- *   odd (checked).
+ *   odd (checked); pmat_inv_trunc needs p prime (not checked), 2 allowed.
  * * The caller owns every input and output buffer; outputs must not alias
  *   inputs.  The context owns its workspace, twiddle tables and plans.
  * * All calls are asynchronous and ordered on the context's stream.  A
@@ -47,7 +50,8 @@ extern "C" {
 enum {
     PM_OK = 0,
     PM_EINVAL = 1,       /* bad argument (dimension, length, modulus, width) */
-    PM_EDOMAIN = 2,      /* an input coefficient is not in [0, p) (debug check) */
+    PM_EDOMAIN = 2,      /* an input coefficient is not in [0, p) (debug check), or
+                            A(0) is singular in pmat_inv_trunc (deferred, pm_sync) */
     PM_ENOMEM = 3,       /* device workspace allocation failed */
     PM_ECUDA = 4,        /* a CUDA runtime call or kernel launch failed */
     PM_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
@@ -202,6 +206,18 @@ int pm_basis(pm_ctx *ctx, uint64_t p, int m, int n, const void *F, int64_t lenF,
 int bivariate_resultant(pm_ctx *ctx, int nprimes, const uint64_t *primes,
                         int dxf, int dyf, const void *f, int dxg, int dyg, const void *g,
                         void *R);
+
+/* Truncated inverse (Sec. 4, "Linear system solving", lifting: S = A^-1 mod
+ * x^t by matrix Newton iteration).  A: DEVICE n x n matrix with entries of
+ * length dA (width w); X: DEVICE output, n x n entries of length t, the unique
+ * power series with A.X = I mod x^t.  Newton step k -> 2k: E = coefficients
+ * k..2k-1 of A.X_k (a middle product), X_2k = X_k - x^k (X_k . E mod x^k) (a
+ * truncated product); the constant term is A(0)^-1 by Gauss-Jordan on the
+ * device.  Requires p prime, 1 <= n <= 128, dA >= 1, 1 <= t <= 2^19.  A(0)
+ * singular mod p is found on the device: X is then undefined and pm_sync
+ * returns PM_EDOMAIN.  Asynchronous; uses the context's driver arena. */
+int pmat_inv_trunc(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA,
+                   int64_t t, void *X);
 
 #ifdef __cplusplus
 }

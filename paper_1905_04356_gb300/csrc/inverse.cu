@@ -1,0 +1,175 @@
+// inverse.cu -- truncated inverse of a polynomial matrix (Sec. 4, "Linear
+// system solving": the lifting solver first computes S = A^-1 mod x^t by
+// matrix Newton iteration).
+//
+// Constant term: X_0 = A(0)^-1 by fraction-free Gauss-Jordan in one CTA
+// (Montgomery arithmetic for odd p, bit arithmetic for p = 2), rows divided
+// by their diagonal entries at the end, so one modular inversion per row.
+// Newton step k -> kk = min(2k, t): since A.X_k = I mod x^k,
+//   E = coefficients k .. kk-1 of A.X_k               (middle product)
+//   X_kk = X_k - x^k (X_k . E mod x^(kk-k))           (truncated product)
+// both through the product hot path (prod_slice), then one negation pass.
+#include <cstring>
+
+#include "host.h"
+
+struct InvArith {
+    u64 p, pn, one, r2;     // Montgomery constants (odd p)
+    int two;                // p = 2: plain bit arithmetic
+};
+
+__device__ __forceinline__ u64 ia_mul(const InvArith &F, u64 a, u64 b)
+{
+    return F.two ? (a & b) : mont_mul(a, b, F.p, F.pn);
+}
+__device__ __forceinline__ u64 ia_in(const InvArith &F, u64 a) { return F.two ? a : mont_mul(a, F.r2, F.p, F.pn); }
+__device__ __forceinline__ u64 ia_out(const InvArith &F, u64 a) { return F.two ? a : mont_mul(a, 1, F.p, F.pn); }
+__device__ u64 ia_inv(const InvArith &F, u64 a)         // a^(p-2), a != 0 (Fermat)
+{
+    if (F.two) return 1;
+    u64 r = F.one, e = F.p - 2;
+    while (e) {
+        if (e & 1) r = mont_mul(r, a, F.p, F.pn);
+        a = mont_mul(a, a, F.p, F.pn);
+        e >>= 1;
+    }
+    return r;
+}
+
+// M: scratch n x 2n (row-major) in global memory.  On success X_0 goes to
+// X[(i n + j) sX]; if A(0) is singular the status word gets PM_EDOMAIN.
+__global__ void __launch_bounds__(1024) k_inv0(InvArith F, const void *A, int w, i64 sA, int n, u64 *M, void *X,
+                                               i64 sX, int *status)
+{
+    __shared__ int piv;
+    __shared__ u64 fcol[128];
+    const int tid = threadIdx.x, nth = blockDim.x, n2 = 2 * n;
+    for (int x = tid; x < n * n2; x += nth) {
+        const int i = x / n2, j = x - i * n2;
+        u64 v;
+        if (j < n) {
+            const i64 idx = ((i64)i * n + j) * sA;
+            v = ia_in(F, w == 8 ? ((const u64 *)A)[idx] : ((const u32 *)A)[idx]);
+        } else v = (j - n == i) ? F.one : 0;
+        M[x] = v;
+    }
+    __syncthreads();
+    for (int c = 0; c < n; c++) {
+        if (tid == 0) piv = n;
+        __syncthreads();
+        for (int r = c + tid; r < n; r += nth)
+            if (M[(i64)r * n2 + c]) atomicMin(&piv, r);
+        __syncthreads();
+        const int r = piv;
+        if (r == n) {                                  // uniform: no pivot in column c
+            if (tid == 0) atomicCAS(status, 0, PM_EDOMAIN);
+            return;
+        }
+        if (r != c)
+            for (int j = tid; j < n2; j += nth) {
+                const u64 a = M[(i64)r * n2 + j];
+                M[(i64)r * n2 + j] = M[(i64)c * n2 + j];
+                M[(i64)c * n2 + j] = a;
+            }
+        __syncthreads();
+        for (int i = tid; i < n; i += nth) fcol[i] = M[(i64)i * n2 + c];
+        __syncthreads();
+        const u64 pv = fcol[c];
+        // rows i != c: row_i <- pv row_i - M[i][c] row_c (fraction-free)
+        for (int x = tid; x < n * n2; x += nth) {
+            const int i = x / n2, j = x - i * n2;
+            if (i == c) continue;
+            M[x] = sub64(ia_mul(F, pv, M[x]), ia_mul(F, fcol[i], M[(i64)c * n2 + j]), F.p);
+        }
+        __syncthreads();
+    }
+    // the left half is now diagonal: X_0 = diag(d)^-1 . right half
+    for (int i = tid; i < n; i += nth) fcol[i] = ia_inv(F, M[(i64)i * n2 + i]);
+    __syncthreads();
+    for (int x = tid; x < n * n; x += nth) {
+        const int i = x / n, j = x - i * n;
+        const u64 v = ia_out(F, ia_mul(F, fcol[i], M[(i64)i * n2 + n + j]));
+        const i64 o = (i64)x * sX;
+        if (w == 8) ((u64 *)X)[o] = v;
+        else ((u32 *)X)[o] = (u32)v;
+    }
+}
+
+// X[e sX + off + j] <- -X[e sX + off + j] mod p for e < count, j < h.
+__global__ void k_negate_slice(void *X, int w, i64 sX, i64 off, i64 h, i64 count, u64 p)
+{
+    const i64 total = count * h;
+    for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < total; x += (i64)gridDim.x * blockDim.x) {
+        const i64 e = x / h, o = e * sX + off + (x - e * h);
+        if (w == 8) {
+            const u64 v = ((u64 *)X)[o];
+            ((u64 *)X)[o] = v ? p - v : 0;
+        } else {
+            const u32 v = ((u32 *)X)[o];
+            ((u32 *)X)[o] = v ? (u32)p - v : 0;
+        }
+    }
+}
+
+#define CKI(call)                                                       \
+    do {                                                                \
+        int _rc = (call);                                               \
+        if (_rc) return _rc;                                            \
+    } while (0)
+
+extern "C" int pmat_inv_trunc(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA, int64_t t, void *X)
+{
+    if (!ctx) return PM_EINVAL;
+    if (w != 4 && w != 8) return pm_fail(ctx, PM_EINVAL, "w must be 4 or 8");
+    if (p < 2 || (w == 4 && p >= (1ull << 32)) || (w == 8 && p >= (1ull << 62)))
+        return pm_fail(ctx, PM_EINVAL, "need 2 <= p < 2^32 (w = 4) or 2^62 (w = 8)");
+    if (n < 1 || dA < 1 || t < 1) return pm_fail(ctx, PM_EINVAL, "need n, dA, t >= 1");
+    if (n > 128) return pm_fail(ctx, PM_EUNSUPPORTED, "pmat_inv_trunc supports n <= 128");
+    if (t > (int64_t(1) << (PM_MAX_LOG2L - 1))) return pm_fail(ctx, PM_EINVAL, "t too large for the transforms");
+    if (!A || !X) return pm_fail(ctx, PM_EINVAL, "null buffer");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return pm_fail(ctx, PM_ECUDA, "cudaSetDevice failed");
+
+    InvArith F;
+    memset(&F, 0, sizeof(F));
+    F.p = p;
+    F.two = p == 2;
+    if (!F.two) {
+        uint64_t inv = 1;                   // p^-1 mod 2^64 by Newton iteration
+        for (int i = 0; i < 7; i++) inv *= 2 - p * inv;
+        F.pn = (uint64_t)0 - inv;
+        F.one = (uint64_t)(((unsigned __int128)1 << 64) % p);
+        F.r2 = (uint64_t)((unsigned __int128)F.one * F.one % p);
+    } else {
+        F.one = 1;
+    }
+    const size_t nn = (size_t)n * n;
+    const int64_t hmax = t / 2 > 0 ? t / 2 : 1;
+    const size_t bM = (nn * 2 * 8 + 255) / 256 * 256, bE = nn * (size_t)hmax * w;
+    CKI(arena_reserve(ctx, bM + bE + 512));
+    u64 *M = (u64 *)arena_alloc(ctx, nn * 2 * 8);
+    void *E = arena_alloc(ctx, bE);
+    if (!M || !E) return pm_fail(ctx, PM_ENOMEM, "arena too small");
+
+    k_inv0<<<1, 1024, 0, ctx->stream>>>(F, A, w, dA, n, M, X, t, ctx->d_status);
+    ctx->launches++;
+    CKI(pm_cuda(ctx, cudaGetLastError(), "k_inv0"));
+    // every coefficient 1 .. t-1 of X is written by exactly one Newton step
+    for (int64_t k = 1; k < t;) {
+        const int64_t kk = 2 * k < t ? 2 * k : t, h = kk - k;
+        const int64_t dAe = dA < kk ? dA : kk;
+        // E = coefficients k .. kk-1 of A . X_k: product length <= kk + k - 1, cyclic length
+        // L >= kk puts every aliased coefficient below k
+        CKI(prod_slice(ctx, p, w, n, n, n, A, dAe, dA, X, k, t, k, h, ceil_log2(kk), E, h));
+        // X[k .. kk) = X_k . E mod x^h (no aliasing), then negated
+        const int64_t dX = k < h ? k : h;
+        CKI(prod_slice(ctx, p, w, n, n, n, X, dX, t, E, h, h, 0, h, ceil_log2(dX + h - 1), (char *)X + k * w, t));
+        const int64_t tot = (int64_t)nn * h;
+        int grid = (int)((tot + 255) / 256);
+        if (grid > 4096) grid = 4096;
+        k_negate_slice<<<grid, 256, 0, ctx->stream>>>(X, w, t, k, h, (int64_t)nn, p);
+        ctx->launches++;
+        CKI(pm_cuda(ctx, cudaGetLastError(), "k_negate_slice"));
+        k = kk;
+    }
+    return PM_OK;
+}

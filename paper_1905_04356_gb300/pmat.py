@@ -68,6 +68,7 @@ def lib():
             "pmat_mul_noalloc": ([u64, i32, i32, i32, i32, P, i64, P, i64, P, P], i32),
             "pm_basis": ([P, u64, i32, i32, P, i64, i64, P, P, P], i32),
             "bivariate_resultant": ([P, i32, P, i32, i32, P, i32, i32, P, P], i32),
+            "pmat_inv_trunc": ([P, u64, i32, i32, P, i64, i64, P], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -200,6 +201,19 @@ def pmat_mul_trunc(ctx: Context, p: int, A, B, t: int, out=None) -> torch.Tensor
     ctx._ck(lib().pmat_mul_trunc(ctx.h, p, width(A), m, n, k, A.data_ptr(), dA, B.data_ptr(), dB, t,
                                  Cout.data_ptr()))
     return Cout
+
+
+def pmat_inv_trunc(ctx: Context, p: int, A, t: int, out=None) -> torch.Tensor:
+    """X = A^-1 mod x^t -> n x n x t (A: n x n x dA with A(0) invertible mod the prime p).
+
+    A singular A(0) is reported by the next ctx.sync() (PM_EDOMAIN)."""
+    A = _dev(A)
+    n, n2, dA = A.shape
+    if n != n2:
+        raise ValueError("A must be square")
+    X = _out(out, (n, n, t), A)
+    ctx._ck(lib().pmat_inv_trunc(ctx.h, p, width(A), n, A.data_ptr(), dA, t, X.data_ptr()))
+    return X
 
 
 def pmat_middle_product(ctx: Context, p: int, A, B, c: int, d: int, out=None) -> torch.Tensor:

@@ -106,6 +106,17 @@ def product_c2(seed: int = 0, ntt_prime: bool = False, m: int = 32, d: int = 409
     return dict(p=p, A=A, B=B)
 
 
+def inverse_w(seed: int = 0, n: int = 32, d: int = 4096, t: int = 4096):
+    """A (n x n, degree < d) modulo a random 60-bit prime and the truncation order t.
+
+    A(0) is uniform, hence invertible except with probability < n / p.
+    """
+    g = rng(seed)
+    p = random_prime(g, 60)
+    A = pmat(g, n, n, d, p, np.uint64)
+    return dict(p=p, A=A, t=t)
+
+
 def pmbasis_c3(seed: int = 0, m: int = 32, n: int = 16, d: int = 8192):
     """F (m x n, length d) modulo a random 60-bit prime, uniform shift 0."""
     g = rng(seed)

@@ -1,0 +1,126 @@
+"""GPU parity of the truncated inverse A^-1 mod x^t (Sec. 4, lifting: matrix Newton iteration).
+
+Bit-exact against the oracle's coefficient recurrence at sizes it finishes quickly (moduli
+2, 3, 97, 2^32 - 5, 998244353, 60- and 62-bit; t = 1, 2, odd and power-of-two lengths; A
+shorter and longer than t; n up to 32, i.e. several pointwise tiles).  At the full size (32 x
+32, dA = t = 4096, 60-bit p) the output is checked by the defining identity A.X = I mod x^t on
+sampled coefficients the oracle computes one by one, and its prefix against the oracle's inverse
+of A mod x^64 (X mod x^64 depends only on A mod x^64).
+"""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+P60 = 1152921504606846883
+P62 = 4611686018427387847
+P32 = 4294967291
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_04356_gb300 import Context, build
+    build.build()
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def _matrix(seed, p, n, dA, w):
+    """A random n x n x dA matrix mod p whose constant term is invertible (a product of unit
+    lower and upper triangular matrices)."""
+    g = synth.rng(seed)
+    dt = np.uint32 if w == 4 else np.uint64
+    A = synth.uniform(g, (n, n, dA), p, dt)
+    rnd = random.Random(seed)
+    Lm = [[(1 if i == j else (rnd.randrange(p) if i > j else 0)) for j in range(n)] for i in range(n)]
+    Um = [[(1 if i == j else (rnd.randrange(p) if i < j else 0)) for j in range(n)] for i in range(n)]
+    A0 = [[sum(Lm[i][l] * Um[l][j] for l in range(n)) % p for j in range(n)] for i in range(n)]
+    A[:, :, 0] = np.array(A0, dtype=np.uint64).astype(dt)
+    return A
+
+
+def _gpu_inv(ctx, p, A, t):
+    from paper_1905_04356_gb300 import pmat
+    X = pmat.pmat_inv_trunc(ctx, p, pmat.to_device(A), t)
+    ctx.sync()
+    return pmat.to_host(X)
+
+
+CASES = [
+    # p, w, n, dA, t
+    (synth.P998, 4, 4, 50, 300),
+    (P60, 8, 3, 17, 100),
+    (P62, 8, 2, 200, 129),
+    (97, 4, 6, 7, 64),
+    (2, 4, 5, 30, 70),
+    (3, 4, 3, 3, 33),
+    (P32, 4, 4, 10, 20),
+    (P60, 8, 5, 9, 1),
+    (P60, 8, 5, 9, 2),
+    (synth.P998, 4, 3, 1, 40),        # constant matrix: X = A^-1, zero beyond
+    (P60, 8, 1, 600, 513),
+    (P60, 8, 32, 64, 200),            # 32 x 32: full pointwise block tiles
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"p{c[0]}_w{c[1]}_n{c[2]}_dA{c[3]}_t{c[4]}" for c in CASES])
+def test_inverse_matches_oracle(ctx, case):
+    p, w, n, dA, t = case
+    A = _matrix(hash(case) & 0xffff, p, n, dA, w)
+    got = _gpu_inv(ctx, p, A, t)
+    exp = oracle.inv_trunc(p, A, t)
+    assert got.shape == (n, n, t)
+    assert np.array_equal(got.astype(np.uint64), exp)
+
+
+def test_full_size_identity_sampled(ctx):
+    """32 x 32, dA = t = 4096, 60-bit p: A.X = I mod x^t on sampled coefficients."""
+    p, n, t = P60, 32, 4096
+    A = _matrix(11, p, n, t, 8)
+    X = _gpu_inv(ctx, p, A, t).astype(np.uint64)
+    rnd = random.Random(2)
+    picks = [(0, 0, 0), (3, 3, 0), (1, 2, 0), (5, 5, t - 1), (31, 0, t - 1)] + \
+        [(rnd.randrange(n), rnd.randrange(n), rnd.randrange(t)) for _ in range(60)]
+    for i, k, j in picks:
+        assert oracle.pmat_coeff(p, A, X, i, k, j) == (1 if (i == k and j == 0) else 0), (i, k, j)
+    assert np.array_equal(X[:, :, :64], oracle.inv_trunc(p, A[:, :, :64], 64))
+
+
+def test_singular_constant_term_is_reported(ctx):
+    from paper_1905_04356_gb300 import PmError, pmat
+    p = 97
+    A = np.zeros((2, 2, 3), dtype=np.uint32)
+    A[0, 0, 1] = 1                                        # diag(x, 1): A(0) singular
+    A[1, 1, 0] = 1
+    pmat.pmat_inv_trunc(ctx, p, pmat.to_device(A), 8)
+    with pytest.raises(PmError) as e:
+        ctx.sync()
+    assert e.value.code == pmat.PM_EDOMAIN
+    # the context stays usable
+    B = _matrix(5, p, 3, 4, 4)
+    assert np.array_equal(_gpu_inv(ctx, p, B, 9).astype(np.uint64), oracle.inv_trunc(p, B, 9))
+
+
+def test_argument_errors(ctx):
+    import torch
+    from paper_1905_04356_gb300 import PmError, pmat
+    A = torch.zeros((3, 3, 4), dtype=torch.int32, device="cuda")
+    with pytest.raises(PmError) as e:
+        pmat.pmat_inv_trunc(ctx, P60, A, 4)                 # w = 4 with p >= 2^32
+    assert e.value.code == pmat.PM_EINVAL
+    with pytest.raises(PmError) as e:
+        pmat.pmat_inv_trunc(ctx, 97, A, 0)                  # t = 0
+    assert e.value.code == pmat.PM_EINVAL
+    big = torch.zeros((129, 129, 1), dtype=torch.int32, device="cuda")
+    with pytest.raises(PmError) as e:
+        pmat.pmat_inv_trunc(ctx, 97, big, 2)
+    assert e.value.code == pmat.PM_EUNSUPPORTED
