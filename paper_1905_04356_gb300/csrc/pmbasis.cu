@@ -53,6 +53,16 @@ __device__ __forceinline__ u64 redc128(u64 hi, u64 lo, u64 p, u64 pn)
     u64 r = hi + __umul64hi(m, p) + (lo != 0);
     return csub64(r, p);
 }
+// Montgomery form of a x - b y mod p with one reduction: T = a x - b y (+ p 2^64 when
+// a x < b y) lies in [0, p 2^64), and redc128(T) = (a x - b y) 2^-64 mod p.
+__device__ __forceinline__ u64 mont_msub(u64 a, u64 x, u64 b, u64 y, u64 p, u64 pn)
+{
+    const u64 l1 = a * x, h1 = __umul64hi(a, x), l2 = b * y, h2 = __umul64hi(b, y);
+    const u64 lo = l1 - l2, b1 = l1 < l2;
+    const bool neg = h1 < h2 || (h1 == h2 && b1);
+    const u64 hi = h1 - h2 - b1 + (neg ? p : 0);
+    return redc128(hi, lo, p, pn);
+}
 __device__ __forceinline__ void mac128(u64 &hi, u64 &lo, u64 a, u64 b)
 {
     u64 l = a * b, h = __umul64hi(a, b);
@@ -112,15 +122,21 @@ __device__ ElimSm elim_carve(u64 *w, int *ip, int m, int n)
 
 // Fraction-free Gauss-Jordan of the n x m matrix E.M (n <= 64, m <= 128) by the
 // first GJ_WARPS warps of the block: lanes own columns, warps own rows (row c in
-// warp c % GJ_WARPS), values stay in registers; per pivot step only the pivot
-// candidates and the pivot row go through shared memory, between two named
-// barriers of the group.  Pivot of column s: the lowest row not yet used with a
-// nonzero entry.  Returns true (uniformly) when every column had a pivot; E.M then
+// warp c % GJ_WARPS), values stay in registers.  Pivot of column s: the lowest row
+// not yet used with a nonzero entry.  One named barrier per pivot step: every warp
+// publishes its candidate row (index and values) into a buffer alternating with the
+// step's parity, then all warps read the winner's row.  Pivot step s updates every
+// row c != r_s as row_c <- pv_s row_c - M[c][s] row_{r_s}, so the diagonal of row r_s
+// ends as d_s = prod_{s' >= s} pv_s', the common multiple of the d_s is
+// D = prod pv = d_0, and D / d_s = prod_{s' < s} pv_s' is recorded as E.fac[s]
+// (E.dpr[n] = D).  Returns true (uniformly) when every column had a pivot; E.M then
 // holds the result and E.perm[s] the pivot row of column s.
 #define GJ_WARPS 8
+#define GJ_CPL_MAX 4
 
 template <int GJ_RPW, int GJ_CPL>
-__device__ bool gj_regs(const LeafArgs &A, ElimSm &E, int *cand, u64 *prow, int *failp)
+__device__ bool gj_regs(const LeafArgs &A, ElimSm &E, int (*cand)[GJ_WARPS], u64 (*crow)[GJ_WARPS][32 * GJ_CPL_MAX],
+                        int *failp)
 {
     int &fail = *failp;
     const int m = A.m, n = A.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -136,41 +152,46 @@ __device__ bool gj_regs(const LeafArgs &A, ElimSm &E, int *cand, u64 *prow, int 
                 const int c = warp + GJ_WARPS * i, col = lane + 32 * t;
                 v[i][t] = (c < n && col < m) ? E.M[c * m + col] : 0;
             }
-        asm volatile("bar.sync 1, %0;" ::"r"(GJ_WARPS * 32));
         unsigned long long used = 0;
-        for (int s = 0; s < n; s++) {
-            const int ls = s & 31, ts = s >> 5;
+        u64 pre = A.one;                                // prod of the pivots so far (thread 0)
+        int s = 0;
+        for (; s < n; s++) {
+            const int ls = s & 31, ts = s >> 5, bf = s & 1;
             // this warp's candidate: lowest unused own row with a nonzero entry in column s
-            int mine = 0x7fffffff;
+            int mine = 0x7fffffff, slot = 0;
 #pragma unroll
             for (int i = GJ_RPW - 1; i >= 0; i--) {
                 const int c = warp + GJ_WARPS * i;
                 u64 x = 0;
 #pragma unroll
                 for (int t = 0; t < GJ_CPL; t++) x = (t == ts) ? v[i][t] : x;
-                if (c < n && !((used >> c) & 1ull) && x) mine = c;
+                if (c < n && !((used >> c) & 1ull) && x) { mine = c; slot = i; }
             }
             mine = __shfl_sync(0xffffffffu, mine, ls);
-            if (lane == 0) cand[warp] = mine;
-            asm volatile("bar.sync 1, %0;" ::"r"(GJ_WARPS * 32));
-            int r = 0x7fffffff;
-#pragma unroll
-            for (int w = 0; w < GJ_WARPS; w++) r = min(r, cand[w]);
-            if (r == 0x7fffffff) break;                 // uniform over the group
-            used |= 1ull << r;
-            if (warp == r % GJ_WARPS) {
-                const int slot = r / GJ_WARPS;
+            slot = __shfl_sync(0xffffffffu, slot, ls);
+            if (lane == 0) cand[bf][warp] = mine;
+            if (mine != 0x7fffffff) {
 #pragma unroll
                 for (int t = 0; t < GJ_CPL; t++) {
                     u64 x = 0;
 #pragma unroll
                     for (int i = 0; i < GJ_RPW; i++) x = (i == slot) ? v[i][t] : x;
-                    prow[lane + 32 * t] = x;
+                    crow[bf][warp][lane + 32 * t] = x;
                 }
             }
-            if (tid == 0) E.perm[s] = r;
             asm volatile("bar.sync 1, %0;" ::"r"(GJ_WARPS * 32));
+            int r = 0x7fffffff;
+#pragma unroll
+            for (int w = 0; w < GJ_WARPS; w++) r = min(r, cand[bf][w]);
+            if (r == 0x7fffffff) break;                 // uniform over the group
+            used |= 1ull << r;
+            const u64 *prow = crow[bf][r % GJ_WARPS];
             const u64 pv = prow[s];
+            if (tid == 0) {
+                E.perm[s] = r;
+                E.fac[s] = pre;
+                pre = mont_mul(pre, pv, p, pn);
+            }
 #pragma unroll
             for (int i = 0; i < GJ_RPW; i++) {
                 const int c = warp + GJ_WARPS * i;
@@ -180,12 +201,13 @@ __device__ bool gj_regs(const LeafArgs &A, ElimSm &E, int *cand, u64 *prow, int 
                 for (int t = 0; t < GJ_CPL; t++) x = (t == ts) ? v[i][t] : x;
                 const u64 f = __shfl_sync(0xffffffffu, x, ls);
 #pragma unroll
-                for (int t = 0; t < GJ_CPL; t++)
-                    v[i][t] = sub64(mont_mul(pv, v[i][t], p, pn), mont_mul(f, prow[lane + 32 * t], p, pn), p);
+                for (int t = 0; t < GJ_CPL; t++) v[i][t] = mont_msub(pv, v[i][t], f, prow[lane + 32 * t], p, pn);
             }
-            if (s == n - 1) break;
         }
-        if (tid == 0 && __popcll(used) != n) fail = 1;
+        if (tid == 0) {
+            if (s != n) fail = 1;
+            E.dpr[n] = pre;
+        }
 #pragma unroll
         for (int i = 0; i < GJ_RPW; i++)
 #pragma unroll
@@ -201,21 +223,22 @@ __device__ bool gj_regs(const LeafArgs &A, ElimSm &E, int *cand, u64 *prow, int 
 // Register tile: GJ_RPW rows per warp (n <= 8 GJ_RPW), GJ_CPL columns per lane (m <= 32 GJ_CPL).
 __device__ bool gj_dispatch(const LeafArgs &A, ElimSm &E)
 {
-    __shared__ int cand[GJ_WARPS];
-    __shared__ u64 prow[32 * 4];
+    __shared__ int cand[2][GJ_WARPS];
+    __shared__ u64 crow[2][GJ_WARPS][32 * GJ_CPL_MAX];
     __shared__ int fail;
     const int rpw = (A.n + GJ_WARPS - 1) / GJ_WARPS, cpl = (A.m + 31) / 32;
+    if (blockDim.x < GJ_WARPS * 32) return false;  // the named barrier needs GJ_WARPS full warps
     if (cpl == 1) {
-        if (rpw <= 1) return gj_regs<1, 1>(A, E, cand, prow, &fail);
-        if (rpw <= 2) return gj_regs<2, 1>(A, E, cand, prow, &fail);
-        if (rpw <= 4) return gj_regs<4, 1>(A, E, cand, prow, &fail);
+        if (rpw <= 1) return gj_regs<1, 1>(A, E, cand, crow, &fail);
+        if (rpw <= 2) return gj_regs<2, 1>(A, E, cand, crow, &fail);
+        if (rpw <= 4) return gj_regs<4, 1>(A, E, cand, crow, &fail);
     } else if (cpl == 2) {
-        if (rpw <= 2) return gj_regs<2, 2>(A, E, cand, prow, &fail);
-        if (rpw <= 4) return gj_regs<4, 2>(A, E, cand, prow, &fail);
-        if (rpw <= 8) return gj_regs<8, 2>(A, E, cand, prow, &fail);
+        if (rpw <= 2) return gj_regs<2, 2>(A, E, cand, crow, &fail);
+        if (rpw <= 4) return gj_regs<4, 2>(A, E, cand, crow, &fail);
+        if (rpw <= 8) return gj_regs<8, 2>(A, E, cand, crow, &fail);
     } else if (cpl <= 4) {
-        if (rpw <= 4) return gj_regs<4, 4>(A, E, cand, prow, &fail);
-        if (rpw <= 8) return gj_regs<8, 4>(A, E, cand, prow, &fail);
+        if (rpw <= 4) return gj_regs<4, 4>(A, E, cand, crow, &fail);
+        if (rpw <= 8) return gj_regs<8, 4>(A, E, cand, crow, &fail);
     }
     return false;   // shapes beyond the register tile take the row-order elimination
 }
@@ -250,35 +273,7 @@ __device__ void mbasis1_scaled(const LeafArgs &A, const u64 *R, const i64 *t, El
         __syncthreads();
         ok = gj_dispatch(A, E);
         if (ok) {
-            // pivots d_s = M[perm[s]][s]: fac[s] = prod_{s' != s} d_s', dpr[n] = prod d
-            if (n <= 32) {
-                if (warp == 0) {
-                    const u64 d = lane < n ? E.M[E.perm[lane] * m + lane] : A.one;
-                    u64 pre = d, suf = d;                       // inclusive scans, both directions
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const u64 a1 = __shfl_up_sync(0xffffffffu, pre, o);
-                        const u64 b1 = __shfl_down_sync(0xffffffffu, suf, o);
-                        if (lane >= o) pre = mont_mul(pre, a1, p, A.pn);
-                        if (lane + o < 32) suf = mont_mul(suf, b1, p, A.pn);
-                    }
-                    u64 pex = __shfl_up_sync(0xffffffffu, pre, 1), sex = __shfl_down_sync(0xffffffffu, suf, 1);
-                    if (lane == 0) pex = A.one;
-                    if (lane == 31) sex = A.one;
-                    if (lane < n) E.fac[lane] = mont_mul(pex, sex, p, A.pn);
-                    const u64 tot = __shfl_sync(0xffffffffu, pre, 31);
-                    if (lane == 0) E.dpr[n] = tot;
-                }
-            } else if (tid == 0) {
-                u64 acc = A.one;
-                for (int s2 = 0; s2 < n; s2++) { E.dpr[s2] = acc; acc = mont_mul(acc, E.M[E.perm[s2] * m + s2], p, A.pn); }
-                E.dpr[n] = acc;
-                u64 suf = A.one;
-                for (int s2 = n - 1; s2 >= 0; s2--) {
-                    E.fac[s2] = mont_mul(E.dpr[s2], suf, p, A.pn);
-                    suf = mont_mul(suf, E.M[E.perm[s2] * m + s2], p, A.pn);
-                }
-            }
-            __syncthreads();
+            // E.fac[s] = D / d_s and E.dpr[n] = D come from the elimination
             for (int x = tid; x < (m - n) * n; x += nth) {
                 const int jp = n + x / n, s2 = x % n;
                 const int j = E.ord[jp], i = E.ord[s2];
@@ -353,10 +348,16 @@ __device__ void mbasis1_scaled(const LeafArgs &A, const u64 *R, const i64 *t, El
     __syncthreads();
     // compact form of the relations: the independent rows in index order, and for
     // every dependent row its coefficients on them
-    if (tid == 0) {
-        int c = 0;
-        for (int i = 0; i < m; i++) if (E.ind[i]) E.ilist[c++] = i;
-        E.misc[4] = c;
+    if (tid < 32) {
+        int base = 0;
+        for (int i0 = 0; i0 < m; i0 += 32) {
+            const int i = i0 + tid;
+            const bool f = i < m && E.ind[i];
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (f) E.ilist[base + __popc(bal & ((1u << tid) - 1u))] = i;
+            base += __popc(bal);
+        }
+        if (tid == 0) E.misc[4] = base;
     }
     __syncthreads();
     const int nind = E.misc[4];
@@ -617,8 +618,9 @@ int leaf(PmbCtx &C, const u64 *F, int64_t sF, int64_t e, const i64 *s_in, u64 *P
         }
     }
     if (!done) {
+        // the opt-in is needed whenever static + dynamic shared memory exceed 48 KB
         const size_t sm = leaf_smem(C.m, C.n);
-        if (sm > 48 * 1024) cudaFuncSetAttribute(k_mbasis_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_mbasis_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_mbasis_leaf<<<1, 512, sm, ctx->stream>>>(A);
     }
     ctx->launches++;
