@@ -88,6 +88,7 @@ struct ElimSm {
     int *ord, *ind, *pcs, *misc, *perm;
     u64 *Wc;     // compact relation: Wc[j * n + b] = W[j][ilist[b]], b < nind
     int *ilist;  // independent rows, misc[4] = their count
+    int *ipos;   // ipos[ilist[b]] = b
 };
 
 __device__ __forceinline__ size_t elim_words(int m, int n)
@@ -96,6 +97,8 @@ __device__ __forceinline__ size_t elim_words(int m, int n)
     return (size_t)m + (size_t)m * m + (size_t)n * m + mx + (n + 1) + (size_t)n * n + (size_t)n * m + n + m +
            (size_t)m * (mx);
 }
+
+__device__ __forceinline__ int elim_ints(int m, int n) { return 4 * m + 2 * n + 8; }
 
 __device__ ElimSm elim_carve(u64 *w, int *ip, int m, int n)
 {
@@ -116,11 +119,13 @@ __device__ ElimSm elim_carve(u64 *w, int *ip, int m, int n)
     E.pcs = ip; ip += n;
     E.perm = ip; ip += n;
     E.misc = ip; ip += 8;
-    E.ilist = ip;
+    E.ilist = ip; ip += m;
+    E.ipos = ip;
     return E;
 }
 
-// Fraction-free Gauss-Jordan of the n x m matrix E.M (n <= 64, m <= 128) by the
+// Fraction-free Gauss-Jordan of the n x m matrix M[c][col] = R[ord[col]][c] (n <= 64,
+// m <= 128; the result is left in E.M) by the
 // first GJ_WARPS warps of the block: lanes own columns, warps own rows (row c in
 // warp c % GJ_WARPS), values stay in registers.  Pivot of column s: the lowest row
 // not yet used with a nonzero entry.  One named barrier per pivot step: every warp
@@ -135,8 +140,8 @@ __device__ ElimSm elim_carve(u64 *w, int *ip, int m, int n)
 #define GJ_CPL_MAX 4
 
 template <int GJ_RPW, int GJ_CPL>
-__device__ bool gj_regs(const LeafArgs &A, ElimSm &E, int (*cand)[GJ_WARPS], u64 (*crow)[GJ_WARPS][32 * GJ_CPL_MAX],
-                        int *failp)
+__device__ bool gj_regs(const LeafArgs &A, const u64 *R, ElimSm &E, int (*cand)[GJ_WARPS],
+                        u64 (*crow)[GJ_WARPS][32 * GJ_CPL_MAX], int *failp, int gn)
 {
     int &fail = *failp;
     const int m = A.m, n = A.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -150,7 +155,7 @@ __device__ bool gj_regs(const LeafArgs &A, ElimSm &E, int (*cand)[GJ_WARPS], u64
 #pragma unroll
             for (int t = 0; t < GJ_CPL; t++) {
                 const int c = warp + GJ_WARPS * i, col = lane + 32 * t;
-                v[i][t] = (c < n && col < m) ? E.M[c * m + col] : 0;
+                v[i][t] = (c < n && col < m) ? R[E.ord[col] * n + c] : 0;   // M[c][col] = R[ord[col]][c]
             }
         unsigned long long used = 0;
         u64 pre = A.one;                                // prod of the pivots so far (thread 0)
@@ -216,29 +221,31 @@ __device__ bool gj_regs(const LeafArgs &A, ElimSm &E, int (*cand)[GJ_WARPS], u64
                 if (c < n && col < m) E.M[c * m + col] = v[i][t];
             }
     }
-    __syncthreads();
+    asm volatile("bar.sync 2, %0;" ::"r"(gn));
     return fail == 0;
 }
 
 // Register tile: GJ_RPW rows per warp (n <= 8 GJ_RPW), GJ_CPL columns per lane (m <= 32 GJ_CPL).
-__device__ bool gj_dispatch(const LeafArgs &A, ElimSm &E)
+// Called by the elimination group (warps 0 .. gn/32 - 1, gn >= GJ_WARPS * 32), which it
+// leaves through named barrier 2.
+__device__ bool gj_dispatch(const LeafArgs &A, const u64 *R, ElimSm &E, int gn)
 {
     __shared__ int cand[2][GJ_WARPS];
     __shared__ u64 crow[2][GJ_WARPS][32 * GJ_CPL_MAX];
     __shared__ int fail;
     const int rpw = (A.n + GJ_WARPS - 1) / GJ_WARPS, cpl = (A.m + 31) / 32;
-    if (blockDim.x < GJ_WARPS * 32) return false;  // the named barrier needs GJ_WARPS full warps
+    if (gn < GJ_WARPS * 32) return false;          // the named barrier needs GJ_WARPS full warps
     if (cpl == 1) {
-        if (rpw <= 1) return gj_regs<1, 1>(A, E, cand, crow, &fail);
-        if (rpw <= 2) return gj_regs<2, 1>(A, E, cand, crow, &fail);
-        if (rpw <= 4) return gj_regs<4, 1>(A, E, cand, crow, &fail);
+        if (rpw <= 1) return gj_regs<1, 1>(A, R, E, cand, crow, &fail, gn);
+        if (rpw <= 2) return gj_regs<2, 1>(A, R, E, cand, crow, &fail, gn);
+        if (rpw <= 4) return gj_regs<4, 1>(A, R, E, cand, crow, &fail, gn);
     } else if (cpl == 2) {
-        if (rpw <= 2) return gj_regs<2, 2>(A, E, cand, crow, &fail);
-        if (rpw <= 4) return gj_regs<4, 2>(A, E, cand, crow, &fail);
-        if (rpw <= 8) return gj_regs<8, 2>(A, E, cand, crow, &fail);
+        if (rpw <= 2) return gj_regs<2, 2>(A, R, E, cand, crow, &fail, gn);
+        if (rpw <= 4) return gj_regs<4, 2>(A, R, E, cand, crow, &fail, gn);
+        if (rpw <= 8) return gj_regs<8, 2>(A, R, E, cand, crow, &fail, gn);
     } else if (cpl <= 4) {
-        if (rpw <= 4) return gj_regs<4, 4>(A, E, cand, crow, &fail);
-        if (rpw <= 8) return gj_regs<8, 4>(A, E, cand, crow, &fail);
+        if (rpw <= 4) return gj_regs<4, 4>(A, R, E, cand, crow, &fail, gn);
+        if (rpw <= 8) return gj_regs<8, 4>(A, R, E, cand, crow, &fail, gn);
     }
     return false;   // shapes beyond the register tile take the row-order elimination
 }
@@ -246,53 +253,64 @@ __device__ bool gj_dispatch(const LeafArgs &A, ElimSm &E)
 // Algorithm 1 on the residual R (m x n, Montgomery) with shift t: rows visited in
 // increasing (t_i, i) order.  Output: ind[i] = 1 for rows that become x e_i; for the
 // other rows j, the scaled relation kap_j R_j = -sum_i W[j][i] R_i (W stored
-// negated), i.e. the row of Q is kap_j e_j + sum_i W[j][i] e_i.  All threads of the
-// block call it; it ends with a barrier.
-__device__ void mbasis1_scaled(const LeafArgs &A, const u64 *R, const i64 *t, ElimSm &E)
+// negated), i.e. the row of Q is kap_j e_j + sum_i W[j][i] e_i.  Called by the
+// elimination group: warps 0 .. gn/32 - 1 of the block (tid < gn, gn a multiple of 32
+// and >= 256), synchronised by named barrier 2, with which it ends.
+#define EBAR() asm volatile("bar.sync 2, %0;" ::"r"(nth))
+__device__ void mbasis1_scaled(const LeafArgs &A, const u64 *R, const i64 *t, ElimSm &E, int gn)
 {
-    const int m = A.m, n = A.n, tid = threadIdx.x, nth = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
+    const int m = A.m, n = A.n, tid = threadIdx.x, nth = gn;
     const u64 p = A.p;
     for (int i = tid; i < m; i += nth) {
         int r = 0;
         const i64 ti = t[i];
         for (int j = 0; j < m; j++) r += (t[j] < ti) || (t[j] == ti && j < i);
         E.ord[r] = i;
-        E.ind[i] = 0;
         E.kap[i] = A.one;
     }
-    for (int x = tid; x < m * m; x += nth) E.W[x] = 0;
-    __syncthreads();
+    EBAR();
     bool ok = false;
     if (m > n) {
-        // fast path: Gauss-Jordan on [R_I^T | R_D^T] (n x m), I = the first n rows in order
-        for (int x = tid; x < n * m; x += nth) {
-            const int c = x / m, pos = x % m;
-            E.M[x] = R[E.ord[pos] * n + c];
+        // fast path: Gauss-Jordan on [R_I^T | R_D^T] (n x m), I = the first n rows in order.
+        // The independent rows are known before the elimination: list them in index order.
+        for (int pos = tid; pos < m; pos += nth) E.ind[E.ord[pos]] = pos < n;
+        EBAR();
+        if (tid < 32) {
+            int base = 0;
+            for (int i0 = 0; i0 < m; i0 += 32) {
+                const int i = i0 + tid;
+                const bool f = i < m && E.ind[i];
+                const unsigned bal = __ballot_sync(0xffffffffu, f);
+                if (f) {
+                    const int b = base + __popc(bal & ((1u << tid) - 1u));
+                    E.ilist[b] = i;
+                    E.ipos[i] = b;
+                }
+                base += __popc(bal);
+            }
+            if (tid == 0) E.misc[4] = base;
         }
-        __syncthreads();
-        ok = gj_dispatch(A, E);
+        ok = gj_dispatch(A, R, E, nth);
         if (ok) {
-            // E.fac[s] = D / d_s and E.dpr[n] = D come from the elimination
+            // E.fac[s] = D / d_s and E.dpr[n] = D come from the elimination; the relation of
+            // dependent row j on independent row i = ord[s] goes to Wc[j][ipos[i]]
             for (int x = tid; x < (m - n) * n; x += nth) {
                 const int jp = n + x / n, s2 = x % n;
                 const int j = E.ord[jp], i = E.ord[s2];
                 const u64 w = mont_mul(E.M[E.perm[s2] * m + jp], E.fac[s2], p, A.pn);
-                E.W[j * m + i] = w ? p - w : 0;
+                E.Wc[j * n + E.ipos[i]] = w ? p - w : 0;
             }
-            for (int pos = tid; pos < m; pos += nth) {
-                const int i = E.ord[pos];
-                if (pos < n) E.ind[i] = 1;
-                else E.kap[i] = E.dpr[n];
-            }
+            for (int pos = n + tid; pos < m; pos += nth) E.kap[E.ord[pos]] = E.dpr[n];
         }
-        __syncthreads();
+        EBAR();
+        if (ok) return;
     }
-    if (!ok) {
+    {
         // general path: rows in order, fraction-free common-denominator elimination
         for (int x = tid; x < m * m; x += nth) E.W[x] = 0;
+        for (int i = tid; i < m; i += nth) E.ind[i] = 0;
         if (tid == 0) { E.misc[2] = 0; E.dpr[0] = A.one; }
-        __syncthreads();
+        EBAR();
         for (int pos = 0; pos < m; pos++) {
             const int r = E.ord[pos];
             const int rank = E.misc[2];
@@ -312,18 +330,18 @@ __device__ void mbasis1_scaled(const LeafArgs &A, const u64 *R, const i64 *t, El
                     E.tv[i] = acc;
                 }
             }
-            __syncthreads();
+            EBAR();
             if (tid == 0) {
                 int pc = -1;
                 for (int c = 0; c < n; c++) if (E.vv[c]) { pc = c; break; }
                 E.misc[3] = pc;
             }
-            __syncthreads();
+            EBAR();
             const int pc = E.misc[3];
             if (pc >= 0) {
                 const u64 pv = E.vv[pc];
                 for (int b = tid; b < rank; b += nth) E.fac[b] = E.bas[b * n + pc];
-                __syncthreads();
+                EBAR();
                 for (int x = tid; x < rank * (n + m); x += nth) {
                     const int b = x / (n + m), c = x % (n + m);
                     if (c < n) E.bas[b * n + c] = sub64(mont_mul(pv, E.bas[b * n + c], p, A.pn), mont_mul(E.fac[b], E.vv[c], p, A.pn), p);
@@ -334,7 +352,7 @@ __device__ void mbasis1_scaled(const LeafArgs &A, const u64 *R, const i64 *t, El
                     if (c < n) E.bas[rank * n + c] = mont_mul(D, E.vv[c], p, A.pn);
                     else E.tb[rank * m + (c - n)] = mont_mul(D, E.tv[c - n], p, A.pn);
                 }
-                __syncthreads();
+                EBAR();
                 if (tid == 0) { E.pcs[rank] = pc; E.misc[2] = rank + 1; E.dpr[0] = mont_mul(pv, D, p, A.pn); E.ind[r] = 1; }
             } else {
                 // dependent: the row of Q is tv (tv[r] = D): kap_r = D, W[r][i] = tv[i]
@@ -342,10 +360,10 @@ __device__ void mbasis1_scaled(const LeafArgs &A, const u64 *R, const i64 *t, El
                     if (i != r) E.W[r * m + i] = E.tv[i];
                 if (tid == 0) E.kap[r] = D;
             }
-            __syncthreads();
+            EBAR();
         }
     }
-    __syncthreads();
+    EBAR();
     // compact form of the relations: the independent rows in index order, and for
     // every dependent row its coefficients on them
     if (tid < 32) {
@@ -359,13 +377,13 @@ __device__ void mbasis1_scaled(const LeafArgs &A, const u64 *R, const i64 *t, El
         }
         if (tid == 0) E.misc[4] = base;
     }
-    __syncthreads();
+    EBAR();
     const int nind = E.misc[4];
     for (int x = tid; x < m * nind; x += nth) {
         const int j = x / nind, b = x % nind;
         E.Wc[j * n + b] = E.W[j * m + E.ilist[b]];
     }
-    __syncthreads();
+    EBAR();
 }
 
 // New value of one coefficient of a dependent row j: kap_j X[j] + sum_i W[j][i] X[i],
@@ -419,7 +437,7 @@ __global__ void __launch_bounds__(512) k_mbasis_leaf(const LeafArgs A)
     for (int k = 0; k < T; k++) {
         for (int x = tid; x < m * n; x += nth) R[x] = G[(i64)x * T + k];
         __syncthreads();
-        mbasis1_scaled(A, R, t, E);
+        mbasis1_scaled(A, R, t, E, nth);
         const int ngl = T - k - 1;
         for (int x = tid; x < m * n * ngl; x += nth) {
             const int a = k + 1 + x % ngl, e = x / ngl, j = e / n, c = e % n;
@@ -455,11 +473,43 @@ __global__ void __launch_bounds__(512) k_mbasis_leaf(const LeafArgs A)
 
 // ------------------------------------------------------------------ leaf kernel, CTA cluster
 // LEAF_CL CTAs; CTA r owns the G columns [r n / CL, (r+1) n / CL) and the P columns
-// [r m / CL, (r+1) m / CL), both in its shared memory (double-buffered).  Each step,
-// every CTA writes its part of the residual into every CTA's residual buffer
-// (distributed shared memory, double-buffered by step parity), one cluster barrier,
-// then every CTA runs the same elimination and updates its own slices.
+// [r m / CL, (r+1) m / CL), both in its shared memory.  The order steps are pipelined
+// over two warp groups: at step k, warps 0 .. LEAF_EW-1 run the elimination of the
+// residual R_k (Algorithm 1) while the other warps apply the previous step's Q_{k-1} to
+// the rest of G (coefficients >= k+1) and to P.  Then every thread helps with the one
+// thing the next elimination waits for: coefficient k+1 of Q_k G, this CTA's columns of
+// R_{k+1}, written into every CTA's residual buffer (distributed shared memory) before
+// one cluster barrier.  G, P, the residuals and the elimination outputs are
+// double-buffered by step parity.
 #define LEAF_CL_MAX 16
+#define LEAF_EW 8
+
+// Q_k applied to this CTA's slices (k = the step of E): G coefficients a >= k+2 of
+// Gs -> Gd (skipped when G is null) and P coefficients 0 .. k+1 of Ps -> Pd, by threads
+// ut = 0 .. un-1.
+__device__ void leaf_apply(const LeafArgs &A, const ElimSm &E, int k, const u64 *Gs, u64 *Gd, const u64 *Ps, u64 *Pd,
+                           int ng, int ngm, int np_, int npm, int ut, int un)
+{
+    const int m = A.m, T = A.T, LP = T + 1;
+    if (Gs) {
+        const int ngl = T - k - 2;
+        for (int x = ut; x < m * ng * ngl; x += un) {
+            const int a = k + 2 + x % ngl, e = x / ngl, j = e / ng, c = e % ng;
+            const i64 o = ((i64)j * ngm + c) * T + a;
+            Gd[o] = E.ind[j] ? Gs[o - 1] : dep_combine(A, E, j, Gs + (i64)c * T + a, (i64)ngm * T);
+        }
+    }
+    const int npc = k + 2;
+    for (int x = ut; x < m * np_ * npc; x += un) {
+        const int a = x % npc, e = x / npc, j = e / np_, c = e % np_;
+        const i64 o = ((i64)j * npm + c) * LP + a;
+        u64 val;
+        if (E.ind[j]) val = a ? Ps[o - 1] : 0;
+        else if (a == k + 1) val = 0;
+        else val = dep_combine(A, E, j, Ps + (i64)c * LP + a, (i64)npm * LP);
+        Pd[o] = val;
+    }
+}
 
 __global__ void __launch_bounds__(512) k_mbasis_leaf_cl(const LeafArgs A)
 {
@@ -468,74 +518,105 @@ __global__ void __launch_bounds__(512) k_mbasis_leaf_cl(const LeafArgs A)
     const int LEAF_CL = (int)cl.num_blocks();
     extern __shared__ __align__(16) unsigned char smraw[];
     const int m = A.m, n = A.n, T = A.T, LP = T + 1;
-    const int tid = threadIdx.x, nth = blockDim.x;
+    const int tid = threadIdx.x, nth = blockDim.x, egn = LEAF_EW * 32;
     const int rk = (int)cl.block_rank();
     const int g0 = rk * n / LEAF_CL, g1 = (rk + 1) * n / LEAF_CL, ng = g1 - g0;
     const int p0 = rk * m / LEAF_CL, p1 = (rk + 1) * m / LEAF_CL, np_ = p1 - p0;
     const int ngm = (n + LEAF_CL - 1) / LEAF_CL, npm = (m + LEAF_CL - 1) / LEAF_CL;
+    const size_t ewn = elim_words(m, n);
+    const int ein = elim_ints(m, n);
     i64 *t = (i64 *)smraw;
     u64 *lam = (u64 *)(t + m);
     u64 *Rb = lam + m;                                  // 2 x m x n
-    u64 *G = Rb + 2 * (size_t)m * n, *Gn = G + (size_t)m * ngm * T;
-    u64 *P = Gn + (size_t)m * ngm * T, *Pn = P + (size_t)m * npm * LP;
-    u64 *ew = Pn + (size_t)m * npm * LP;
-    int *ei = (int *)(ew + elim_words(m, n));
-    ElimSm E = elim_carve(ew, ei, m, n);
+    u64 *G0 = Rb + 2 * (size_t)m * n, *G1 = G0 + (size_t)m * ngm * T;
+    u64 *P0 = G1 + (size_t)m * ngm * T, *P1 = P0 + (size_t)m * npm * LP;
+    u64 *ew = P1 + (size_t)m * npm * LP;               // 2 elimination outputs
+    int *ei = (int *)(ew + 2 * ewn);
 
-    // G slice: G[(i*ngm + cl)*T + a] = F[i][g0 + cl][a]; P slice: identity columns
+    // G slice: G0[(i*ngm + cl)*T + a] = F[i][g0 + cl][a]; P slice: identity columns
     for (int i = tid; i < m; i += nth) { t[i] = A.s_in[i]; lam[i] = A.one; }
     for (int x = tid; x < m * ng * T; x += nth) {
         const int a = x % T, e = x / T, i = e / ng, c = e % ng;
-        G[((i64)i * ngm + c) * T + a] = mmul(A.F[((i64)i * n + g0 + c) * A.sF + a], A.r2, A);
+        G0[((i64)i * ngm + c) * T + a] = mmul(A.F[((i64)i * n + g0 + c) * A.sF + a], A.r2, A);
     }
     for (int x = tid; x < m * np_ * LP; x += nth) {
         const int a = x % LP, e = x / LP, i = e / np_, c = e % np_;
-        P[((i64)i * npm + c) * LP + a] = (a == 0 && i == p0 + c) ? A.one : 0;
+        P0[((i64)i * npm + c) * LP + a] = (a == 0 && i == p0 + c) ? A.one : 0;
     }
     __syncthreads();
-    for (int k = 0; k < T; k++) {
-        u64 *R = Rb + (size_t)(k & 1) * m * n;
-        // scatter this CTA's residual columns to every CTA of the cluster
-        for (int x = tid; x < LEAF_CL * m * ng; x += nth) {
-            const int dst = x / (m * ng), e = x % (m * ng), i = e / ng, c = e % ng;
-            u64 *rR = cl.map_shared_rank(R, dst);
-            rR[i * n + g0 + c] = G[((i64)i * ngm + c) * T + k];
-        }
-        cl.sync();
-        mbasis1_scaled(A, R, t, E);
-        const int ngl = T - k - 1;
-        for (int x = tid; x < m * ng * ngl; x += nth) {
-            const int a = k + 1 + x % ngl, e = x / ngl, j = e / ng, c = e % ng;
-            const i64 o = ((i64)j * ngm + c) * T + a;
-            Gn[o] = E.ind[j] ? G[o - 1] : dep_combine(A, E, j, G + (i64)c * T + a, (i64)ngm * T);
-        }
-        const int npc = k + 2;
-        for (int x = tid; x < m * np_ * npc; x += nth) {
-            const int a = x % npc, e = x / npc, j = e / np_, c = e % np_;
-            const i64 o = ((i64)j * npm + c) * LP + a;
-            u64 val;
-            if (E.ind[j]) val = a ? P[o - 1] : 0;
-            else if (a == k + 1) val = 0;
-            else val = dep_combine(A, E, j, P + (i64)c * LP + a, (i64)npm * LP);
-            Pn[o] = val;
-        }
-        __syncthreads();
-        for (int i = tid; i < m; i += nth) {
-            if (E.ind[i]) t[i] += 1;
-            else lam[i] = mmul(E.kap[i], lam[i], A);
-        }
-        { u64 *s2 = G; G = Gn; Gn = s2; s2 = P; P = Pn; Pn = s2; }
-        __syncthreads();
+    // R_0: coefficient 0 of this CTA's G columns, to every CTA
+    for (int x = tid; x < LEAF_CL * m * ng; x += nth) {
+        const int dst = x / (m * ng), e = x % (m * ng), i = e / ng, c = e % ng;
+        u64 *rR = cl.map_shared_rank(Rb, dst);
+        rR[i * n + g0 + c] = G0[((i64)i * ngm + c) * T];
     }
-    for (int i = tid; i < m; i += nth) E.kap[i] = mmul(mpow(lam[i], A.p - 2, A), 1, A);   // plain lam_i^-1
+    for (int k = 0; k < T; k++) {
+        cl.sync();                                      // R_k is complete in every CTA
+        const u64 *R = Rb + (size_t)(k & 1) * m * n;
+        const ElimSm Ek = elim_carve(ew + (k & 1) * ewn, ei + (k & 1) * ein, m, n);
+        u64 *Gk = (k & 1) ? G1 : G0;                   // G after k steps (coefficients >= k+1)
+        if (tid < egn) {
+            ElimSm Ew = Ek;
+            mbasis1_scaled(A, R, t, Ew, egn);
+        } else if (k > 0) {
+            const ElimSm Ep = elim_carve(ew + ((k - 1) & 1) * ewn, ei + ((k - 1) & 1) * ein, m, n);
+            leaf_apply(A, Ep, k - 1, (k & 1) ? G0 : G1, Gk, (k & 1) ? P0 : P1, (k & 1) ? P1 : P0, ng, ngm, np_, npm,
+                       tid - egn, nth - egn);
+        }
+        __syncthreads();
+        if (k + 1 < T) {
+            // R_{k+1}: coefficient k+1 of Q_k G for this CTA's columns, to every CTA.  Entry
+            // (j, c) is taken by 16 threads: the kap term and the independent rows' terms are
+            // spread over them and summed by shuffles (every lane takes part), and thread h
+            // stores the entry into CTA h.
+            u64 *Rn = Rb + (size_t)((k + 1) & 1) * m * n;
+            const int nind = Ek.misc[4], h = tid & 15;
+            const i64 rs = (i64)ngm * T;
+            for (int e0 = 0; e0 < m * ng; e0 += nth / 16) {
+                const int e = e0 + tid / 16;
+                const bool act = e < m * ng;
+                const int j = act ? e / ng : 0, c = act ? e % ng : 0;
+                const bool dep = act && !Ek.ind[j];
+                const u64 *X = Gk + (i64)c * T + k + 1;
+                u64 hi = 0, lo = 0, acc = 0;
+                if (dep) {
+                    int cnt = 0;
+                    if (h == 0) { mac128(hi, lo, Ek.kap[j], X[(i64)j * rs]); cnt = 1; }
+                    for (int b = h; b < nind; b += 16) {
+                        mac128(hi, lo, Ek.Wc[j * n + b], X[(i64)Ek.ilist[b] * rs]);
+                        if (++cnt == A.chunk) { acc = add64(acc, redc128(hi, lo, A.p, A.pn), A.p); hi = lo = 0; cnt = 0; }
+                    }
+                }
+                u64 val = add64(acc, redc128(hi, lo, A.p, A.pn), A.p);
+#pragma unroll
+                for (int o = 8; o >= 1; o >>= 1) val = add64(val, __shfl_xor_sync(0xffffffffu, val, o, 16), A.p);
+                if (act && !dep) val = R[j * n + g0 + c];
+                if (act && h < LEAF_CL) cl.map_shared_rank(Rn, h)[j * n + g0 + c] = val;
+            }
+        }
+        for (int i = tid; i < m; i += nth) {
+            if (Ek.ind[i]) t[i] += 1;
+            else lam[i] = mmul(Ek.kap[i], lam[i], A);
+        }
+    }
+    // P after T steps: Q_{T-1} applied to P after T-1 steps
+    __syncthreads();
+    {
+        const ElimSm El = elim_carve(ew + ((T - 1) & 1) * ewn, ei + ((T - 1) & 1) * ein, m, n);
+        leaf_apply(A, El, T - 1, nullptr, nullptr, ((T - 1) & 1) ? P1 : P0, (T & 1) ? P1 : P0, ng, ngm, np_, npm, tid,
+                   nth);
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += nth) lam[i] = mmul(mpow(lam[i], A.p - 2, A), 1, A);   // plain lam_i^-1
     if (rk == 0)
         for (int i = tid; i < m; i += nth) A.s_out[i] = t[i];
     __syncthreads();
+    const u64 *Pf = (T & 1) ? P1 : P0;
     for (int x = tid; x < m * np_ * LP; x += nth) {
         const int a = x % LP, e = x / LP, i = e / np_, c = e % np_;
-        A.P[((i64)i * m + p0 + c) * A.sP + a] = mmul(P[((i64)i * npm + c) * LP + a], E.kap[i], A);
+        A.P[((i64)i * m + p0 + c) * A.sP + a] = mmul(Pf[((i64)i * npm + c) * LP + a], lam[i], A);
     }
-    cl.sync();   // no CTA leaves while others may still write into its residual buffers
+    cl.sync();   // no CTA leaves while others may still access its shared memory
 }
 
 static size_t elim_bytes(int m, int n)
@@ -543,7 +624,7 @@ static size_t elim_bytes(int m, int n)
     const int mx = m > n ? m : n;
     const size_t words = (size_t)m + (size_t)m * m + (size_t)n * m + mx + (n + 1) + (size_t)n * n + (size_t)n * m + n + m +
                          (size_t)m * mx;
-    return words * 8 + ((size_t)3 * m + 2 * n + 8) * 4;
+    return words * 8 + ((size_t)4 * m + 2 * n + 8) * 4;
 }
 
 static size_t leaf_smem(int m, int n)
@@ -555,7 +636,7 @@ static size_t leaf_cl_smem(int m, int n, int T, int LEAF_CL)
 {
     const int ngm = (n + LEAF_CL - 1) / LEAF_CL, npm = (m + LEAF_CL - 1) / LEAF_CL;
     return (size_t)2 * m * 8 + (size_t)2 * m * n * 8 + (size_t)2 * m * ngm * T * 8 + (size_t)2 * m * npm * (T + 1) * 8 +
-           elim_bytes(m, n) + 64;
+           2 * elim_bytes(m, n) + 64;
 }
 
 // ------------------------------------------------------------------ host recursion
