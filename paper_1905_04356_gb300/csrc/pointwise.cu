@@ -272,6 +272,50 @@ cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long lon
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ inner dimension 1
+// C[i][c] = A[i][0] B[0][c] at every point (n = 1: outer products, e.g. many
+// polynomials times one chirp).  One thread per point keeps B's k <= PW1_KMAX
+// residues in registers and streams PW1_ROWS rows of A; every access is coalesced
+// across the points of a warp.  Memory-bound: A and C once, B once per row group.
+#define PW1_THREADS 256
+#define PW1_ROWS 16
+#define PW1_KMAX 8
+
+int pw1_blocks(const PwJob &j)
+{
+    return ((j.L + PW1_THREADS - 1) / PW1_THREADS) * ((j.m + PW1_ROWS - 1) / PW1_ROWS);
+}
+bool pw1_supported(const PwJob &j) { return j.n == 1 && j.k <= PW1_KMAX; }
+
+__global__ void __launch_bounds__(PW1_THREADS) k_pointwise_n1(const __grid_constant__ JobPack<PwJob> pk)
+{
+    const int b = blockIdx.x;
+    const int jb = find_job_pw(pk.blk_start, b);
+    const PwJob &J = pk.jobs[jb];
+    const int L = J.L, k = J.k;
+    const int npb = (L + PW1_THREADS - 1) / PW1_THREADS;
+    const int rel = b - pk.blk_start[jb];
+    const int pt = (rel % npb) * PW1_THREADS + threadIdx.x, i0 = (rel / npb) * PW1_ROWS;
+    if (pt >= L) return;
+    u32 bv[PW1_KMAX];
+#pragma unroll
+    for (int c = 0; c < PW1_KMAX; c++) bv[c] = c < k ? __ldg(J.B + (i64)c * L + pt) : 0u;
+    const int i1 = min(J.m, i0 + PW1_ROWS);
+    for (int i = i0; i < i1; i++) {
+        const u32 a = __ldcs(J.A + (i64)i * L + pt);
+#pragma unroll
+        for (int c = 0; c < PW1_KMAX; c++)
+            if (c < k) __stcs(J.C + ((i64)i * k + c) * L + pt, reduce64((u64)a * bv[c], J.P));
+    }
+}
+
+cudaError_t launch_pointwise_n1(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches)
+{
+    k_pointwise_n1<<<pk.blk_start[pk.njobs], PW1_THREADS, 0, st>>>(pk);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ CRT
 #define CRT_THREADS 256
 #define CRT_PER_THREAD 4

@@ -74,6 +74,9 @@ CASES = [
     (P60, 8, 36, 57, 51, 70, 50),
     (P62, 8, 33, 2, 70, 25, 25),
     (97, 4, 2, 300, 2, 30, 20),
+    # inner dimension 1 (outer products, streaming kernel): many rows, k = 1 and k = 5
+    (P60, 8, 37, 1, 5, 300, 200),
+    (synth.P998, 4, 300, 1, 1, 151, 4000),
 ]
 
 
