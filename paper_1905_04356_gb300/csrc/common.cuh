@@ -86,6 +86,37 @@ __device__ __forceinline__ u64 mont_mul(u64 a, u64 b, u64 p, u64 pn)
     u64 r = hi + __umul64hi(m, p) + (lo != 0);
     return csub64(r, p);
 }
+// Montgomery reduction of a 128-bit T = hi 2^64 + lo < p 2^64: T 2^-64 mod p
+__device__ __forceinline__ u64 redc128(u64 hi, u64 lo, u64 p, u64 pn)
+{
+    u64 m = lo * pn;
+    u64 r = hi + __umul64hi(m, p) + (lo != 0);
+    return csub64(r, p);
+}
+// (hi, lo) <- (hi, lo) - b y, plus p 2^64 when that goes negative: keeps T in [0, p 2^64)
+__device__ __forceinline__ void sub128_mod(u64 &hi, u64 &lo, u64 b, u64 y, u64 p)
+{
+    const u64 l2 = b * y, h2 = __umul64hi(b, y);
+    const u64 b1 = lo < l2;
+    const bool neg = hi < h2 || (hi == h2 && b1);
+    lo -= l2;
+    hi = hi - h2 - b1 + (neg ? p : 0);
+}
+// Montgomery forms with one reduction: (a x - b y) 2^-64 mod p and
+// (a x - b y - c z) 2^-64 mod p, for operands below p < 2^62
+__device__ __forceinline__ u64 mont_msub(u64 a, u64 x, u64 b, u64 y, u64 p, u64 pn)
+{
+    u64 lo = a * x, hi = __umul64hi(a, x);
+    sub128_mod(hi, lo, b, y, p);
+    return redc128(hi, lo, p, pn);
+}
+__device__ __forceinline__ u64 mont_msub2(u64 a, u64 x, u64 b, u64 y, u64 c, u64 z, u64 p, u64 pn)
+{
+    u64 lo = a * x, hi = __umul64hi(a, x);
+    sub128_mod(hi, lo, b, y, p);
+    sub128_mod(hi, lo, c, z, p);
+    return redc128(hi, lo, p, pn);
+}
 __device__ __forceinline__ u64 add64(u64 a, u64 b, u64 p) { u64 s = a + b; return s >= p ? s - p : s; }
 __device__ __forceinline__ u64 sub64(u64 a, u64 b, u64 p) { return a >= b ? a - b : a + (p - b); }
 

@@ -46,23 +46,6 @@ struct LeafArgs {
 };
 
 // ------------------------------------------------------------------ device arithmetic
-__device__ __forceinline__ u64 redc128(u64 hi, u64 lo, u64 p, u64 pn)
-{
-    // (hi 2^64 + lo) / 2^64 mod p for hi 2^64 + lo < p 2^64
-    u64 m = lo * pn;
-    u64 r = hi + __umul64hi(m, p) + (lo != 0);
-    return csub64(r, p);
-}
-// Montgomery form of a x - b y mod p with one reduction: T = a x - b y (+ p 2^64 when
-// a x < b y) lies in [0, p 2^64), and redc128(T) = (a x - b y) 2^-64 mod p.
-__device__ __forceinline__ u64 mont_msub(u64 a, u64 x, u64 b, u64 y, u64 p, u64 pn)
-{
-    const u64 l1 = a * x, h1 = __umul64hi(a, x), l2 = b * y, h2 = __umul64hi(b, y);
-    const u64 lo = l1 - l2, b1 = l1 < l2;
-    const bool neg = h1 < h2 || (h1 == h2 && b1);
-    const u64 hi = h1 - h2 - b1 + (neg ? p : 0);
-    return redc128(hi, lo, p, pn);
-}
 __device__ __forceinline__ void mac128(u64 &hi, u64 &lo, u64 a, u64 b)
 {
     u64 l = a * b, h = __umul64hi(a, b);

@@ -169,13 +169,14 @@ __global__ void __launch_bounds__(256) k_res_euclid(const __grid_constant__ ResP
             const u64 lcA = A[da];
             const int sh = da - b;
             if (sh >= 1) {
-                const u64 t = sub64(mm(lcB, A[da - 1], I), mm(lcA, B[b - 1], I), I.p);
+                const u64 t = mont_msub(lcB, A[da - 1], lcA, B[b - 1], I.p, I.pn);
                 const u64 f1 = mm(lcB, lcA, I);
                 __syncwarp();                       // every lane has read A[da], A[da - 1]
                 for (int c = lane; c <= da - 2; c += 32) {
-                    u64 x = mm(lcB2, A[c], I);
-                    if (c >= sh) x = sub64(x, mm(f1, B[c - sh], I), I.p);
-                    if (c >= sh - 1) x = sub64(x, mm(t, B[c - sh + 1], I), I.p);
+                    u64 x;
+                    if (c >= sh) x = mont_msub2(lcB2, A[c], f1, B[c - sh], t, B[c - sh + 1], I.p, I.pn);
+                    else if (c == sh - 1) x = mont_msub(lcB2, A[c], t, B[0], I.p, I.pn);
+                    else x = mm(lcB2, A[c], I);
                     A[c] = x;
                 }
                 s += 2;
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(256) k_res_euclid(const __grid_constant__ ResP
                 da = warp_deg(A, da - 2);
             } else {
                 __syncwarp();
-                for (int c = lane; c <= da - 1; c += 32) A[c] = sub64(mm(lcB, A[c], I), mm(lcA, B[c], I), I.p);
+                for (int c = lane; c <= da - 1; c += 32) A[c] = mont_msub(lcB, A[c], lcA, B[c], I.p, I.pn);
                 s += 1;
                 __syncwarp();
                 da = warp_deg(A, da - 1);
