@@ -445,11 +445,11 @@ int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
         stage_end(ctx, tok);
         // 2. pointwise products (jobs of any length share launches): tensor-core limb
         //    products where the shape allows (m, n, k <= 32) when that form is requested,
-        //    outer products (n = 1) by a streaming kernel, the staged CUDA-core 64-bit
-        //    form otherwise
+        //    small inner dimensions (n <= 8) by a streaming kernel (one launch per n), the
+        //    staged CUDA-core 64-bit form otherwise
         tok = stage_begin(ctx, PM_STAGE_POINTWISE);
         {
-            std::vector<PwJob> jobs, tjobs, ojobs; std::vector<int> nb, tnb, onb;
+            std::vector<PwJob> jobs, tjobs, sjobs[9]; std::vector<int> nb, tnb, snb[9];
             for (int r = r0; r < r1; r++) {
                 const ProdReq &q = reqs[r];
                 const Plan &P = plan[r];
@@ -460,16 +460,17 @@ int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
                     j.A = (u32 *)(b.A + i * P.bA); j.B = (u32 *)(b.B + i * P.bB); j.C = (u32 *)(b.C + i * P.bC);
                     j.m = q.m; j.n = q.n; j.k = q.k; j.L = 1 << q.lg; j.P = prime_dev(*P.pr[i], q.lg);
                     if (ctx->opt_pointwise == 2 && tc_supported(j)) { tjobs.push_back(j); tnb.push_back(tc_blocks(j)); }
-                    else if (pw1_supported(j)) { ojobs.push_back(j); onb.push_back(pw1_blocks(j)); }
+                    else if (pws_supported(j)) { sjobs[j.n].push_back(j); snb[j.n].push_back(pws_blocks(j)); }
                     else { const int nbk = pw_plan(j); jobs.push_back(j); nb.push_back(nbk); }
                 }
             }
             if (!jobs.empty())
                 CKI(launch_packs(ctx, jobs, nb, [&](const JobPack<PwJob> &pk) {
                     return launch_pointwise(pk, ctx->stream, &ctx->launches); }));
-            if (!ojobs.empty())
-                CKI(launch_packs(ctx, ojobs, onb, [&](const JobPack<PwJob> &pk) {
-                    return launch_pointwise_n1(pk, ctx->stream, &ctx->launches); }));
+            for (int nn = 1; nn <= 8; nn++)
+                if (!sjobs[nn].empty())
+                    CKI(launch_packs(ctx, sjobs[nn], snb[nn], [&](const JobPack<PwJob> &pk) {
+                        return launch_pointwise_sn(pk, ctx->stream, &ctx->launches); }));
             if (!tjobs.empty())
                 CKI(launch_packs(ctx, tjobs, tnb, [&](const JobPack<PwJob> &pk) {
                     return launch_pointwise_tc(pk, ctx->d_status, ctx->stream, &ctx->launches); }));

@@ -194,9 +194,9 @@ cudaError_t launch_ntt_fwd_cols(const JobPack<ColJob> &pk, int lg, cudaStream_t 
 cudaError_t launch_ntt_inv_cols(const JobPack<ColJob> &pk, int lg, cudaStream_t st, long long *launches);
 cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
 int pw_plan(PwJob &j);
-cudaError_t launch_pointwise_n1(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
-bool pw1_supported(const PwJob &j);
-int pw1_blocks(const PwJob &j);
+cudaError_t launch_pointwise_sn(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
+bool pws_supported(const PwJob &j);
+int pws_blocks(const PwJob &j);
 cudaError_t launch_crt(const JobPack<CrtJob> &pk, cudaStream_t st, long long *launches);
 cudaError_t launch_pointwise_tc(const JobPack<PwJob> &pk, int *status, cudaStream_t st, long long *launches);
 bool tc_supported(const PwJob &j);

@@ -272,46 +272,77 @@ cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long lon
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ inner dimension 1
-// C[i][c] = A[i][0] B[0][c] at every point (n = 1: outer products, e.g. many
-// polynomials times one chirp).  One thread per point keeps B's k <= PW1_KMAX
-// residues in registers and streams PW1_ROWS rows of A; every access is coalesced
-// across the points of a warp.  Memory-bound: A and C once, B once per row group.
-#define PW1_THREADS 256
-#define PW1_ROWS 16
-#define PW1_KMAX 8
+// ------------------------------------------------------------------ small inner dimension
+// C = A B at every point for n <= PWS_NMAX: the work is n multiply-adds per output, so
+// the kernel is bound by the m k output writes.  One thread per point keeps an n x 8
+// block of B's residues in registers and streams PWS_ROWS rows of A (n residues each);
+// an output is one 64-bit sum of n <= 8 products below 2^60, reduced once.  Every
+// access is coalesced across the points of a warp.  Blocks: points x row groups x
+// column chunks of 8 (n <= 4) or 4 (n > 4, to stay near 100 registers).
+#define PWS_THREADS 256
+#define PWS_ROWS 16
+#define PWS_NMAX 8
 
-int pw1_blocks(const PwJob &j)
+static int pws_kc(int n) { return n <= 4 ? 8 : 4; }
+
+int pws_blocks(const PwJob &j)
 {
-    return ((j.L + PW1_THREADS - 1) / PW1_THREADS) * ((j.m + PW1_ROWS - 1) / PW1_ROWS);
+    const int kc = pws_kc(j.n);
+    return ((j.L + PWS_THREADS - 1) / PWS_THREADS) * ((j.m + PWS_ROWS - 1) / PWS_ROWS) * ((j.k + kc - 1) / kc);
 }
-bool pw1_supported(const PwJob &j) { return j.n == 1 && j.k <= PW1_KMAX; }
+bool pws_supported(const PwJob &j) { return j.n <= PWS_NMAX; }
 
-__global__ void __launch_bounds__(PW1_THREADS) k_pointwise_n1(const __grid_constant__ JobPack<PwJob> pk)
+template <int N, int PWS_KC>
+__global__ void __launch_bounds__(PWS_THREADS) k_pointwise_sn(const __grid_constant__ JobPack<PwJob> pk)
 {
     const int b = blockIdx.x;
     const int jb = find_job_pw(pk.blk_start, b);
     const PwJob &J = pk.jobs[jb];
     const int L = J.L, k = J.k;
-    const int npb = (L + PW1_THREADS - 1) / PW1_THREADS;
-    const int rel = b - pk.blk_start[jb];
-    const int pt = (rel % npb) * PW1_THREADS + threadIdx.x, i0 = (rel / npb) * PW1_ROWS;
+    const int npb = (L + PWS_THREADS - 1) / PWS_THREADS, nrg = (J.m + PWS_ROWS - 1) / PWS_ROWS;
+    int rel = b - pk.blk_start[jb];
+    const int pt = (rel % npb) * PWS_THREADS + threadIdx.x;
+    rel /= npb;
+    const int i0 = (rel % nrg) * PWS_ROWS, c0 = (rel / nrg) * PWS_KC;
     if (pt >= L) return;
-    u32 bv[PW1_KMAX];
+    const int kcv = min(PWS_KC, k - c0);
+    u32 bv[N][PWS_KC];
 #pragma unroll
-    for (int c = 0; c < PW1_KMAX; c++) bv[c] = c < k ? __ldg(J.B + (i64)c * L + pt) : 0u;
-    const int i1 = min(J.m, i0 + PW1_ROWS);
+    for (int l = 0; l < N; l++)
+#pragma unroll
+        for (int c = 0; c < PWS_KC; c++) bv[l][c] = c < kcv ? __ldg(J.B + ((i64)l * k + c0 + c) * L + pt) : 0u;
+    const int i1 = min(J.m, i0 + PWS_ROWS);
     for (int i = i0; i < i1; i++) {
-        const u32 a = __ldcs(J.A + (i64)i * L + pt);
+        u32 av[N];
 #pragma unroll
-        for (int c = 0; c < PW1_KMAX; c++)
-            if (c < k) __stcs(J.C + ((i64)i * k + c) * L + pt, reduce64((u64)a * bv[c], J.P));
+        for (int l = 0; l < N; l++) av[l] = __ldg(J.A + ((i64)i * N + l) * L + pt);
+#pragma unroll
+        for (int c = 0; c < PWS_KC; c++) {
+            if (c < kcv) {
+                u64 acc = 0;
+#pragma unroll
+                for (int l = 0; l < N; l++) acc += (u64)av[l] * bv[l][c];
+                __stcs(J.C + ((i64)i * k + c0 + c) * L + pt, reduce64(acc, J.P));
+            }
+        }
     }
 }
 
-cudaError_t launch_pointwise_n1(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches)
+// one launch per inner dimension n (every job of the pack has the same n)
+cudaError_t launch_pointwise_sn(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches)
 {
-    k_pointwise_n1<<<pk.blk_start[pk.njobs], PW1_THREADS, 0, st>>>(pk);
+    const int nb = pk.blk_start[pk.njobs];
+    switch (pk.jobs[0].n) {
+    case 1: k_pointwise_sn<1, 8><<<nb, PWS_THREADS, 0, st>>>(pk); break;
+    case 2: k_pointwise_sn<2, 8><<<nb, PWS_THREADS, 0, st>>>(pk); break;
+    case 3: k_pointwise_sn<3, 8><<<nb, PWS_THREADS, 0, st>>>(pk); break;
+    case 4: k_pointwise_sn<4, 8><<<nb, PWS_THREADS, 0, st>>>(pk); break;
+    case 5: k_pointwise_sn<5, 4><<<nb, PWS_THREADS, 0, st>>>(pk); break;
+    case 6: k_pointwise_sn<6, 4><<<nb, PWS_THREADS, 0, st>>>(pk); break;
+    case 7: k_pointwise_sn<7, 4><<<nb, PWS_THREADS, 0, st>>>(pk); break;
+    case 8: k_pointwise_sn<8, 4><<<nb, PWS_THREADS, 0, st>>>(pk); break;
+    default: return cudaErrorInvalidValue;
+    }
     ++*launches;
     return cudaGetLastError();
 }
