@@ -322,7 +322,7 @@ static int fwd_entries_per_block(int lg)
     return th / tpt;
 }
 
-// Forward jobs of one operand modulo one prime (a column pass first when L > 2^13).
+// Forward jobs of one operand modulo one prime (a column pass first when L > 2^14).
 static void add_forward(const PrimeDev &P, const void *src, int mode, int64_t src_stride, int64_t src_len,
                         int entries, u32 *dst, int lg, std::vector<FwdJob> &blk, std::vector<int> &blk_n,
                         std::vector<ColJob> &col, std::vector<int> &col_n)

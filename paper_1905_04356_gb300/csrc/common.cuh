@@ -19,7 +19,7 @@ typedef uint64_t u64;
 typedef int64_t i64;
 
 #define PM_MAX_LOG2L 20      // largest transform: 2^20 points
-#define PM_LB_LOG2 13        // transforms up to 2^13 points run in one CTA
+#define PM_LB_LOG2 14        // transforms up to 2^14 points run in one CTA
 #define PM_MAXJ 32           // job descriptors per launch
 #define PM_MAXK 6            // CRT primes per product
 

@@ -12,8 +12,8 @@
 //    forward pass reads the caller's coefficients directly (reduction mod q and
 //    zero padding fused), the last inverse pass writes the requested slice
 //    directly (scaling by L^-1 fused).
-//  * Transforms longer than 2^13 points: a column kernel runs the top stages
-//    on 32-column tiles (coalesced rows), the block kernel the bottom 13.
+//  * Transforms longer than 2^14 points: a column kernel runs the top stages
+//    on column tiles (coalesced rows), the block kernel the bottom 14.
 //  * Twiddles: one table per prime, twf[h + r] = omega_{2h}^r with its Shoup
 //    companion, so every stage reads a contiguous run and any transform length
 //    shares the same table.
@@ -190,8 +190,9 @@ __device__ __forceinline__ void fwd_pass16(u32 (&v)[16], u32 *X, const FwdJob &J
     }
 }
 
+// 2^14 points: one CTA of 1024 threads (two per SM); shorter transforms: 512 threads, four CTAs per SM
 template <int LG>
-__global__ void __launch_bounds__(512, 4) k_ntt_fwd_block(const __grid_constant__ JobPack<FwdJob> pk)
+__global__ void __launch_bounds__(LG == 14 ? 1024 : 512, LG == 14 ? 2 : 4) k_ntt_fwd_block(const __grid_constant__ JobPack<FwdJob> pk)
 {
     extern __shared__ u32 sm[];
     constexpr int L = 1 << LG, TPT = L >> 4, B0 = ((LG - 1) & 3) + 1;
@@ -281,7 +282,7 @@ __device__ __forceinline__ void inv_pass16(u32 (&v)[16], u32 *X, const InvJob &J
 }
 
 template <int LG>
-__global__ void __launch_bounds__(512, 4) k_ntt_inv_block(const __grid_constant__ JobPack<InvJob> pk)
+__global__ void __launch_bounds__(LG == 14 ? 1024 : 512, LG == 14 ? 2 : 4) k_ntt_inv_block(const __grid_constant__ JobPack<InvJob> pk)
 {
     extern __shared__ u32 sm[];
     constexpr int L = 1 << LG, TPT = L >> 4, B0 = ((LG - 1) & 3) + 1;
@@ -356,6 +357,7 @@ cudaError_t launch_ntt_fwd_block(const JobPack<FwdJob> &pk, int lg, cudaStream_t
     case 11: return fwd_lg<11>(pk, st);
     case 12: return fwd_lg<12>(pk, st);
     case 13: return fwd_lg<13>(pk, st);
+    case 14: return fwd_lg<14>(pk, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -374,12 +376,13 @@ cudaError_t launch_ntt_inv_block(const JobPack<InvJob> &pk, int lg, cudaStream_t
     case 11: return inv_lg<11>(pk, st);
     case 12: return inv_lg<12>(pk, st);
     case 13: return inv_lg<13>(pk, st);
+    case 14: return inv_lg<14>(pk, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
 // ------------------------------------------------------------------ column passes
-// Transform length L = 2^lg > 2^13: R1 = L / 2^13 rows per column.  A block takes
+// Transform length L = 2^lg > 2^14: R1 = L / 2^14 rows per column.  A block takes
 // a tile of TC = 4096 / R1 consecutive columns (at least 32) and all R1 rows, so
 // every tile holds 4096 points; rows of a tile are contiguous runs of TC words.
 #define COLS_POINTS 4096

@@ -65,8 +65,10 @@ CASES = [
     (2, 4, 3, 3, 3, 50, 20),
     (COMPOSITE, 4, 3, 4, 2, 90, 45),
     (P60, 8, 2, 3, 2, 4000, 4500),        # L = 2^13, one CTA per transform
-    (synth.P998, 4, 2, 2, 3, 5000, 4000),  # L = 2^14: column path
+    (synth.P998, 4, 2, 2, 3, 5000, 4000),  # L = 2^14: one CTA of 1024 threads
     (P60, 8, 2, 2, 1, 9000, 7000),         # L = 2^14, 5 primes
+    (synth.P998, 4, 1, 2, 1, 9000, 8000),  # L = 2^15: column pass of 2 rows, then 2^14-point blocks
+    (P60, 8, 1, 1, 2, 9000, 8000),         # L = 2^15, 5 primes
     # pointwise block plans: a slice left empty in the last inner chunk (n = 32 + 5),
     # 2 x 2 block tiles with two chunks, uneven tiles, several column tiles, 4 slices
     (P60, 8, 4, 37, 8, 50, 40),
@@ -121,7 +123,7 @@ def test_middle_product_matches_oracle(ctx, p, w):
 
 
 def test_long_transform_sampled(ctx):
-    """1 x 2 . 2 x 1 with lengths 40000 / 30000: L = 2^17 (column path, 7 top stages)."""
+    """1 x 2 . 2 x 1 with lengths 40000 / 30000: L = 2^17 (column path, 3 top stages)."""
     p = P60
     g = synth.rng(3)
     A = _rand(g, p, (1, 2, 40000), 8)
