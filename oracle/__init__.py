@@ -15,7 +15,8 @@ of the paper its C function follows:
   evaluation / Euclid / interpolation method.
 * ``matinv`` / ``inv_trunc``: Sec. 4 (linear system solving by lifting): the
   inverse of a constant matrix and the truncated inverse A^-1 mod x^t, by
-  definition.
+  definition.  ``solve_series``: the series solution A^-1 b mod x^N (what
+  Dixon's lifting computes), by definition.
 """
 from __future__ import annotations
 
@@ -63,6 +64,8 @@ def lib():
         L.orc_matinv.argtypes = [u64, i32, P, P]
         L.orc_inv_trunc.restype = i32
         L.orc_inv_trunc.argtypes = [u64, i32, P, i64, i64, P]
+        L.orc_solve_series.restype = i32
+        L.orc_solve_series.argtypes = [u64, i32, P, i64, P, i64, i64, P]
         _lib = L
     return _lib
 
@@ -195,6 +198,20 @@ def inv_trunc(p, A, t, threads=None):
     if rc[0]:
         raise SingularError("A(0) is singular mod p")
     return X
+
+
+def solve_series(p, A, b, N, threads=None):
+    """A^-1 b mod x^N (A: n x n x dA with A(0) invertible mod the prime p, b: n x 1 x db): n x 1 x N."""
+    A, b = _u64(A), _u64(b)
+    n, n2, dA = A.shape
+    assert n == n2 and b.shape[0] == n and b.shape[1] == 1
+    v = np.zeros((n, 1, N), dtype=np.uint64)
+    rc = []
+    _with_threads(threads, lambda: rc.append(lib().orc_solve_series(p, n, _ptr(A), dA, _ptr(b), b.shape[2], N,
+                                                                       _ptr(v))))
+    if rc[0]:
+        raise SingularError("A(0) is singular mod p")
+    return v
 
 
 def powmod(a, e, p):

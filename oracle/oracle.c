@@ -39,6 +39,10 @@
  *                    invertible, taken by its definition -- the power series
  *                    X with A.X = I mod x^t, coefficient by coefficient:
  *                    X_0 = A_0^-1, X_j = -A_0^-1 (A_1 X_{j-1} + ... + A_j X_0).
+ *   orc_solve_series Sec. 4, lifting: the power-series solution
+ *                    v = A^-1 b mod x^N that Dixon's algorithm produces, by
+ *                    its definition A.v = b mod x^N: v_0 = A_0^-1 b_0,
+ *                    v_j = A_0^-1 (b_j - A_1 v_{j-1} - ... - A_j v_0).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -512,5 +516,35 @@ int orc_inv_trunc(u64 p, int n, const u64 *A, i64 dA, i64 t, u64 *X)
             }
     }
     free(A0); free(A0i); free(Sj);
+    return 0;
+}
+
+/* v (n x 1, length N) = A^-1 b mod x^N for A (n x n, length dA) with A(0)
+ * invertible and b (n x 1, length db): v_j = A_0^-1 (b_j - sum_{i=1..j} A_i v_{j-i}).
+ * Returns 0, or 1 if A(0) is singular (v untouched). */
+int orc_solve_series(u64 p, int n, const u64 *A, i64 dA, const u64 *b, i64 db, i64 N, u64 *v)
+{
+    size_t nn = (size_t)n * n;
+    u64 *A0 = (u64 *)calloc(nn, sizeof(u64)), *A0i = (u64 *)calloc(nn, sizeof(u64));
+    u64 *rj = (u64 *)malloc(sizeof(u64) * n);
+    for (size_t e = 0; e < nn; e++) A0[e] = A[e * dA];
+    if (orc_matinv(p, n, A0, A0i)) { free(A0); free(A0i); free(rj); return 1; }
+    memset(v, 0, sizeof(u64) * (size_t)n * N);
+    for (i64 j = 0; j < N; j++) {
+        /* r_j = b_j - sum_{i=1..min(j, dA-1)} A_i v_{j-i} */
+        for (int r = 0; r < n; r++) {
+            u128 acc = 0;
+            for (i64 i = 1; i <= j && i < dA; i++)
+                for (int l = 0; l < n; l++) acc_add(&acc, A[((size_t)r * n + l) * dA + i], v[(size_t)l * N + (j - i)], p);
+            const u64 bj = j < db ? b[(size_t)r * db + j] % p : 0;
+            rj[r] = f_sub(bj, (u64)(acc % p), p);
+        }
+        for (int r = 0; r < n; r++) {
+            u128 acc = 0;
+            for (int l = 0; l < n; l++) acc_add(&acc, A0i[(size_t)r * n + l], rj[l], p);
+            v[(size_t)r * N + j] = (u64)(acc % p);
+        }
+    }
+    free(A0); free(A0i); free(rj);
     return 0;
 }

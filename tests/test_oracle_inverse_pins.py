@@ -127,3 +127,44 @@ def test_constant_matrix_and_singular_constant_term():
     A[1, 1, 0] = 1
     with pytest.raises(oracle.SingularError):
         oracle.inv_trunc(p, A, 4)
+
+
+# ------------------------------------------------------------ series solution (Dixon's output)
+@pytest.mark.parametrize("p", PRIMES)
+@pytest.mark.parametrize("n,dA,db,N", [(1, 1, 1, 1), (1, 3, 2, 10), (2, 4, 4, 13), (3, 5, 2, 20), (4, 3, 6, 9)])
+def test_series_solution_defining_identity(p, n, dA, db, N):
+    """A.v = b mod x^N with Kronecker-substitution products."""
+    rnd = random.Random(hash((p, n, dA, db, N)) & 0xffff)
+    A = _rand(rnd, p, n, n, dA)
+    A[:, :, 0] = np.array(_rand_invertible_const(rnd, p, n), dtype=np.uint64)
+    b = _rand(rnd, p, n, 1, db)
+    v = oracle.solve_series(p, A, b, N)
+    assert v.shape == (n, 1, N)
+    Av = np.array(pyref.ks_pmat_mul(p, A.tolist(), v.tolist()), dtype=object)
+    got = [[[int(Av[i, 0, t]) if t < Av.shape[2] else 0 for t in range(N)]] for i in range(n)]
+    exp = [[[int(b[i, 0, t]) if t < db else 0 for t in range(N)]] for i in range(n)]
+    assert got == exp
+
+
+@pytest.mark.parametrize("p", [97, synth.P998, P62])
+def test_series_solution_scalar_closed_form(p):
+    """(1 - a x) v = 1 + c x: v_0 = 1, v_j = a^(j-1) (a + c) for j >= 1."""
+    a, c = 1234567 % p, 7654321 % p
+    A = np.array([[[1, (p - a) % p]]], dtype=np.uint64)
+    b = np.array([[[1, c]]], dtype=np.uint64)
+    v = oracle.solve_series(p, A, b, 30)
+    assert [int(x) for x in v[0, 0]] == [1] + [pow(a, j - 1, p) * (a + c) % p for j in range(1, 30)]
+
+
+def test_series_solution_prefix_and_singular():
+    p = synth.P998
+    rnd = random.Random(9)
+    A = _rand(rnd, p, 3, 3, 4)
+    A[:, :, 0] = np.array(_rand_invertible_const(rnd, p, 3), dtype=np.uint64)
+    b = _rand(rnd, p, 3, 1, 4)
+    assert np.array_equal(oracle.solve_series(p, A, b, 8), oracle.solve_series(p, A, b, 20)[:, :, :8])
+    S = np.zeros((2, 2, 2), dtype=np.uint64)
+    S[0, 0, 1] = 1
+    S[1, 1, 0] = 1
+    with pytest.raises(oracle.SingularError):
+        oracle.solve_series(p, S, np.ones((2, 1, 1), dtype=np.uint64), 4)
