@@ -44,9 +44,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the PM-Basis / batched / resultant / inverse timings")
-    ap.add_argument("--extra", default="pm_basis,resultant,batched,inverse",
-                    help="comma-separated subset of pm_basis, resultant, batched, inverse")
+                    help="skip the PM-Basis / batched / resultant / inverse / solve timings")
+    ap.add_argument("--extra", default="pm_basis,resultant,batched,inverse,solve",
+                    help="comma-separated subset of pm_basis, resultant, batched, inverse, solve")
     return ap.parse_args()
 
 
@@ -182,10 +182,11 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------- other workloads (reported under "extra")
-def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"), reps=3):
+def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse", "solve"), reps=3):
     """PM-Basis (F 32x16, order 8192, 60-bit p), 512 batched uneven products, resultants
     (deg_x = deg_y = 150, 1 prime and 16 primes), the truncated inverse of a 32x32 matrix of
-    degree < 4096 mod x^4096 (60-bit p): ms per call, CUDA events on the stream."""
+    degree < 4096 mod x^4096 and the lifted series solution of A v = b mod x^32768 (same A, b of
+    degree < 4096; 60-bit p): ms per call, CUDA events on the stream."""
     import numpy as np
     import torch
     import synth
@@ -249,10 +250,25 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"
         out["inv_trunc_stage_ms"] = {k: round(v[0], 3) for k, v in st.items() if v[1]}
         return out
 
+    def solve():
+        W = synth.solve_w(0)
+        A, b = pmat.to_device(W["A"]), pmat.to_device(W["b"])
+        v = torch.empty((32, 1, W["N"]), dtype=A.dtype, device="cuda")
+        run = lambda: pmat.pmat_solve_series(ctx, W["p"], A, b, W["N"], out=v)  # noqa: E731
+        out = {"solve_series_32x32_d4096_N32768_ms": round(ev_ms(run, reps), 3)}
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
+        ctx.stage_times()
+        run()
+        st = ctx.stage_times()
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
+        ctx.sync()
+        out["solve_series_stage_ms"] = {k: round(v2[0], 3) for k, v2 in st.items() if v2[1]}
+        return out
+
     out = {}
     with torch.cuda.stream(s):
         for name, fn in (("pm_basis", pm_basis), ("resultant", resultant), ("batched", batched),
-                         ("inverse", inverse)):
+                         ("inverse", inverse), ("solve", solve)):
             if name in which:
                 out.update(fn())
     return out

@@ -16,6 +16,8 @@
  *   pmat_inv_trunc                Sec. 4, "Linear system solving": the
  *                                 truncated inverse A^-1 mod x^t by matrix
  *                                 Newton iteration
+ *   pmat_solve_series             Sec. 4, lifting: A^-1 b mod x^N by Dixon's
+ *                                 algorithm over the truncated inverse
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -51,7 +53,8 @@ enum {
     PM_OK = 0,
     PM_EINVAL = 1,       /* bad argument (dimension, length, modulus, width) */
     PM_EDOMAIN = 2,      /* an input coefficient is not in [0, p) (debug check), or
-                            A(0) is singular in pmat_inv_trunc (deferred, pm_sync) */
+                            A(0) is singular in pmat_inv_trunc / pmat_solve_series
+                            (deferred, pm_sync) */
     PM_ENOMEM = 3,       /* device workspace allocation failed */
     PM_ECUDA = 4,        /* a CUDA runtime call or kernel launch failed */
     PM_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
@@ -218,6 +221,19 @@ int bivariate_resultant(pm_ctx *ctx, int nprimes, const uint64_t *primes,
  * returns PM_EDOMAIN.  Asynchronous; uses the context's driver arena. */
 int pmat_inv_trunc(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA,
                    int64_t t, void *X);
+
+/* Power-series solution of A v = b (Sec. 4, "Linear system solving", lifting:
+ * Dixon's algorithm).  A: DEVICE n x n matrix, entries of length dA (width w);
+ * b: DEVICE n x 1 matrix, entries of length db; v: DEVICE output n x 1, entries
+ * of length N, v = A^-1 b mod x^N.  With delta = max(dA, db) and S = A^-1 mod
+ * x^delta (pmat_inv_trunc's method): y_i = S r_i mod x^delta, r_{i+1} = (r_i -
+ * A y_i) / x^delta from r_0 = b, v = sum_i y_i x^(i delta): ceil(N / delta)
+ * truncated products and middle products on the hot path.  Requires p prime,
+ * 1 <= n <= 128, dA, db, N >= 1, 2 delta <= 2^20, N <= 2^19.  A(0) singular:
+ * v is undefined and pm_sync returns PM_EDOMAIN.  Asynchronous; uses the
+ * context's driver arena. */
+int pmat_solve_series(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA,
+                      const void *b, int64_t db, int64_t N, void *v);
 
 #ifdef __cplusplus
 }

@@ -445,11 +445,12 @@ int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
         stage_end(ctx, tok);
         // 2. pointwise products (jobs of any length share launches): tensor-core limb
         //    products where the shape allows (m, n, k <= 32) when that form is requested,
-        //    small inner dimensions (n <= 8) by a streaming kernel (one launch per n), the
-        //    staged CUDA-core 64-bit form otherwise
+        //    small inner dimensions (n <= 8) by a streaming kernel (one launch per n),
+        //    matrix-vector products (k = 1, n <= 64) by another, the staged CUDA-core
+        //    64-bit form otherwise
         tok = stage_begin(ctx, PM_STAGE_POINTWISE);
         {
-            std::vector<PwJob> jobs, tjobs, sjobs[9]; std::vector<int> nb, tnb, snb[9];
+            std::vector<PwJob> jobs, tjobs, sjobs[9], vjobs; std::vector<int> nb, tnb, snb[9], vnb;
             for (int r = r0; r < r1; r++) {
                 const ProdReq &q = reqs[r];
                 const Plan &P = plan[r];
@@ -461,12 +462,16 @@ int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
                     j.m = q.m; j.n = q.n; j.k = q.k; j.L = 1 << q.lg; j.P = prime_dev(*P.pr[i], q.lg);
                     if (ctx->opt_pointwise == 2 && tc_supported(j)) { tjobs.push_back(j); tnb.push_back(tc_blocks(j)); }
                     else if (pws_supported(j)) { sjobs[j.n].push_back(j); snb[j.n].push_back(pws_blocks(j)); }
+                    else if (pwv_supported(j)) { vjobs.push_back(j); vnb.push_back(pwv_blocks(j)); }
                     else { const int nbk = pw_plan(j); jobs.push_back(j); nb.push_back(nbk); }
                 }
             }
             if (!jobs.empty())
                 CKI(launch_packs(ctx, jobs, nb, [&](const JobPack<PwJob> &pk) {
                     return launch_pointwise(pk, ctx->stream, &ctx->launches); }));
+            if (!vjobs.empty())
+                CKI(launch_packs(ctx, vjobs, vnb, [&](const JobPack<PwJob> &pk) {
+                    return launch_pointwise_mv(pk, ctx->stream, &ctx->launches); }));
             for (int nn = 1; nn <= 8; nn++)
                 if (!sjobs[nn].empty())
                     CKI(launch_packs(ctx, sjobs[nn], snb[nn], [&](const JobPack<PwJob> &pk) {

@@ -197,6 +197,9 @@ int pw_plan(PwJob &j);
 cudaError_t launch_pointwise_sn(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
 bool pws_supported(const PwJob &j);
 int pws_blocks(const PwJob &j);
+cudaError_t launch_pointwise_mv(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
+bool pwv_supported(const PwJob &j);
+int pwv_blocks(const PwJob &j);
 cudaError_t launch_crt(const JobPack<CrtJob> &pk, cudaStream_t st, long long *launches);
 cudaError_t launch_pointwise_tc(const JobPack<PwJob> &pk, int *status, cudaStream_t st, long long *launches);
 bool tc_supported(const PwJob &j);

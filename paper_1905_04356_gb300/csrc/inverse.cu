@@ -117,18 +117,21 @@ __global__ void k_negate_slice(void *X, int w, i64 sX, i64 off, i64 h, i64 count
         if (_rc) return _rc;                                            \
     } while (0)
 
-extern "C" int pmat_inv_trunc(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA, int64_t t, void *X)
+static int check_inverse_args(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA, int64_t t, void *X)
 {
-    if (!ctx) return PM_EINVAL;
     if (w != 4 && w != 8) return pm_fail(ctx, PM_EINVAL, "w must be 4 or 8");
     if (p < 2 || (w == 4 && p >= (1ull << 32)) || (w == 8 && p >= (1ull << 62)))
         return pm_fail(ctx, PM_EINVAL, "need 2 <= p < 2^32 (w = 4) or 2^62 (w = 8)");
     if (n < 1 || dA < 1 || t < 1) return pm_fail(ctx, PM_EINVAL, "need n, dA, t >= 1");
-    if (n > 128) return pm_fail(ctx, PM_EUNSUPPORTED, "pmat_inv_trunc supports n <= 128");
-    if (t > (int64_t(1) << (PM_MAX_LOG2L - 1))) return pm_fail(ctx, PM_EINVAL, "t too large for the transforms");
+    if (n > 128) return pm_fail(ctx, PM_EUNSUPPORTED, "n <= 128 is supported");
+    if (t > (int64_t(1) << (PM_MAX_LOG2L - 1))) return pm_fail(ctx, PM_EINVAL, "length too large for the transforms");
     if (!A || !X) return pm_fail(ctx, PM_EINVAL, "null buffer");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return pm_fail(ctx, PM_ECUDA, "cudaSetDevice failed");
+    return PM_OK;
+}
 
+static InvArith inv_arith(uint64_t p)
+{
     InvArith F;
     memset(&F, 0, sizeof(F));
     F.p = p;
@@ -142,14 +145,24 @@ extern "C" int pmat_inv_trunc(pm_ctx *ctx, uint64_t p, int w, int n, const void 
     } else {
         F.one = 1;
     }
-    const size_t nn = (size_t)n * n;
-    const int64_t hmax = t / 2 > 0 ? t / 2 : 1;
-    const size_t bM = (nn * 2 * 8 + 255) / 256 * 256, bE = nn * (size_t)hmax * w;
-    CKI(arena_reserve(ctx, bM + bE + 512));
-    u64 *M = (u64 *)arena_alloc(ctx, nn * 2 * 8);
-    void *E = arena_alloc(ctx, bE);
-    if (!M || !E) return pm_fail(ctx, PM_ENOMEM, "arena too small");
+    return F;
+}
 
+static void negate_slice(pm_ctx *ctx, void *X, int w, int64_t sX, int64_t off, int64_t h, int64_t count, uint64_t p)
+{
+    const int64_t tot = count * h;
+    int grid = (int)((tot + 255) / 256);
+    if (grid > 4096) grid = 4096;
+    k_negate_slice<<<grid, 256, 0, ctx->stream>>>(X, w, sX, off, h, count, p);
+    ctx->launches++;
+}
+
+// X = A^-1 mod x^t with scratch M (n x 2n u64) and E (n x n x max(t/2, 1) words of width w).
+static int inv_trunc_core(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA, int64_t t, void *X,
+                          u64 *M, void *E)
+{
+    const InvArith F = inv_arith(p);
+    const int64_t nn = (int64_t)n * n;
     k_inv0<<<1, 1024, 0, ctx->stream>>>(F, A, w, dA, n, M, X, t, ctx->d_status);
     ctx->launches++;
     CKI(pm_cuda(ctx, cudaGetLastError(), "k_inv0"));
@@ -163,13 +176,69 @@ extern "C" int pmat_inv_trunc(pm_ctx *ctx, uint64_t p, int w, int n, const void 
         // X[k .. kk) = X_k . E mod x^h (no aliasing), then negated
         const int64_t dX = k < h ? k : h;
         CKI(prod_slice(ctx, p, w, n, n, n, X, dX, t, E, h, h, 0, h, ceil_log2(dX + h - 1), (char *)X + k * w, t));
-        const int64_t tot = (int64_t)nn * h;
-        int grid = (int)((tot + 255) / 256);
-        if (grid > 4096) grid = 4096;
-        k_negate_slice<<<grid, 256, 0, ctx->stream>>>(X, w, t, k, h, (int64_t)nn, p);
-        ctx->launches++;
+        negate_slice(ctx, X, w, t, k, h, nn, p);
         CKI(pm_cuda(ctx, cudaGetLastError(), "k_negate_slice"));
         k = kk;
+    }
+    return PM_OK;
+}
+
+static size_t inv_scratch_words(int n, int64_t t, int w, size_t *bE)
+{
+    const int64_t hmax = t / 2 > 0 ? t / 2 : 1;
+    *bE = (size_t)n * n * (size_t)hmax * w;
+    return (size_t)n * n * 2;
+}
+
+extern "C" int pmat_inv_trunc(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA, int64_t t, void *X)
+{
+    if (!ctx) return PM_EINVAL;
+    CKI(check_inverse_args(ctx, p, w, n, A, dA, t, X));
+    size_t bE;
+    const size_t wM = inv_scratch_words(n, t, w, &bE);
+    CKI(arena_reserve(ctx, wM * 8 + bE + 512));
+    u64 *M = (u64 *)arena_alloc(ctx, wM * 8);
+    void *E = arena_alloc(ctx, bE);
+    if (!M || !E) return pm_fail(ctx, PM_ENOMEM, "arena too small");
+    return inv_trunc_core(ctx, p, w, n, A, dA, t, X, M, E);
+}
+
+// Dixon's lifting (Sec. 4): with delta = max(dA, db) and S = A^-1 mod x^delta,
+//   y_i = S r_i mod x^delta,  r_{i+1} = (r_i - A y_i) / x^delta = -(coefficients
+//   delta .. 2 delta - 1 of A y_i)   (r_i has length delta and A y_i = r_i mod x^delta),
+// from r_0 = b; v = sum_i y_i x^(i delta).  Both steps are products on the hot path.
+extern "C" int pmat_solve_series(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA, const void *b,
+                                 int64_t db, int64_t N, void *v)
+{
+    if (!ctx) return PM_EINVAL;
+    CKI(check_inverse_args(ctx, p, w, n, A, dA, N, v));
+    if (db < 1 || !b) return pm_fail(ctx, PM_EINVAL, "need db >= 1 and b");
+    const int64_t delta = dA > db ? dA : db;
+    if (2 * delta > (int64_t(1) << PM_MAX_LOG2L)) return pm_fail(ctx, PM_EINVAL, "degree too large for the transforms");
+    size_t bE;
+    const size_t wM = inv_scratch_words(n, delta, w, &bE);
+    const size_t bS = (size_t)n * n * delta * w, bR = (size_t)n * delta * w;
+    CKI(arena_reserve(ctx, wM * 8 + bE + bS + bR + 4 * 256));
+    u64 *M = (u64 *)arena_alloc(ctx, wM * 8);
+    void *E = arena_alloc(ctx, bE);
+    void *S = arena_alloc(ctx, bS);
+    void *R = arena_alloc(ctx, bR);
+    if (!M || !E || !S || !R) return pm_fail(ctx, PM_ENOMEM, "arena too small");
+    CKI(inv_trunc_core(ctx, p, w, n, A, dA, delta, S, M, E));
+    // r_0 = b, zero-padded to length delta
+    CKI(pm_cuda(ctx, cudaMemsetAsync(R, 0, bR, ctx->stream), "residual"));
+    CKI(pm_cuda(ctx, cudaMemcpy2DAsync(R, (size_t)delta * w, b, (size_t)db * w, (size_t)db * w, (size_t)n,
+                                       cudaMemcpyDeviceToDevice, ctx->stream), "residual"));
+    for (int64_t i = 0, off = 0; off < N; i++, off += delta) {
+        const int64_t len = N - off < delta ? N - off : delta;
+        char *y = (char *)v + off * w;
+        // y_i = S r_i mod x^len (no aliasing)
+        CKI(prod_slice(ctx, p, w, n, n, 1, S, len, delta, R, len, delta, 0, len, ceil_log2(2 * len - 1), y, N));
+        if (off + delta >= N) break;
+        // r_{i+1} = -(coefficients delta .. 2 delta - 1 of A y_i) (no aliasing)
+        CKI(prod_slice(ctx, p, w, n, n, 1, A, dA, dA, y, delta, N, delta, delta, ceil_log2(dA + delta - 1), R, delta));
+        negate_slice(ctx, R, w, delta, 0, delta, n, p);
+        CKI(pm_cuda(ctx, cudaGetLastError(), "k_negate_slice"));
     }
     return PM_OK;
 }

@@ -347,6 +347,66 @@ cudaError_t launch_pointwise_sn(const JobPack<PwJob> &pk, cudaStream_t st, long 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ matrix-vector (k = 1)
+// c_i = sum_l A[i][l] b_l at every point, 8 < n <= PWV_NMAX: one thread per point keeps
+// b (n residues, zero-padded to NB) in registers and streams PWV_ROWS rows of A; each
+// output is a 64-bit (hi, lo) carry-chain sum, folded lazily to lo + (hi 2^32 mod q)
+// every 16 products (below 2^32 + 2q + 16 (q-1)^2 < 2^64) and reduced once.  Bound by
+// reading A once.
+#define PWV_THREADS 256
+#define PWV_ROWS 16
+#define PWV_NMAX 64
+
+int pwv_blocks(const PwJob &j) { return ((j.L + PWV_THREADS - 1) / PWV_THREADS) * ((j.m + PWV_ROWS - 1) / PWV_ROWS); }
+bool pwv_supported(const PwJob &j) { return j.k == 1 && j.n > PWS_NMAX && j.n <= PWV_NMAX; }
+
+template <int NB>
+__global__ void __launch_bounds__(PWV_THREADS) k_pointwise_mv(const __grid_constant__ JobPack<PwJob> pk)
+{
+    const int b = blockIdx.x;
+    const int jb = find_job_pw(pk.blk_start, b);
+    const PwJob &J = pk.jobs[jb];
+    const int L = J.L, n = J.n;
+    const u32 q = J.P.q, r32 = J.P.r32, r32s = J.P.r32s;
+    const int npb = (L + PWV_THREADS - 1) / PWV_THREADS;
+    const int rel = b - pk.blk_start[jb];
+    const int pt = (rel % npb) * PWV_THREADS + threadIdx.x, i0 = (rel / npb) * PWV_ROWS;
+    if (pt >= L) return;
+    u32 bv[NB];
+#pragma unroll
+    for (int l = 0; l < NB; l++) bv[l] = l < n ? __ldg(J.B + (i64)l * L + pt) : 0u;
+    const int i1 = min(J.m, i0 + PWV_ROWS);
+    for (int i = i0; i < i1; i++) {
+        const u32 *arow = J.A + (i64)i * n * L + pt;
+        u32 lo = 0, hi = 0;
+#pragma unroll
+        for (int l0 = 0; l0 < NB; l0 += 16) {
+#pragma unroll
+            for (int l = l0; l < l0 + 16; l++) {
+                const u32 a = l < n ? __ldcs(arow + (i64)l * L) : 0u;
+                asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;" : "+r"(lo), "+r"(hi) : "r"(a), "r"(bv[l]));
+            }
+            if (l0 + 16 < NB) {
+                const u32 t = shoup_mul(hi, r32, r32s, q);
+                asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, 0, 0;" : "+r"(lo), "=r"(hi) : "r"(t));
+            }
+        }
+        J.C[(i64)i * L + pt] = reduce64(((u64)hi << 32) | lo, J.P);
+    }
+}
+
+cudaError_t launch_pointwise_mv(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches)
+{
+    int nmax = 0;
+    for (int i = 0; i < pk.njobs; i++) nmax = pk.jobs[i].n > nmax ? pk.jobs[i].n : nmax;
+    const int nb = pk.blk_start[pk.njobs];
+    if (nmax <= 16) k_pointwise_mv<16><<<nb, PWV_THREADS, 0, st>>>(pk);
+    else if (nmax <= 32) k_pointwise_mv<32><<<nb, PWV_THREADS, 0, st>>>(pk);
+    else k_pointwise_mv<64><<<nb, PWV_THREADS, 0, st>>>(pk);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ CRT
 #define CRT_THREADS 256
 #define CRT_PER_THREAD 4

@@ -69,6 +69,7 @@ def lib():
             "pm_basis": ([P, u64, i32, i32, P, i64, i64, P, P, P], i32),
             "bivariate_resultant": ([P, i32, P, i32, i32, P, i32, i32, P, P], i32),
             "pmat_inv_trunc": ([P, u64, i32, i32, P, i64, i64, P], i32),
+            "pmat_solve_series": ([P, u64, i32, i32, P, i64, P, i64, i64, P], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -214,6 +215,19 @@ def pmat_inv_trunc(ctx: Context, p: int, A, t: int, out=None) -> torch.Tensor:
     X = _out(out, (n, n, t), A)
     ctx._ck(lib().pmat_inv_trunc(ctx.h, p, width(A), n, A.data_ptr(), dA, t, X.data_ptr()))
     return X
+
+
+def pmat_solve_series(ctx: Context, p: int, A, b, N: int, out=None) -> torch.Tensor:
+    """v = A^-1 b mod x^N -> n x 1 x N (A: n x n x dA with A(0) invertible mod the prime p,
+    b: n x 1 x db, same width).  A singular A(0) is reported by the next ctx.sync() (PM_EDOMAIN)."""
+    A, b = _dev(A), _dev(b)
+    n, n2, dA = A.shape
+    if n != n2 or b.shape[0] != n or b.shape[1] != 1 or b.dtype != A.dtype:
+        raise ValueError("A must be n x n and b n x 1 of the same width")
+    v = _out(out, (n, 1, N), A)
+    ctx._ck(lib().pmat_solve_series(ctx.h, p, width(A), n, A.data_ptr(), dA, b.data_ptr(), b.shape[2], N,
+                                    v.data_ptr()))
+    return v
 
 
 def pmat_middle_product(ctx: Context, p: int, A, B, c: int, d: int, out=None) -> torch.Tensor:

@@ -124,3 +124,66 @@ def test_argument_errors(ctx):
     with pytest.raises(PmError) as e:
         pmat.pmat_inv_trunc(ctx, 97, big, 2)
     assert e.value.code == pmat.PM_EUNSUPPORTED
+
+
+# ------------------------------------------------------------ series solution by Dixon's lifting
+def _vector(seed, p, n, db, w):
+    g = synth.rng(seed)
+    return synth.uniform(g, (n, 1, db), p, np.uint32 if w == 4 else np.uint64)
+
+
+def _gpu_solve(ctx, p, A, b, N):
+    from paper_1905_04356_gb300 import pmat
+    v = pmat.pmat_solve_series(ctx, p, pmat.to_device(A), pmat.to_device(b), N)
+    ctx.sync()
+    return pmat.to_host(v)
+
+
+SOLVE_CASES = [
+    # p, w, n, dA, db, N  (delta = max(dA, db) is the Dixon digit length)
+    (synth.P998, 4, 4, 50, 30, 300),
+    (P60, 8, 3, 17, 17, 100),
+    (P62, 8, 2, 20, 40, 129),
+    (97, 4, 5, 7, 3, 64),
+    (2, 4, 5, 30, 10, 70),
+    (3, 4, 3, 3, 3, 33),
+    (P60, 8, 32, 64, 64, 256),       # 32 x 32: staged pointwise blocks with k = 1
+    (P60, 8, 4, 40, 40, 25),         # N below one digit
+    (synth.P998, 4, 3, 9, 9, 1),
+]
+
+
+@pytest.mark.parametrize("case", SOLVE_CASES, ids=[f"p{c[0]}_w{c[1]}_n{c[2]}_dA{c[3]}_db{c[4]}_N{c[5]}"
+                                                   for c in SOLVE_CASES])
+def test_series_solution_matches_oracle(ctx, case):
+    p, w, n, dA, db, N = case
+    A = _matrix(hash(case) & 0xffff, p, n, dA, w)
+    b = _vector(hash(case) & 0xfff, p, n, db, w)
+    got = _gpu_solve(ctx, p, A, b, N)
+    assert got.shape == (n, 1, N)
+    assert np.array_equal(got.astype(np.uint64), oracle.solve_series(p, A, b, N))
+
+
+def test_series_solution_full_size_sampled(ctx):
+    """32 x 32, dA = db = 4096, N = 8 digits: A.v = b mod x^N on sampled coefficients."""
+    p, n, d, N = P60, 32, 4096, 8 * 4096
+    A = _matrix(21, p, n, d, 8)
+    b = _vector(22, p, n, d, 8)
+    v = _gpu_solve(ctx, p, A, b, N).astype(np.uint64)
+    rnd = random.Random(4)
+    picks = [(0, 0), (7, 4095), (31, 4096), (3, N - 1)] + [(rnd.randrange(n), rnd.randrange(N)) for _ in range(40)]
+    for i, t in picks:
+        exp = int(b[i, 0, t]) if t < d else 0
+        assert oracle.pmat_coeff(p, A, v, i, 0, t) == exp, (i, t)
+    assert np.array_equal(v[:, :, :64], oracle.solve_series(p, A[:, :, :64], b[:, :, :64], 64))
+
+
+def test_series_solution_singular_constant_term(ctx):
+    from paper_1905_04356_gb300 import PmError, pmat
+    A = np.zeros((2, 2, 3), dtype=np.uint32)
+    A[0, 0, 1] = 1
+    A[1, 1, 0] = 1
+    pmat.pmat_solve_series(ctx, 97, pmat.to_device(A), pmat.to_device(np.ones((2, 1, 2), dtype=np.uint32)), 8)
+    with pytest.raises(PmError) as e:
+        ctx.sync()
+    assert e.value.code == pmat.PM_EDOMAIN

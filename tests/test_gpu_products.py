@@ -79,6 +79,11 @@ CASES = [
     # inner dimension 1 (outer products, streaming kernel): many rows, k = 1 and k = 5
     (P60, 8, 37, 1, 5, 300, 200),
     (synth.P998, 4, 300, 1, 1, 151, 4000),
+    # matrix-vector products (k = 1, 8 < n <= 64, streaming kernel with a padded register block)
+    (P60, 8, 32, 32, 1, 100, 90),
+    (synth.P998, 4, 5, 17, 1, 60, 70),
+    (97, 4, 3, 64, 1, 30, 20),
+    (P62, 8, 7, 40, 1, 50, 50),
 ]
 
 
