@@ -16,7 +16,8 @@ of the paper its C function follows:
 * ``matinv`` / ``inv_trunc``: Sec. 4 (linear system solving by lifting): the
   inverse of a constant matrix and the truncated inverse A^-1 mod x^t, by
   definition.  ``solve_series``: the series solution A^-1 b mod x^N (what
-  Dixon's lifting computes), by definition.
+  Dixon's lifting computes), by definition.  ``inv_slices``: the high-order
+  lifting slices of A^-1, read off the truncated inverse.
 """
 from __future__ import annotations
 
@@ -64,6 +65,8 @@ def lib():
         L.orc_matinv.argtypes = [u64, i32, P, P]
         L.orc_inv_trunc.restype = i32
         L.orc_inv_trunc.argtypes = [u64, i32, P, i64, i64, P]
+        L.orc_inv_slices.restype = i32
+        L.orc_inv_slices.argtypes = [u64, i32, P, i64, i32, P]
         L.orc_solve_series.restype = i32
         L.orc_solve_series.argtypes = [u64, i32, P, i64, P, i64, i64, P]
         _lib = L
@@ -212,6 +215,20 @@ def solve_series(p, A, b, N, threads=None):
     if rc[0]:
         raise SingularError("A(0) is singular mod p")
     return v
+
+
+def inv_slices(p, A, K, threads=None):
+    """High-order lifting slices: K x n x n x (2D+1) with slice i = coefficients
+    (2^i - 1) D .. (2^i + 1) D of A^-1 (A: n x n x dA, D = dA - 1, A(0) invertible)."""
+    A = _u64(A)
+    n, n2, dA = A.shape
+    assert n == n2 and dA >= 2
+    S = np.zeros((K, n, n, 2 * (dA - 1) + 1), dtype=np.uint64)
+    rc = []
+    _with_threads(threads, lambda: rc.append(lib().orc_inv_slices(p, n, _ptr(A), dA, K, _ptr(S))))
+    if rc[0]:
+        raise SingularError("A(0) is singular mod p")
+    return S
 
 
 def powmod(a, e, p):

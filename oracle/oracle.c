@@ -39,6 +39,9 @@
  *                    invertible, taken by its definition -- the power series
  *                    X with A.X = I mod x^t, coefficient by coefficient:
  *                    X_0 = A_0^-1, X_j = -A_0^-1 (A_1 X_{j-1} + ... + A_j X_0).
+ *   orc_inv_slices   Sec. 4, high-order lifting: the slices S_i of A^-1,
+ *                    coefficients (2^i - 1)(d - 1) .. (2^i + 1)(d - 1) of the
+ *                    truncated inverse above (d = the length of A).
  *   orc_solve_series Sec. 4, lifting: the power-series solution
  *                    v = A^-1 b mod x^N that Dixon's algorithm produces, by
  *                    its definition A.v = b mod x^N: v_0 = A_0^-1 b_0,
@@ -546,5 +549,25 @@ int orc_solve_series(u64 p, int n, const u64 *A, i64 dA, const u64 *b, i64 db, i
         }
     }
     free(A0); free(A0i); free(rj);
+    return 0;
+}
+
+/* The high-order lifting slices (Sec. 4): S_i (n x n, length 2D + 1, D = dA - 1) =
+ * coefficients (2^i - 1) D .. (2^i + 1) D of A^-1, for i = 0 .. K-1, read off the
+ * truncated inverse.  Output S[((i n + r) n + c)(2D + 1) + t].  Returns 0, or 1 if
+ * A(0) is singular. */
+int orc_inv_slices(u64 p, int n, const u64 *A, i64 dA, int K, u64 *S)
+{
+    const i64 D = dA - 1, w = 2 * D + 1;
+    const i64 t = ((i64)1 << (K - 1)) * D + D + 1;          /* through (2^(K-1) + 1) D */
+    size_t nn = (size_t)n * n;
+    u64 *X = (u64 *)malloc(sizeof(u64) * nn * t);
+    if (orc_inv_trunc(p, n, A, dA, t, X)) { free(X); return 1; }
+    for (int i = 0; i < K; i++) {
+        const i64 s0 = (((i64)1 << i) - 1) * D;
+        for (size_t e = 0; e < nn; e++)
+            for (i64 j = 0; j < w; j++) S[((size_t)i * nn + e) * w + j] = X[e * t + s0 + j];
+    }
+    free(X);
     return 0;
 }

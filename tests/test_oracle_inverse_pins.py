@@ -168,3 +168,42 @@ def test_series_solution_prefix_and_singular():
     S[1, 1, 0] = 1
     with pytest.raises(oracle.SingularError):
         oracle.solve_series(p, S, np.ones((2, 1, 1), dtype=np.uint64), 4)
+
+
+# ------------------------------------------------------------ high-order lifting slices
+@pytest.mark.parametrize("p", [97, synth.P998, P62])
+@pytest.mark.parametrize("D", [1, 3, 5])
+def test_slices_sit_at_the_stated_degrees(p, D):
+    """A = 1 - a x^D (length D + 1): A^-1 = sum_j a^j x^(jD), so slice i, coefficients
+    (2^i - 1) D .. (2^i + 1) D, is a^(2^i - 1), 0 .. 0, a^(2^i), 0 .. 0, a^(2^i + 1) with D - 1
+    zeros between."""
+    a = 98765 % p
+    A = np.zeros((1, 1, D + 1), dtype=np.uint64)
+    A[0, 0, 0] = 1
+    A[0, 0, D] = (p - a) % p
+    K = 5
+    S = oracle.inv_slices(p, A, K)
+    for i in range(K):
+        exp = [0] * (2 * D + 1)
+        for j, e in ((0, (1 << i) - 1), (D, 1 << i), (2 * D, (1 << i) + 1)):
+            exp[j] = pow(a, e, p)
+        assert [int(v) for v in S[i, 0, 0]] == exp, i
+
+
+def test_slices_match_the_truncated_inverse_and_the_recurrence():
+    """Slice i is the truncated inverse's coefficients (2^i - 1) D .. (2^i + 1) D, and for i >= 1
+    coefficients D .. 2D of A.S_i vanish (they are coefficients of A.A^-1 = I above degree D)."""
+    p = synth.P998
+    rnd = random.Random(13)
+    n, dA, K = 3, 5, 4
+    D = dA - 1
+    A = _rand(rnd, p, n, n, dA)
+    A[:, :, 0] = np.array(_rand_invertible_const(rnd, p, n), dtype=np.uint64)
+    S = oracle.inv_slices(p, A, K)
+    X = oracle.inv_trunc(p, A, ((1 << (K - 1)) + 1) * D + 1)
+    for i in range(K):
+        s0 = ((1 << i) - 1) * D
+        assert np.array_equal(S[i], X[:, :, s0:s0 + 2 * D + 1])
+        if i >= 1:
+            AS = np.array(pyref.ks_pmat_mul(p, A.tolist(), S[i].tolist()), dtype=object)
+            assert not any(int(AS[r, c, t]) for r in range(n) for c in range(n) for t in range(D, 2 * D + 1))
