@@ -44,9 +44,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the PM-Basis / batched / resultant / inverse / solve timings")
-    ap.add_argument("--extra", default="pm_basis,resultant,batched,inverse,solve",
-                    help="comma-separated subset of pm_basis, resultant, batched, inverse, solve")
+                    help="skip the PM-Basis / batched / resultant / inverse / solve / slices timings")
+    ap.add_argument("--extra", default="pm_basis,resultant,batched,inverse,solve,slices",
+                    help="comma-separated subset of pm_basis, resultant, batched, inverse, solve, slices")
     return ap.parse_args()
 
 
@@ -182,11 +182,12 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------- other workloads (reported under "extra")
-def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse", "solve"), reps=3):
+def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse", "solve", "slices"), reps=3):
     """PM-Basis (F 32x16, order 8192, 60-bit p), 512 batched uneven products, resultants
     (deg_x = deg_y = 150, 1 prime and 16 primes), the truncated inverse of a 32x32 matrix of
     degree < 4096 mod x^4096 and the lifted series solution of A v = b mod x^32768 (same A, b of
-    degree < 4096; 60-bit p): ms per call, CUDA events on the stream."""
+    degree < 4096; 60-bit p), six high-order lifting slices of the same A^-1: ms per call, CUDA
+    events on the stream."""
     import numpy as np
     import torch
     import synth
@@ -265,10 +266,19 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"
         out["solve_series_stage_ms"] = {k: round(v2[0], 3) for k, v2 in st.items() if v2[1]}
         return out
 
+    def slices():
+        W = synth.inverse_w(0)
+        A = pmat.to_device(W["A"])
+        S = torch.empty((6, 32, 32, 2 * 4096 - 1), dtype=A.dtype, device="cuda")
+        run = lambda: pmat.pmat_inv_slices(ctx, W["p"], A, 6, out=S)  # noqa: E731
+        out = {"inv_slices_32x32_d4096_K6_ms": round(ev_ms(run, reps), 3)}
+        ctx.sync()
+        return out
+
     out = {}
     with torch.cuda.stream(s):
         for name, fn in (("pm_basis", pm_basis), ("resultant", resultant), ("batched", batched),
-                         ("inverse", inverse), ("solve", solve)):
+                         ("inverse", inverse), ("solve", solve), ("slices", slices)):
             if name in which:
                 out.update(fn())
     return out

@@ -18,6 +18,8 @@
  *                                 Newton iteration
  *   pmat_solve_series             Sec. 4, lifting: A^-1 b mod x^N by Dixon's
  *                                 algorithm over the truncated inverse
+ *   pmat_inv_slices               Sec. 4, high-order lifting: slices of A^-1
+ *                                 at degrees around 2^i (d - 1)
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -53,8 +55,8 @@ enum {
     PM_OK = 0,
     PM_EINVAL = 1,       /* bad argument (dimension, length, modulus, width) */
     PM_EDOMAIN = 2,      /* an input coefficient is not in [0, p) (debug check), or
-                            A(0) is singular in pmat_inv_trunc / pmat_solve_series
-                            (deferred, pm_sync) */
+                            A(0) is singular in pmat_inv_trunc / pmat_solve_series /
+                            pmat_inv_slices (deferred, pm_sync) */
     PM_ENOMEM = 3,       /* device workspace allocation failed */
     PM_ECUDA = 4,        /* a CUDA runtime call or kernel launch failed */
     PM_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
@@ -234,6 +236,19 @@ int pmat_inv_trunc(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t
  * context's driver arena. */
 int pmat_solve_series(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA,
                       const void *b, int64_t db, int64_t N, void *v);
+
+/* High-order lifting slices (Sec. 4, "Linear system solving": Storjohann's
+ * high-order lifting).  A: DEVICE n x n matrix, entries of length dA >= 2 (width
+ * w), A(0) invertible; D = dA - 1.  S: DEVICE output, K slices of n x n entries
+ * of length 2D + 1: coefficient t of entry (r, c) of slice i, at
+ * S[((i n + r) n + c)(2D + 1) + t], is coefficient (2^i - 1) D + t of A^-1.
+ * Slice 0 is A^-1 mod x^(2D+1) by Newton iteration; each further slice takes
+ * four products of degree about D on the hot path, through the residues
+ * E_m = x^-m (I - A (A^-1 mod x^m)) at m = 2^i D - D and 2^i D.  Requires p
+ * prime, 1 <= n <= 128, 1 <= K <= 24, 3D + 1 <= 2^20.  A(0) singular: S is
+ * undefined and pm_sync returns PM_EDOMAIN.  Asynchronous; uses the driver arena. */
+int pmat_inv_slices(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA, int K,
+                    void *S);
 
 #ifdef __cplusplus
 }

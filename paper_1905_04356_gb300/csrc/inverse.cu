@@ -111,6 +111,18 @@ __global__ void k_negate_slice(void *X, int w, i64 sX, i64 off, i64 h, i64 count
     }
 }
 
+// E (count entries of length len) <- the identity: coefficient 0 of the diagonal entries is 1
+__global__ void k_identity(void *E, int w, int n, i64 len)
+{
+    const i64 total = (i64)n * n * len;
+    for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < total; x += (i64)gridDim.x * blockDim.x) {
+        const i64 e = x / len, t = x - e * len;
+        const u64 v = (t == 0 && e / n == e % n) ? 1 : 0;
+        if (w == 8) ((u64 *)E)[x] = v;
+        else ((u32 *)E)[x] = (u32)v;
+    }
+}
+
 #define CKI(call)                                                       \
     do {                                                                \
         int _rc = (call);                                               \
@@ -239,6 +251,71 @@ extern "C" int pmat_solve_series(pm_ctx *ctx, uint64_t p, int w, int n, const vo
         CKI(prod_slice(ctx, p, w, n, n, 1, A, dA, dA, y, delta, N, delta, delta, ceil_log2(dA + delta - 1), R, delta));
         negate_slice(ctx, R, w, delta, 0, delta, n, p);
         CKI(pm_cuda(ctx, cudaGetLastError(), "k_negate_slice"));
+    }
+    return PM_OK;
+}
+
+// High-order lifting (Sec. 4; Storjohann): the slices S_i = coefficients (2^i - 1) D ..
+// (2^i + 1) D of X = A^-1, D = dA - 1, with the residues E_m = x^-m (I - A (X mod x^m)) =
+// A (X div x^m) mod x^(D+1) (degree <= D).  From X = (X mod x^m) + x^m X E_m, with
+// c = 2^i D:
+//   lower half of S_{i+1} = coefficients D .. 2D-1 of S_i E_{c-D}
+//   upper half of S_{i+1} = coefficients D .. 2D   of S_i E_c
+//   E_{2c-D} = A . S_{i+1}[0 .. D] mod x^(D+1),  E_2c = A . S_{i+1}[D .. 2D] mod x^(D+1)
+// from S_0 = A^-1 mod x^(2D+1) (Newton), E_0 = I and E_D = A . S_0[D .. 2D] mod x^(D+1):
+// four products per slice, two by two in one batched call.
+extern "C" int pmat_inv_slices(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA, int K, void *S)
+{
+    if (!ctx) return PM_EINVAL;
+    if (dA < 2 || K < 1 || K > 24) return pm_fail(ctx, PM_EINVAL, "need dA >= 2 and 1 <= K <= 24");
+    const int64_t D = dA - 1, W = 2 * D + 1;
+    CKI(check_inverse_args(ctx, p, w, n, A, dA, W, S));
+    if (3 * D + 1 > (int64_t(1) << PM_MAX_LOG2L)) return pm_fail(ctx, PM_EINVAL, "degree too large for the transforms");
+    const size_t nn = (size_t)n * n;
+    size_t bE;
+    const size_t wM = inv_scratch_words(n, W, w, &bE);
+    const size_t bR = nn * (size_t)(D + 1) * w;
+    CKI(arena_reserve(ctx, wM * 8 + bE + 2 * bR + 4 * 256));
+    u64 *M = (u64 *)arena_alloc(ctx, wM * 8);
+    void *E = arena_alloc(ctx, bE);
+    char *Elo = (char *)arena_alloc(ctx, bR), *Ehi = (char *)arena_alloc(ctx, bR);
+    if (!M || !E || !Elo || !Ehi) return pm_fail(ctx, PM_ENOMEM, "arena too small");
+    char *S0 = (char *)S;
+    const size_t slice = nn * (size_t)W * w;
+    CKI(inv_trunc_core(ctx, p, w, n, A, dA, W, S0, M, E));
+    if (K == 1) return PM_OK;
+    {
+        const int64_t tot = (int64_t)nn * (D + 1);
+        int grid = (int)((tot + 255) / 256);
+        if (grid > 4096) grid = 4096;
+        k_identity<<<grid, 256, 0, ctx->stream>>>(Elo, w, n, D + 1);
+        ctx->launches++;
+        CKI(pm_cuda(ctx, cudaGetLastError(), "k_identity"));
+    }
+    auto req = [&](const void *Ap, int64_t da, int64_t sa, const void *Bp, int64_t db, int64_t sb, int64_t off,
+                   int64_t len, int lg, void *Cp, int64_t sc) {
+        ProdReq q;
+        q.p = p; q.w = w; q.m = n; q.n = n; q.k = n; q.lg = lg < 4 ? 4 : lg;
+        q.A = Ap; q.dA = da; q.sA = sa; q.B = Bp; q.dB = db; q.sB = sb;
+        q.off = off; q.len = len; q.C = Cp; q.sC = sc;
+        return q;
+    };
+    const int lgE = ceil_log2(2 * D + 1), lgS = ceil_log2(3 * D + 1);   // no aliasing in either
+    {
+        ProdReq q = req(A, dA, dA, S0 + D * w, D + 1, W, 0, D + 1, lgE, Ehi, D + 1);   // E_D
+        CKI(prod_batch(ctx, &q, 1));
+    }
+    for (int i = 1; i < K; i++) {
+        const char *Sp = S0 + (size_t)(i - 1) * slice;
+        char *Sc = S0 + (size_t)i * slice;
+        ProdReq q[2] = {req(Sp, W, W, Elo, D + 1, D + 1, D, D, lgS, Sc, W),                    // lower half
+                        req(Sp, W, W, Ehi, D + 1, D + 1, D, D + 1, lgS, Sc + D * w, W)};       // upper half
+        CKI(prod_batch(ctx, q, 2));
+        if (i + 1 < K) {
+            ProdReq r[2] = {req(A, dA, dA, Sc, D + 1, W, 0, D + 1, lgE, Elo, D + 1),
+                            req(A, dA, dA, Sc + D * w, D + 1, W, 0, D + 1, lgE, Ehi, D + 1)};
+            CKI(prod_batch(ctx, r, 2));
+        }
     }
     return PM_OK;
 }

@@ -70,6 +70,7 @@ def lib():
             "bivariate_resultant": ([P, i32, P, i32, i32, P, i32, i32, P, P], i32),
             "pmat_inv_trunc": ([P, u64, i32, i32, P, i64, i64, P], i32),
             "pmat_solve_series": ([P, u64, i32, i32, P, i64, P, i64, i64, P], i32),
+            "pmat_inv_slices": ([P, u64, i32, i32, P, i64, i32, P], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -228,6 +229,18 @@ def pmat_solve_series(ctx: Context, p: int, A, b, N: int, out=None) -> torch.Ten
     ctx._ck(lib().pmat_solve_series(ctx.h, p, width(A), n, A.data_ptr(), dA, b.data_ptr(), b.shape[2], N,
                                     v.data_ptr()))
     return v
+
+
+def pmat_inv_slices(ctx: Context, p: int, A, K: int, out=None) -> torch.Tensor:
+    """High-order lifting slices -> K x n x n x (2D+1): slice i = coefficients (2^i - 1) D ..
+    (2^i + 1) D of A^-1 (A: n x n x dA, D = dA - 1, A(0) invertible mod the prime p)."""
+    A = _dev(A)
+    n, n2, dA = A.shape
+    if n != n2:
+        raise ValueError("A must be square")
+    S = _out(out, (K, n, n, 2 * (dA - 1) + 1), A)
+    ctx._ck(lib().pmat_inv_slices(ctx.h, p, width(A), n, A.data_ptr(), dA, K, S.data_ptr()))
+    return S
 
 
 def pmat_middle_product(ctx: Context, p: int, A, B, c: int, d: int, out=None) -> torch.Tensor:

@@ -187,3 +187,48 @@ def test_series_solution_singular_constant_term(ctx):
     with pytest.raises(PmError) as e:
         ctx.sync()
     assert e.value.code == pmat.PM_EDOMAIN
+
+
+# ------------------------------------------------------------ high-order lifting slices
+SLICE_CASES = [
+    # p, w, n, dA, K
+    (synth.P998, 4, 3, 5, 5),
+    (P60, 8, 2, 9, 4),
+    (P62, 8, 4, 3, 6),
+    (97, 4, 5, 7, 4),
+    (2, 4, 3, 4, 4),
+    (P60, 8, 32, 17, 4),             # 32 x 32 blocks
+    (synth.P998, 4, 1, 2, 8),        # D = 1
+    (P60, 8, 3, 6, 1),               # slice 0 only
+]
+
+
+@pytest.mark.parametrize("case", SLICE_CASES, ids=[f"p{c[0]}_w{c[1]}_n{c[2]}_dA{c[3]}_K{c[4]}" for c in SLICE_CASES])
+def test_inverse_slices_match_oracle(ctx, case):
+    from paper_1905_04356_gb300 import pmat
+    p, w, n, dA, K = case
+    A = _matrix(hash(case) & 0xffff, p, n, dA, w)
+    S = pmat.pmat_inv_slices(ctx, p, pmat.to_device(A), K)
+    ctx.sync()
+    got = pmat.to_host(S).astype(np.uint64)
+    assert got.shape == (K, n, n, 2 * dA - 1)
+    assert np.array_equal(got, oracle.inv_slices(p, A, K))
+
+
+def test_inverse_slices_full_size_properties(ctx):
+    """32 x 32, dA = 4096 (D = 4095), 5 slices (the last one reaches degree 17 D): slice 0's
+    prefix against the oracle, slice 1's lower half equal to slice 0's upper part (both are
+    coefficients D .. 2D-1 of A^-1), and A.S_i zero in degrees D .. 2D on sampled entries."""
+    from paper_1905_04356_gb300 import pmat
+    p, n, dA, K = P60, 32, 4096, 5
+    D = dA - 1
+    A = _matrix(31, p, n, dA, 8)
+    S = pmat.to_host(pmat.pmat_inv_slices(ctx, p, pmat.to_device(A), K)).astype(np.uint64)
+    ctx.sync()
+    assert np.array_equal(S[0][:, :, :64], oracle.inv_trunc(p, A[:, :, :64], 64))
+    assert np.array_equal(S[1][:, :, :D], S[0][:, :, D:2 * D])
+    rnd = random.Random(8)
+    for i in (1, K - 1):
+        for _ in range(12):
+            r, c, t = rnd.randrange(n), rnd.randrange(n), rnd.randrange(D, 2 * D + 1)
+            assert oracle.pmat_coeff(p, A, S[i], r, c, t) == 0, (i, r, c, t)
