@@ -11,6 +11,7 @@ of the paper its C function follows:
 * ``pmat_mul`` / ``pmat_mul_trunc`` / ``pmat_middle_product`` / ``pmat_coeff``:
   Sec. 2, polynomial (matrix) multiplication and MiddleProduct(F, G, c, d).
 * ``mbasis1``: Algorithm 1.  ``mbasis``: Algorithm 2.  ``pmbasis``: Algorithm 3.
+  ``mintbasis``: Algorithm 4.  ``pmintbasis``: Algorithm 5.
 * ``univ_resultant`` / ``bivariate_resultant``: Sec. 5.2, the direct
   evaluation / Euclid / interpolation method.
 * ``matinv`` / ``inv_trunc``: Sec. 4 (linear system solving by lifting): the
@@ -67,6 +68,10 @@ def lib():
         L.orc_inv_trunc.argtypes = [u64, i32, P, i64, i64, P]
         L.orc_inv_slices.restype = i32
         L.orc_inv_slices.argtypes = [u64, i32, P, i64, i32, P]
+        L.orc_mintbasis.restype = None
+        L.orc_mintbasis.argtypes = [u64, i32, i32, P, i64, P, P, P, P]
+        L.orc_pmintbasis.restype = None
+        L.orc_pmintbasis.argtypes = [u64, i32, i32, P, i64, P, P, i64, P, P]
         L.orc_solve_series.restype = i32
         L.orc_solve_series.argtypes = [u64, i32, P, i64, P, i64, i64, P]
         _lib = L
@@ -143,6 +148,30 @@ def pmbasis(p, F, d, s, T=32, threads=None):
     rd = np.zeros(m, dtype=np.int64)
     _with_threads(threads, lambda: lib().orc_pmbasis(
         p, m, n, _ptr(F), lenF, d, _ptr(s), T, _ptr(P), _ptr(rd)))
+    return P, rd
+
+
+def mintbasis(p, E, alpha, s):
+    """Algorithm 4: E is m x n x sigma (E[:, :, l] = E_l at point alpha[l]); returns (P, rdeg_s(P))."""
+    E = _u64(E)
+    m, n, sigma = E.shape
+    al = _u64(alpha)
+    s = np.ascontiguousarray(np.asarray(s, dtype=np.int64))
+    P = np.zeros((m, m, sigma + 1), dtype=np.uint64)
+    rd = np.zeros(m, dtype=np.int64)
+    lib().orc_mintbasis(p, m, n, _ptr(E), sigma, _ptr(al), _ptr(s), _ptr(P), _ptr(rd))
+    return P, rd
+
+
+def pmintbasis(p, E, alpha, s, T=32):
+    """Algorithm 5 with threshold T: returns (P, rdeg_s(P))."""
+    E = _u64(E)
+    m, n, sigma = E.shape
+    al = _u64(alpha)
+    s = np.ascontiguousarray(np.asarray(s, dtype=np.int64))
+    P = np.zeros((m, m, sigma + 1), dtype=np.uint64)
+    rd = np.zeros(m, dtype=np.int64)
+    lib().orc_pmintbasis(p, m, n, _ptr(E), sigma, _ptr(al), _ptr(s), T, _ptr(P), _ptr(rd))
     return P, rd
 
 

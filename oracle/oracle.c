@@ -29,6 +29,12 @@
  *   orc_pmbasis      Algorithm 3 (PM-Basis): divide and conquer with the
  *                    threshold T, the first half of order ceil(d/2), and the
  *                    residual as a middle product.
+ *   orc_mintbasis    Algorithm 4 (M-IntBasis): R = P(alpha_k) E_k, Q =
+ *                    M-Basis-1(R, t) with x read as x - alpha_k, P <- Q.P,
+ *                    t <- rdeg_s(P) (Sec. 3, "Interpolant bases").
+ *   orc_pmintbasis   Algorithm 5 (PM-IntBasis): divide and conquer with the
+ *                    threshold T, the residual being P1 evaluated at the second
+ *                    half of the points times the second half of E.
  *   orc_univ_resultant / orc_bivariate_resultant
  *                    Sec. 5.2, the "Direct" method: evaluate in x, take
  *                    univariate resultants in y by the Euclidean algorithm,
@@ -570,4 +576,104 @@ int orc_inv_slices(u64 p, int n, const u64 *A, i64 dA, int K, u64 *S)
     }
     free(X);
     return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Interpolant bases (Sec. 3, Algorithms 4 and 5)                       */
+/* ------------------------------------------------------------------ */
+
+/* P(a) for an entry of length len (Horner). */
+static u64 poly_eval(const u64 *f, i64 len, u64 a, u64 p)
+{
+    u64 v = 0;
+    for (i64 e = len - 1; e >= 0; e--) v = f_add(f_mul(v, a, p), f[e], p);
+    return v;
+}
+
+/* Algorithm 4: E[(i n + j) sigma + l] = entry (i, j) of E_l, points alpha[l];
+ * P: m x m, length sigma + 1; rdeg = rdeg_s(P). */
+void orc_mintbasis(u64 p, int m, int n, const u64 *E, i64 sigma, const u64 *alpha, const i64 *s,
+                   u64 *P, i64 *rdeg)
+{
+    const i64 len = sigma + 1;
+    u64 *R = (u64 *)malloc(sizeof(u64) * (size_t)m * n);
+    u64 *Q = (u64 *)malloc(sizeof(u64) * (size_t)m * m * 2);
+    u64 *Pv = (u64 *)malloc(sizeof(u64) * (size_t)m * m);
+    u64 *Pn = (u64 *)calloc((size_t)m * m * len, sizeof(u64));
+    i64 *t = (i64 *)malloc(sizeof(i64) * m);
+    i64 degP = 0;
+    memset(P, 0, sizeof(u64) * (size_t)m * m * len);
+    for (int i = 0; i < m; i++) P[((i64)i * m + i) * len] = 1;
+    for (int i = 0; i < m; i++) t[i] = s[i];
+    for (i64 k = 0; k < sigma; k++) {
+        const u64 a = alpha[k] % p;
+        /* a. R = P(alpha_k) E_k */
+        for (i64 e = 0; e < (i64)m * m; e++) Pv[e] = poly_eval(P + e * len, degP + 1, a, p);
+        for (int i = 0; i < m; i++)
+            for (int j = 0; j < n; j++) {
+                u128 acc = 0;
+                for (int l = 0; l < m; l++) acc_add(&acc, Pv[(i64)i * m + l], E[((i64)l * n + j) * sigma + k], p);
+                R[(i64)i * n + j] = (u64)(acc % p);
+            }
+        /* b. Q = M-Basis-1(R, t), x read as x - alpha_k: Q0 <- Q0 - alpha_k Q1 */
+        orc_mbasis1(p, m, n, R, t, Q);
+        for (i64 e = 0; e < (i64)m * m; e++) Q[e * 2] = f_sub(Q[e * 2], f_mul(a, Q[e * 2 + 1], p), p);
+        /* c. P <- Q.P, t <- rdeg_s(P) */
+        const i64 degN = degP + 1 < sigma ? degP + 1 : sigma;
+        for (int i = 0; i < m; i++)
+            for (int j = 0; j < m; j++) {
+                u64 *out = Pn + ((i64)i * m + j) * len;
+                for (i64 c = 0; c <= degN; c++) {
+                    u128 acc = 0;
+                    for (int l = 0; l < m; l++) {
+                        const u64 q0 = Q[((i64)i * m + l) * 2], q1 = Q[((i64)i * m + l) * 2 + 1];
+                        const u64 *Plj = P + ((i64)l * m + j) * len;
+                        if (q0 && c <= degP) acc_add(&acc, q0, Plj[c], p);
+                        if (q1 && c >= 1 && c - 1 <= degP) acc_add(&acc, q1, Plj[c - 1], p);
+                    }
+                    out[c] = (u64)(acc % p);
+                }
+            }
+        degP = degN;
+        memcpy(P, Pn, sizeof(u64) * (size_t)m * m * len);
+        orc_rdeg(m, m, P, len, s, t);
+    }
+    for (int i = 0; i < m; i++) rdeg[i] = t[i];
+    free(R); free(Q); free(Pv); free(Pn); free(t);
+}
+
+/* Algorithm 5 with threshold T (Algorithm 4 if sigma <= T). */
+void orc_pmintbasis(u64 p, int m, int n, const u64 *E, i64 sigma, const u64 *alpha, const i64 *s, i64 T,
+                    u64 *P, i64 *rdeg)
+{
+    if (sigma <= T) { orc_mintbasis(p, m, n, E, sigma, alpha, s, P, rdeg); return; }
+    const i64 s1 = (sigma + 1) / 2, s2 = sigma / 2;
+    /* step 2: P1 = PM-IntBasis(E_1..s1, alpha_1..s1, s) */
+    u64 *E1 = (u64 *)malloc(sizeof(u64) * (size_t)m * n * s1);
+    for (i64 e = 0; e < (i64)m * n; e++)
+        for (i64 l = 0; l < s1; l++) E1[e * s1 + l] = E[e * sigma + l];
+    u64 *P1 = (u64 *)malloc(sizeof(u64) * (size_t)m * m * (s1 + 1));
+    i64 *t1 = (i64 *)malloc(sizeof(i64) * m);
+    orc_pmintbasis(p, m, n, E1, s1, alpha, s, T, P1, t1);
+    /* step 3: R_l = P1(alpha_{s1+l}) E_{s1+l} */
+    u64 *R = (u64 *)malloc(sizeof(u64) * (size_t)m * n * (s2 > 0 ? s2 : 1));
+    u64 *Pv = (u64 *)malloc(sizeof(u64) * (size_t)m * m);
+    for (i64 l = 0; l < s2; l++) {
+        const u64 a = alpha[s1 + l] % p;
+        for (i64 e = 0; e < (i64)m * m; e++) Pv[e] = poly_eval(P1 + e * (s1 + 1), s1 + 1, a, p);
+        for (int i = 0; i < m; i++)
+            for (int j = 0; j < n; j++) {
+                u128 acc = 0;
+                for (int k = 0; k < m; k++) acc_add(&acc, Pv[(i64)i * m + k], E[((i64)k * n + j) * sigma + s1 + l], p);
+                R[((i64)i * n + j) * s2 + l] = (u64)(acc % p);
+            }
+    }
+    /* steps 4-5: t = rdeg_s(P1); P2 = PM-IntBasis(R, alpha_{s1+1..sigma}, t) */
+    u64 *P2 = (u64 *)malloc(sizeof(u64) * (size_t)m * m * (s2 + 1));
+    i64 *t2 = (i64 *)malloc(sizeof(i64) * m);
+    orc_pmintbasis(p, m, n, R, s2, alpha + s1, t1, T, P2, t2);
+    /* step 6: P = P2 P1 */
+    orc_pmat_slice(p, m, m, m, P2, s2 + 1, P1, s1 + 1, 0, sigma + 1, P);
+    orc_rdeg(m, m, P, sigma + 1, s, rdeg);
+    free(E1); free(P1); free(t1); free(R); free(Pv); free(P2); free(t2);
 }
