@@ -11,6 +11,8 @@
  *   pmat_mul_batched              many independent products in one call
  *   pm_basis                      Sec. 3, Algorithm 3 (PM-Basis) over
  *                                 Algorithms 1-2 (M-Basis-1, M-Basis)
+ *   pm_intbasis                   Sec. 3, Algorithm 5 (PM-IntBasis) over
+ *                                 Algorithm 4 (M-IntBasis), geometric points
  *   bivariate_resultant           Sec. 5.2, resultant of bivariate
  *                                 polynomials (the direct method)
  *   pmat_inv_trunc                Sec. 4, "Linear system solving": the
@@ -198,6 +200,21 @@ int pmat_mul_noalloc(uint64_t p, int w, int m, int n, int k,
  * stream).  Requires p odd, 1 <= n, 1 <= m, d >= 1. */
 int pm_basis(pm_ctx *ctx, uint64_t p, int m, int n, const void *F, int64_t lenF,
              int64_t d, const int64_t *shift, void *P, int64_t *rdeg_out);
+
+/* PM-IntBasis (Sec. 3, "Interpolant bases", Algorithm 5; leaves: Algorithm 4)
+ * at the geometric progression of points alpha_l = c q^l, l < sigma.
+ * E: DEVICE uint64_t, m x n entries of length sigma, E[(i*n + j)*sigma + l] =
+ * entry (i, j) of the matrix E_l attached to alpha_l.  shift: HOST
+ * int64_t[m].  P: DEVICE output, m x m entries of length sigma+1, the
+ * s-ordered weak Popov interpolant basis with P(alpha_l) E_l = 0 for every l
+ * that Algorithm 4 returns (Algorithm 5 returns the same basis).  rdeg_out:
+ * HOST int64_t[m] receiving rdeg_s(P) (this call synchronises the stream).
+ * The residual of a node (P1 at the second half of the points) is evaluated
+ * by a chirp middle product on the product path.  Requires p an odd prime
+ * < 2^62, c in [0, p), q in [1, p), 1 <= m, n <= 128, sigma >= 1; the points
+ * need not be distinct.  Returns PM_EINVAL on bad arguments. */
+int pm_intbasis(pm_ctx *ctx, uint64_t p, int m, int n, const void *E, int64_t sigma,
+                uint64_t c, uint64_t q, const int64_t *shift, void *P, int64_t *rdeg_out);
 
 /* Res_y(f, g) in F_p[x] for f, g in F_p[x, y] with formal y-degrees dyf,
  * dyg and x-degrees <= dxf, dxg (Sec. 5.2, the direct evaluation /

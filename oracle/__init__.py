@@ -72,6 +72,8 @@ def lib():
         L.orc_mintbasis.argtypes = [u64, i32, i32, P, i64, P, P, P, P]
         L.orc_pmintbasis.restype = None
         L.orc_pmintbasis.argtypes = [u64, i32, i32, P, i64, P, P, i64, P, P]
+        L.orc_pmat_eval.restype = None
+        L.orc_pmat_eval.argtypes = [u64, i32, i32, P, i64, u64, P]
         L.orc_solve_series.restype = i32
         L.orc_solve_series.argtypes = [u64, i32, P, i64, P, i64, i64, P]
         _lib = L
@@ -173,6 +175,15 @@ def pmintbasis(p, E, alpha, s, T=32):
     rd = np.zeros(m, dtype=np.int64)
     lib().orc_pmintbasis(p, m, n, _ptr(E), sigma, _ptr(al), _ptr(s), T, _ptr(P), _ptr(rd))
     return P, rd
+
+
+def pmat_eval(p, X, a):
+    """X(a) for an r x c x len polynomial matrix: an r x c uint64 array."""
+    X = _u64(X)
+    r, c, length = X.shape
+    out = np.zeros((r, c), dtype=np.uint64)
+    lib().orc_pmat_eval(p, r, c, _ptr(X), length, a, _ptr(out))
+    return out
 
 
 def rdeg(P, s):

@@ -32,6 +32,8 @@
  *   orc_mintbasis    Algorithm 4 (M-IntBasis): R = P(alpha_k) E_k, Q =
  *                    M-Basis-1(R, t) with x read as x - alpha_k, P <- Q.P,
  *                    t <- rdeg_s(P) (Sec. 3, "Interpolant bases").
+ *   orc_pmat_eval    value of every entry of a polynomial matrix at a point
+ *                    (Horner), to check P(alpha_l) E_l = 0.
  *   orc_pmintbasis   Algorithm 5 (PM-IntBasis): divide and conquer with the
  *                    threshold T, the residual being P1 evaluated at the second
  *                    half of the points times the second half of E.
@@ -588,6 +590,12 @@ static u64 poly_eval(const u64 *f, i64 len, u64 a, u64 p)
     u64 v = 0;
     for (i64 e = len - 1; e >= 0; e--) v = f_add(f_mul(v, a, p), f[e], p);
     return v;
+}
+
+/* out[e] = X_e(a) for the r x c entries of X (length len), by Horner's rule. */
+void orc_pmat_eval(u64 p, int r, int c, const u64 *X, i64 len, u64 a, u64 *out)
+{
+    for (i64 e = 0; e < (i64)r * c; e++) out[e] = poly_eval(X + e * len, len, a % p, p);
 }
 
 /* Algorithm 4: E[(i n + j) sigma + l] = entry (i, j) of E_l, points alpha[l];

@@ -43,6 +43,7 @@ struct LeafArgs {
     i64 sP;
     u64 *G0, *G1;            // residual series, m x n x T (Montgomery), double buffer
     u64 *P0, *P1;            // basis, m x m x (T + 1) (Montgomery), double buffer
+    const u64 *alpha;        // interpolant leaves: the T points (Montgomery); null for approximants
 };
 
 // ------------------------------------------------------------------ device arithmetic
@@ -393,6 +394,9 @@ __device__ __forceinline__ u64 dep_combine(const LeafArgs &A, const ElimSm &E, i
 // ------------------------------------------------------------------ leaf kernel, one CTA
 // G and P in global memory (double-buffered); for shapes whose slices do not fit
 // the cluster kernel's shared memory.
+// IP: interpolant leaf (Algorithm 4): the residual list holds P(alpha_l) E_l, independent
+// rows are multiplied by (x - alpha_k) (by alpha_l - alpha_k in the list) instead of x.
+template <bool IP>
 __global__ void __launch_bounds__(512) k_mbasis_leaf(const LeafArgs A)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -424,14 +428,20 @@ __global__ void __launch_bounds__(512) k_mbasis_leaf(const LeafArgs A)
         const int ngl = T - k - 1;
         for (int x = tid; x < m * n * ngl; x += nth) {
             const int a = k + 1 + x % ngl, e = x / ngl, j = e / n, c = e % n;
-            Gn[(i64)e * T + a] = E.ind[j] ? G[(i64)e * T + a - 1] : dep_combine(A, E, j, G + (i64)c * T + a, (i64)n * T);
+            u64 val;
+            if (!E.ind[j]) val = dep_combine(A, E, j, G + (i64)c * T + a, (i64)n * T);
+            else if (IP) val = mmul(sub64(A.alpha[a], A.alpha[k], A.p), G[(i64)e * T + a], A);
+            else val = G[(i64)e * T + a - 1];
+            Gn[(i64)e * T + a] = val;
         }
         const int np = k + 2;
         for (int x = tid; x < m * m * np; x += nth) {
             const int a = x % np, e = x / np, j = e / m, c = e % m;
             u64 val;
-            if (E.ind[j]) val = a ? P[(i64)e * LP + a - 1] : 0;
-            else if (a == k + 1) val = 0;
+            if (E.ind[j]) {
+                val = a ? P[(i64)e * LP + a - 1] : 0;
+                if (IP && a <= k) val = sub64(val, mmul(A.alpha[k], P[(i64)e * LP + a], A), A.p);
+            } else if (a == k + 1) val = 0;
             else val = dep_combine(A, E, j, P + (i64)c * LP + a, (i64)m * LP);
             Pn[(i64)e * LP + a] = val;
         }
@@ -470,6 +480,7 @@ __global__ void __launch_bounds__(512) k_mbasis_leaf(const LeafArgs A)
 // Q_k applied to this CTA's slices (k = the step of E): G coefficients a >= k+2 of
 // Gs -> Gd (skipped when G is null) and P coefficients 0 .. k+1 of Ps -> Pd, by threads
 // ut = 0 .. un-1.
+template <bool IP>
 __device__ void leaf_apply(const LeafArgs &A, const ElimSm &E, int k, const u64 *Gs, u64 *Gd, const u64 *Ps, u64 *Pd,
                            int ng, int ngm, int np_, int npm, int ut, int un)
 {
@@ -479,7 +490,11 @@ __device__ void leaf_apply(const LeafArgs &A, const ElimSm &E, int k, const u64 
         for (int x = ut; x < m * ng * ngl; x += un) {
             const int a = k + 2 + x % ngl, e = x / ngl, j = e / ng, c = e % ng;
             const i64 o = ((i64)j * ngm + c) * T + a;
-            Gd[o] = E.ind[j] ? Gs[o - 1] : dep_combine(A, E, j, Gs + (i64)c * T + a, (i64)ngm * T);
+            u64 val;
+            if (!E.ind[j]) val = dep_combine(A, E, j, Gs + (i64)c * T + a, (i64)ngm * T);
+            else if (IP) val = mmul(sub64(A.alpha[a], A.alpha[k], A.p), Gs[o], A);
+            else val = Gs[o - 1];
+            Gd[o] = val;
         }
     }
     const int npc = k + 2;
@@ -487,13 +502,16 @@ __device__ void leaf_apply(const LeafArgs &A, const ElimSm &E, int k, const u64 
         const int a = x % npc, e = x / npc, j = e / np_, c = e % np_;
         const i64 o = ((i64)j * npm + c) * LP + a;
         u64 val;
-        if (E.ind[j]) val = a ? Ps[o - 1] : 0;
-        else if (a == k + 1) val = 0;
+        if (E.ind[j]) {
+            val = a ? Ps[o - 1] : 0;
+            if (IP && a <= k) val = sub64(val, mmul(A.alpha[k], Ps[o], A), A.p);
+        } else if (a == k + 1) val = 0;
         else val = dep_combine(A, E, j, Ps + (i64)c * LP + a, (i64)npm * LP);
         Pd[o] = val;
     }
 }
 
+template <bool IP>
 __global__ void __launch_bounds__(512) k_mbasis_leaf_cl(const LeafArgs A)
 {
     namespace cg = cooperative_groups;
@@ -543,8 +561,8 @@ __global__ void __launch_bounds__(512) k_mbasis_leaf_cl(const LeafArgs A)
             mbasis1_scaled(A, R, t, Ew, egn);
         } else if (k > 0) {
             const ElimSm Ep = elim_carve(ew + ((k - 1) & 1) * ewn, ei + ((k - 1) & 1) * ein, m, n);
-            leaf_apply(A, Ep, k - 1, (k & 1) ? G0 : G1, Gk, (k & 1) ? P0 : P1, (k & 1) ? P1 : P0, ng, ngm, np_, npm,
-                       tid - egn, nth - egn);
+            leaf_apply<IP>(A, Ep, k - 1, (k & 1) ? G0 : G1, Gk, (k & 1) ? P0 : P1, (k & 1) ? P1 : P0, ng, ngm, np_,
+                           npm, tid - egn, nth - egn);
         }
         __syncthreads();
         if (k + 1 < T) {
@@ -573,7 +591,8 @@ __global__ void __launch_bounds__(512) k_mbasis_leaf_cl(const LeafArgs A)
                 u64 val = add64(acc, redc128(hi, lo, A.p, A.pn), A.p);
 #pragma unroll
                 for (int o = 8; o >= 1; o >>= 1) val = add64(val, __shfl_xor_sync(0xffffffffu, val, o, 16), A.p);
-                if (act && !dep) val = R[j * n + g0 + c];
+                if (act && !dep)   // independent rows: x R_k (approximants), (alpha_{k+1} - alpha_k) G_{k+1} (interpolants)
+                    val = IP ? mmul(sub64(A.alpha[k + 1], A.alpha[k], A.p), X[(i64)j * rs], A) : R[j * n + g0 + c];
                 if (act && h < LEAF_CL) cl.map_shared_rank(Rn, h)[j * n + g0 + c] = val;
             }
         }
@@ -586,8 +605,8 @@ __global__ void __launch_bounds__(512) k_mbasis_leaf_cl(const LeafArgs A)
     __syncthreads();
     {
         const ElimSm El = elim_carve(ew + ((T - 1) & 1) * ewn, ei + ((T - 1) & 1) * ein, m, n);
-        leaf_apply(A, El, T - 1, nullptr, nullptr, ((T - 1) & 1) ? P1 : P0, (T & 1) ? P1 : P0, ng, ngm, np_, npm, tid,
-                   nth);
+        leaf_apply<IP>(A, El, T - 1, nullptr, nullptr, ((T - 1) & 1) ? P1 : P0, (T & 1) ? P1 : P0, ng, ngm, np_, npm,
+                       tid, nth);
     }
     __syncthreads();
     for (int i = tid; i < m; i += nth) lam[i] = mmul(mpow(lam[i], A.p - 2, A), 1, A);   // plain lam_i^-1
@@ -631,6 +650,10 @@ struct PmbCtx {
     LeafArgs base;     // p-dependent constants + leaf scratch
     int m, n;
     int64_t T;
+    // interpolant bases at the points c q^l (Algorithm 5): the points (Montgomery), the
+    // chirp q^C(t) (plain) and q^-C(t) (Montgomery), t < sigma; c and q (plain)
+    const u64 *alpha, *h, *hinv;
+    u64 c, q;
 };
 
 // Bytes of arena the recursion on order e needs (P1, shifts, R, P2 per level).
@@ -646,20 +669,25 @@ size_t rec_bytes(int m, int n, int64_t e, int64_t T)
     return own + (left > right ? left : right);
 }
 
-int leaf(PmbCtx &C, const u64 *F, int64_t sF, int64_t e, const i64 *s_in, u64 *P, int64_t sP, i64 *s_out)
+// alpha: null for an approximant leaf, else the leaf's e points (Montgomery form).
+int leaf(PmbCtx &C, const u64 *F, int64_t sF, int64_t e, const i64 *s_in, u64 *P, int64_t sP, i64 *s_out,
+         const u64 *alpha = nullptr)
 {
     pm_ctx *ctx = C.ctx;
     LeafArgs A = C.base;
     A.T = (int)e;
     A.F = F; A.sF = sF; A.s_in = s_in; A.s_out = s_out; A.P = P; A.sP = sP;
+    A.alpha = alpha;
+    void (*k_cl)(LeafArgs) = alpha ? k_mbasis_leaf_cl<true> : k_mbasis_leaf_cl<false>;
+    void (*k_one)(LeafArgs) = alpha ? k_mbasis_leaf<true> : k_mbasis_leaf<false>;
     int tok = stage_begin(ctx, PM_STAGE_LEAF);
     bool done = false;
     if (C.use_cluster) {
         for (int clsz = LEAF_CL_MAX; clsz >= 8 && !done; clsz /= 2) {
             const size_t smc = leaf_cl_smem(C.m, C.n, (int)e, clsz);
             if (smc > 200 * 1024) continue;
-            cudaFuncSetAttribute(k_mbasis_leaf_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
-            if (clsz > 8) cudaFuncSetAttribute(k_mbasis_leaf_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaFuncSetAttribute(k_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+            if (clsz > 8) cudaFuncSetAttribute(k_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(clsz);
             cfg.blockDim = dim3(512);
@@ -673,19 +701,19 @@ int leaf(PmbCtx &C, const u64 *F, int64_t sF, int64_t e, const i64 *s_in, u64 *P
             cfg.attrs = at;
             cfg.numAttrs = 1;
             int ncl = 0;
-            if (cudaOccupancyMaxActiveClusters(&ncl, k_mbasis_leaf_cl, &cfg) != cudaSuccess || ncl < 1) {
+            if (cudaOccupancyMaxActiveClusters(&ncl, k_cl, &cfg) != cudaSuccess || ncl < 1) {
                 cudaGetLastError();
                 continue;
             }
-            if (cudaLaunchKernelEx(&cfg, k_mbasis_leaf_cl, A) == cudaSuccess) done = true;
+            if (cudaLaunchKernelEx(&cfg, k_cl, A) == cudaSuccess) done = true;
             else cudaGetLastError();
         }
     }
     if (!done) {
         // the opt-in is needed whenever static + dynamic shared memory exceed 48 KB
         const size_t sm = leaf_smem(C.m, C.n);
-        cudaFuncSetAttribute(k_mbasis_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_mbasis_leaf<<<1, 512, sm, ctx->stream>>>(A);
+        cudaFuncSetAttribute(k_one, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_one<<<1, 512, sm, ctx->stream>>>(A);
     }
     ctx->launches++;
     cudaError_t err = cudaGetLastError();
@@ -718,28 +746,138 @@ int rec(PmbCtx &C, const u64 *F, int64_t sF, int64_t e, const i64 *s_in, u64 *P,
     return PM_OK;
 }
 
-}  // namespace
+// ------------------------------------------------------------------ interpolant bases (Algorithm 5)
+// Points alpha_l = c q^l.  The residual of a node, R_l = P1(alpha_{o+e1+l}) E_{e1+l},
+// needs P1 at a geometric progression: with C(t) = t (t - 1) / 2 and c' = c q^(o+e1),
+// P1(c' q^i) = q^-C(i) sum_e (a_e c'^e q^-C(e)) q^C(i+e) (Sec. 2, evaluation at a
+// geometric progression), the middle product of the scaled, reversed coefficients of
+// every entry of P1 with the chirp q^C(t) on the product hot path; then a batch of
+// e2 constant m x m by m x n products mod p.
 
-extern "C" int pm_basis(pm_ctx *ctx, uint64_t p, int m, int n, const void *F, int64_t lenF, int64_t d,
-                        const int64_t *shift, void *P, int64_t *rdeg_out)
+// alpha_t = c q^t (Montgomery), h_t = q^C(t) (plain), hinv_t = q^-C(t) (Montgomery)
+__global__ void k_ip_tables(const LeafArgs A, u64 qm, u64 qim, u64 cm, u64 *alpha, u64 *h, u64 *hinv, int64_t N)
 {
-    if (!ctx) return PM_EINVAL;
-    if (m < 1 || n < 1 || d < 1 || lenF < 1) return pm_fail(ctx, PM_EINVAL, "need m, n, d, lenF >= 1");
-    if (p < 3 || !(p & 1) || p >= (1ull << 62)) return pm_fail(ctx, PM_EINVAL, "pm_basis needs an odd prime p < 2^62");
-    if (m > 128 || n > 128) return pm_fail(ctx, PM_EUNSUPPORTED, "pm_basis supports m, n <= 128");
-    if (!F || !shift || !P || !rdeg_out) return pm_fail(ctx, PM_EINVAL, "null buffer");
-    if (d + 1 > (1 << PM_MAX_LOG2L)) return pm_fail(ctx, PM_EINVAL, "order too large for the transforms");
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return pm_fail(ctx, PM_ECUDA, "cudaSetDevice failed");
-    const size_t sm = leaf_smem(m, n);
-    if (sm > 200 * 1024) return pm_fail(ctx, PM_EUNSUPPORTED, "leaf workspace too large");
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        const u64 c2 = (u64)t * (u64)(t > 0 ? t - 1 : 0) / 2;
+        alpha[t] = mmul(cm, mpow(qm, (u64)t, A), A);
+        h[t] = mmul(mpow(qm, c2, A), 1, A);
+        hinv[t] = mpow(qim, c2, A);
+    }
+}
 
-    PmbCtx C;
+// u_e = c'^e q^-C(e) (Montgomery), e < E
+__global__ void k_ip_uvec(const LeafArgs A, u64 cpm, const u64 *hinv, u64 *u, int E)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
+        u[e] = mmul(mpow(cpm, (u64)e, A), hinv[e], A);
+}
+
+// U[r][E-1-e] = P1[r][e] u_e (plain), r < rows
+__global__ void k_ip_prep(const LeafArgs A, const u64 *P1, int64_t sP1, const u64 *u, u64 *U, int64_t rows, int E)
+{
+    const int64_t total = rows * E;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = x / E;
+        const int e = (int)(x % E);
+        U[r * E + (E - 1 - e)] = mmul(P1[r * sP1 + e], u[e], A);
+    }
+}
+
+// R[i][j][l] = q^-C(l) sum_k S[i][k][l] E[k][j][l], l < L: S holds q^C(l) P1(c' q^l)
+// (m x m, entry stride L), E the second half of the points (entry stride sE), plain values.
+__global__ void k_ip_resid(const LeafArgs A, const u64 *S, const u64 *E, int64_t sE, const u64 *hinv, u64 *R,
+                           int64_t L)
+{
+    const int m = A.m, n = A.n;
+    const int64_t total = (int64_t)m * n * L;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = x % L, e = x / L;
+        const int i = (int)(e / n), j = (int)(e % n);
+        u64 hi = 0, lo = 0, acc = 0;
+        int cnt = 0;
+        for (int k = 0; k < m; k++) {
+            mac128(hi, lo, S[((int64_t)i * m + k) * L + l], E[((int64_t)k * n + j) * sE + l]);
+            if (++cnt == A.chunk) { acc = add64(acc, redc128(hi, lo, A.p, A.pn), A.p); hi = lo = 0; cnt = 0; }
+        }
+        acc = add64(acc, redc128(hi, lo, A.p, A.pn), A.p);   // sum / 2^64
+        R[x] = mmul(mmul(acc, hinv[l], A), A.r2, A);
+    }
+}
+
+int ip_grid(int64_t total)
+{
+    const int64_t b = (total + 255) / 256;
+    return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+}
+
+size_t rec_ip_bytes(int m, int n, int64_t e, int64_t T)
+{
+    if (e <= T) return 0;
+    const int64_t e1 = (e + 1) / 2, e2 = e / 2;
+    const size_t mm = (size_t)m * m;
+    const size_t own = 2 * al256(mm * (e1 + 1) * 8) + al256((size_t)m * 8) + al256((size_t)(e1 + 1) * 8) +
+                       al256(mm * e2 * 8) + al256((size_t)m * n * e2 * 8) + al256(mm * (e2 + 1) * 8);
+    size_t left = rec_ip_bytes(m, n, e1, T), right = rec_ip_bytes(m, n, e2, T);
+    return own + (left > right ? left : right);
+}
+
+// P (m x m, length e + 1, stride sP) = PM-IntBasis of E (m x n, e points from point o,
+// entry stride sE) for the shift s_in; s_out = rdeg_s(P).
+int rec_ip(PmbCtx &C, const u64 *E, int64_t sE, int64_t e, int64_t o, const i64 *s_in, u64 *P, int64_t sP, i64 *s_out)
+{
+    if (e <= C.T) return leaf(C, E, sE, e, s_in, P, sP, s_out, C.alpha + o);
+    pm_ctx *ctx = C.ctx;
+    const int m = C.m, n = C.n;
+    const LeafArgs &A = C.base;
+    const int64_t e1 = (e + 1) / 2, e2 = e / 2, E1 = e1 + 1, mm = (int64_t)m * m;
+    const size_t mark = ctx->arena.used;
+    u64 *P1 = (u64 *)arena_alloc(ctx, (size_t)mm * E1 * 8);
+    i64 *s1 = (i64 *)arena_alloc(ctx, (size_t)m * 8);
+    u64 *U = (u64 *)arena_alloc(ctx, (size_t)mm * E1 * 8);
+    u64 *u = (u64 *)arena_alloc(ctx, (size_t)E1 * 8);
+    u64 *S = (u64 *)arena_alloc(ctx, (size_t)mm * e2 * 8);
+    u64 *R = (u64 *)arena_alloc(ctx, (size_t)m * n * e2 * 8);
+    u64 *P2 = (u64 *)arena_alloc(ctx, (size_t)mm * (e2 + 1) * 8);
+    if (!P1 || !s1 || !U || !u || !S || !R || !P2) return pm_fail(ctx, PM_ENOMEM, "PM-IntBasis arena exhausted");
+    // step 2: P1 = PM-IntBasis(E_0 .. E_{e1-1}, alpha_o .. alpha_{o+e1-1}, s)
+    CKI(rec_ip(C, E, sE, e1, o, s_in, P1, E1, s1));
+    // step 3: R_l = P1(alpha_{o+e1+l}) E_{e1+l}, l < e2
+    {
+        const u64 cp = host_mulmod(C.c % A.p, host_powmod(C.q, (uint64_t)(o + e1), A.p), A.p);
+        const u64 cpm = host_mulmod(cp, A.one, A.p);
+        int tok = stage_begin(ctx, PM_STAGE_OTHER);
+        k_ip_uvec<<<ip_grid(E1), 256, 0, ctx->stream>>>(A, cpm, C.hinv, u, (int)E1);
+        k_ip_prep<<<ip_grid(mm * E1), 256, 0, ctx->stream>>>(A, P1, E1, u, U, mm, (int)E1);
+        ctx->launches += 2;
+        cudaError_t err = cudaGetLastError();
+        stage_end(ctx, tok);
+        CKI(pm_cuda(ctx, err, "k_ip_prep"));
+        CKI(prod_slice(ctx, A.p, 8, (int)mm, 1, 1, U, E1, E1, C.h, e1 + e2, e1 + e2, e1, e2, ceil_log2(e1 + e2), S, e2));
+        tok = stage_begin(ctx, PM_STAGE_OTHER);
+        k_ip_resid<<<ip_grid((int64_t)m * n * e2), 256, 0, ctx->stream>>>(A, S, E + e1, sE, C.hinv, R, e2);
+        ctx->launches++;
+        err = cudaGetLastError();
+        stage_end(ctx, tok);
+        CKI(pm_cuda(ctx, err, "k_ip_resid"));
+    }
+    // steps 4-5: P2 = PM-IntBasis(R, alpha_{o+e1} .. alpha_{o+e-1}, rdeg_s(P1))
+    CKI(rec_ip(C, R, e2, e2, o + e1, s1, P2, e2 + 1, s_out));
+    // step 6: P = P2 P1 (degree <= e)
+    CKI(prod_slice(ctx, A.p, 8, m, m, m, P2, e2 + 1, e2 + 1, P1, E1, E1, 0, e + 1, ceil_log2(e + 1), P, sP));
+    ctx->arena.used = mark;
+    return PM_OK;
+}
+
+// Constants and leaf scratch shared by both entry points.
+int pmb_setup(pm_ctx *ctx, PmbCtx &C, uint64_t p, int m, int n, int64_t Tl, size_t extra)
+{
     C.ctx = ctx;
     C.use_cluster = ctx->opt_leaf_cluster != 0;
     C.m = m;
     C.n = n;
     C.T = ctx->opt_T;
-    const int64_t Tl = d < C.T ? d : C.T;   // largest leaf order
+    C.alpha = C.h = C.hinv = nullptr;
+    C.c = C.q = 0;
     LeafArgs &A = C.base;
     memset(&A, 0, sizeof(A));
     A.p = p;
@@ -752,19 +890,84 @@ extern "C" int pm_basis(pm_ctx *ctx, uint64_t p, int m, int n, const void *F, in
     A.n = n;
     uint64_t ch = ~0ull / p;
     A.chunk = (int)(ch > 16 ? 16 : ch);
-
-    // arena: recursion buffers + leaf scratch + the two shift vectors
     const size_t leafG = (size_t)m * n * Tl * 8, leafP = (size_t)m * m * (Tl + 1) * 8;
-    const size_t padF = lenF < d ? al256((size_t)m * n * d * 8) : 0;
-    const size_t need = rec_bytes(m, n, d, C.T) + 2 * al256(leafG) + 2 * al256(leafP) + 2 * al256((size_t)m * 8) + padF;
-    CKI(arena_reserve(ctx, need));
+    CKI(arena_reserve(ctx, extra + 2 * al256(leafG) + 2 * al256(leafP)));
     A.G0 = (u64 *)arena_alloc(ctx, leafG);
     A.G1 = (u64 *)arena_alloc(ctx, leafG);
     A.P0 = (u64 *)arena_alloc(ctx, leafP);
     A.P1 = (u64 *)arena_alloc(ctx, leafP);
+    if (!A.G0 || !A.G1 || !A.P0 || !A.P1) return pm_fail(ctx, PM_ENOMEM, "arena too small");
+    return PM_OK;
+}
+
+int pmb_check(pm_ctx *ctx, uint64_t p, int m, int n, int64_t d)
+{
+    if (m < 1 || n < 1 || d < 1) return pm_fail(ctx, PM_EINVAL, "need m, n >= 1 and an order >= 1");
+    if (p < 3 || !(p & 1) || p >= (1ull << 62)) return pm_fail(ctx, PM_EINVAL, "need an odd prime p < 2^62");
+    if (m > 128 || n > 128) return pm_fail(ctx, PM_EUNSUPPORTED, "m, n <= 128 supported");
+    if (d + 1 > (1 << PM_MAX_LOG2L)) return pm_fail(ctx, PM_EINVAL, "order too large for the transforms");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return pm_fail(ctx, PM_ECUDA, "cudaSetDevice failed");
+    if (leaf_smem(m, n) > 200 * 1024) return pm_fail(ctx, PM_EUNSUPPORTED, "leaf workspace too large");
+    return PM_OK;
+}
+
+}  // namespace
+
+extern "C" int pm_intbasis(pm_ctx *ctx, uint64_t p, int m, int n, const void *E, int64_t sigma, uint64_t c,
+                           uint64_t q, const int64_t *shift, void *P, int64_t *rdeg_out)
+{
+    if (!ctx) return PM_EINVAL;
+    CKI(pmb_check(ctx, p, m, n, sigma));
+    if (!E || !shift || !P || !rdeg_out) return pm_fail(ctx, PM_EINVAL, "null buffer");
+    if (c >= p || q == 0 || q >= p) return pm_fail(ctx, PM_EINVAL, "need c in [0, p) and q in [1, p)");
+    PmbCtx C;
+    const int64_t T = ctx->opt_T, Tl = sigma < T ? sigma : T;
+    const size_t need = rec_ip_bytes(m, n, sigma, T) + 3 * al256((size_t)sigma * 8) + 2 * al256((size_t)m * 8);
+    CKI(pmb_setup(ctx, C, p, m, n, Tl, need));
+    const LeafArgs &A = C.base;
+    u64 *alpha = (u64 *)arena_alloc(ctx, (size_t)sigma * 8);
+    u64 *h = (u64 *)arena_alloc(ctx, (size_t)sigma * 8);
+    u64 *hinv = (u64 *)arena_alloc(ctx, (size_t)sigma * 8);
     i64 *s_in = (i64 *)arena_alloc(ctx, (size_t)m * 8);
     i64 *s_out = (i64 *)arena_alloc(ctx, (size_t)m * 8);
-    if (!A.G0 || !A.G1 || !A.P0 || !A.P1 || !s_in || !s_out) return pm_fail(ctx, PM_ENOMEM, "arena too small");
+    if (!alpha || !h || !hinv || !s_in || !s_out) return pm_fail(ctx, PM_ENOMEM, "arena too small");
+    C.alpha = alpha;
+    C.h = h;
+    C.hinv = hinv;
+    C.c = c;
+    C.q = q;
+    {
+        const u64 qm = host_mulmod(q, A.one, p), qim = host_mulmod(host_powmod(q, p - 2, p), A.one, p);
+        const u64 cm = host_mulmod(c, A.one, p);
+        int tok = stage_begin(ctx, PM_STAGE_OTHER);
+        k_ip_tables<<<ip_grid(sigma), 256, 0, ctx->stream>>>(A, qm, qim, cm, alpha, h, hinv, sigma);
+        ctx->launches++;
+        cudaError_t err = cudaGetLastError();
+        stage_end(ctx, tok);
+        CKI(pm_cuda(ctx, err, "k_ip_tables"));
+    }
+    CKI(pm_cuda(ctx, cudaMemcpyAsync(s_in, shift, (size_t)m * 8, cudaMemcpyHostToDevice, ctx->stream), "shift H2D"));
+    CKI(rec_ip(C, (const u64 *)E, sigma, sigma, 0, s_in, (u64 *)P, sigma + 1, s_out));
+    CKI(pm_cuda(ctx, cudaMemcpyAsync(rdeg_out, s_out, (size_t)m * 8, cudaMemcpyDeviceToHost, ctx->stream), "rdeg D2H"));
+    CKI(pm_cuda(ctx, cudaStreamSynchronize(ctx->stream), "pm_intbasis sync"));
+    return PM_OK;
+}
+
+extern "C" int pm_basis(pm_ctx *ctx, uint64_t p, int m, int n, const void *F, int64_t lenF, int64_t d,
+                        const int64_t *shift, void *P, int64_t *rdeg_out)
+{
+    if (!ctx) return PM_EINVAL;
+    CKI(pmb_check(ctx, p, m, n, d));
+    if (lenF < 1) return pm_fail(ctx, PM_EINVAL, "need lenF >= 1");
+    if (!F || !shift || !P || !rdeg_out) return pm_fail(ctx, PM_EINVAL, "null buffer");
+    PmbCtx C;
+    const int64_t T = ctx->opt_T, Tl = d < T ? d : T;   // largest leaf order
+    // arena: recursion buffers + leaf scratch + the two shift vectors
+    const size_t padF = lenF < d ? al256((size_t)m * n * d * 8) : 0;
+    CKI(pmb_setup(ctx, C, p, m, n, Tl, rec_bytes(m, n, d, T) + 2 * al256((size_t)m * 8) + padF));
+    i64 *s_in = (i64 *)arena_alloc(ctx, (size_t)m * 8);
+    i64 *s_out = (i64 *)arena_alloc(ctx, (size_t)m * 8);
+    if (!s_in || !s_out) return pm_fail(ctx, PM_ENOMEM, "arena too small");
     // only F mod x^d is read: a shorter F is copied into a zero-padded buffer of length d
     const u64 *Fd = (const u64 *)F;
     int64_t sF = lenF;

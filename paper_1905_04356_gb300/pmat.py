@@ -67,6 +67,7 @@ def lib():
             "pmat_mul_batched": ([P, i32, C.POINTER(pmat_desc)], i32),
             "pmat_mul_noalloc": ([u64, i32, i32, i32, i32, P, i64, P, i64, P, P], i32),
             "pm_basis": ([P, u64, i32, i32, P, i64, i64, P, P, P], i32),
+            "pm_intbasis": ([P, u64, i32, i32, P, i64, u64, u64, P, P, P], i32),
             "bivariate_resultant": ([P, i32, P, i32, i32, P, i32, i32, P, P], i32),
             "pmat_inv_trunc": ([P, u64, i32, i32, P, i64, i64, P], i32),
             "pmat_solve_series": ([P, u64, i32, i32, P, i64, P, i64, i64, P], i32),
@@ -282,6 +283,23 @@ def pm_basis(ctx: Context, p: int, F: torch.Tensor, d: int, shift, out=None):
     P = _out(out, (m, m, d + 1), F)
     rd = np.zeros(m, dtype=np.int64)
     ctx._ck(lib().pm_basis(ctx.h, p, m, n, F.data_ptr(), lenF, d, s.ctypes.data, P.data_ptr(), rd.ctypes.data))
+    return P, rd
+
+
+def pm_intbasis(ctx: Context, p: int, E: torch.Tensor, c: int, q: int, shift, out=None):
+    """PM-IntBasis (Algorithm 5) at the points c q^l: E is m x n x sigma (E[:, :, l] goes with
+    c q^l); returns (P as m x m x (sigma+1) uint64 bits, rdeg_s(P) as int64 array)."""
+    E = _dev(E)
+    if width(E) != 8:
+        raise TypeError("pm_intbasis takes 64-bit coefficients")
+    m, n, sigma = E.shape
+    s = np.ascontiguousarray(np.asarray(shift, dtype=np.int64))
+    if s.shape != (m,):
+        raise ValueError("shift must have m entries")
+    P = _out(out, (m, m, sigma + 1), E)
+    rd = np.zeros(m, dtype=np.int64)
+    ctx._ck(lib().pm_intbasis(ctx.h, p, m, n, E.data_ptr(), sigma, c, q, s.ctypes.data, P.data_ptr(),
+                              rd.ctypes.data))
     return P, rd
 
 

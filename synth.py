@@ -135,6 +135,17 @@ def pmbasis_c3(seed: int = 0, m: int = 32, n: int = 16, d: int = 8192):
     return dict(p=p, F=F, d=d, shift=np.zeros(m, dtype=np.int64))
 
 
+def intbasis_w(seed: int = 0, m: int = 32, n: int = 16, sigma: int = 8192):
+    """E (m x n, sigma matrices) modulo a random 60-bit prime at the points c q^l with c, q
+    drawn uniformly from [2, p - 1), uniform shift 0."""
+    g = rng(seed)
+    p = random_prime(g, 60)
+    E = pmat(g, m, n, sigma, p, np.uint64)
+    c = int(g.integers(2, p - 1))
+    q = int(g.integers(2, p - 1))
+    return dict(p=p, E=E, c=c, q=q, shift=np.zeros(m, dtype=np.int64))
+
+
 def loguniform_int(g, lo: int, hi: int) -> int:
     """floor(exp(U[ln lo, ln (hi+1))))."""
     return int(math.floor(math.exp(g.uniform(math.log(lo), math.log(hi + 1)))))

@@ -96,3 +96,16 @@ def test_mintbasis_dimension_counts_brute_force():
             dim = round(np.log(count) / np.log(p))
             assert p ** dim == count
             assert dim == sum(max(0, delta - int(r) + 1) for r in rd)
+
+
+@pytest.mark.parametrize("p", [7, 97, P60])
+def test_pmat_eval_is_the_power_sum(p):
+    """oracle.pmat_eval (Horner) against sum_e X_e a^e taken with Python integers."""
+    rnd = random.Random(p & 0xffff)
+    X = _rand_pmat(rnd, p, 3, 4, 9)
+    for a in (0, 1, p - 1, rnd.randrange(p)):
+        got = oracle.pmat_eval(p, X, a)
+        for i in range(3):
+            for j in range(4):
+                want = sum(int(X[i, j, e]) * pow(a, e, p) for e in range(9)) % p
+                assert int(got[i, j]) == want
