@@ -386,16 +386,14 @@ def main():
             pmat.pmat_mul(ctx, W998["p"], A2, B2, out=C2)
         ts998 = timed(lambda i: pmat.pmat_mul(ctx, W998["p"], A2, B2, out=C2), args.steps)
 
-        # ---- end to end: pinned host buffers, copies inside the timed region
+        # ---- end to end: pmat_mul_host on pinned host buffers, every host<->device copy
+        #      inside the timed region (overlapped with the stages by the library)
         Ap = torch.from_numpy(Ah.view(np.int64)).pin_memory()
         Bp = torch.from_numpy(Bh.view(np.int64)).pin_memory()
         Cp = torch.empty((m, k, lenC), dtype=torch.int64).pin_memory()
 
         def e2e_step(i):
-            A.copy_(Ap, non_blocking=True)
-            B.copy_(Bp, non_blocking=True)
-            pmat.pmat_mul(ctx, p, A, B, out=Cd)
-            Cp.copy_(Cd, non_blocking=True)
+            pmat.pmat_mul_host(ctx, p, Ap, Bp, out=Cp)
 
         for i in range(2):
             e2e_step(i)

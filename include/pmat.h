@@ -9,6 +9,8 @@
  *   pmat_middle_product           Sec. 2, "Polynomial multiplication":
  *                                 MiddleProduct(F, G, c, d)
  *   pmat_mul_batched              many independent products in one call
+ *   pmat_mul_host                 the same product from and to host memory,
+ *                                 copies overlapped with the stages
  *   pm_basis                      Sec. 3, Algorithm 3 (PM-Basis) over
  *                                 Algorithms 1-2 (M-Basis-1, M-Basis)
  *   pm_intbasis                   Sec. 3, Algorithm 5 (PM-IntBasis) over
@@ -77,8 +79,12 @@ enum {
                                default 32 (Sec. 3, "Interpolant bases") */
     PM_OPT_DEBUG_CHECKS = 3, /* 1 = check inputs are in [0, p) (PM_EDOMAIN) */
     PM_OPT_STAGE_TIMING = 4, /* 1 = record CUDA events around every stage (see pm_stage_times) */
-    PM_OPT_LEAF_CLUSTER = 5  /* PM-Basis leaves: 1 = a cluster of 8 CTAs with the basis in shared
-                                memory (default), 0 = one CTA with the basis in global memory */
+    PM_OPT_LEAF_CLUSTER = 5, /* PM-Basis / PM-IntBasis leaves: 1 = a cluster of up to 16 CTAs with
+                                the basis in shared memory (default), 0 = one CTA with the basis
+                                in global memory */
+    PM_OPT_HOST_CHUNKS = 6   /* pmat_mul_host: chunks of output entries whose inverse transforms,
+                                recombination and copy back are pipelined (0 = automatic,
+                                default; else 1 .. m k) */
 };
 
 /* Stages reported by pm_stage_times. */
@@ -133,6 +139,18 @@ int pm_stage_times(pm_ctx *ctx, double *ms, int64_t *launches);
  * coefficients need).  Requires m, n, k, dA, dB >= 1. */
 int pmat_mul(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k,
              const void *A, int64_t dA, const void *B, int64_t dB, void *C);
+
+/* pmat_mul with A, B and C in HOST memory (same layouts).  The uploads run on
+ * a second stream owned by the context and are overlapped with the stages:
+ * B and A are transformed as their row chunks land, the pointwise products
+ * run once, and the output entries are inverse-transformed, recombined and
+ * copied back in chunks, each copy overlapping the next chunk's work.  Page-locked (pinned) host buffers are needed for
+ * the copies to overlap; pageable ones give the same result.  Asynchronous
+ * like the device calls: C is complete after pm_sync(), and A, B, C must
+ * stay valid until then.  Returns PM_EUNSUPPORTED when the product's device
+ * workspace would exceed 16 GB (use pmat_mul on device buffers). */
+int pmat_mul_host(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k,
+                  const void *A, int64_t dA, const void *B, int64_t dB, void *C);
 
 /* C (m x k, length t) = A . B mod x^t (Sec. 2; the truncated product used by
  * Newton iteration in Sec. 4.3).  Requires t >= 1; coefficients of degree

@@ -365,6 +365,21 @@ static int launch_packs(pm_ctx *ctx, const std::vector<J> &jobs, const std::vect
     return PM_OK;
 }
 
+// Forward jobs of one transform length: column passes first, then the blocks.
+static int launch_fwd_lists(pm_ctx *ctx, const std::vector<FwdJob> &blk, const std::vector<int> &bn,
+                            const std::vector<ColJob> &col, const std::vector<int> &cn, int lg)
+{
+    if (!col.empty())
+        CKI(launch_packs(ctx, col, cn, [&](const JobPack<ColJob> &pk) {
+            return launch_ntt_fwd_cols(pk, lg, ctx->stream, &ctx->launches); }));
+    if (!blk.empty()) {
+        const int blg = lg > PM_LB_LOG2 ? PM_LB_LOG2 : lg;
+        CKI(launch_packs(ctx, blk, bn, [&](const JobPack<FwdJob> &pk) {
+            return launch_ntt_fwd_block(pk, blg, ctx->stream, &ctx->launches); }));
+    }
+    return PM_OK;
+}
+
 namespace {
 struct Plan {
     std::vector<PrimeSlot *> pr;
@@ -372,7 +387,100 @@ struct Plan {
     size_t bA, bB, bC, bR, total;
     int64_t out_len;
 };
+
+// Pointwise jobs sorted by kernel form.
+struct PwLists {
+    std::vector<PwJob> jobs, tjobs, sjobs[9], vjobs;
+    std::vector<int> nb, tnb, snb[9], vnb;
+};
+
+// Inverse-transform jobs of one transform length (a column pass after the blocks when L > 2^14).
+struct InvLists {
+    std::vector<InvJob> blk;
+    std::vector<int> bn;
+    std::vector<ColJob> col;
+    std::vector<int> cn;
+};
 }  // namespace
+
+// Pointwise m x n . n x k products at every point of one prime's transforms: tensor-core limb
+// products where the shape allows (m, n, k <= 32) when that form is requested, small inner
+// dimensions (n <= 8) by a streaming kernel (one launch per n), matrix-vector products
+// (k = 1, n <= 64) by another, the staged CUDA-core 64-bit form otherwise.
+static void add_pointwise(pm_ctx *ctx, PwLists &pl, u32 *A, u32 *B, u32 *C, int m, int n, int k, int lg,
+                          const PrimeDev &D)
+{
+    PwJob j;
+    memset(&j, 0, sizeof(j));
+    j.A = A; j.B = B; j.C = C;
+    j.m = m; j.n = n; j.k = k; j.L = 1 << lg; j.P = D;
+    if (ctx->opt_pointwise == 2 && tc_supported(j)) { pl.tjobs.push_back(j); pl.tnb.push_back(tc_blocks(j)); }
+    else if (pws_supported(j)) { pl.sjobs[j.n].push_back(j); pl.snb[j.n].push_back(pws_blocks(j)); }
+    else if (pwv_supported(j)) { pl.vjobs.push_back(j); pl.vnb.push_back(pwv_blocks(j)); }
+    else { const int nbk = pw_plan(j); pl.jobs.push_back(j); pl.nb.push_back(nbk); }
+}
+
+static int launch_pointwise_lists(pm_ctx *ctx, const PwLists &pl)
+{
+    if (!pl.jobs.empty())
+        CKI(launch_packs(ctx, pl.jobs, pl.nb, [&](const JobPack<PwJob> &pk) {
+            return launch_pointwise(pk, ctx->stream, &ctx->launches); }));
+    if (!pl.vjobs.empty())
+        CKI(launch_packs(ctx, pl.vjobs, pl.vnb, [&](const JobPack<PwJob> &pk) {
+            return launch_pointwise_mv(pk, ctx->stream, &ctx->launches); }));
+    for (int nn = 1; nn <= 8; nn++)
+        if (!pl.sjobs[nn].empty())
+            CKI(launch_packs(ctx, pl.sjobs[nn], pl.snb[nn], [&](const JobPack<PwJob> &pk) {
+                return launch_pointwise_sn(pk, ctx->stream, &ctx->launches); }));
+    if (!pl.tjobs.empty())
+        CKI(launch_packs(ctx, pl.tjobs, pl.tnb, [&](const JobPack<PwJob> &pk) {
+            return launch_pointwise_tc(pk, ctx->d_status, ctx->stream, &ctx->launches); }));
+    return PM_OK;
+}
+
+// Inverse transforms of eC entries (src, stride L) modulo one prime; coefficients off ..
+// off+out_len-1 of each go to dst (entry stride dstride) in the given mode (1 = u32 residues,
+// 4 / 8 = the caller's element width).
+static void add_inverse(InvLists &il, const PrimeDev &D, u32 *src, void *dst, int64_t dstride, int mode,
+                        int64_t off, int64_t out_len, int64_t eC, int lg)
+{
+    const int64_t L = int64_t(1) << lg;
+    if (lg <= PM_LB_LOG2) {
+        InvJob j;
+        j.src = src; j.dst = dst; j.src_stride = L; j.dst_stride = dstride;
+        j.out_off = (int)off; j.out_len = (int)out_len; j.dst_mode = mode; j.count = (int)eC; j.P = D;
+        const int epb = fwd_entries_per_block(lg);
+        il.blk.push_back(j);
+        il.bn.push_back((int)((eC + epb - 1) / epb));
+    } else {
+        const int64_t nbk = L >> PM_LB_LOG2;
+        InvJob j;
+        j.src = src; j.dst = src; j.src_stride = 1 << PM_LB_LOG2; j.dst_stride = 1 << PM_LB_LOG2;
+        j.out_off = 0; j.out_len = 0; j.dst_mode = 0; j.count = (int)(eC * nbk); j.P = D;
+        const int epb = fwd_entries_per_block(PM_LB_LOG2);
+        il.blk.push_back(j);
+        il.bn.push_back((int)((eC * nbk + epb - 1) / epb));
+        ColJob c;
+        c.src = src; c.dst = dst; c.src_stride = L; c.dst_stride = dstride;
+        c.src_len = 0; c.mode = mode; c.count = (int)eC; c.out_off = (int)off;
+        c.out_len = (int)out_len; c._pad = 0; c.P = D;
+        il.col.push_back(c);
+        il.cn.push_back((int)eC * blocks_per_entry_cols(lg));
+    }
+}
+
+static int launch_inverse_lists(pm_ctx *ctx, const InvLists &il, int lg)
+{
+    if (!il.blk.empty()) {
+        const int blg = lg > PM_LB_LOG2 ? PM_LB_LOG2 : lg;
+        CKI(launch_packs(ctx, il.blk, il.bn, [&](const JobPack<InvJob> &pk) {
+            return launch_ntt_inv_block(pk, blg, ctx->stream, &ctx->launches); }));
+    }
+    if (!il.col.empty())
+        CKI(launch_packs(ctx, il.col, il.cn, [&](const JobPack<ColJob> &pk) {
+            return launch_ntt_inv_cols(pk, lg, ctx->stream, &ctx->launches); }));
+    return PM_OK;
+}
 
 #define PM_BATCH_WS_CAP (16ull << 30)   // workspace bytes per chunk of a batch
 
@@ -433,104 +541,39 @@ int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
                     add_forward(D, q.B, q.w, q.sB, q.dB, q.n * q.k, (u32 *)(b.B + i * P.bB), lg, blk, bn, col, cn);
                 }
             }
-            if (!col.empty())
-                CKI(launch_packs(ctx, col, cn, [&](const JobPack<ColJob> &pk) {
-                    return launch_ntt_fwd_cols(pk, lg, ctx->stream, &ctx->launches); }));
-            if (!blk.empty()) {
-                const int blg = lg > PM_LB_LOG2 ? PM_LB_LOG2 : lg;
-                CKI(launch_packs(ctx, blk, bn, [&](const JobPack<FwdJob> &pk) {
-                    return launch_ntt_fwd_block(pk, blg, ctx->stream, &ctx->launches); }));
-            }
+            CKI(launch_fwd_lists(ctx, blk, bn, col, cn, lg));
         }
         stage_end(ctx, tok);
-        // 2. pointwise products (jobs of any length share launches): tensor-core limb
-        //    products where the shape allows (m, n, k <= 32) when that form is requested,
-        //    small inner dimensions (n <= 8) by a streaming kernel (one launch per n),
-        //    matrix-vector products (k = 1, n <= 64) by another, the staged CUDA-core
-        //    64-bit form otherwise
+        // 2. pointwise products (jobs of any length share launches)
         tok = stage_begin(ctx, PM_STAGE_POINTWISE);
         {
-            std::vector<PwJob> jobs, tjobs, sjobs[9], vjobs; std::vector<int> nb, tnb, snb[9], vnb;
+            PwLists pl;
             for (int r = r0; r < r1; r++) {
                 const ProdReq &q = reqs[r];
                 const Plan &P = plan[r];
                 const Bufs &b = buf[r - r0];
-                for (size_t i = 0; i < P.pr.size(); i++) {
-                    PwJob j;
-                    memset(&j, 0, sizeof(j));
-                    j.A = (u32 *)(b.A + i * P.bA); j.B = (u32 *)(b.B + i * P.bB); j.C = (u32 *)(b.C + i * P.bC);
-                    j.m = q.m; j.n = q.n; j.k = q.k; j.L = 1 << q.lg; j.P = prime_dev(*P.pr[i], q.lg);
-                    if (ctx->opt_pointwise == 2 && tc_supported(j)) { tjobs.push_back(j); tnb.push_back(tc_blocks(j)); }
-                    else if (pws_supported(j)) { sjobs[j.n].push_back(j); snb[j.n].push_back(pws_blocks(j)); }
-                    else if (pwv_supported(j)) { vjobs.push_back(j); vnb.push_back(pwv_blocks(j)); }
-                    else { const int nbk = pw_plan(j); jobs.push_back(j); nb.push_back(nbk); }
-                }
+                for (size_t i = 0; i < P.pr.size(); i++)
+                    add_pointwise(ctx, pl, (u32 *)(b.A + i * P.bA), (u32 *)(b.B + i * P.bB), (u32 *)(b.C + i * P.bC),
+                                  q.m, q.n, q.k, q.lg, prime_dev(*P.pr[i], q.lg));
             }
-            if (!jobs.empty())
-                CKI(launch_packs(ctx, jobs, nb, [&](const JobPack<PwJob> &pk) {
-                    return launch_pointwise(pk, ctx->stream, &ctx->launches); }));
-            if (!vjobs.empty())
-                CKI(launch_packs(ctx, vjobs, vnb, [&](const JobPack<PwJob> &pk) {
-                    return launch_pointwise_mv(pk, ctx->stream, &ctx->launches); }));
-            for (int nn = 1; nn <= 8; nn++)
-                if (!sjobs[nn].empty())
-                    CKI(launch_packs(ctx, sjobs[nn], snb[nn], [&](const JobPack<PwJob> &pk) {
-                        return launch_pointwise_sn(pk, ctx->stream, &ctx->launches); }));
-            if (!tjobs.empty())
-                CKI(launch_packs(ctx, tjobs, tnb, [&](const JobPack<PwJob> &pk) {
-                    return launch_pointwise_tc(pk, ctx->d_status, ctx->stream, &ctx->launches); }));
+            CKI(launch_pointwise_lists(ctx, pl));
         }
         stage_end(ctx, tok);
         // 3. inverse transforms, scaled, writing each slice, binned by length
         tok = stage_begin(ctx, PM_STAGE_INV);
         for (int lg = 4; lg <= PM_MAX_LOG2L; lg++) {
-            std::vector<InvJob> blk; std::vector<int> bn;
-            std::vector<ColJob> col; std::vector<int> cn;
-            const int64_t L = int64_t(1) << lg;
+            InvLists il;
             for (int r = r0; r < r1; r++) {
                 const ProdReq &q = reqs[r];
                 if (q.lg != lg) continue;
                 const Plan &P = plan[r];
                 const Bufs &b = buf[r - r0];
-                const int mode = P.direct ? q.w : 1;
-                const int64_t eC = (int64_t)q.m * q.k;
-                for (size_t i = 0; i < P.pr.size(); i++) {
-                    PrimeDev D = prime_dev(*P.pr[i], lg);
-                    u32 *src = (u32 *)(b.C + i * P.bC);
-                    void *dst = P.direct ? q.C : (void *)(b.R + i * P.bR);
-                    const int64_t dstride = P.direct ? q.sC : q.len;
-                    if (lg <= PM_LB_LOG2) {
-                        InvJob j;
-                        j.src = src; j.dst = dst; j.src_stride = L; j.dst_stride = dstride;
-                        j.out_off = (int)q.off; j.out_len = (int)P.out_len; j.dst_mode = mode; j.count = (int)eC; j.P = D;
-                        const int epb = fwd_entries_per_block(lg);
-                        blk.push_back(j);
-                        bn.push_back((int)((eC + epb - 1) / epb));
-                    } else {
-                        const int64_t nbk = L >> PM_LB_LOG2;
-                        InvJob j;
-                        j.src = src; j.dst = src; j.src_stride = 1 << PM_LB_LOG2; j.dst_stride = 1 << PM_LB_LOG2;
-                        j.out_off = 0; j.out_len = 0; j.dst_mode = 0; j.count = (int)(eC * nbk); j.P = D;
-                        const int epb = fwd_entries_per_block(PM_LB_LOG2);
-                        blk.push_back(j);
-                        bn.push_back((int)((eC * nbk + epb - 1) / epb));
-                        ColJob c;
-                        c.src = src; c.dst = dst; c.src_stride = L; c.dst_stride = dstride;
-                        c.src_len = 0; c.mode = mode; c.count = (int)eC; c.out_off = (int)q.off;
-                        c.out_len = (int)P.out_len; c._pad = 0; c.P = D;
-                        col.push_back(c);
-                        cn.push_back((int)eC * blocks_per_entry_cols(lg));
-                    }
-                }
+                for (size_t i = 0; i < P.pr.size(); i++)
+                    add_inverse(il, prime_dev(*P.pr[i], lg), (u32 *)(b.C + i * P.bC),
+                                P.direct ? q.C : (void *)(b.R + i * P.bR), P.direct ? q.sC : q.len, P.direct ? q.w : 1,
+                                q.off, P.out_len, (int64_t)q.m * q.k, lg);
             }
-            if (!blk.empty()) {
-                const int blg = lg > PM_LB_LOG2 ? PM_LB_LOG2 : lg;
-                CKI(launch_packs(ctx, blk, bn, [&](const JobPack<InvJob> &pk) {
-                    return launch_ntt_inv_block(pk, blg, ctx->stream, &ctx->launches); }));
-            }
-            if (!col.empty())
-                CKI(launch_packs(ctx, col, cn, [&](const JobPack<ColJob> &pk) {
-                    return launch_ntt_inv_cols(pk, lg, ctx->stream, &ctx->launches); }));
+            CKI(launch_inverse_lists(ctx, il, lg));
         }
         stage_end(ctx, tok);
         // 4. CRT recombination into values mod p
@@ -630,6 +673,8 @@ int pm_destroy(pm_ctx *ctx)
     if (ctx->d_status) cudaFree(ctx->d_status);
     for (auto &mk : ctx->marks) { cudaEventDestroy(mk.a); cudaEventDestroy(mk.b); }
     for (auto e : ctx->spare) cudaEventDestroy(e);
+    for (auto e : ctx->hev) cudaEventDestroy(e);
+    if (ctx->copy) cudaStreamDestroy(ctx->copy);
     if (ctx->own) cudaStreamDestroy(ctx->own);
     delete ctx;
     return PM_OK;
@@ -655,6 +700,10 @@ int pm_set_option(pm_ctx *ctx, int key, int64_t value)
         return PM_OK;
     case PM_OPT_LEAF_CLUSTER:
         ctx->opt_leaf_cluster = value ? 1 : 0;
+        return PM_OK;
+    case PM_OPT_HOST_CHUNKS:
+        if (value < 0 || value > (1 << 20)) return pm_fail(ctx, PM_EINVAL, "host chunk count out of range");
+        ctx->opt_host_chunks = (int)value;
         return PM_OK;
     default:
         return pm_fail(ctx, PM_EINVAL, "unknown option key");
@@ -711,7 +760,7 @@ int pm_stage_times(pm_ctx *ctx, double *ms, int64_t *launches)
 }
 
 static int check_common(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA,
-                        const void *B, int64_t dB, const void *C)
+                        const void *B, int64_t dB, const void *C, bool device_inputs = true)
 {
     if (!ctx) return PM_EINVAL;
     if (m < 1 || n < 1 || k < 1) return pm_fail(ctx, PM_EINVAL, "dimensions must be >= 1");
@@ -723,8 +772,142 @@ static int check_common(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, con
     if (!A || !B || !C) return pm_fail(ctx, PM_EINVAL, "null buffer");
     if (dA > (1 << PM_MAX_LOG2L) || dB > (1 << PM_MAX_LOG2L)) return pm_fail(ctx, PM_EINVAL, "length exceeds 2^20");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return pm_fail(ctx, PM_ECUDA, "cudaSetDevice failed");
-    CKI(debug_check(ctx, A, (int64_t)m * n * dA, w, p));
-    CKI(debug_check(ctx, B, (int64_t)n * k * dB, w, p));
+    if (device_inputs) {
+        CKI(debug_check(ctx, A, (int64_t)m * n * dA, w, p));
+        CKI(debug_check(ctx, B, (int64_t)n * k * dB, w, p));
+    }
+    return PM_OK;
+}
+
+// Rows [r0, r1) of chunk c when `rows` rows are cut into `nc` nearly equal chunks.
+static void chunk_rows(int rows, int nc, int c, int &r0, int &r1)
+{
+    r0 = (int)((int64_t)rows * c / nc);
+    r1 = (int)((int64_t)rows * (c + 1) / nc);
+}
+
+// The full product with A, B and C in host memory.  The uploads run on a second stream, B then
+// A, each in up to two row chunks transformed as they land; the pointwise products run once over
+// the whole product (cutting them by rows would reload B's transforms per chunk); the inverse
+// transforms and the CRT then run in chunks of output entries, each copied back on the copy
+// stream while the next chunk computes.
+static int mul_host(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA,
+                    const void *B, int64_t dB, void *C)
+{
+    const int64_t len = dA + dB - 1;
+    const int lg = ceil_log2(len) < 4 ? 4 : ceil_log2(len);
+    if (lg > PM_MAX_LOG2L) return pm_fail(ctx, PM_EINVAL, "product longer than 2^20");
+    const int64_t L = int64_t(1) << lg;
+    std::vector<PrimeSlot *> pr;
+    bool direct = false;
+    CKI(choose_primes(ctx, p, n, dA < dB ? dA : dB, lg, pr, direct));
+    for (auto *sl : pr) CKI(slot_tables(ctx, *sl, lg));
+    const size_t K = pr.size();
+    const size_t eA = (size_t)m * n, eB = (size_t)n * k, eC = (size_t)m * k;
+    const size_t bAh = eA * dA * w, bBh = eB * dB * w, bCh = eC * len * w;
+    const size_t bA = align256(eA * L * 4), bB = align256(eB * L * 4), bC = align256(eC * L * 4);
+    const size_t bR = direct ? 0 : K * eC * len * 4;
+    const size_t total = align256(bAh) + align256(bBh) + align256(bCh) + K * (bA + bB + bC) + align256(bR);
+    if (total > PM_BATCH_WS_CAP) return pm_fail(ctx, PM_EUNSUPPORTED, "pmat_mul_host: product too large for one pass");
+    // chunk counts: pipelining pays once a chunk's copy is a few MB
+    const int ncA = (bAh >= (8u << 20) && m >= 2) ? 2 : 1;
+    const int ncB = (bBh >= (8u << 20) && n >= 2) ? 2 : 1;
+    int ncO = (int)(bCh >> 23);                          // about one chunk per 8 MB of output, 1 .. 6
+    ncO = ncO < 1 ? 1 : (ncO > 6 ? 6 : ncO);
+    if (ctx->opt_host_chunks > 0) ncO = ctx->opt_host_chunks;
+    if ((size_t)ncO > eC) ncO = (int)eC;
+    void *ws = nullptr;
+    CKI(ws_reserve(ctx, total + 256, &ws));
+    char *cur = (char *)ws;
+    char *Ad = cur; cur += align256(bAh);
+    char *Bd = cur; cur += align256(bBh);
+    char *Cd = cur; cur += align256(bCh);
+    char *TA = cur; cur += K * bA;
+    char *TB = cur; cur += K * bB;
+    char *TC = cur; cur += K * bC;
+    char *R = cur;
+    if (!ctx->copy) CK(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+    const int nev = 2 + ncA + ncB + ncO;
+    while ((int)ctx->hev.size() < nev) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->hev.push_back(e);
+    }
+    cudaEvent_t *ev = ctx->hev.data();   // 0: start, then B chunks, A chunks, output chunks, end
+    cudaEvent_t *evB = ev + 1, *evA = evB + ncB, *evO = evA + ncA, evEnd = evO[ncO];
+    cudaStream_t cs = ctx->copy;
+    CK(cudaEventRecord(ev[0], ctx->stream));   // the workspace is free (stream order)
+    CK(cudaStreamWaitEvent(cs, ev[0], 0));
+    // uploads, then the forward transforms of each chunk once it has landed
+    struct Up { const char *h; char *d; int rows, ncol; int64_t dl; char *T; size_t bT; cudaEvent_t *e; int nc; };
+    const Up ups[2] = {{(const char *)B, Bd, n, k, dB, TB, bB, evB, ncB}, {(const char *)A, Ad, m, n, dA, TA, bA, evA, ncA}};
+    for (const Up &u : ups)
+        for (int c = 0; c < u.nc; c++) {
+            int r0, r1;
+            chunk_rows(u.rows, u.nc, c, r0, r1);
+            const size_t o = (size_t)r0 * u.ncol * u.dl * w, sz = (size_t)(r1 - r0) * u.ncol * u.dl * w;
+            CK(cudaMemcpyAsync(u.d + o, u.h + o, sz, cudaMemcpyHostToDevice, cs));
+            CK(cudaEventRecord(u.e[c], cs));
+        }
+    for (const Up &u : ups)
+        for (int c = 0; c < u.nc; c++) {
+            int r0, r1;
+            chunk_rows(u.rows, u.nc, c, r0, r1);
+            CK(cudaStreamWaitEvent(ctx->stream, u.e[c], 0));
+            CKI(debug_check(ctx, u.d + (size_t)r0 * u.ncol * u.dl * w, (int64_t)(r1 - r0) * u.ncol * u.dl, w, p));
+            int tok = stage_begin(ctx, PM_STAGE_FWD);
+            std::vector<FwdJob> blk; std::vector<int> bn;
+            std::vector<ColJob> col; std::vector<int> cn;
+            for (size_t i = 0; i < K; i++)
+                add_forward(prime_dev(*pr[i], lg), u.d + (size_t)r0 * u.ncol * u.dl * w, w, u.dl, u.dl,
+                            (r1 - r0) * u.ncol, (u32 *)(u.T + i * u.bT) + (size_t)r0 * u.ncol * L, lg, blk, bn, col,
+                            cn);
+            CKI(launch_fwd_lists(ctx, blk, bn, col, cn, lg));
+            stage_end(ctx, tok);
+        }
+    int tok = stage_begin(ctx, PM_STAGE_POINTWISE);
+    {
+        PwLists pl;
+        for (size_t i = 0; i < K; i++)
+            add_pointwise(ctx, pl, (u32 *)(TA + i * bA), (u32 *)(TB + i * bB), (u32 *)(TC + i * bC), m, n, k, lg,
+                          prime_dev(*pr[i], lg));
+        CKI(launch_pointwise_lists(ctx, pl));
+    }
+    stage_end(ctx, tok);
+    // output entries [e0, e1) per chunk: inverse transforms, CRT (residue planes of the chunk
+    // packed: K planes of (e1 - e0) * len words), copy back
+    for (int c = 0; c < ncO; c++) {
+        const int64_t e0 = (int64_t)eC * c / ncO, e1 = (int64_t)eC * (c + 1) / ncO, ce = e1 - e0;
+        char *Rc = R + K * (size_t)e0 * len * 4;
+        char *Cc = Cd + (size_t)e0 * len * w;
+        tok = stage_begin(ctx, PM_STAGE_INV);
+        {
+            InvLists il;
+            for (size_t i = 0; i < K; i++)
+                add_inverse(il, prime_dev(*pr[i], lg), (u32 *)(TC + i * bC) + (size_t)e0 * L,
+                            direct ? (void *)Cc : (void *)(Rc + i * (size_t)ce * len * 4), len, direct ? w : 1, 0, len,
+                            ce, lg);
+            CKI(launch_inverse_lists(ctx, il, lg));
+        }
+        stage_end(ctx, tok);
+        if (!direct) {
+            tok = stage_begin(ctx, PM_STAGE_CRT);
+            CrtJob j;
+            memset(&j, 0, sizeof(j));
+            fill_crt(j, pr, p);
+            j.res = (const u32 *)Rc; j.dst = Cc; j.count = ce * len; j.len = len; j.dst_stride = len; j.w = w;
+            std::vector<CrtJob> jobs(1, j);
+            std::vector<int> nb(1, crt_blocks(j));
+            CKI(launch_packs(ctx, jobs, nb, [&](const JobPack<CrtJob> &pk) {
+                return launch_crt(pk, ctx->stream, &ctx->launches); }));
+            stage_end(ctx, tok);
+        }
+        CK(cudaEventRecord(evO[c], ctx->stream));
+        CK(cudaStreamWaitEvent(cs, evO[c], 0));
+        CK(cudaMemcpyAsync((char *)C + (size_t)e0 * len * w, Cc, (size_t)ce * len * w, cudaMemcpyDeviceToHost, cs));
+    }
+    CK(cudaEventRecord(evEnd, cs));
+    CK(cudaStreamWaitEvent(ctx->stream, evEnd, 0));   // later work on the stream follows the copies
     return PM_OK;
 }
 
@@ -736,6 +919,13 @@ int pmat_mul(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A,
     const int lg = ceil_log2(len);
     if (lg > PM_MAX_LOG2L) return pm_fail(ctx, PM_EINVAL, "product longer than 2^20");
     return prod_slice(ctx, p, w, m, n, k, A, dA, dA, B, dB, dB, 0, len, lg, C, len);
+}
+
+int pmat_mul_host(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA, const void *B,
+                  int64_t dB, void *C)
+{
+    CKI(check_common(ctx, p, w, m, n, k, A, dA, B, dB, C, false));
+    return mul_host(ctx, p, w, m, n, k, A, dA, B, dB, C);
 }
 
 int pmat_mul_trunc(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA, const void *B,

@@ -37,9 +37,12 @@ struct pm_ctx {
     Arena arena;                      // driver buffers (PM-Basis, resultant)
     int opt_timing = 0;
     int opt_leaf_cluster = 1;         // PM-Basis leaves on a CTA cluster (0 = one CTA)
+    int opt_host_chunks = 0;          // pmat_mul_host output chunks (0 = automatic)
     struct Mark { int stage; cudaEvent_t a, b; long long launches; };
     std::vector<Mark> marks;          // recorded stage intervals
     std::vector<cudaEvent_t> spare;   // reusable events
+    cudaStream_t copy = nullptr;      // host<->device copies of pmat_mul_host (created on first use)
+    std::vector<cudaEvent_t> hev;     // its ordering events
 };
 
 // Stage timing: stage_begin returns a token; stage_end closes it.

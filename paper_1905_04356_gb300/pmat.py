@@ -23,7 +23,8 @@ LIB_PATH = os.path.join(HERE, "libpmat.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pmat.h")
 
 PM_OK, PM_EINVAL, PM_EDOMAIN, PM_ENOMEM, PM_ECUDA, PM_ETIMEOUT, PM_EUNSUPPORTED, PM_ESCRATCH = range(8)
-PM_OPT_POINTWISE, PM_OPT_THRESHOLD, PM_OPT_DEBUG_CHECKS, PM_OPT_STAGE_TIMING, PM_OPT_LEAF_CLUSTER = 1, 2, 3, 4, 5
+(PM_OPT_POINTWISE, PM_OPT_THRESHOLD, PM_OPT_DEBUG_CHECKS, PM_OPT_STAGE_TIMING, PM_OPT_LEAF_CLUSTER,
+ PM_OPT_HOST_CHUNKS) = 1, 2, 3, 4, 5, 6
 PM_NSTAGES = 8
 STAGES = ["fwd_ntt", "pointwise", "inv_ntt", "crt", "leaf", "other"]
 STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_EDOMAIN", 3: "PM_ENOMEM", 4: "PM_ECUDA",
@@ -62,6 +63,7 @@ def lib():
             "pm_kernel_launches": ([P], i64),
             "pm_stage_times": ([P, P, P], i32),
             "pmat_mul": ([P, u64, i32, i32, i32, i32, P, i64, P, i64, P], i32),
+            "pmat_mul_host": ([P, u64, i32, i32, i32, i32, P, i64, P, i64, P], i32),
             "pmat_mul_trunc": ([P, u64, i32, i32, i32, i32, P, i64, P, i64, i64, P], i32),
             "pmat_middle_product": ([P, u64, i32, i32, i32, i32, P, i64, P, i64, i64, i64, P], i32),
             "pmat_mul_batched": ([P, i32, C.POINTER(pmat_desc)], i32),
@@ -192,6 +194,33 @@ def pmat_mul(ctx: Context, p: int, A: torch.Tensor, B: torch.Tensor, out=None) -
         raise ValueError("shape/dtype mismatch")
     Cout = _out(out, (m, k, dA + dB - 1), A)
     ctx._ck(lib().pmat_mul(ctx.h, p, width(A), m, n, k, A.data_ptr(), dA, B.data_ptr(), dB, Cout.data_ptr()))
+    return Cout
+
+
+def _host(t: torch.Tensor) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("expected a CPU tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t
+
+
+def pmat_mul_host(ctx: Context, p: int, A: torch.Tensor, B: torch.Tensor, out=None) -> torch.Tensor:
+    """C = A . B mod p with A, B and C in host memory (pinned for overlap); asynchronous like the
+    device calls: read C after ctx.sync()."""
+    A, B = _host(A), _host(B)
+    m, n, dA = A.shape
+    n2, k, dB = B.shape
+    if n != n2 or A.dtype != B.dtype:
+        raise ValueError("shape/dtype mismatch")
+    shape = (m, k, dA + dB - 1)
+    if out is None:
+        Cout = torch.empty(shape, dtype=A.dtype, pin_memory=A.is_pinned())
+    else:
+        if tuple(out.shape) != shape or out.dtype != A.dtype:
+            raise ValueError(f"out must be {shape} of {A.dtype}")
+        Cout = _host(out)
+    ctx._ck(lib().pmat_mul_host(ctx.h, p, width(A), m, n, k, A.data_ptr(), dA, B.data_ptr(), dB, Cout.data_ptr()))
     return Cout
 
 
