@@ -72,6 +72,8 @@ def lib():
         L.orc_mintbasis.argtypes = [u64, i32, i32, P, i64, P, P, P, P]
         L.orc_pmintbasis.restype = None
         L.orc_pmintbasis.argtypes = [u64, i32, i32, P, i64, P, P, i64, P, P]
+        L.orc_scale.restype = None
+        L.orc_scale.argtypes = [u64, P, i64, u64]
         L.orc_pmat_eval.restype = None
         L.orc_pmat_eval.argtypes = [u64, i32, i32, P, i64, u64, P]
         L.orc_solve_series.restype = i32
@@ -255,6 +257,46 @@ def solve_series(p, A, b, N, threads=None):
     if rc[0]:
         raise SingularError("A(0) is singular mod p")
     return v
+
+
+def solve(p, A, b, threads=None):
+    """Sec. 4, linear system solving by lifting: (u, f) with A u = f b, f monic of minimal degree
+    (A: n x n x dA with A(0) invertible mod the prime p, b: n x 1 x db).
+
+    The steps of the lifting solver: v = A^-1 b mod x^N (the series solution above, which is
+    what the truncated inverse and Dixon's lifting compute), then vector rational reconstruction
+    by an approximant basis of the (n+1) x n matrix [v^T; -I] at order N.  With
+    D1 = n (dA - 1) >= deg f and D2 = (n - 1)(dA - 1) + db - 1 >= deg u (Cramer's rule) and
+    N = D1 + D2 + 1, the basis is taken for the shift (-D1, -D2, ..., -D2): its one row of
+    non-positive shifted degree is [f, u^T] up to a constant, since two solutions within the
+    degree bounds agree modulo x^N on a polynomial identity of degree < N.  Returns
+    (u as n x 1 x (D2+1), f as D1+1 coefficients), both normalised so that f is monic.
+    """
+    A, b = _u64(A), _u64(b)
+    n, n2, dA = A.shape
+    assert n == n2 and b.shape[0] == n and b.shape[1] == 1
+    db = b.shape[2]
+    D1 = n * (dA - 1)
+    D2 = (n - 1) * (dA - 1) + db - 1
+    N = D1 + D2 + 1
+    v = solve_series(p, A, b, N, threads)
+    F = np.zeros((n + 1, n, N), dtype=np.uint64)
+    F[0] = v[:, 0, :]
+    for i in range(n):
+        F[1 + i, i, 0] = (p - 1) % p
+    s = [-D1] + [-D2] * n
+    P, rd = pmbasis(p, F, N, s, threads=threads)
+    r = int(np.argmin(rd))
+    if rd[r] > 0:
+        raise SingularError("no solution within the degree bounds")
+    f = np.ascontiguousarray(P[r, 0, :D1 + 1])
+    u = np.ascontiguousarray(P[r, 1:, :D2 + 1]).reshape(n, 1, D2 + 1)
+    nz = np.nonzero(f)[0]
+    lc = int(f[nz[-1]])
+    inv = powmod(lc, p - 2, p)
+    lib().orc_scale(p, _ptr(f), f.size, inv)
+    lib().orc_scale(p, _ptr(u), u.size, inv)
+    return u, f
 
 
 def inv_slices(p, A, K, threads=None):

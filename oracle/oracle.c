@@ -50,6 +50,8 @@
  *   orc_inv_slices   Sec. 4, high-order lifting: the slices S_i of A^-1,
  *                    coefficients (2^i - 1)(d - 1) .. (2^i + 1)(d - 1) of the
  *                    truncated inverse above (d = the length of A).
+ *   orc_scale        multiplication of a coefficient array by a constant (the
+ *                    normalisation of the lifting solver's output, Sec. 4).
  *   orc_solve_series Sec. 4, lifting: the power-series solution
  *                    v = A^-1 b mod x^N that Dixon's algorithm produces, by
  *                    its definition A.v = b mod x^N: v_0 = A_0^-1 b_0,
@@ -590,6 +592,12 @@ static u64 poly_eval(const u64 *f, i64 len, u64 a, u64 p)
     u64 v = 0;
     for (i64 e = len - 1; e >= 0; e--) v = f_add(f_mul(v, a, p), f[e], p);
     return v;
+}
+
+/* x[i] <- c x[i] mod p for i < count. */
+void orc_scale(u64 p, u64 *x, i64 count, u64 c)
+{
+    for (i64 i = 0; i < count; i++) x[i] = f_mul(x[i] % p, c % p, p);
 }
 
 /* out[e] = X_e(a) for the r x c entries of X (length len), by Horner's rule. */
