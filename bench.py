@@ -44,9 +44,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the PM-Basis / batched / resultant / inverse / solve / slices / intbasis timings")
-    ap.add_argument("--extra", default="pm_basis,resultant,batched,inverse,solve,slices,intbasis",
-                    help="comma-separated subset of pm_basis, resultant, batched, inverse, solve, slices, intbasis")
+                    help="skip the timings of the drivers (see --extra)")
+    ap.add_argument("--extra", default="pm_basis,resultant,batched,inverse,solve,slices,intbasis,linsolve",
+                    help="comma-separated subset of pm_basis, resultant, batched, inverse, solve, slices, "
+                         "intbasis, linsolve")
     return ap.parse_args()
 
 
@@ -182,13 +183,14 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------- other workloads (reported under "extra")
-def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse", "solve", "slices", "intbasis"),
-                    reps=3):
+def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse", "solve", "slices", "intbasis",
+                                   "linsolve"), reps=3):
     """PM-Basis (F 32x16, order 8192, 60-bit p), 512 batched uneven products, resultants
     (deg_x = deg_y = 150, 1 prime and 16 primes), the truncated inverse of a 32x32 matrix of
     degree < 4096 mod x^4096 and the lifted series solution of A v = b mod x^32768 (same A, b of
     degree < 4096; 60-bit p), six high-order lifting slices of the same A^-1, PM-IntBasis (E 32x16
-    at 8192 geometric points, 60-bit p): ms per call, CUDA events on the stream."""
+    at 8192 geometric points, 60-bit p), the lifting solver A u = f b (16x16, length 256, 60-bit
+    p): ms per call, CUDA events on the stream."""
     import numpy as np
     import torch
     import synth
@@ -291,10 +293,24 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"
         out["pm_intbasis_stage_ms"] = {k: round(v[0], 2) for k, v in st.items() if v[1]}
         return out
 
+    def linsolve():
+        W = synth.linsolve_w(0)
+        A, b = pmat.to_device(W["A"]), pmat.to_device(W["b"])
+        run = lambda: pmat.pmat_solve(ctx, W["p"], A, b)  # noqa: E731
+        out = {"solve_16x16_d256_ms": round(ev_ms(run, reps), 2)}
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
+        ctx.stage_times()
+        run()
+        st = ctx.stage_times()
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
+        out["solve_stage_ms"] = {k: round(v[0], 2) for k, v in st.items() if v[1]}
+        return out
+
     out = {}
     with torch.cuda.stream(s):
         for name, fn in (("pm_basis", pm_basis), ("resultant", resultant), ("batched", batched),
-                         ("inverse", inverse), ("solve", solve), ("slices", slices), ("intbasis", intbasis)):
+                         ("inverse", inverse), ("solve", solve), ("slices", slices), ("intbasis", intbasis),
+                         ("linsolve", linsolve)):
             if name in which:
                 out.update(fn())
     return out

@@ -24,6 +24,9 @@
  *                                 algorithm over the truncated inverse
  *   pmat_inv_slices               Sec. 4, high-order lifting: slices of A^-1
  *                                 at degrees around 2^i (d - 1)
+ *   pmat_solve                    Sec. 4, lifting solver: (u, f) with
+ *                                 A u = f b by Dixon's lifting and vector
+ *                                 rational reconstruction (PM-Basis)
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -271,6 +274,21 @@ int pmat_inv_trunc(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t
  * context's driver arena. */
 int pmat_solve_series(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA,
                       const void *b, int64_t db, int64_t N, void *v);
+
+/* Linear system solving by lifting (Sec. 4, "Linear system solving"): the
+ * pair (u, f) with A u = f b, f monic of minimal degree.  A: DEVICE n x n
+ * matrix of uint64_t, entries of length dA, A(0) invertible mod p; b: DEVICE
+ * n x 1, entries of length db.  With D1 = n (dA - 1) and D2 = (n - 1)(dA - 1)
+ * + db - 1 (Cramer's bounds on deg f and deg u): v = A^-1 b mod x^N, N = D1 +
+ * D2 + 1 (pmat_solve_series), then vector rational reconstruction by an
+ * approximant basis of [v^T; -I] at order N for the shift (-D1, -D2, ...,
+ * -D2) (pm_basis): its row of non-positive shifted degree is [f, u^T].
+ * Outputs: u DEVICE n x 1 of length D2 + 1, f DEVICE length D1 + 1 (zero
+ * beyond the degrees), deg_out HOST int64_t[2] = (deg f, deg u; -1 for
+ * u = 0).  Synchronises the stream.  Requires p an odd prime < 2^62,
+ * 1 <= n <= 127, dA, db >= 1, N <= 2^19.  A(0) singular: PM_EDOMAIN. */
+int pmat_solve(pm_ctx *ctx, uint64_t p, int n, const void *A, int64_t dA,
+               const void *b, int64_t db, void *u, void *f, int64_t *deg_out);
 
 /* High-order lifting slices (Sec. 4, "Linear system solving": Storjohann's
  * high-order lifting).  A: DEVICE n x n matrix, entries of length dA >= 2 (width

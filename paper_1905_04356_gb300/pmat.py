@@ -70,6 +70,7 @@ def lib():
             "pmat_mul_noalloc": ([u64, i32, i32, i32, i32, P, i64, P, i64, P, P], i32),
             "pm_basis": ([P, u64, i32, i32, P, i64, i64, P, P, P], i32),
             "pm_intbasis": ([P, u64, i32, i32, P, i64, u64, u64, P, P, P], i32),
+            "pmat_solve": ([P, u64, i32, P, i64, P, i64, P, P, P], i32),
             "bivariate_resultant": ([P, i32, P, i32, i32, P, i32, i32, P, P], i32),
             "pmat_inv_trunc": ([P, u64, i32, i32, P, i64, i64, P], i32),
             "pmat_solve_series": ([P, u64, i32, i32, P, i64, P, i64, i64, P], i32),
@@ -313,6 +314,26 @@ def pm_basis(ctx: Context, p: int, F: torch.Tensor, d: int, shift, out=None):
     rd = np.zeros(m, dtype=np.int64)
     ctx._ck(lib().pm_basis(ctx.h, p, m, n, F.data_ptr(), lenF, d, s.ctypes.data, P.data_ptr(), rd.ctypes.data))
     return P, rd
+
+
+def pmat_solve(ctx: Context, p: int, A: torch.Tensor, b: torch.Tensor):
+    """Lifting solver (Sec. 4): (u, f, deg f, deg u) with A u = f b, f monic of minimal degree.
+    A: n x n x dA, b: n x 1 x db (64-bit); u: n x 1 x (D2+1), f: D1+1 (device tensors)."""
+    A, b = _dev(A), _dev(b)
+    if width(A) != 8 or width(b) != 8:
+        raise TypeError("pmat_solve takes 64-bit coefficients")
+    n, n2, dA = A.shape
+    if n != n2 or tuple(b.shape[:2]) != (n, 1):
+        raise ValueError("A must be n x n and b n x 1")
+    db = b.shape[2]
+    D1 = n * (dA - 1)
+    D2 = (n - 1) * (dA - 1) + db - 1
+    u = torch.empty((n, 1, D2 + 1), dtype=A.dtype, device=A.device)
+    f = torch.empty((D1 + 1,), dtype=A.dtype, device=A.device)
+    dg = np.zeros(2, dtype=np.int64)
+    ctx._ck(lib().pmat_solve(ctx.h, p, n, A.data_ptr(), dA, b.data_ptr(), db, u.data_ptr(), f.data_ptr(),
+                             dg.ctypes.data))
+    return u, f, int(dg[0]), int(dg[1])
 
 
 def pm_intbasis(ctx: Context, p: int, E: torch.Tensor, c: int, q: int, shift, out=None):

@@ -127,6 +127,15 @@ def solve_w(seed: int = 0, n: int = 32, d: int = 4096, digits: int = 8):
     return dict(p=p, A=A, b=b, N=digits * d)
 
 
+def linsolve_w(seed: int = 0, n: int = 16, d: int = 256):
+    """A (n x n, length d) and b (n x 1, length d) modulo a random 60-bit prime."""
+    g = rng(seed)
+    p = random_prime(g, 60)
+    A = pmat(g, n, n, d, p, np.uint64)
+    b = pmat(g, n, 1, d, p, np.uint64)
+    return dict(p=p, A=A, b=b)
+
+
 def pmbasis_c3(seed: int = 0, m: int = 32, n: int = 16, d: int = 8192):
     """F (m x n, length d) modulo a random 60-bit prime, uniform shift 0."""
     g = rng(seed)
