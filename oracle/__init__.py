@@ -72,6 +72,8 @@ def lib():
         L.orc_mintbasis.argtypes = [u64, i32, i32, P, i64, P, P, P, P]
         L.orc_pmintbasis.restype = None
         L.orc_pmintbasis.argtypes = [u64, i32, i32, P, i64, P, P, i64, P, P]
+        L.orc_bivariate_resultant_villard.restype = i32
+        L.orc_bivariate_resultant_villard.argtypes = [u64, i32, i32, P, i32, i32, P, i32, P]
         L.orc_scale.restype = None
         L.orc_scale.argtypes = [u64, P, i64, u64]
         L.orc_pmat_eval.restype = None
@@ -215,6 +217,37 @@ def bivariate_resultant(p, f, g, threads=None):
         p, dxf, dyf, _ptr(f), dxg, dyg, _ptr(g), _ptr(R))))
     if rc[0] != 0:
         raise ValueError("too few evaluation points in F_p")
+    return R
+
+
+def villard_m(dyf, dyg, dxf, dxg):
+    """Default block size of the Villard variant: ceil(n^0.4) for the partial degree
+    n = max of the degrees (the choice reported in Sec. 5.2), at most min(dyf, dyg)."""
+    import math
+    n = max(dxf, dxg, dyf, dyg)
+    m = 1
+    while m ** 2.5 < n:      # smallest m with m >= n^0.4
+        m += 1
+    return max(1, min(m, dyf, dyg))
+
+
+def bivariate_resultant_villard(p, f, g, m=0, threads=None):
+    """Res_y(f, g) by the variant of Algorithm 6 (Sec. 5.2); same layout and output as
+    bivariate_resultant.  m = 0 takes villard_m."""
+    f, g = _u64(f), _u64(g)
+    dyf, dxf = f.shape[0] - 1, f.shape[1] - 1
+    dyg, dxg = g.shape[0] - 1, g.shape[1] - 1
+    if m <= 0:
+        m = villard_m(dyf, dyg, dxf, dxg)
+    D = dxf * dyg + dxg * dyf
+    R = np.zeros(D + 1, dtype=np.uint64)
+    rc = []
+    _with_threads(threads, lambda: rc.append(lib().orc_bivariate_resultant_villard(
+        p, dxf, dyf, _ptr(f), dxg, dyg, _ptr(g), m, _ptr(R))))
+    if rc[0] == 1:
+        raise ValueError("too few evaluation points in F_p")
+    if rc[0] == 2:
+        raise ValueError("det Q vanishes at the normalisation point: input not generic")
     return R
 
 

@@ -37,6 +37,11 @@
  *   orc_pmintbasis   Algorithm 5 (PM-IntBasis): divide and conquer with the
  *                    threshold T, the residual being P1 evaluated at the second
  *                    half of the points times the second half of E.
+ *   orc_bivariate_resultant_villard
+ *                    Sec. 5.2, the variant of Algorithm 6: values of the
+ *                    top-right block H of the inverse Sylvester matrix, an
+ *                    interpolant basis of [H; -I] giving H = Q^-1 R, det Q
+ *                    normalised by one direct value of the resultant.
  *   orc_univ_resultant / orc_bivariate_resultant
  *                    Sec. 5.2, the "Direct" method: evaluate in x, take
  *                    univariate resultants in y by the Euclidean algorithm,
@@ -385,6 +390,42 @@ u64 orc_univ_resultant(u64 p, const u64 *A0, i64 a, const u64 *B0, i64 b)
  * Points x = 0, 1, 2, ... where lc_y(f)(x) lc_y(g)(x) = 0 are skipped, so at
  * the points used the univariate degrees equal the formal ones and the
  * resultant specialises.  Returns 0 on success, -1 if p has too few points. */
+/* R (N coefficients) interpolating the values vs (overwritten) at the increasing
+ * non-negative integer points xs, by Newton divided differences. */
+static void interp_int_points(u64 p, const u64 *xs, u64 *vs, i64 N, u64 *R)
+{
+    /* Newton divided differences; x_i - x_{i-j} is a positive integer at most
+     * xs[N-1], so a table of inverses of 1..xs[N-1] serves every level.
+     * Level j: c_i <- (c_i - c_{i-1}) / (x_i - x_{i-j}) for i >= j. */
+    u64 xmax = xs[N - 1];
+    u64 *inv = (u64 *)malloc(sizeof(u64) * (xmax + 2));
+    u64 *c = vs, *c2 = (u64 *)malloc(sizeof(u64) * N);
+    inv[0] = 0;
+#pragma omp parallel for schedule(static)
+    for (i64 e = 1; e <= (i64)xmax; e++) inv[e] = orc_invmod((u64)e, p);
+    for (i64 j = 1; j < N; j++) {
+#pragma omp parallel for schedule(static) if (N - j > 4096)
+        for (i64 i = j; i < N; i++)
+            c2[i] = f_mul(f_sub(c[i], c[i - 1], p), inv[xs[i] - xs[i - j]], p);
+        memcpy(c + j, c2 + j, sizeof(u64) * (N - j));
+    }
+    /* Newton form -> monomial form, from the innermost factor out:
+     * R <- R.(x - x_i) + c_i for i = N-2 .. 0, starting from R = c_{N-1}. */
+    u64 *Rn = c2;
+    memset(R, 0, sizeof(u64) * N);
+    R[0] = c[N - 1];
+    for (i64 i = N - 2, deg = 0; i >= 0; i--, deg++) {
+        u64 xi = xs[i];
+        Rn[deg + 1] = R[deg];
+#pragma omp parallel for schedule(static) if (deg > 4096)
+        for (i64 e = 1; e <= deg; e++) Rn[e] = f_sub(R[e - 1], f_mul(xi, R[e], p), p);
+        Rn[0] = f_sub(c[i], f_mul(xi, R[0], p), p);
+        memcpy(R, Rn, sizeof(u64) * (deg + 2));
+    }
+    free(c2);
+    free(inv);
+}
+
 int orc_bivariate_resultant(u64 p, int dxf, int dyf, const u64 *f, int dxg, int dyg,
                             const u64 *g, u64 *R)
 {
@@ -423,36 +464,8 @@ int orc_bivariate_resultant(u64 p, int dxf, int dyf, const u64 *f, int dxg, int 
         }
         free(fa); free(ga);
     }
-    /* Newton divided differences; x_i - x_{i-j} is a positive integer at most
-     * xs[N-1], so a table of inverses of 1..xs[N-1] serves every level.
-     * Level j: c_i <- (c_i - c_{i-1}) / (x_i - x_{i-j}) for i >= j. */
-    u64 xmax = xs[N - 1];
-    u64 *inv = (u64 *)malloc(sizeof(u64) * (xmax + 2));
-    u64 *c = vs, *c2 = (u64 *)malloc(sizeof(u64) * N);
-    inv[0] = 0;
-#pragma omp parallel for schedule(static)
-    for (i64 e = 1; e <= (i64)xmax; e++) inv[e] = orc_invmod((u64)e, p);
-    for (i64 j = 1; j < N; j++) {
-#pragma omp parallel for schedule(static) if (N - j > 4096)
-        for (i64 i = j; i < N; i++)
-            c2[i] = f_mul(f_sub(c[i], c[i - 1], p), inv[xs[i] - xs[i - j]], p);
-        memcpy(c + j, c2 + j, sizeof(u64) * (N - j));
-    }
-    /* Newton form -> monomial form, from the innermost factor out:
-     * R <- R.(x - x_i) + c_i for i = N-2 .. 0, starting from R = c_{N-1}. */
-    u64 *Rn = c2;
-    memset(R, 0, sizeof(u64) * N);
-    R[0] = c[N - 1];
-    for (i64 i = N - 2, deg = 0; i >= 0; i--, deg++) {
-        u64 xi = xs[i];
-        Rn[deg + 1] = R[deg];
-#pragma omp parallel for schedule(static) if (deg > 4096)
-        for (i64 e = 1; e <= deg; e++) Rn[e] = f_sub(R[e - 1], f_mul(xi, R[e], p), p);
-        Rn[0] = f_sub(c[i], f_mul(xi, R[0], p), p);
-        memcpy(R, Rn, sizeof(u64) * (deg + 2));
-    }
-    free(c2);
-    free(xs); free(vs); free(inv);
+    interp_int_points(p, xs, vs, N, R);
+    free(xs); free(vs);
     return 0;
 }
 
@@ -692,4 +705,121 @@ void orc_pmintbasis(u64 p, int m, int n, const u64 *E, i64 sigma, const u64 *alp
     orc_pmat_slice(p, m, m, m, P2, s2 + 1, P1, s1 + 1, 0, sigma + 1, P);
     orc_rdeg(m, m, P, sigma + 1, s, rdeg);
     free(E1); free(P1); free(t1); free(R); free(Pv); free(P2); free(t2);
+}
+
+/* det M mod p (M: n x n, row-major, destroyed) by Gaussian elimination. */
+static u64 det_destroy(u64 p, int n, u64 *M)
+{
+    u64 det = 1 % p;
+    for (int c = 0; c < n; c++) {
+        int r = -1;
+        for (int i = c; i < n; i++) if (M[(size_t)i * n + c]) { r = i; break; }
+        if (r < 0) return 0;
+        if (r != c) {
+            for (int j = 0; j < n; j++) {
+                u64 t = M[(size_t)r * n + j];
+                M[(size_t)r * n + j] = M[(size_t)c * n + j];
+                M[(size_t)c * n + j] = t;
+            }
+            det = f_neg(det, p);
+        }
+        const u64 pv = M[(size_t)c * n + c];
+        det = f_mul(det, pv, p);
+        const u64 iv = orc_invmod(pv, p);
+        for (int i = c + 1; i < n; i++) {
+            const u64 fct = f_mul(M[(size_t)i * n + c], iv, p);
+            if (!fct) continue;
+            for (int j = c; j < n; j++)
+                M[(size_t)i * n + j] = f_sub(M[(size_t)i * n + j], f_mul(fct, M[(size_t)c * n + j], p), p);
+        }
+    }
+    return det;
+}
+
+/* The specialisations a(z) = f(x, z), b(z) = g(x, z) at x. */
+static void specialise(u64 p, int dx, int dy, const u64 *f, u64 x, u64 *out)
+{
+    for (int j = 0; j <= dy; j++) {
+        u64 v = 0;
+        for (int i = dx; i >= 0; i--) v = f_add(f_mul(v, x, p), f[(i64)j * (dx + 1) + i], p);
+        out[j] = v;
+    }
+}
+
+/* Sec. 5.2, the variant of Algorithm 6 (Determinant) for Res_z(f, g): with P(x) the
+ * Sylvester matrix of f, g in z (nu = dyf + dyg), H the m x m block of P^-1 named below,
+ * delta = 2 ceil(nu / m) d + 1 values of H, an interpolant basis of [H; -I] (Algorithm 5)
+ * whose first m rows give (Q, R) with H = Q^-1 R (the fraction-reconstruction statement of
+ * Sec. 3), det Q = lambda Res (generic input), lambda fixed by one direct value of Res.
+ * P(x) is the matrix of (u, v) -> u f + v g on the unknowns (u_0 .. u_{dyg-1}, v_0 ..
+ * v_{dyf-1}) with the equations ordered by decreasing power of z; H is its top-right
+ * quadrant: H[i][j] = u_i of the solution of u f + v g = z^(m-1-j).  Columns are taken here
+ * in increasing power (H J, J the reversal), which leaves Q unchanged.
+ * Points: the smallest non-negative integers where both leading coefficients and Res are
+ * nonzero (delta of them) for H; 0 .. D for det Q.  Returns 0, or 1 when the points run out
+ * (Res identically zero, or p too small), 2 when det Q vanishes at the normalisation point
+ * (input not generic). */
+int orc_bivariate_resultant_villard(u64 p, int dxf, int dyf, const u64 *f, int dxg, int dyg, const u64 *g, int m,
+                                    u64 *R)
+{
+    const int nu = dyf + dyg, d = dxf > dxg ? dxf : dxg;
+    const i64 delta = 2 * (i64)((nu + m - 1) / m) * d + 1;
+    const i64 D = (i64)dxf * dyg + (i64)dxg * dyf, N = D + 1;
+    u64 *xs = (u64 *)malloc(sizeof(u64) * delta);
+    u64 *E = (u64 *)calloc((size_t)2 * m * m * delta, sizeof(u64));
+    u64 *S = (u64 *)malloc(sizeof(u64) * (size_t)nu * nu);
+    u64 *Si = (u64 *)malloc(sizeof(u64) * (size_t)nu * nu);
+    u64 *fa = (u64 *)malloc(sizeof(u64) * (dyf + 1));
+    u64 *ga = (u64 *)malloc(sizeof(u64) * (dyg + 1));
+    int rc = 0;
+    i64 cnt = 0;
+    u64 res0 = 0;
+    /* at most D + dxf + dxg integers are roots of Res or of a leading coefficient */
+    const u64 xlim = (u64)(delta + D + dxf + dxg + 1);
+    for (u64 x = 0; cnt < delta; x++) {
+        if (x >= p || x >= xlim) { rc = 1; break; }
+        specialise(p, dxf, dyf, f, x, fa);
+        specialise(p, dxg, dyg, g, x, ga);
+        if (!fa[dyf] || !ga[dyg]) continue;
+        /* Sylvester matrix, equation row r <-> coefficient of z^(nu-1-r) */
+        memset(S, 0, sizeof(u64) * (size_t)nu * nu);
+        for (int j = 0; j < dyg; j++)
+            for (int t = 0; t <= dyf; t++) S[(size_t)(nu - 1 - (j + t)) * nu + j] = fa[t];
+        for (int j = 0; j < dyf; j++)
+            for (int t = 0; t <= dyg; t++) S[(size_t)(nu - 1 - (j + t)) * nu + dyg + j] = ga[t];
+        if (orc_matinv(p, nu, S, Si)) continue;      /* Res(x) = 0 */
+        if (cnt == 0) res0 = orc_univ_resultant(p, fa, dyf, ga, dyg);
+        for (int i = 0; i < m; i++)
+            for (int j = 0; j < m; j++)                 /* column nu-1-j <-> z^j */
+                E[((i64)i * m + j) * delta + cnt] = Si[(size_t)i * nu + (nu - 1 - j)];
+        xs[cnt++] = x;
+    }
+    if (!rc) {
+        for (int i = 0; i < m; i++)
+            for (i64 l = 0; l < delta; l++) E[((i64)(m + i) * m + i) * delta + l] = f_neg(1 % p, p);
+        const int mm = 2 * m;
+        u64 *P = (u64 *)malloc(sizeof(u64) * (size_t)mm * mm * (delta + 1));
+        i64 *s0 = (i64 *)calloc(mm, sizeof(i64)), *rd = (i64 *)malloc(sizeof(i64) * mm);
+        orc_pmintbasis(p, mm, m, E, delta, xs, s0, 32, P, rd);
+        /* det Q at 0 .. D and at the normalisation point xs[0] */
+        u64 *ys = (u64 *)malloc(sizeof(u64) * N), *pts = (u64 *)malloc(sizeof(u64) * N);
+        u64 *Qv = (u64 *)malloc(sizeof(u64) * (size_t)m * m);
+        const i64 len = delta + 1;
+        for (i64 t = 0; t <= N; t++) {
+            const u64 x = t < N ? (u64)t : xs[0];
+            for (int i = 0; i < m; i++)
+                for (int j = 0; j < m; j++) Qv[i * m + j] = poly_eval(P + ((i64)i * mm + j) * len, len, x, p);
+            const u64 dq = det_destroy(p, m, Qv);
+            if (t < N) { ys[t] = dq; pts[t] = x; }
+            else if (!dq) rc = 2;
+            else {
+                const u64 scale = f_mul(res0, orc_invmod(dq, p), p);
+                for (i64 k = 0; k < N; k++) ys[k] = f_mul(ys[k], scale, p);
+            }
+        }
+        if (!rc) interp_int_points(p, pts, ys, N, R);
+        free(P); free(s0); free(rd); free(ys); free(pts); free(Qv);
+    }
+    free(xs); free(E); free(S); free(Si); free(fa); free(ga);
+    return rc;
 }
