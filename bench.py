@@ -45,9 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the timings of the drivers (see --extra)")
-    ap.add_argument("--extra", default="pm_basis,resultant,batched,inverse,solve,slices,intbasis,linsolve",
+    ap.add_argument("--extra", default="pm_basis,resultant,batched,inverse,solve,slices,intbasis,linsolve,villard",
                     help="comma-separated subset of pm_basis, resultant, batched, inverse, solve, slices, "
-                         "intbasis, linsolve")
+                         "intbasis, linsolve, villard")
     return ap.parse_args()
 
 
@@ -184,13 +184,14 @@ def run_reference(args, rank):
 
 # ---------------------------------------------------------------- other workloads (reported under "extra")
 def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse", "solve", "slices", "intbasis",
-                                   "linsolve"), reps=3):
+                                   "linsolve", "villard"), reps=3):
     """PM-Basis (F 32x16, order 8192, 60-bit p), 512 batched uneven products, resultants
     (deg_x = deg_y = 150, 1 prime and 16 primes), the truncated inverse of a 32x32 matrix of
     degree < 4096 mod x^4096 and the lifted series solution of A v = b mod x^32768 (same A, b of
     degree < 4096; 60-bit p), six high-order lifting slices of the same A^-1, PM-IntBasis (E 32x16
     at 8192 geometric points, 60-bit p), the lifting solver A u = f b (16x16, length 256, 60-bit
-    p): ms per call, CUDA events on the stream."""
+    p), the Villard-variant resultant (deg 150 / 150, 1 prime): ms per call, CUDA events on the
+    stream."""
     import numpy as np
     import torch
     import synth
@@ -306,11 +307,24 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"
         out["solve_stage_ms"] = {k: round(v[0], 2) for k, v in st.items() if v[1]}
         return out
 
+    def villard():
+        R = synth.resultant_c5(0, nprimes=1)
+        f1, g1 = pmat.to_device(np.stack(R["f"][:1])), pmat.to_device(np.stack(R["g"][:1]))
+        run = lambda: pmat.bivariate_resultant_villard(ctx, R["primes"][:1], f1, g1)  # noqa: E731
+        out = {"resultant_villard_150_1prime_ms": round(ev_ms(run, reps), 2)}
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
+        ctx.stage_times()
+        run()
+        st = ctx.stage_times()
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
+        out["resultant_villard_stage_ms"] = {k: round(v[0], 2) for k, v in st.items() if v[1]}
+        return out
+
     out = {}
     with torch.cuda.stream(s):
         for name, fn in (("pm_basis", pm_basis), ("resultant", resultant), ("batched", batched),
                          ("inverse", inverse), ("solve", solve), ("slices", slices), ("intbasis", intbasis),
-                         ("linsolve", linsolve)):
+                         ("linsolve", linsolve), ("villard", villard)):
             if name in which:
                 out.update(fn())
     return out

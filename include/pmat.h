@@ -17,6 +17,9 @@
  *                                 Algorithm 4 (M-IntBasis), geometric points
  *   bivariate_resultant           Sec. 5.2, resultant of bivariate
  *                                 polynomials (the direct method)
+ *   bivariate_resultant_villard   Sec. 5.2, the same by the variant of
+ *                                 Algorithm 6 (values of a block of the
+ *                                 inverse Sylvester matrix, PM-IntBasis)
  *   pmat_inv_trunc                Sec. 4, "Linear system solving": the
  *                                 truncated inverse A^-1 mod x^t by matrix
  *                                 Newton iteration
@@ -249,6 +252,23 @@ int pm_intbasis(pm_ctx *ctx, uint64_t p, int m, int n, const void *E, int64_t si
 int bivariate_resultant(pm_ctx *ctx, int nprimes, const uint64_t *primes,
                         int dxf, int dyf, const void *f, int dxg, int dyg, const void *g,
                         void *R);
+
+/* Res_y(f, g) by the variant of Algorithm 6 in Sec. 5.2 (same layouts, output
+ * and conventions as bivariate_resultant).  With P(x) the Sylvester matrix of
+ * f, g in y (nu = dyf + dyg, entries of degree <= d = max(dxf, dxg)) and H the
+ * top-right m x m block of P^-1 (equations ordered by decreasing power of y):
+ * H at delta = 2 ceil(nu / m) d + 1 points c q^l by one extended Euclidean
+ * algorithm per point; pm_intbasis on [H; -I] gives H = Q^-1 R (Sec. 3,
+ * fraction reconstruction); det Q at the D + 1 points, normalised by Res at
+ * the first point, is interpolated.  Requires generic input: every value of
+ * the normalised det Q at the delta points is checked against Res there, and
+ * a mismatch returns PM_EUNSUPPORTED.  m = 0 takes ceil(n^0.4) for the
+ * largest partial degree n (the choice of Sec. 5.2), clamped to min(dyf,
+ * dyg); m <= 16.  Requires dyf, dyg >= 1, an x-degree >= 1, every prime odd,
+ * below 2^62 and above 2 max(D + 1, delta).  Synchronises the stream. */
+int bivariate_resultant_villard(pm_ctx *ctx, int nprimes, const uint64_t *primes,
+                                int dxf, int dyf, const void *f, int dxg, int dyg,
+                                const void *g, int m, void *R);
 
 /* Truncated inverse (Sec. 4, "Linear system solving", lifting: S = A^-1 mod
  * x^t by matrix Newton iteration).  A: DEVICE n x n matrix with entries of

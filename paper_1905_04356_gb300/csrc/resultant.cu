@@ -18,11 +18,18 @@
 //     Newton-to-monomial change of basis is, by the q-binomial theorem,
 //     R_m w_m = sum_t c_{m+t} w_{m+t} (-1)^t q^C(t) / w_t.  Both are
 //     truncated products of length N on the hot path.
+// The Villard variant (bivariate_resultant_villard, Sec. 5.2 over Algorithm 6) shares the
+// evaluation, the interpolation and the product path; its own kernels are the per-point
+// extended Euclid that yields H(alpha) and Res(alpha), the per-point determinant of Q and the
+// normalisation; the interpolant basis comes from pm_intbasis.
+//
 // The points are c q^i (the substitution x -> c x, undone on the result's
 // coefficients): they must be distinct (q^l != 1 for 0 < l < N) and keep the
 // leading y-coefficients nonzero; a pair (c, q) that fails either is replaced
 // by the next candidate.  By uniqueness of the resultant the output does not
 // depend on the points.
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -287,6 +294,177 @@ __global__ void k_res_interp3(const __grid_constant__ ResPack P)
         I.R[m] = mm(mm(I.Y[P.N - 1 - m], I.winv[m], I), mpw(I.cim, (u64)m, I), I);   // undo x -> c x
 }
 
+
+// ------------------------------------------------------------------ Villard variant (Sec. 5.2)
+// Algorithm 6 with values: H(alpha) = top-right m x m block of P(alpha)^-1, P the Sylvester
+// matrix of f(alpha, z), g(alpha, z) as the map (u, v) -> u f + v g with the equations
+// ordered by decreasing power of z.  Column j (taken here in increasing power, which leaves
+// the fraction denominator unchanged) is the u-part of the solution of u f + v g = z^j:
+// u = z^j s mod g with s f + t g = 1 (extended Euclid), so H[i][j] = [z^i] (z^j s mod g).
+#define VIL_WARPS 4
+#define VIL_MMAX 16
+
+// One warp per point l < P.N: extended Euclid on (f_alpha, g_alpha) with exact division,
+// tracking the cofactor of f and Res(f_alpha, g_alpha); writes H(alpha_l) and the -I block
+// into Eip (2m x m x P.N, plain) and Res into resv[l] (plain); Res = 0 sets flag bit 4.
+__global__ void __launch_bounds__(32 * VIL_WARPS) k_vil_xgcd(const __grid_constant__ ResPack P, int dmax, int m,
+                                                            u64 *Eip, u64 *resv)
+{
+    extern __shared__ u64 smv[];
+    const ResInst &I = P.in[0];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int pt = blockIdx.x * VIL_WARPS + wid;
+    if (pt >= P.N) return;
+    const int W = dmax + 2;
+    u64 *A = smv + (size_t)wid * 5 * W, *B = A + W, *sA = B + W, *sB = sA + W, *G = sB + W;
+    const u64 *val = I.Vt + (i64)pt * P.J;
+    for (int c = lane; c < W; c += 32) {
+        A[c] = c <= P.dyf ? val[c] : 0;
+        B[c] = c <= P.dyg ? val[P.dyf + 1 + c] : 0;
+        G[c] = B[c];
+        sA[c] = c == 0 ? I.one : 0;
+        sB[c] = 0;
+    }
+    __syncwarp();
+    int a = P.dyf, b = P.dyg, dsA = 0, dsB = -1;
+    u64 acc = I.one;
+    bool neg = false, zero = false;
+    while (b > 0) {
+        const u64 inv = mpw(B[b], I.p - 2, I);
+        int da = a;
+        while (da >= b) {
+            const u64 cq = mm(A[da], inv, I);
+            const int sh = da - b;
+            __syncwarp();
+            for (int i = lane; i < b; i += 32) A[sh + i] = sub64(A[sh + i], mm(cq, B[i], I), I.p);
+            for (int i = lane; i <= dsB && sh + i < W; i += 32) sA[sh + i] = sub64(sA[sh + i], mm(cq, sB[i], I), I.p);
+            __syncwarp();
+            if (lane == 0) A[da] = 0;
+            __syncwarp();
+            da = da > 0 ? warp_deg(A, da - 1) : -1;
+        }
+        const int dsR = a >= b ? (dsA > a - b + dsB ? dsA : a - b + dsB) : dsA;
+        const int r = da;
+        if (r < 0) { zero = true; break; }
+        neg ^= (a & b & 1);
+        acc = mm(acc, mpw(B[b], (u64)(a - r), I), I);
+        u64 *t = A; A = B; B = t;                  // (A, B) <- (B, R), cofactors alike
+        t = sA; sA = sB; sB = t;
+        a = b; b = r;
+        dsA = dsB; dsB = dsR;
+        __syncwarp();
+    }
+    u64 *H = Eip;
+    const i64 sig = P.N;
+    if (zero) {
+        for (int x = lane; x < 2 * m * m; x += 32) H[(i64)x * sig + pt] = 0;
+        if (lane == 0) { resv[pt] = 0; atomicOr(P.flag, 4); }
+        return;
+    }
+    // Res = (-1)^.. acc B0^a; s = sB / B0
+    const u64 b0 = B[0];
+    if (lane == 0) {
+        u64 res = mm(mm(acc, mpw(b0, (u64)a, I), I), 1, I);
+        if (neg && res) res = I.p - res;
+        resv[pt] = res;
+    }
+    const u64 binv = mpw(b0, I.p - 2, I);
+    const int n2 = P.dyg;
+    u64 *u = sA, *tmp = A;                         // sA and A are free now
+    for (int c = lane; c < W; c += 32) u[c] = c < n2 ? mm(sB[c], binv, I) : 0;
+    __syncwarp();
+    const u64 ginv = mpw(G[n2], I.p - 2, I);
+    for (int j = 0; j < m; j++) {
+        for (int i = lane; i < m; i += 32) H[((i64)i * m + j) * sig + pt] = mm(u[i], 1, I);
+        if (j + 1 == m) break;
+        const u64 t = mm(u[n2 - 1], ginv, I);       // u <- z u mod g
+        for (int i = lane; i < n2; i += 32) tmp[i] = sub64(i ? u[i - 1] : 0, mm(t, G[i], I), I.p);
+        __syncwarp();
+        for (int i = lane; i < n2; i += 32) u[i] = tmp[i];
+        __syncwarp();
+    }
+    for (int x = lane; x < m * m; x += 32) {
+        const int i = x / m, j = x % m;
+        H[((i64)(m + i) * m + j) * sig + pt] = i == j ? I.p - 1 : 0;
+    }
+}
+
+// ue[e] = c^e q^-C(e) (Montgomery), e < LQ
+__global__ void k_vil_uvec(const __grid_constant__ ResPack P, u64 *ue, int LQ)
+{
+    const ResInst &I = P.in[0];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < LQ; e += gridDim.x * blockDim.x)
+        ue[e] = mm(mpw(I.cm, (u64)e, I), I.hinv[e], I);
+}
+
+// Ua2[r][LQ-1-e] = Q_r[e] ue[e] (plain), r = i m + j for the top-left m x m block of the
+// 2m x 2m basis Pb (entry stride sP)
+__global__ void k_vil_prep_q(const __grid_constant__ ResPack P, const u64 *Pb, i64 sP, int m, const u64 *ue, u64 *Ua2,
+                             int LQ)
+{
+    const ResInst &I = P.in[0];
+    const i64 total = (i64)m * m * LQ;
+    for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < total; x += (i64)gridDim.x * blockDim.x) {
+        const int e = (int)(x % LQ), r = (int)(x / LQ), i = r / m, j = r % m;
+        Ua2[(i64)r * LQ + (LQ - 1 - e)] = mm(Pb[((i64)i * 2 * m + j) * sP + e], ue[e], I);
+    }
+}
+
+// v[l] = det Q(c q^l) (plain), l < P.N: Q(c q^l)[i][j] = q^-C(l) S2[i m + j][l]
+__global__ void k_vil_det(const __grid_constant__ ResPack P, const u64 *S2, int m, u64 *v)
+{
+    const ResInst &I = P.in[0];
+    u64 M[VIL_MMAX * VIL_MMAX];
+    for (i64 l = blockIdx.x * (i64)blockDim.x + threadIdx.x; l < P.N; l += (i64)gridDim.x * blockDim.x) {
+        const u64 hl = mm(I.hinv[l], I.r2, I);     // q^-C(l) R^2: plain x this = Montgomery form
+        for (int x = 0; x < m * m; x++) M[x] = mm(S2[(i64)x * P.N + l], hl, I);
+        u64 det = I.one;
+        bool neg = false;
+        for (int c = 0; c < m && det; c++) {
+            int r = c;
+            while (r < m && M[r * m + c] == 0) r++;
+            if (r == m) { det = 0; break; }
+            if (r != c) {
+                for (int j = c; j < m; j++) { const u64 t = M[r * m + j]; M[r * m + j] = M[c * m + j]; M[c * m + j] = t; }
+                neg = !neg;
+            }
+            const u64 pv = M[c * m + c];
+            det = mm(det, pv, I);
+            const u64 pinv = mpw(pv, I.p - 2, I);
+            for (int r2 = c + 1; r2 < m; r2++) {
+                const u64 fct = mm(M[r2 * m + c], pinv, I);
+                if (!fct) continue;
+                for (int j = c + 1; j < m; j++) M[r2 * m + j] = sub64(M[r2 * m + j], mm(fct, M[c * m + j], I), I.p);
+            }
+        }
+        u64 d = mm(det, 1, I);
+        if (neg && d) d = I.p - d;
+        v[l] = d;
+    }
+}
+
+// sc[0] = Res(alpha_0) / det Q(alpha_0) (Montgomery); det Q(alpha_0) = 0 sets flag bit 16
+__global__ void k_vil_norm(const __grid_constant__ ResPack P, const u64 *resv, const u64 *v, u64 *sc)
+{
+    const ResInst &I = P.in[0];
+    if (threadIdx.x || blockIdx.x) return;
+    if (v[0] == 0) { atomicOr(P.flag, 16); sc[0] = 0; return; }
+    sc[0] = mm(mm(resv[0], I.r2, I), mpw(mm(v[0], I.r2, I), I.p - 2, I), I);
+}
+
+// v[l] <- v[l] sc; the first nchk values must equal the directly computed resultants (else
+// flag bit 8: det Q is not a constant multiple of Res, the input is not generic)
+__global__ void k_vil_scale(const __grid_constant__ ResPack P, const u64 *resv, const u64 *sc, u64 *v, int nchk)
+{
+    const ResInst &I = P.in[0];
+    const u64 c = sc[0];
+    for (i64 l = blockIdx.x * (i64)blockDim.x + threadIdx.x; l < P.N; l += (i64)gridDim.x * blockDim.x) {
+        const u64 x = mm(v[l], c, I);
+        v[l] = x;
+        if (l < nchk && x != resv[l]) atomicOr(P.flag, 8);
+    }
+}
+
 // ------------------------------------------------------------------ host driver
 static uint64_t mont_pn(uint64_t p)
 {
@@ -441,6 +619,200 @@ extern "C" int bivariate_resultant(pm_ctx *ctx, int nprimes, const uint64_t *pri
                 alpha[0] += 2;
                 scale[0] += 1;
             }
+        }
+    }
+    return PM_OK;
+}
+
+// ------------------------------------------------------------------ Villard variant, host
+// One prime, points c q^l.  flag bits: 1 points not distinct, 2 a leading coefficient
+// vanishes at an H point, 4 Res vanishes at an H point, 16 det Q vanishes at the first
+// point (all four: try the next (c, q)); 8 det Q is not a multiple of Res (input not generic).
+static int vil_one(pm_ctx *ctx, uint64_t p, uint64_t q, uint64_t c, int dxf, int dyf, const u64 *f, int dxg, int dyg,
+                   const u64 *g, int m, u64 *R, int *h_flag)
+{
+    const int nu = dyf + dyg, d = dxf > dxg ? dxf : dxg, E = d + 1, J = dyf + dyg + 2, dmax = dyf > dyg ? dyf : dyg;
+    const int64_t D = (int64_t)dxf * dyg + (int64_t)dxg * dyf, N = D + 1;
+    const int64_t delta = 2 * (int64_t)((nu + m - 1) / m) * d + 1;
+    const int64_t NP = N > delta ? N : delta;                   // points covered by the tables
+    const int64_t NE = NP + (E > delta + 1 ? E : delta + 1);    // chirp length bound
+    const int64_t m2 = 2 * m;
+    // buffers (stream-ordered; pm_intbasis below owns the driver arena)
+    const size_t words = 4 * (size_t)NE + (size_t)J * E + 2 * (size_t)J * delta + (size_t)m2 * m * delta + delta +
+                         (size_t)m2 * m2 * (delta + 1) + (size_t)m * m * (delta + 1) + (delta + 1) +
+                         (size_t)m * m * N + 9 * (size_t)N + 64;
+    char *buf = nullptr;
+    if (cudaMallocAsync((void **)&buf, words * 8 + 32 * 256, ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return pm_fail(ctx, PM_ENOMEM, "Villard resultant workspace allocation failed");
+    }
+    size_t used = 0;
+    auto A = [&](size_t n) { u64 *r = (u64 *)(buf + used); used += (n * 8 + 255) & ~size_t(255); return r; };
+    ResPack pk;
+    memset(&pk, 0, sizeof(pk));
+    pk.count = 1; pk.dxf = dxf; pk.dyf = dyf; pk.dxg = dxg; pk.dyg = dyg;
+    pk.E = E; pk.J = J;
+    ResInst &I = pk.in[0];
+    I.p = p;
+    I.pn = mont_pn(p);
+    I.one = (uint64_t)(((unsigned __int128)1 << 64) % p);
+    I.r2 = (uint64_t)((unsigned __int128)I.one * I.one % p);
+    I.qm = (uint64_t)((unsigned __int128)(q % p) * I.one % p);
+    I.qim = (uint64_t)((unsigned __int128)host_powmod(q % p, p - 2, p) * I.one % p);
+    I.cm = (uint64_t)((unsigned __int128)(c % p) * I.one % p);
+    I.cim = (uint64_t)((unsigned __int128)host_powmod(c % p, p - 2, p) * I.one % p);
+    I.f = f; I.g = g; I.R = R;
+    I.qp = A(NE); I.h = A(NE); I.hinv = A(NE); I.Hb = A(NE);
+    I.Ua = A((size_t)J * E); I.S = A((size_t)J * delta); I.Vt = A((size_t)J * delta);
+    u64 *Eip = A((size_t)m2 * m * delta), *resv = A(delta), *Pb = A((size_t)m2 * m2 * (delta + 1));
+    u64 *Ua2 = A((size_t)m * m * (delta + 1)), *ue = A(delta + 1), *S2 = A((size_t)m * m * N);
+    I.v = A(N); I.w = A(N); I.winv = A(N); I.Va = A(N); I.Eb = A(N); I.Cp = A(N); I.Ur = A(N); I.Y = A(N);
+    u64 *sc = A(8);
+    pk.flag = (int *)A(8);
+    int rc = PM_OK;
+    do {
+        if ((rc = pm_cuda(ctx, cudaMemsetAsync(pk.flag, 0, sizeof(int), ctx->stream), "flag"))) break;
+        // chirp tables for every length below, distinctness of the NP points
+        ResPack pt = pk;
+        pt.N = (int)NP; pt.NE = (int)NE;
+        int tok = stage_begin(ctx, PM_STAGE_OTHER);
+        k_res_powers<<<(int)((NE + 255) / 256 < 1024 ? (NE + 255) / 256 : 1024), 256, 0, ctx->stream>>>(pt);
+        // 1. f, g at the delta points (chirp middle product), point-major Montgomery values
+        ResPack pe = pk;
+        pe.N = (int)delta; pe.NE = (int)(delta + E - 1);
+        k_res_prep_eval<<<(J * E + 255) / 256, 256, 0, ctx->stream>>>(pe);
+        ctx->launches += 2;
+        stage_end(ctx, tok);
+        if ((rc = pm_cuda(ctx, cudaGetLastError(), "Villard prep"))) break;
+        {
+            ProdReq r1;
+            r1.p = p; r1.w = 8; r1.m = J; r1.n = 1; r1.k = 1;
+            r1.A = I.Ua; r1.dA = E; r1.sA = E; r1.B = I.Hb; r1.dB = delta + E - 1; r1.sB = delta + E - 1;
+            r1.off = E - 1; r1.len = delta; r1.C = I.S; r1.sC = delta;
+            r1.lg = ceil_log2((int64_t)E - 1 + delta);
+            if (r1.lg < 4) r1.lg = 4;
+            if ((rc = prod_batch(ctx, &r1, 1))) break;
+        }
+        tok = stage_begin(ctx, PM_STAGE_OTHER);
+        k_res_eval_finish<<<1024, 256, 0, ctx->stream>>>(pe);
+        // 2. H(alpha_l) and Res(alpha_l) by the extended Euclidean algorithm, one warp per point
+        const size_t smv = (size_t)VIL_WARPS * 5 * (dmax + 2) * 8;
+        if (smv > 48 * 1024) cudaFuncSetAttribute(k_vil_xgcd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv);
+        k_vil_xgcd<<<(int)((delta + VIL_WARPS - 1) / VIL_WARPS), 32 * VIL_WARPS, smv, ctx->stream>>>(pe, dmax, m, Eip,
+                                                                                                     resv);
+        ctx->launches += 2;
+        stage_end(ctx, tok);
+        if ((rc = pm_cuda(ctx, cudaGetLastError(), "Villard Euclid"))) break;
+        if ((rc = pm_cuda(ctx, cudaMemcpyAsync(h_flag, pk.flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+                          "flag")))
+            break;
+        if ((rc = pm_cuda(ctx, cudaStreamSynchronize(ctx->stream), "flag sync"))) break;
+        if (*h_flag) break;
+        // 3. interpolant basis of [H; -I] at the delta points (Algorithm 5); Q = its top-left block
+        std::vector<int64_t> s0(m2, 0), rdeg(m2, 0);
+        if ((rc = pm_intbasis(ctx, p, (int)m2, m, Eip, delta, c % p, q % p, s0.data(), Pb, rdeg.data()))) break;
+        int64_t LQ = 1;
+        for (int i = 0; i < m; i++) LQ = rdeg[i] + 1 > LQ ? rdeg[i] + 1 : LQ;
+        if (LQ > delta + 1) LQ = delta + 1;
+        // 4. det Q at the N points c q^l: chirp evaluation of the m^2 entries, a determinant per point
+        ResPack pq = pk;
+        pq.N = (int)N;
+        tok = stage_begin(ctx, PM_STAGE_OTHER);
+        k_vil_uvec<<<(int)((LQ + 255) / 256), 256, 0, ctx->stream>>>(pq, ue, (int)LQ);
+        k_vil_prep_q<<<(int)(((int64_t)m * m * LQ + 255) / 256 < 4096 ? ((int64_t)m * m * LQ + 255) / 256 : 4096), 256,
+                       0, ctx->stream>>>(pq, Pb, delta + 1, m, ue, Ua2, (int)LQ);
+        ctx->launches += 2;
+        stage_end(ctx, tok);
+        if ((rc = pm_cuda(ctx, cudaGetLastError(), "Villard Q prep"))) break;
+        {
+            ProdReq r2;
+            r2.p = p; r2.w = 8; r2.m = m * m; r2.n = 1; r2.k = 1;
+            r2.A = Ua2; r2.dA = LQ; r2.sA = LQ; r2.B = I.Hb; r2.dB = N + LQ - 1; r2.sB = N + LQ - 1;
+            r2.off = LQ - 1; r2.len = N; r2.C = S2; r2.sC = N;
+            r2.lg = ceil_log2(LQ - 1 + N);
+            if (r2.lg < 4) r2.lg = 4;
+            if ((rc = prod_batch(ctx, &r2, 1))) break;
+        }
+        tok = stage_begin(ctx, PM_STAGE_OTHER);
+        k_vil_det<<<(int)((N + 127) / 128), 128, 0, ctx->stream>>>(pq, S2, m, I.v);
+        k_vil_norm<<<1, 32, 0, ctx->stream>>>(pq, resv, I.v, sc);
+        k_vil_scale<<<(int)((N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024), 256, 0, ctx->stream>>>(
+            pq, resv, sc, I.v, (int)(delta < N ? delta : N));
+        ctx->launches += 3;
+        stage_end(ctx, tok);
+        if ((rc = pm_cuda(ctx, cudaGetLastError(), "Villard det"))) break;
+        if ((rc = pm_cuda(ctx, cudaMemcpyAsync(h_flag, pk.flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+                          "flag")))
+            break;
+        if ((rc = pm_cuda(ctx, cudaStreamSynchronize(ctx->stream), "flag sync"))) break;
+        if (*h_flag) break;
+        // 5. interpolation at the N points (as in the direct method)
+        tok = stage_begin(ctx, PM_STAGE_OTHER);
+        k_res_wscan<<<1, 1024, 0, ctx->stream>>>(pq);
+        k_res_interp1<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(pq);
+        ctx->launches += 2;
+        stage_end(ctx, tok);
+        if ((rc = pm_cuda(ctx, cudaGetLastError(), "Villard interp"))) break;
+        ProdReq ri;
+        ri.p = p; ri.w = 8; ri.m = 1; ri.n = 1; ri.k = 1;
+        ri.dA = N; ri.sA = N; ri.dB = N; ri.sB = N; ri.off = 0; ri.len = N; ri.sC = N;
+        ri.lg = ceil_log2(2 * N - 1);
+        if (ri.lg < 4) ri.lg = 4;
+        ri.A = I.Va; ri.B = I.Eb; ri.C = I.Cp;
+        if ((rc = prod_batch(ctx, &ri, 1))) break;
+        tok = stage_begin(ctx, PM_STAGE_OTHER);
+        k_res_interp2<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(pq);
+        ctx->launches++;
+        stage_end(ctx, tok);
+        ri.A = I.Ur; ri.B = I.Eb; ri.C = I.Y;
+        if ((rc = prod_batch(ctx, &ri, 1))) break;
+        tok = stage_begin(ctx, PM_STAGE_OTHER);
+        k_res_interp3<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(pq);
+        ctx->launches++;
+        stage_end(ctx, tok);
+        rc = pm_cuda(ctx, cudaGetLastError(), "Villard interp");
+    } while (0);
+    cudaFreeAsync(buf, ctx->stream);
+    return rc;
+}
+
+extern "C" int bivariate_resultant_villard(pm_ctx *ctx, int nprimes, const uint64_t *primes, int dxf, int dyf,
+                                           const void *f, int dxg, int dyg, const void *g, int m, void *R)
+{
+    if (!ctx) return PM_EINVAL;
+    if (nprimes < 1 || !primes || !f || !g || !R) return pm_fail(ctx, PM_EINVAL, "bad arguments");
+    if (dxf < 0 || dxg < 0 || dyf < 1 || dyg < 1) return pm_fail(ctx, PM_EINVAL, "need dyf, dyg >= 1 and dxf, dxg >= 0");
+    if (dxf == 0 && dxg == 0) return pm_fail(ctx, PM_EINVAL, "need an x-degree >= 1");
+    if (dyf > 2047 || dyg > 2047) return pm_fail(ctx, PM_EUNSUPPORTED, "y-degree above 2047");
+    if (m <= 0) {   // ceil(n^0.4) for the partial degree n (Sec. 5.2)
+        const int n = std::max(std::max(dxf, dxg), std::max(dyf, dyg));
+        m = 1;
+        while (std::pow((double)m, 2.5) < (double)n) m++;
+    }
+    m = std::min(m, std::min(dyf, dyg));
+    if (m > VIL_MMAX) return pm_fail(ctx, PM_EUNSUPPORTED, "block size m above 16");
+    const int nu = dyf + dyg, d = std::max(dxf, dxg);
+    const int64_t D = (int64_t)dxf * dyg + (int64_t)dxg * dyf, N = D + 1;
+    const int64_t delta = 2 * (int64_t)((nu + m - 1) / m) * d + 1;
+    const int64_t NP = std::max(N, delta);
+    if (2 * N - 1 > (1 << PM_MAX_LOG2L) || NP + delta + d + 1 > (1 << PM_MAX_LOG2L) || delta + 1 > (1 << PM_MAX_LOG2L))
+        return pm_fail(ctx, PM_EINVAL, "resultant degree too large for the transforms");
+    for (int i = 0; i < nprimes; i++)
+        if (!(primes[i] & 1) || primes[i] < 3 || primes[i] >= (1ull << 62) || primes[i] <= (uint64_t)(2 * NP))
+            return pm_fail(ctx, PM_EINVAL, "each prime must be odd, below 2^62 and above twice the point count");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return pm_fail(ctx, PM_ECUDA, "cudaSetDevice failed");
+    const size_t nf = (size_t)(dyf + 1) * (dxf + 1), ng = (size_t)(dyg + 1) * (dxg + 1);
+    for (int i = 0; i < nprimes; i++) {
+        uint64_t q = 3, c = 1;
+        for (int attempt = 0;; attempt++) {
+            if (attempt >= 64) return pm_fail(ctx, PM_EUNSUPPORTED, "no usable geometric progression found");
+            int flag = 0;
+            CKI(vil_one(ctx, primes[i], q, c, dxf, dyf, (const u64 *)f + i * nf, dxg, dyg, (const u64 *)g + i * ng, m,
+                        (u64 *)R + (size_t)i * N, &flag));
+            if (!flag) break;
+            if (flag & 8) return pm_fail(ctx, PM_EUNSUPPORTED, "input not generic for the Villard variant");
+            q += 2;
+            c += 1;
         }
     }
     return PM_OK;

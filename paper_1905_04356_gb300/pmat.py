@@ -71,6 +71,7 @@ def lib():
             "pm_basis": ([P, u64, i32, i32, P, i64, i64, P, P, P], i32),
             "pm_intbasis": ([P, u64, i32, i32, P, i64, u64, u64, P, P, P], i32),
             "pmat_solve": ([P, u64, i32, P, i64, P, i64, P, P, P], i32),
+            "bivariate_resultant_villard": ([P, i32, P, i32, i32, P, i32, i32, P, i32, P], i32),
             "bivariate_resultant": ([P, i32, P, i32, i32, P, i32, i32, P, P], i32),
             "pmat_inv_trunc": ([P, u64, i32, i32, P, i64, i64, P], i32),
             "pmat_solve_series": ([P, u64, i32, i32, P, i64, P, i64, i64, P], i32),
@@ -351,6 +352,25 @@ def pm_intbasis(ctx: Context, p: int, E: torch.Tensor, c: int, q: int, shift, ou
     ctx._ck(lib().pm_intbasis(ctx.h, p, m, n, E.data_ptr(), sigma, c, q, s.ctypes.data, P.data_ptr(),
                               rd.ctypes.data))
     return P, rd
+
+
+def bivariate_resultant_villard(ctx: Context, primes, f: torch.Tensor, g: torch.Tensor, m: int = 0,
+                                out=None) -> torch.Tensor:
+    """Res_y(f, g) modulo each prime by the variant of Algorithm 6 (Sec. 5.2); same layout as
+    bivariate_resultant; m = 0 takes the default block size."""
+    f, g = _dev(f), _dev(g)
+    if f.dim() == 2:
+        f, g = f.unsqueeze(0), g.unsqueeze(0)
+    npr, dyf1, dxf1 = f.shape
+    _, dyg1, dxg1 = g.shape
+    pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint64).reshape(-1))
+    if len(pr) != npr:
+        raise ValueError("one prime per instance")
+    D = (dxf1 - 1) * (dyg1 - 1) + (dxg1 - 1) * (dyf1 - 1)
+    R = _out(out, (npr, D + 1), f)
+    ctx._ck(lib().bivariate_resultant_villard(ctx.h, npr, pr.ctypes.data, dxf1 - 1, dyf1 - 1, f.data_ptr(),
+                                              dxg1 - 1, dyg1 - 1, g.data_ptr(), m, R.data_ptr()))
+    return R
 
 
 def bivariate_resultant(ctx: Context, primes, f: torch.Tensor, g: torch.Tensor, out=None) -> torch.Tensor:
