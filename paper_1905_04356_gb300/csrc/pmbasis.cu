@@ -235,12 +235,87 @@ __device__ bool gj_dispatch(const LeafArgs &A, const u64 *R, ElimSm &E, int gn)
 }
 
 // Algorithm 1 on the residual R (m x n, Montgomery) with shift t: rows visited in
-// increasing (t_i, i) order.  Output: ind[i] = 1 for rows that become x e_i; for the
+// increasing (t_i, i) order (rows with a zero residual may be moved last: same output).  Output: ind[i] = 1 for rows that become x e_i; for the
 // other rows j, the scaled relation kap_j R_j = -sum_i W[j][i] R_i (W stored
 // negated), i.e. the row of Q is kap_j e_j + sum_i W[j][i] e_i.  Called by the
 // elimination group: warps 0 .. gn/32 - 1 of the block (tid < gn, gn a multiple of 32
 // and >= 256), synchronised by named barrier 2, with which it ends.
 #define EBAR() asm volatile("bar.sync 2, %0;" ::"r"(nth))
+// Fast path of Algorithm 1: Gauss-Jordan on [R_I^T | R_D^T] (n x m), I = the first n rows of
+// E.ord; false (nothing written but scratch) when those rows are dependent.
+__device__ __forceinline__ bool mbasis1_fast(const LeafArgs &A, const u64 *R, ElimSm &E, int nth)
+{
+    const int m = A.m, n = A.n, tid = threadIdx.x;
+    const u64 p = A.p;
+    // the independent rows are known before the elimination: list them in index order
+    for (int pos = tid; pos < m; pos += nth) E.ind[E.ord[pos]] = pos < n;
+    EBAR();
+    if (tid < 32) {
+        int base = 0;
+        for (int i0 = 0; i0 < m; i0 += 32) {
+            const int i = i0 + tid;
+            const bool f = i < m && E.ind[i];
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (f) {
+                const int b = base + __popc(bal & ((1u << tid) - 1u));
+                E.ilist[b] = i;
+                E.ipos[i] = b;
+            }
+            base += __popc(bal);
+        }
+        if (tid == 0) E.misc[4] = base;
+    }
+    const bool ok = gj_dispatch(A, R, E, nth);
+    if (ok) {
+        // E.fac[s] = D / d_s and E.dpr[n] = D come from the elimination; the relation of
+        // dependent row j on independent row i = ord[s] goes to Wc[j][ipos[i]]
+        for (int x = tid; x < (m - n) * n; x += nth) {
+            const int jp = n + x / n, s2 = x % n;
+            const int j = E.ord[jp], i = E.ord[s2];
+            const u64 w = mont_mul(E.M[E.perm[s2] * m + jp], E.fac[s2], p, A.pn);
+            E.Wc[j * n + E.ipos[i]] = w ? p - w : 0;
+        }
+        for (int pos = n + tid; pos < m; pos += nth) E.kap[E.ord[pos]] = E.dpr[n];
+    }
+    EBAR();
+    return ok;
+}
+
+// Rows whose residual is zero, moved to the end of E.ord for a second try of the fast path.
+// Such rows are dependent with the trivial relation (their row of Q is e_j) wherever they
+// come, and change neither the independent set nor the other rows' relations, so the output
+// is still Algorithm 1's.  This keeps the fast path once a row has become an approximant of
+// every order (the solution row of a reconstruction).  False (order unchanged) when no row is
+// zero.
+__device__ __forceinline__ bool zero_rows_last(const LeafArgs &A, const u64 *R, const i64 *t, ElimSm &E, int nth)
+{
+    const int m = A.m, n = A.n, tid = threadIdx.x, lane = tid & 31;
+    // one warp per row, lanes over the columns, one vote; flags in E.ipos (m ints, rewritten
+    // by the fast path's listing only after the reordering has read them)
+    for (int i = tid >> 5; i < m; i += nth >> 5) {
+        bool nz = false;
+        for (int c = lane; c < n; c += 32) nz |= R[i * n + c] != 0;
+        nz = __any_sync(0xffffffffu, nz);
+        if (lane == 0) E.ipos[i] = !nz;
+    }
+    EBAR();
+    int nzero = 0;
+    for (int j = 0; j < m; j++) nzero += E.ipos[j];
+    if (nzero == 0) return false;        // uniform: every thread read the same flags
+    for (int i = tid; i < m; i += nth) {
+        int r = 0;
+        const i64 ti = t[i];
+        const int zi = E.ipos[i];
+        for (int j = 0; j < m; j++) {
+            const int zj = E.ipos[j];
+            r += (zj < zi) || (zj == zi && ((t[j] < ti) || (t[j] == ti && j < i)));
+        }
+        E.ord[r] = i;
+    }
+    EBAR();
+    return true;
+}
+
 __device__ void mbasis1_scaled(const LeafArgs &A, const u64 *R, const i64 *t, ElimSm &E, int gn)
 {
     const int m = A.m, n = A.n, tid = threadIdx.x, nth = gn;
@@ -253,41 +328,9 @@ __device__ void mbasis1_scaled(const LeafArgs &A, const u64 *R, const i64 *t, El
         E.kap[i] = A.one;
     }
     EBAR();
-    bool ok = false;
     if (m > n) {
-        // fast path: Gauss-Jordan on [R_I^T | R_D^T] (n x m), I = the first n rows in order.
-        // The independent rows are known before the elimination: list them in index order.
-        for (int pos = tid; pos < m; pos += nth) E.ind[E.ord[pos]] = pos < n;
-        EBAR();
-        if (tid < 32) {
-            int base = 0;
-            for (int i0 = 0; i0 < m; i0 += 32) {
-                const int i = i0 + tid;
-                const bool f = i < m && E.ind[i];
-                const unsigned bal = __ballot_sync(0xffffffffu, f);
-                if (f) {
-                    const int b = base + __popc(bal & ((1u << tid) - 1u));
-                    E.ilist[b] = i;
-                    E.ipos[i] = b;
-                }
-                base += __popc(bal);
-            }
-            if (tid == 0) E.misc[4] = base;
-        }
-        ok = gj_dispatch(A, R, E, nth);
-        if (ok) {
-            // E.fac[s] = D / d_s and E.dpr[n] = D come from the elimination; the relation of
-            // dependent row j on independent row i = ord[s] goes to Wc[j][ipos[i]]
-            for (int x = tid; x < (m - n) * n; x += nth) {
-                const int jp = n + x / n, s2 = x % n;
-                const int j = E.ord[jp], i = E.ord[s2];
-                const u64 w = mont_mul(E.M[E.perm[s2] * m + jp], E.fac[s2], p, A.pn);
-                E.Wc[j * n + E.ipos[i]] = w ? p - w : 0;
-            }
-            for (int pos = n + tid; pos < m; pos += nth) E.kap[E.ord[pos]] = E.dpr[n];
-        }
-        EBAR();
-        if (ok) return;
+        if (mbasis1_fast(A, R, E, nth)) return;
+        if (zero_rows_last(A, R, t, E, nth) && mbasis1_fast(A, R, E, nth)) return;
     }
     {
         // general path: rows in order, fraction-free common-denominator elimination
