@@ -411,6 +411,15 @@ def main():
         st = ctx.stage_times()
         ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
 
+        # ---- the same step captured once in a CUDA graph and replayed (L2 flushed between
+        #      replays, outside the events)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            pmat.pmat_mul(ctx, p, A, B, out=Cd)
+        for _ in range(3):
+            graph.replay()
+        ts_graph = timed(lambda i: graph.replay(), args.steps)
+
         # ---- same sizes modulo 998244353 (one NTT prime, uint32)
         for _ in range(3):
             pmat.pmat_mul(ctx, W998["p"], A2, B2, out=C2)
@@ -472,6 +481,7 @@ def main():
             "step_compulsory_bytes": compulsory,
             "step_compulsory_GBps": round(compulsory / (ms_step * 1e-3) / 1e9, 1),
             "step_compulsory_frac_hbm": round(compulsory / (ms_step * 1e-3) / 1e9 / peak, 4),
+            "graph_replay_ms_per_step": round(sum(ts_graph) / len(ts_graph), 4),
             "c2_p998_ms": round(sum(ts998) / len(ts998), 4),
             "wall_s_timed_region": round(t_wall, 3),
             "paper_context": PAPER_CONTEXT,
