@@ -420,6 +420,24 @@ def main():
             graph.replay()
         ts_graph = timed(lambda i: graph.replay(), args.steps)
 
+        # ---- the same step with the tensor-core pointwise form (8-bit limbs in bf16 on tcgen05,
+        #      fp32 accumulation in tensor memory, limb recombination on the CUDA cores): its time,
+        #      its pointwise stage, and exact equality with the CUDA-core output
+        Ctc = torch.empty_like(Cd)
+        ctx.set_option(pmat.PM_OPT_POINTWISE, 2)
+        for _ in range(3):
+            pmat.pmat_mul(ctx, p, A, B, out=Ctc)
+        ts_tc = timed(lambda i: pmat.pmat_mul(ctx, p, A, B, out=Ctc), args.steps)
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
+        ctx.stage_times()
+        timed(lambda i: pmat.pmat_mul(ctx, p, A, B, out=Ctc), 5)
+        st_tc = ctx.stage_times()
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
+        ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
+        pmat.pmat_mul(ctx, p, A, B, out=Cd)
+        torch.cuda.synchronize()
+        tc_equal = bool(torch.equal(Ctc, Cd))
+
         # ---- same sizes modulo 998244353 (one NTT prime, uint32)
         for _ in range(3):
             pmat.pmat_mul(ctx, W998["p"], A2, B2, out=C2)
@@ -463,6 +481,19 @@ def main():
             "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic_for(*kname[dom]),
             "algorithmic_bytes_per_launch": alg[dom], "launch_ms": round(dom_ms, 4),
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback"}
+    def tc_report(ts_tc, st_tc, st_cc, pk):
+        """The tensor-core pointwise form on the same step: its pointwise stage against the
+        CUDA-core one, and its tensor throughput (limb flops) against the measured bf16 peak."""
+        tc_pw = st_tc["pointwise"][0] / max(1, st_tc["pointwise"][1])
+        cc_pw = st_cc["pointwise"][0] / max(1, st_cc["pointwise"][1])
+        limb_flops = K * L * (4 * m) * n * (4 * k) * 2            # per point: (4m x n) . (n x 4k)
+        bf16 = pk["bf16_tflops"] if pk else 1900.0
+        tf = limb_flops / (tc_pw * 1e-3) / 1e12
+        return {"step_ms": round(sum(ts_tc) / len(ts_tc), 4), "pointwise_ms": round(tc_pw, 4),
+                "cuda_core_pointwise_ms": round(cc_pw, 4), "outputs_equal": tc_equal,
+                "limb_tflops": round(tf, 1), "bf16_peak_tflops": bf16, "tensor_frac": round(tf / bf16, 4),
+                "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops)" if pk else "fallback"}
+
     compulsory = (eA * dA + eB * dB) * 8 + eC * lenC * 8
     value = job_value(ms_step, world)
     out = {
@@ -482,6 +513,7 @@ def main():
             "step_compulsory_GBps": round(compulsory / (ms_step * 1e-3) / 1e9, 1),
             "step_compulsory_frac_hbm": round(compulsory / (ms_step * 1e-3) / 1e9 / peak, 4),
             "graph_replay_ms_per_step": round(sum(ts_graph) / len(ts_graph), 4),
+            "tensor_core_vs_cuda_core": tc_report(ts_tc, st_tc, stages, pk),
             "c2_p998_ms": round(sum(ts998) / len(ts998), 4),
             "wall_s_timed_region": round(t_wall, 3),
             "paper_context": PAPER_CONTEXT,
