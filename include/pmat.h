@@ -88,9 +88,14 @@ enum {
     PM_OPT_LEAF_CLUSTER = 5, /* PM-Basis / PM-IntBasis leaves: 1 = a cluster of up to 16 CTAs with
                                 the basis in shared memory (default), 0 = one CTA with the basis
                                 in global memory */
-    PM_OPT_HOST_CHUNKS = 6   /* pmat_mul_host: chunks of output entries whose inverse transforms,
+    PM_OPT_HOST_CHUNKS = 6,  /* pmat_mul_host: chunks of output entries whose inverse transforms,
                                 recombination and copy back are pipelined (0 = automatic,
                                 default; else 1 .. m k) */
+    PM_OPT_TEST_WITHHOLD_MMA = 7 /* test hook for the bounded device waits: 1 = the tensor-core
+                                pointwise kernel issues no MMA for its first point in block 0,
+                                so that block's wait gives up after 1024 polls; the call's
+                                output is undefined and pm_sync returns PM_ETIMEOUT.  Nothing
+                                is in flight when the wait gives up.  Default 0. */
 };
 
 /* Stages reported by pm_stage_times. */
@@ -129,6 +134,14 @@ const char *pm_last_error(pm_ctx *ctx);
 /* Number of CUDA kernel launches issued by this context since creation
  * (a diagnostic counter; it includes set-up kernels). */
 int64_t pm_kernel_launches(pm_ctx *ctx);
+
+/* Algorithmic work of every product this context ran since creation (or the
+ * last reset), whichever entry point or driver issued it: out3[0] = the
+ * compulsory bytes (inputs read once, outputs written once), out3[1] = the
+ * pointwise modular multiply-adds (primes x transform points x m n k),
+ * out3[2] = the NTT butterflies (primes x transforms x (L/2) log2 L).  HOST
+ * int64_t[3].  reset != 0 zeroes the counters after reading them. */
+int pm_work_counters(pm_ctx *ctx, int64_t *out3, int reset);
 
 /* With PM_OPT_STAGE_TIMING on, every stage of every call is bracketed by
  * CUDA events on the context's stream.  This call synchronises the stream,

@@ -12,6 +12,8 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "host.h"
 
 // ------------------------------------------------------------------ errors
@@ -204,8 +206,14 @@ static cudaEvent_t take_event(pm_ctx *ctx)
     return e;
 }
 
+// Every stage is also an NVTX range (named by stage) for timeline tools; the ranges cost a
+// function-pointer test when no tool is attached.
+static const char *const kStageNames[PM_NSTAGES] = {"pm:fwd_ntt", "pm:pointwise", "pm:inv_ntt", "pm:crt", "pm:leaf",
+                                                    "pm:other"};
+
 int stage_begin(pm_ctx *ctx, int stage)
 {
+    nvtxRangePushA(stage >= 0 && stage < PM_NSTAGES ? kStageNames[stage] : "pm:stage");
     if (!ctx->opt_timing) return -1;
     pm_ctx::Mark mk;
     mk.stage = stage;
@@ -219,6 +227,7 @@ int stage_begin(pm_ctx *ctx, int stage)
 
 void stage_end(pm_ctx *ctx, int token)
 {
+    nvtxRangePop();
     if (token < 0 || token >= (int)ctx->marks.size()) return;
     pm_ctx::Mark &mk = ctx->marks[token];
     mk.launches = ctx->launches - mk.launches;
@@ -380,6 +389,18 @@ static int launch_fwd_lists(pm_ctx *ctx, const std::vector<FwdJob> &blk, const s
     return PM_OK;
 }
 
+// Algorithmic work of one product (the measure the roofline fractions use): the compulsory
+// bytes (inputs read once, the output written once), the pointwise modular multiply-adds
+// (K primes x L points x m n k) and the butterflies of every transform (K (mn + nk + mk)
+// transforms of (L/2) lg L butterflies).
+static void count_work(pm_ctx *ctx, int K, int lg, int w, int m, int n, int k, int64_t dA, int64_t dB, int64_t len)
+{
+    const int64_t L = int64_t(1) << lg;
+    ctx->work[0] += ((int64_t)m * n * dA + (int64_t)n * k * dB + (int64_t)m * k * len) * w;
+    ctx->work[1] += (int64_t)K * L * m * n * k;
+    ctx->work[2] += (int64_t)K * ((int64_t)m * n + (int64_t)n * k + (int64_t)m * k) * (L / 2) * lg;
+}
+
 namespace {
 struct Plan {
     std::vector<PrimeSlot *> pr;
@@ -434,7 +455,7 @@ static int launch_pointwise_lists(pm_ctx *ctx, const PwLists &pl)
                 return launch_pointwise_sn(pk, ctx->stream, &ctx->launches); }));
     if (!pl.tjobs.empty())
         CKI(launch_packs(ctx, pl.tjobs, pl.tnb, [&](const JobPack<PwJob> &pk) {
-            return launch_pointwise_tc(pk, ctx->d_status, ctx->stream, &ctx->launches); }));
+            return launch_pointwise_tc(pk, ctx->d_status, ctx->stream, &ctx->launches, ctx->opt_withhold); }));
     return PM_OK;
 }
 
@@ -504,6 +525,10 @@ int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
     }
     for (int r = 0; r < count; r++)
         for (auto *s : plan[r].pr) CKI(slot_tables(ctx, *s, reqs[r].lg));
+    for (int r = 0; r < count; r++) {
+        const ProdReq &q = reqs[r];
+        count_work(ctx, (int)plan[r].pr.size(), q.lg, q.w, q.m, q.n, q.k, q.dA, q.dB, q.len);
+    }
 
     // ---- chunks under the workspace cap
     int r0 = 0;
@@ -701,6 +726,9 @@ int pm_set_option(pm_ctx *ctx, int key, int64_t value)
     case PM_OPT_LEAF_CLUSTER:
         ctx->opt_leaf_cluster = value ? 1 : 0;
         return PM_OK;
+    case PM_OPT_TEST_WITHHOLD_MMA:
+        ctx->opt_withhold = value ? 1 : 0;
+        return PM_OK;
     case PM_OPT_HOST_CHUNKS:
         if (value < 0 || value > (1 << 20)) return pm_fail(ctx, PM_EINVAL, "host chunk count out of range");
         ctx->opt_host_chunks = (int)value;
@@ -739,6 +767,15 @@ int pm_sync(pm_ctx *ctx)
 const char *pm_last_error(pm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int64_t pm_kernel_launches(pm_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int pm_work_counters(pm_ctx *ctx, int64_t *out3, int reset)
+{
+    if (!ctx || !out3) return PM_EINVAL;
+    for (int i = 0; i < 3; i++) out3[i] = ctx->work[i];
+    if (reset)
+        for (int i = 0; i < 3; i++) ctx->work[i] = 0;
+    return PM_OK;
+}
 
 int pm_stage_times(pm_ctx *ctx, double *ms, int64_t *launches)
 {
@@ -803,6 +840,7 @@ static int mul_host(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const v
     CKI(choose_primes(ctx, p, n, dA < dB ? dA : dB, lg, pr, direct));
     for (auto *sl : pr) CKI(slot_tables(ctx, *sl, lg));
     const size_t K = pr.size();
+    count_work(ctx, (int)K, lg, w, m, n, k, dA, dB, len);
     const size_t eA = (size_t)m * n, eB = (size_t)n * k, eC = (size_t)m * k;
     const size_t bAh = eA * dA * w, bBh = eB * dB * w, bCh = eC * len * w;
     const size_t bA = align256(eA * L * 4), bB = align256(eB * L * 4), bC = align256(eC * L * 4);

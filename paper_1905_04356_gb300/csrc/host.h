@@ -33,11 +33,13 @@ struct pm_ctx {
     void *ws = nullptr;
     size_t ws_size = 0;
     long long launches = 0;
+    int64_t work[3] = {0, 0, 0};      // product work: compulsory bytes, pointwise MACs, butterflies
     int *d_status = nullptr;          // deferred device status (0 = OK)
     Arena arena;                      // driver buffers (PM-Basis, resultant)
     int opt_timing = 0;
     int opt_leaf_cluster = 1;         // PM-Basis leaves on a CTA cluster (0 = one CTA)
     int opt_host_chunks = 0;          // pmat_mul_host output chunks (0 = automatic)
+    int opt_withhold = 0;             // test hook: the tensor-core pointwise kernel withholds an MMA
     struct Mark { int stage; cudaEvent_t a, b; long long launches; };
     std::vector<Mark> marks;          // recorded stage intervals
     std::vector<cudaEvent_t> spare;   // reusable events

@@ -48,7 +48,8 @@ __device__ __forceinline__ uint32_t f32_to_u(uint32_t bits)
 int tc_blocks(const PwJob &j) { return (j.L + TC_PTS - 1) / TC_PTS; }
 
 template <int KP>
-__global__ void __launch_bounds__(TC_THREADS) k_pointwise_tc(const __grid_constant__ JobPack<PwJob> pk, int *status)
+__global__ void __launch_bounds__(TC_THREADS) k_pointwise_tc(const __grid_constant__ JobPack<PwJob> pk, int *status,
+                                                              int withhold)
 {
     constexpr int N = 4 * KP;                      // MMA N (columns: limb v, column c)
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -127,7 +128,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_pointwise_tc(const __grid_consta
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) {
+        // withhold (test hook): block 0 issues no MMA for its first point, so nothing is in
+        // flight and its wait below must give up
+        const bool issue = !(withhold && blockIdx.x == 0 && pp == 0);
+        if (tid == 0 && issue) {
             for (int ks = 0; ks < ksteps; ks++) {
                 const uint64_t ad = tc_desc(smem_u32(opA) + ks * 256), bd = tc_desc(smem_u32(opB) + ks * 256);
                 asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
@@ -139,7 +143,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_pointwise_tc(const __grid_consta
         }
         // ---- bounded wait for the MMA (phase pp & 1)
         uint32_t done = 0;
-        for (int it = 0; it < (1 << 24) && !done; it++)
+        const int polls = issue ? (1 << 24) : (1 << 10);   // short only where nothing was issued
+        for (int it = 0; it < polls && !done; it++)
             asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                          " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(smem_u32(&mbar)), "r"((uint32_t)(pp & 1)));
         ok = __syncthreads_and(done) != 0;           // one decision for the whole block
@@ -199,17 +204,18 @@ static size_t tc_smem() { return 16384 + 3 * 1024 * TC_PTS * 4; }   // operands 
 
 bool tc_supported(const PwJob &j) { return j.m <= 32 && j.n <= 32 && j.k <= 32 && j.L >= 16; }
 
-cudaError_t launch_pointwise_tc(const JobPack<PwJob> &pk, int *status, cudaStream_t st, long long *launches)
+cudaError_t launch_pointwise_tc(const JobPack<PwJob> &pk, int *status, cudaStream_t st, long long *launches,
+                                int withhold)
 {
     int kmax = 0;
     for (int i = 0; i < pk.njobs; i++) kmax = pk.jobs[i].k > kmax ? pk.jobs[i].k : kmax;
     const size_t sm = tc_smem();
     if (kmax <= 16) {
         cudaFuncSetAttribute(k_pointwise_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_pointwise_tc<16><<<pk.blk_start[pk.njobs], TC_THREADS, sm, st>>>(pk, status);
+        k_pointwise_tc<16><<<pk.blk_start[pk.njobs], TC_THREADS, sm, st>>>(pk, status, withhold);
     } else {
         cudaFuncSetAttribute(k_pointwise_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_pointwise_tc<32><<<pk.blk_start[pk.njobs], TC_THREADS, sm, st>>>(pk, status);
+        k_pointwise_tc<32><<<pk.blk_start[pk.njobs], TC_THREADS, sm, st>>>(pk, status, withhold);
     }
     ++*launches;
     return cudaGetLastError();

@@ -24,7 +24,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "pmat.h")
 
 PM_OK, PM_EINVAL, PM_EDOMAIN, PM_ENOMEM, PM_ECUDA, PM_ETIMEOUT, PM_EUNSUPPORTED, PM_ESCRATCH = range(8)
 (PM_OPT_POINTWISE, PM_OPT_THRESHOLD, PM_OPT_DEBUG_CHECKS, PM_OPT_STAGE_TIMING, PM_OPT_LEAF_CLUSTER,
- PM_OPT_HOST_CHUNKS) = 1, 2, 3, 4, 5, 6
+ PM_OPT_HOST_CHUNKS, PM_OPT_TEST_WITHHOLD_MMA) = 1, 2, 3, 4, 5, 6, 7
 PM_NSTAGES = 8
 STAGES = ["fwd_ntt", "pointwise", "inv_ntt", "crt", "leaf", "other"]
 STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_EDOMAIN", 3: "PM_ENOMEM", 4: "PM_ECUDA",
@@ -71,6 +71,7 @@ def lib():
             "pm_basis": ([P, u64, i32, i32, P, i64, i64, P, P, P], i32),
             "pm_intbasis": ([P, u64, i32, i32, P, i64, u64, u64, P, P, P], i32),
             "pmat_solve": ([P, u64, i32, P, i64, P, i64, P, P, P], i32),
+            "pm_work_counters": ([P, P, i32], i32),
             "bivariate_resultant_villard": ([P, i32, P, i32, i32, P, i32, i32, P, i32, P], i32),
             "bivariate_resultant": ([P, i32, P, i32, i32, P, i32, i32, P, P], i32),
             "pmat_inv_trunc": ([P, u64, i32, i32, P, i64, i64, P], i32),
@@ -170,6 +171,12 @@ class Context:
 
     def launches(self) -> int:
         return int(lib().pm_kernel_launches(self.h))
+
+    def work(self, reset: bool = False):
+        """{"bytes", "macs", "butterflies"}: algorithmic work of the products run so far."""
+        out = np.zeros(3, dtype=np.int64)
+        self._ck(lib().pm_work_counters(self.h, out.ctypes.data, 1 if reset else 0))
+        return {"bytes": int(out[0]), "macs": int(out[1]), "butterflies": int(out[2])}
 
     def stage_times(self):
         """{stage: (ms, launches)} recorded since the last call (needs PM_OPT_STAGE_TIMING)."""

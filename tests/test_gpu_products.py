@@ -227,3 +227,53 @@ def test_tensor_core_and_cuda_core_pointwise_agree_with_oracle(ctx, case):
             assert np.array_equal(got.astype(np.uint64), exp), mode
     finally:
         ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable(ctx):
+    """The tensor-core kernel's wait for its MMA is bounded.  With the test hook, block 0 issues
+    no MMA for its first point (nothing in flight), its wait gives up, the kernel frees its
+    tensor memory and returns, and pm_sync reports PM_ETIMEOUT; the next products on the same
+    context are exact."""
+    from paper_1905_04356_gb300 import PmError, pmat
+    p = P60
+    g = synth.rng(31)
+    A = synth.uniform(g, (4, 4, 64), p, np.uint64)
+    B = synth.uniform(g, (4, 4, 64), p, np.uint64)
+    dA, dB = pmat.to_device(A), pmat.to_device(B)
+    ctx.set_option(pmat.PM_OPT_POINTWISE, 2)
+    ctx.set_option(pmat.PM_OPT_TEST_WITHHOLD_MMA, 1)
+    try:
+        pmat.pmat_mul(ctx, p, dA, dB)
+        with pytest.raises(PmError) as e:
+            ctx.sync()
+        assert e.value.code == pmat.PM_ETIMEOUT
+    finally:
+        ctx.set_option(pmat.PM_OPT_TEST_WITHHOLD_MMA, 0)
+    try:
+        for mode in (2, 1):
+            ctx.set_option(pmat.PM_OPT_POINTWISE, mode)
+            got = pmat.to_host(pmat.pmat_mul(ctx, p, dA, dB))
+            ctx.sync()
+            assert np.array_equal(got, oracle.pmat_mul(p, A, B)), mode
+    finally:
+        ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
+
+
+def test_work_counters_count_each_product(ctx):
+    """pm_work_counters: compulsory bytes, pointwise MACs and butterflies of a product modulo
+    998244353 (one prime, L the next power of two above the output length)."""
+    from paper_1905_04356_gb300 import pmat
+    p, m, n, k, dA, dB = synth.P998, 3, 5, 2, 17, 33
+    g = synth.rng(77)
+    A = synth.uniform(g, (m, n, dA), p, np.uint32)
+    B = synth.uniform(g, (n, k, dB), p, np.uint32)
+    ctx.work(reset=True)
+    pmat.pmat_mul(ctx, p, pmat.to_device(A), pmat.to_device(B))
+    ctx.sync()
+    w = ctx.work(reset=True)
+    lenC = dA + dB - 1
+    lg = max(4, (lenC - 1).bit_length())
+    L = 1 << lg
+    assert w["bytes"] == (m * n * dA + n * k * dB + m * k * lenC) * 4
+    assert w["macs"] == L * m * n * k
+    assert w["butterflies"] == (m * n + n * k + m * k) * (L // 2) * lg
