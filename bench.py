@@ -215,11 +215,22 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"
         out = {"pm_basis_32x16_d8192_ms": round(ev_ms(run, reps), 2)}
         ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
         ctx.stage_times()
+        ctx.work(reset=True)
         run()
         st = ctx.stage_times()
+        wk = ctx.work(reset=True)
         ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
         out["pm_basis_stage_ms"] = {k: round(v[0], 2) for k, v in st.items() if v[1]}
         out["pm_basis_leaf_us_per_order_step"] = round(st["leaf"][0] * 1000 / W["d"], 2)
+        # the product work of one call (library counters) over the product stages' time
+        prod_ms = sum(st[k][0] for k in ("fwd_ntt", "pointwise", "inv_ntt", "crt"))
+        pk = peaks()
+        out["pm_basis_product_work"] = {
+            "bytes": wk["bytes"], "pointwise_macs": wk["macs"], "butterflies": wk["butterflies"],
+            "product_stage_ms": round(prod_ms, 2),
+            "compulsory_GBps": round(wk["bytes"] / (prod_ms * 1e-3) / 1e9, 1),
+            "compulsory_frac_hbm": round(wk["bytes"] / (prod_ms * 1e-3) / 1e9 / (pk["hbm_gbs"] if pk else 6800.0), 4),
+            "gmacs_per_s": round(wk["macs"] / (prod_ms * 1e-3) / 1e9, 1)}
         return out
 
     def resultant():
