@@ -249,7 +249,21 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"
                 for i, it in enumerate(items)]
         n0 = ctx.launches()
         ms = ev_ms(lambda: pmat.pmat_mul_batched(ctx, dev, outs), 2)
-        return {"batched_512_ms": round(ms, 2), "batched_512_launches_per_call": (ctx.launches() - n0) // 3}
+        out = {"batched_512_ms": round(ms, 2), "batched_512_launches_per_call": (ctx.launches() - n0) // 3}
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
+        ctx.stage_times()
+        ctx.work(reset=True)
+        pmat.pmat_mul_batched(ctx, dev, outs)
+        st = ctx.stage_times()
+        wk = ctx.work(reset=True)
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
+        out["batched_512_stage_ms"] = {k: round(v[0], 2) for k, v in st.items() if v[1]}
+        pk = peaks()
+        out["batched_512_work"] = {"bytes": wk["bytes"], "pointwise_macs": wk["macs"], "butterflies": wk["butterflies"],
+                                   "compulsory_frac_hbm": round(wk["bytes"] / (ms * 1e-3) / 1e9 /
+                                                                (pk["hbm_gbs"] if pk else 6800.0), 4),
+                                   "gmacs_per_s": round(wk["macs"] / (ms * 1e-3) / 1e9, 1)}
+        return out
 
     def inverse():
         W = synth.inverse_w(0)
