@@ -159,17 +159,28 @@ int pm_stage_times(pm_ctx *ctx, double *ms, int64_t *launches);
 int pmat_mul(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k,
              const void *A, int64_t dA, const void *B, int64_t dB, void *C);
 
-/* pmat_mul with A, B and C in HOST memory (same layouts).  The uploads run on
- * a second stream owned by the context and are overlapped with the stages:
- * B and A are transformed as their row chunks land, the pointwise products
- * run once, and the output entries are inverse-transformed, recombined and
- * copied back in chunks, each copy overlapping the next chunk's work.  Page-locked (pinned) host buffers are needed for
- * the copies to overlap; pageable ones give the same result.  Asynchronous
- * like the device calls: C is complete after pm_sync(), and A, B, C must
- * stay valid until then.  Returns PM_EUNSUPPORTED when the product's device
- * workspace would exceed 16 GB (use pmat_mul on device buffers). */
+/* pmat_mul with A, B and C in HOST memory (same layouts).  Uploads and
+ * downloads run on two streams owned by the context, overlapped with the
+ * stages: B and A are transformed as their row chunks land, the pointwise
+ * products run once, and the output entries are inverse-transformed,
+ * recombined and copied back in chunks, each copy overlapping the next
+ * chunk's work.  Consecutive calls overlap too: they alternate between two
+ * device staging sets, so a call's download runs during the next call's
+ * work, and the next call's upload during this call's.  The context's
+ * stream does not wait for the downloads until something needs them: the
+ * next device product on the context, pm_sync, pm_set_stream or
+ * pm_host_join.  Page-locked (pinned) host buffers are needed for the copies
+ * to overlap; pageable ones give the same result.  C is complete after
+ * pm_sync() (or after pm_host_join() and the stream's completion), and A, B,
+ * C must stay valid until then.  Returns PM_EUNSUPPORTED when the product's
+ * device workspace would exceed 16 GB (use pmat_mul on device buffers). */
 int pmat_mul_host(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k,
                   const void *A, int64_t dA, const void *B, int64_t dB, void *C);
+
+/* Make the context's stream wait for every download pmat_mul_host has
+ * issued, so that work or events recorded on the stream afterwards follow
+ * them.  Does not block the host. */
+int pm_host_join(pm_ctx *ctx);
 
 /* C (m x k, length t) = A . B mod x^t (Sec. 2; the truncated product used by
  * Newton iteration in Sec. 4.3).  Requires t >= 1; coefficients of degree

@@ -149,6 +149,15 @@ static PrimeDev prime_dev(const PrimeSlot &s, int lg)
 }
 
 // ------------------------------------------------------------------ memory
+int host_join(pm_ctx *ctx)
+{
+    if (!ctx->host_pending) return PM_OK;
+    for (int b = 0; b < 2; b++)
+        if (ctx->out_rec[b]) CK(cudaStreamWaitEvent(ctx->stream, ctx->out_free[b], 0));
+    ctx->host_pending = false;
+    return PM_OK;
+}
+
 int ws_reserve(pm_ctx *ctx, size_t bytes, void **out)
 {
     if (bytes > ctx->ws_size) {
@@ -507,6 +516,7 @@ static int launch_inverse_lists(pm_ctx *ctx, const InvLists &il, int lg)
 
 int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
 {
+    CKI(host_join(ctx));   // the workspace may hold a staging set a download still reads
     // ---- plan every request; size the twiddle tables before any job takes their addresses
     std::vector<Plan> plan(count);
     for (int r = 0; r < count; r++) {
@@ -698,8 +708,16 @@ int pm_destroy(pm_ctx *ctx)
     if (ctx->d_status) cudaFree(ctx->d_status);
     for (auto &mk : ctx->marks) { cudaEventDestroy(mk.a); cudaEventDestroy(mk.b); }
     for (auto e : ctx->spare) cudaEventDestroy(e);
+    if (ctx->up) cudaStreamSynchronize(ctx->up);
+    if (ctx->dn) cudaStreamSynchronize(ctx->dn);
     for (auto e : ctx->hev) cudaEventDestroy(e);
-    if (ctx->copy) cudaStreamDestroy(ctx->copy);
+    for (int i = 0; i < 2; i++) {
+        if (ctx->in_free[i]) cudaEventDestroy(ctx->in_free[i]);
+        if (ctx->out_free[i]) cudaEventDestroy(ctx->out_free[i]);
+    }
+    if (ctx->ws_ready) cudaEventDestroy(ctx->ws_ready);
+    if (ctx->up) cudaStreamDestroy(ctx->up);
+    if (ctx->dn) cudaStreamDestroy(ctx->dn);
     if (ctx->own) cudaStreamDestroy(ctx->own);
     delete ctx;
     return PM_OK;
@@ -741,6 +759,7 @@ int pm_set_option(pm_ctx *ctx, int key, int64_t value)
 int pm_set_stream(pm_ctx *ctx, void *cuda_stream)
 {
     if (!ctx) return PM_EINVAL;
+    CKI(host_join(ctx));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own;
     if (!ctx->stream) {
@@ -754,6 +773,7 @@ int pm_sync(pm_ctx *ctx)
 {
     if (!ctx) return PM_EINVAL;
     CK(cudaSetDevice(ctx->device));
+    CKI(host_join(ctx));
     CK(cudaStreamSynchronize(ctx->stream));
     int st = 0;
     CK(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -845,7 +865,8 @@ static int mul_host(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const v
     const size_t bAh = eA * dA * w, bBh = eB * dB * w, bCh = eC * len * w;
     const size_t bA = align256(eA * L * 4), bB = align256(eB * L * 4), bC = align256(eC * L * 4);
     const size_t bR = direct ? 0 : K * eC * len * 4;
-    const size_t total = align256(bAh) + align256(bBh) + align256(bCh) + K * (bA + bB + bC) + align256(bR);
+    const size_t stage = align256(bAh) + align256(bBh) + align256(bCh);   // one staging set
+    const size_t total = 2 * stage + K * (bA + bB + bC) + align256(bR);
     if (total > PM_BATCH_WS_CAP) return pm_fail(ctx, PM_EUNSUPPORTED, "pmat_mul_host: product too large for one pass");
     // chunk counts: pipelining pays once a chunk's copy is a few MB
     const int ncA = (bAh >= (8u << 20) && m >= 2) ? 2 : 1;
@@ -854,28 +875,56 @@ static int mul_host(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const v
     ncO = ncO < 1 ? 1 : (ncO > 6 ? 6 : ncO);
     if (ctx->opt_host_chunks > 0) ncO = ctx->opt_host_chunks;
     if ((size_t)ncO > eC) ncO = (int)eC;
+    // A new layout or a larger workspace: let every pending download finish first (the old
+    // staging sets may move), and make the uploads wait for the (re)allocation.
+    const bool relayout = stage != ctx->host_stage || total + 256 > ctx->ws_size;
+    if (relayout) {
+        CKI(host_join(ctx));
+        ctx->in_rec[0] = ctx->in_rec[1] = ctx->out_rec[0] = ctx->out_rec[1] = false;
+        ctx->host_stage = stage;
+    }
     void *ws = nullptr;
     CKI(ws_reserve(ctx, total + 256, &ws));
-    char *cur = (char *)ws;
+    // the workspace moved (this call or another user grew it): the staging sets are new memory
+    // that the upload stream may touch only after its allocation on the context's stream
+    const bool moved = ws != ctx->host_ws;
+    if (moved) {
+        ctx->in_rec[0] = ctx->in_rec[1] = ctx->out_rec[0] = ctx->out_rec[1] = false;
+        ctx->host_ws = ws;
+    }
+    const int sb = ctx->host_parity;                   // this call's staging set
+    ctx->host_parity ^= 1;
+    char *cur = (char *)ws + sb * stage;
     char *Ad = cur; cur += align256(bAh);
     char *Bd = cur; cur += align256(bBh);
-    char *Cd = cur; cur += align256(bCh);
+    char *Cd = cur;
+    cur = (char *)ws + 2 * stage;
     char *TA = cur; cur += K * bA;
     char *TB = cur; cur += K * bB;
     char *TC = cur; cur += K * bC;
     char *R = cur;
-    if (!ctx->copy) CK(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
-    const int nev = 2 + ncA + ncB + ncO;
+    if (!ctx->up) CK(cudaStreamCreateWithFlags(&ctx->up, cudaStreamNonBlocking));
+    if (!ctx->dn) CK(cudaStreamCreateWithFlags(&ctx->dn, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; i++) {
+        if (!ctx->in_free[i]) CK(cudaEventCreateWithFlags(&ctx->in_free[i], cudaEventDisableTiming));
+        if (!ctx->out_free[i]) CK(cudaEventCreateWithFlags(&ctx->out_free[i], cudaEventDisableTiming));
+    }
+    if (!ctx->ws_ready) CK(cudaEventCreateWithFlags(&ctx->ws_ready, cudaEventDisableTiming));
+    const int nev = ncA + ncB + ncO;
     while ((int)ctx->hev.size() < nev) {
         cudaEvent_t e;
         CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         ctx->hev.push_back(e);
     }
-    cudaEvent_t *ev = ctx->hev.data();   // 0: start, then B chunks, A chunks, output chunks, end
-    cudaEvent_t *evB = ev + 1, *evA = evB + ncB, *evO = evA + ncA, evEnd = evO[ncO];
-    cudaStream_t cs = ctx->copy;
-    CK(cudaEventRecord(ev[0], ctx->stream));   // the workspace is free (stream order)
-    CK(cudaStreamWaitEvent(cs, ev[0], 0));
+    cudaEvent_t *ev = ctx->hev.data();   // B chunks, A chunks, output chunks
+    cudaEvent_t *evB = ev, *evA = evB + ncB, *evO = evA + ncA;
+    cudaStream_t cs = ctx->up;
+    if (relayout || moved) {                           // the workspace exists in stream order
+        CK(cudaEventRecord(ctx->ws_ready, ctx->stream));
+        CK(cudaStreamWaitEvent(cs, ctx->ws_ready, 0));
+    }
+    // the staging set's previous inputs have been transformed (the call two back)
+    if (ctx->in_rec[sb]) CK(cudaStreamWaitEvent(cs, ctx->in_free[sb], 0));
     // uploads, then the forward transforms of each chunk once it has landed
     struct Up { const char *h; char *d; int rows, ncol; int64_t dl; char *T; size_t bT; cudaEvent_t *e; int nc; };
     const Up ups[2] = {{(const char *)B, Bd, n, k, dB, TB, bB, evB, ncB}, {(const char *)A, Ad, m, n, dA, TA, bA, evA, ncA}};
@@ -903,6 +952,8 @@ static int mul_host(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const v
             CKI(launch_fwd_lists(ctx, blk, bn, col, cn, lg));
             stage_end(ctx, tok);
         }
+    CK(cudaEventRecord(ctx->in_free[sb], ctx->stream));   // this staging set's inputs are consumed
+    ctx->in_rec[sb] = true;
     int tok = stage_begin(ctx, PM_STAGE_POINTWISE);
     {
         PwLists pl;
@@ -912,6 +963,8 @@ static int mul_host(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const v
         CKI(launch_pointwise_lists(ctx, pl));
     }
     stage_end(ctx, tok);
+    // the staging set's previous outputs have been downloaded (the call two back)
+    if (ctx->out_rec[sb]) CK(cudaStreamWaitEvent(ctx->stream, ctx->out_free[sb], 0));
     // output entries [e0, e1) per chunk: inverse transforms, CRT (residue planes of the chunk
     // packed: K planes of (e1 - e0) * len words), copy back
     for (int c = 0; c < ncO; c++) {
@@ -941,11 +994,13 @@ static int mul_host(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const v
             stage_end(ctx, tok);
         }
         CK(cudaEventRecord(evO[c], ctx->stream));
-        CK(cudaStreamWaitEvent(cs, evO[c], 0));
-        CK(cudaMemcpyAsync((char *)C + (size_t)e0 * len * w, Cc, (size_t)ce * len * w, cudaMemcpyDeviceToHost, cs));
+        CK(cudaStreamWaitEvent(ctx->dn, evO[c], 0));
+        CK(cudaMemcpyAsync((char *)C + (size_t)e0 * len * w, Cc, (size_t)ce * len * w, cudaMemcpyDeviceToHost,
+                           ctx->dn));
     }
-    CK(cudaEventRecord(evEnd, cs));
-    CK(cudaStreamWaitEvent(ctx->stream, evEnd, 0));   // later work on the stream follows the copies
+    CK(cudaEventRecord(ctx->out_free[sb], ctx->dn));
+    ctx->out_rec[sb] = true;
+    ctx->host_pending = true;     // joined by host_join: the next device product, pm_sync, pm_host_join
     return PM_OK;
 }
 
@@ -957,6 +1012,13 @@ int pmat_mul(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A,
     const int lg = ceil_log2(len);
     if (lg > PM_MAX_LOG2L) return pm_fail(ctx, PM_EINVAL, "product longer than 2^20");
     return prod_slice(ctx, p, w, m, n, k, A, dA, dA, B, dB, dB, 0, len, lg, C, len);
+}
+
+int pm_host_join(pm_ctx *ctx)
+{
+    if (!ctx) return PM_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return pm_fail(ctx, PM_ECUDA, "cudaSetDevice failed");
+    return host_join(ctx);
 }
 
 int pmat_mul_host(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA, const void *B,

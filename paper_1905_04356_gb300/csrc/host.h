@@ -43,9 +43,23 @@ struct pm_ctx {
     struct Mark { int stage; cudaEvent_t a, b; long long launches; };
     std::vector<Mark> marks;          // recorded stage intervals
     std::vector<cudaEvent_t> spare;   // reusable events
-    cudaStream_t copy = nullptr;      // host<->device copies of pmat_mul_host (created on first use)
-    std::vector<cudaEvent_t> hev;     // its ordering events
+    // pmat_mul_host: uploads and downloads on their own streams (created on first use), two
+    // staging sets used by alternate calls so that one call's download overlaps the next
+    // call's work; the context's stream joins the downloads lazily (host_join)
+    cudaStream_t up = nullptr, dn = nullptr;
+    std::vector<cudaEvent_t> hev;     // per-chunk ordering events
+    cudaEvent_t in_free[2] = {nullptr, nullptr};   // staging set's inputs consumed (context stream)
+    cudaEvent_t out_free[2] = {nullptr, nullptr};  // staging set's outputs downloaded (dn)
+    cudaEvent_t ws_ready = nullptr;                // workspace (re)allocated (context stream)
+    bool in_rec[2] = {false, false}, out_rec[2] = {false, false};
+    bool host_pending = false;        // downloads the context's stream has not joined yet
+    int host_parity = 0;
+    size_t host_stage = 0;            // bytes of one staging set in the current layout
+    void *host_ws = nullptr;          // the workspace the staging sets were laid out in
 };
+
+// Make the context's stream wait for every pending pmat_mul_host download (no-op if none).
+int host_join(pm_ctx *ctx);
 
 // Stage timing: stage_begin returns a token; stage_end closes it.
 int stage_begin(pm_ctx *ctx, int stage);

@@ -72,6 +72,7 @@ def lib():
             "pm_intbasis": ([P, u64, i32, i32, P, i64, u64, u64, P, P, P], i32),
             "pmat_solve": ([P, u64, i32, P, i64, P, i64, P, P, P], i32),
             "pm_work_counters": ([P, P, i32], i32),
+            "pm_host_join": ([P], i32),
             "bivariate_resultant_villard": ([P, i32, P, i32, i32, P, i32, i32, P, i32, P], i32),
             "bivariate_resultant": ([P, i32, P, i32, i32, P, i32, i32, P, P], i32),
             "pmat_inv_trunc": ([P, u64, i32, i32, P, i64, i64, P], i32),
@@ -172,6 +173,10 @@ class Context:
     def launches(self) -> int:
         return int(lib().pm_kernel_launches(self.h))
 
+    def host_join(self):
+        """Make the context's stream wait for the downloads of earlier pmat_mul_host calls."""
+        self._ck(lib().pm_host_join(self.h))
+
     def work(self, reset: bool = False):
         """{"bytes", "macs", "butterflies"}: algorithmic work of the products run so far."""
         out = np.zeros(3, dtype=np.int64)
@@ -215,8 +220,8 @@ def _host(t: torch.Tensor) -> torch.Tensor:
 
 
 def pmat_mul_host(ctx: Context, p: int, A: torch.Tensor, B: torch.Tensor, out=None) -> torch.Tensor:
-    """C = A . B mod p with A, B and C in host memory (pinned for overlap); asynchronous like the
-    device calls: read C after ctx.sync()."""
+    """C = A . B mod p with A, B and C in host memory (pinned for overlap); asynchronous, and
+    consecutive calls overlap: read C after ctx.sync()."""
     A, B = _host(A), _host(B)
     m, n, dA = A.shape
     n2, k, dB = B.shape

@@ -123,3 +123,26 @@ def test_host_product_then_device_work_is_ordered(ctx):
     ctx.sync()
     assert np.array_equal(C.numpy().view(np.uint64), oracle.pmat_mul(P60, A, B))
     assert np.array_equal(pmat.to_host(C2), oracle.pmat_mul(P60, A2, B2))
+
+
+def test_host_products_back_to_back(ctx):
+    """Consecutive host products overlap (alternating staging sets, downloads joined lazily):
+    five calls with different inputs and outputs, one sync, every result exact; then a device
+    product on the same context, which must wait for the pending downloads."""
+    from paper_1905_04356_gb300 import pmat
+    g = synth.rng(8080)
+    shapes = [(16, 1, 16, 2100, 2100), (16, 1, 16, 2100, 2100), (8, 4, 8, 900, 3000), (16, 1, 16, 2100, 2100),
+              (8, 4, 8, 900, 3000)]
+    ins, outs = [], []
+    for (m, n, k, dA, dB) in shapes:
+        A = synth.uniform(g, (m, n, dA), P60, np.uint64)
+        B = synth.uniform(g, (n, k, dB), P60, np.uint64)
+        ins.append((A, B))
+        outs.append(pmat.pmat_mul_host(ctx, P60, _host_tensor(A, True), _host_tensor(B, True)))
+    A2 = synth.uniform(g, (4, 4, 300), P60, np.uint64)
+    B2 = synth.uniform(g, (4, 4, 300), P60, np.uint64)
+    C2 = pmat.pmat_mul(ctx, P60, pmat.to_device(A2), pmat.to_device(B2))
+    ctx.sync()
+    for (A, B), C in zip(ins, outs):
+        assert np.array_equal(C.numpy().view(np.uint64), oracle.pmat_mul(P60, A, B))
+    assert np.array_equal(pmat.to_host(C2), oracle.pmat_mul(P60, A2, B2))
