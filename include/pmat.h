@@ -88,9 +88,11 @@ enum {
     PM_OPT_LEAF_CLUSTER = 5, /* PM-Basis / PM-IntBasis leaves: 1 = a cluster of up to 16 CTAs with
                                 the basis in shared memory (default), 0 = one CTA with the basis
                                 in global memory */
-    PM_OPT_HOST_CHUNKS = 6,  /* pmat_mul_host: chunks of output entries whose inverse transforms,
-                                recombination and copy back are pipelined (0 = automatic,
-                                default; else 1 .. m k) */
+    PM_OPT_HOST_CHUNKS = 6,  /* pmat_mul_host output chunks: 0 (default) = one, the fastest
+                                for calls in a row (a call's download overlaps the next call);
+                                N >= 1 = N chunks of output entries whose inverse transforms,
+                                recombination and copy back are pipelined, for the latency of
+                                a call on its own */
     PM_OPT_TEST_WITHHOLD_MMA = 7 /* test hook for the bounded device waits: 1 = the tensor-core
                                 pointwise kernel issues no MMA for its first point in block 0,
                                 so that block's wait gives up after 1024 polls; the call's

@@ -1,10 +1,11 @@
 """GPU parity of pmat_mul_host (the product from and to host memory, copies overlapped with the
 stages) against the CPU oracle.
 
-The shapes exercise every chunking branch: no chunking (small outputs), output entries in 4
-chunks, A and B uploaded in two row chunks, uneven chunk counts set by option (more chunks than
-output entries included), transforms longer than 2^14 points (column passes), the direct
-NTT-prime mode with 32-bit words, pageable and pinned host buffers.
+The shapes exercise every chunking branch: small operands (one forward launch for both), A or B
+of 8 MB or more (two row chunks each, transformed as they land), one output chunk (the default,
+consecutive calls overlapping) and N output chunks set by option (more chunks than output
+entries included); transforms longer than 2^14 points (column passes), the direct NTT-prime
+mode with 32-bit words, pageable and pinned host buffers.
 The full-size 32x32 products are checked against the SHA-256 of the oracle's output.
 """
 import numpy as np
@@ -50,10 +51,10 @@ CASES = [
     # p, w, m, n, k, dA, dB, pinned
     (P60, 8, 3, 5, 2, 17, 33, True),            # tiny: one chunk everywhere
     (synth.P998, 4, 7, 3, 9, 300, 1000, False),  # direct mode, 32-bit words, pageable buffers
-    (P60, 8, 16, 1, 16, 2100, 2100, True),      # output in 4 chunks
-    (P60, 8, 2, 1, 64, 4096, 4096, True),       # output in 4 chunks, m = 2
-    (P60, 8, 64, 2, 2, 4200, 8, True),          # A in 2 row chunks
-    (P60, 8, 8, 2, 16, 64, 32768, True),        # B in 2 chunks, L = 2^16 (column passes)
+    (P60, 8, 16, 1, 16, 2100, 2100, True),      # 8.6 MB of output
+    (P60, 8, 2, 1, 64, 4096, 4096, True),       # m = 2
+    (P60, 8, 64, 2, 2, 8200, 8, True),          # A of 8.4 MB: 2 row chunks
+    (P60, 8, 8, 2, 16, 64, 32768, True),        # B of 8.4 MB: 2 row chunks, L = 2^16 (column passes)
     (P32, 4, 9, 2, 16, 700, 1500, True),        # 32-bit words through the CRT
 ]
 
@@ -84,6 +85,23 @@ def test_host_product_full_size_matches_oracle_fingerprint(ctx, name, ntt_prime)
     got = _run(ctx, W["p"], W["A"], W["B"]).astype(np.uint64)
     assert list(got.shape) == gold["shape"]
     assert hashlib.sha256(np.ascontiguousarray(got).tobytes()).hexdigest() == gold["sha256"]
+
+
+@pytest.mark.parametrize("case", [CASES[2], CASES[4], CASES[5]], ids=["out4", "A_rows", "B_rows_cols"])
+def test_host_product_latency_form(ctx, case):
+    """An explicit output chunk count (the latency form): 4 output chunks pipelined with their
+    downloads, with A or B in two row chunks where they are 8 MB or more."""
+    from paper_1905_04356_gb300 import pmat
+    p, w, m, n, k, dA, dB, pinned = case
+    g = synth.rng((m * 17 + dB) & 0xffff)
+    A = synth.uniform(g, (m, n, dA), p, np.uint64)
+    B = synth.uniform(g, (n, k, dB), p, np.uint64)
+    ctx.set_option(pmat.PM_OPT_HOST_CHUNKS, 4)
+    try:
+        got = _run(ctx, p, A, B, pinned)
+    finally:
+        ctx.set_option(pmat.PM_OPT_HOST_CHUNKS, 0)
+    assert np.array_equal(got, oracle.pmat_mul(p, A, B))
 
 
 @pytest.mark.parametrize("chunks", [1, 3, 7, 40])
