@@ -304,9 +304,15 @@ __global__ void k_res_interp3(const __grid_constant__ ResPack P)
 #define VIL_WARPS 4
 #define VIL_MMAX 16
 
-// One warp per point l < P.N: extended Euclid on (f_alpha, g_alpha) with exact division,
-// tracking the cofactor of f and Res(f_alpha, g_alpha); writes H(alpha_l) and the -I block
-// into Eip (2m x m x P.N, plain) and Res into resv[l] (plain); Res = 0 sets flag bit 4.
+// One warp per point l < P.N: the extended Euclidean algorithm on (f_alpha, g_alpha) by
+// pseudo-division, tracking the cofactor of f and Res(f_alpha, g_alpha); writes H(alpha_l) and
+// the -I block into Eip (2m x m x P.N, plain) and Res into resv[l] (plain); Res = 0 sets flag
+// bit 4.  Each quotient term is one pseudo-division step A <- lc(B) A - lc(A) y^sh B, applied
+// to the cofactor alike (the relation A = s_A f + t_A g is linear), so no inversion is needed
+// until the end: with s steps, prem = lc(B)^s (A mod B), hence Res(A, B) = (-1)^(ab)
+// lc(B)^(a-r) Res(B, prem) / lc(B)^(s b); the factors are recorded per remainder and the
+// powers taken at the end (one inversion), and the final constant B0 = s_B f + t_B g gives
+// s = s_B / B0 (another).  H then needs lc(g)^-1 (a third).
 __global__ void __launch_bounds__(32 * VIL_WARPS) k_vil_xgcd(const __grid_constant__ ResPack P, int dmax, int m,
                                                             u64 *Eip, u64 *resv)
 {
@@ -316,7 +322,8 @@ __global__ void __launch_bounds__(32 * VIL_WARPS) k_vil_xgcd(const __grid_consta
     const int pt = blockIdx.x * VIL_WARPS + wid;
     if (pt >= P.N) return;
     const int W = dmax + 2;
-    u64 *A = smv + (size_t)wid * 5 * W, *B = A + W, *sA = B + W, *sB = sA + W, *G = sB + W;
+    u64 *A = smv + (size_t)wid * 8 * W, *B = A + W, *sA = B + W, *sB = sA + W, *G = sB + W;
+    u64 *rl = G + W, *rn = rl + W, *rd = rn + W;       // per remainder: lc(B), a - r, s b
     const u64 *val = I.Vt + (i64)pt * P.J;
     for (int c = lane; c < W; c += 32) {
         A[c] = c <= P.dyf ? val[c] : 0;
@@ -326,32 +333,38 @@ __global__ void __launch_bounds__(32 * VIL_WARPS) k_vil_xgcd(const __grid_consta
         sB[c] = 0;
     }
     __syncwarp();
-    int a = P.dyf, b = P.dyg, dsA = 0, dsB = -1;
-    u64 acc = I.one;
+    int a = P.dyf, b = P.dyg, dsA = 0, dsB = -1, nr = 0;
     bool neg = false, zero = false;
     while (b > 0) {
-        const u64 inv = mpw(B[b], I.p - 2, I);
-        int da = a;
+        const u64 lcB = B[b];
+        int da = a, st = 0;
         while (da >= b) {
-            const u64 cq = mm(A[da], inv, I);
+            const u64 lcA = A[da];
             const int sh = da - b;
-            __syncwarp();
-            for (int i = lane; i < b; i += 32) A[sh + i] = sub64(A[sh + i], mm(cq, B[i], I), I.p);
-            for (int i = lane; i <= dsB && sh + i < W; i += 32) sA[sh + i] = sub64(sA[sh + i], mm(cq, sB[i], I), I.p);
+            const int top = dsA > sh + dsB ? dsA : sh + dsB;
+            __syncwarp();                                // every lane has read A[da]
+            for (int i = lane; i < da; i += 32)
+                A[i] = i >= sh ? mont_msub(lcB, A[i], lcA, B[i - sh], I.p, I.pn) : mm(lcB, A[i], I);
+            for (int i = lane; i <= top && i < W; i += 32) {
+                const u64 y = (i >= sh && i - sh <= dsB) ? sB[i - sh] : 0;
+                sA[i] = mont_msub(lcB, sA[i], lcA, y, I.p, I.pn);
+            }
+            dsA = top < W - 1 ? top : W - 1;
+            st++;
             __syncwarp();
             if (lane == 0) A[da] = 0;
             __syncwarp();
             da = da > 0 ? warp_deg(A, da - 1) : -1;
         }
-        const int dsR = a >= b ? (dsA > a - b + dsB ? dsA : a - b + dsB) : dsA;
         const int r = da;
         if (r < 0) { zero = true; break; }
         neg ^= (a & b & 1);
-        acc = mm(acc, mpw(B[b], (u64)(a - r), I), I);
-        u64 *t = A; A = B; B = t;                  // (A, B) <- (B, R), cofactors alike
+        if (lane == 0) { rl[nr] = lcB; rn[nr] = (u64)(a - r); rd[nr] = (u64)st * (u64)b; }
+        nr++;
+        u64 *t = A; A = B; B = t;                        // (A, B) <- (B, prem), cofactors alike
         t = sA; sA = sB; sB = t;
         a = b; b = r;
-        dsA = dsB; dsB = dsR;
+        const int d2 = dsA; dsA = dsB; dsB = d2;
         __syncwarp();
     }
     u64 *H = Eip;
@@ -361,23 +374,32 @@ __global__ void __launch_bounds__(32 * VIL_WARPS) k_vil_xgcd(const __grid_consta
         if (lane == 0) { resv[pt] = 0; atomicOr(P.flag, 4); }
         return;
     }
-    // Res = (-1)^.. acc B0^a; s = sB / B0
+    // Res = (-1)^.. prod lc^(a-r) B0^a / prod lc^(s b): 32 records at a time, one inversion
     const u64 b0 = B[0];
+    u64 num = I.one, den = I.one;
+    for (int i = lane; i < nr; i += 32) {
+        num = mm(num, mpw(rl[i], rn[i], I), I);
+        den = mm(den, mpw(rl[i], rd[i], I), I);
+    }
+    for (int o = 16; o >= 1; o >>= 1) {
+        num = mm(num, __shfl_xor_sync(0xffffffffu, num, o), I);
+        den = mm(den, __shfl_xor_sync(0xffffffffu, den, o), I);
+    }
     if (lane == 0) {
-        u64 res = mm(mm(acc, mpw(b0, (u64)a, I), I), 1, I);
+        u64 res = mm(mm(mm(num, mpw(b0, (u64)a, I), I), mpw(den, I.p - 2, I), I), 1, I);
         if (neg && res) res = I.p - res;
         resv[pt] = res;
     }
     const u64 binv = mpw(b0, I.p - 2, I);
     const int n2 = P.dyg;
-    u64 *u = sA, *tmp = A;                         // sA and A are free now
+    u64 *u = sA, *tmp = A;                               // sA and A are free now
     for (int c = lane; c < W; c += 32) u[c] = c < n2 ? mm(sB[c], binv, I) : 0;
     __syncwarp();
     const u64 ginv = mpw(G[n2], I.p - 2, I);
     for (int j = 0; j < m; j++) {
         for (int i = lane; i < m; i += 32) H[((i64)i * m + j) * sig + pt] = mm(u[i], 1, I);
         if (j + 1 == m) break;
-        const u64 t = mm(u[n2 - 1], ginv, I);       // u <- z u mod g
+        const u64 t = mm(u[n2 - 1], ginv, I);            // u <- y u mod g
         for (int i = lane; i < n2; i += 32) tmp[i] = sub64(i ? u[i - 1] : 0, mm(t, G[i], I), I.p);
         __syncwarp();
         for (int i = lane; i < n2; i += 32) u[i] = tmp[i];
@@ -696,7 +718,7 @@ static int vil_one(pm_ctx *ctx, uint64_t p, uint64_t q, uint64_t c, int dxf, int
         tok = stage_begin(ctx, PM_STAGE_OTHER);
         k_res_eval_finish<<<1024, 256, 0, ctx->stream>>>(pe);
         // 2. H(alpha_l) and Res(alpha_l) by the extended Euclidean algorithm, one warp per point
-        const size_t smv = (size_t)VIL_WARPS * 5 * (dmax + 2) * 8;
+        const size_t smv = (size_t)VIL_WARPS * 8 * (dmax + 2) * 8;
         if (smv > 48 * 1024) cudaFuncSetAttribute(k_vil_xgcd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv);
         k_vil_xgcd<<<(int)((delta + VIL_WARPS - 1) / VIL_WARPS), 32 * VIL_WARPS, smv, ctx->stream>>>(pe, dmax, m, Eip,
                                                                                                      resv);
