@@ -2,7 +2,7 @@
 
 Bit-exact: every residue of every tested output must match (the products
 are exact; there is no tolerance).  Sizes span several transform tiles, the
-column path (transforms longer than 2^13 points) and ragged lengths; the
+column path (transforms longer than 2^14 points) and ragged lengths; the
 full-size workloads are checked on sampled coefficients the oracle computes
 one by one.
 """
