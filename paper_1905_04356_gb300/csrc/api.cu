@@ -775,6 +775,8 @@ int pm_sync(pm_ctx *ctx)
     CK(cudaSetDevice(ctx->device));
     CKI(host_join(ctx));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->up) CK(cudaStreamSynchronize(ctx->up));   // also copies a failed call left in flight
+    if (ctx->dn) CK(cudaStreamSynchronize(ctx->dn));
     int st = 0;
     CK(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st) {
