@@ -468,6 +468,14 @@ def main():
             pmat.pmat_mul(ctx, W998["p"], A2, B2, out=C2)
         ts998 = timed(lambda i: pmat.pmat_mul(ctx, W998["p"], A2, B2, out=C2), args.steps)
 
+        # ---- the 4x4 . 4x4, length-256 product mod 998244353 (latency-bound: reported in us)
+        W1 = synth.product_c1(0)
+        A1, B1 = pmat.to_device(W1["A"]), pmat.to_device(W1["B"])
+        C1 = torch.empty((4, 4, 511), dtype=A1.dtype, device="cuda")
+        for _ in range(3):
+            pmat.pmat_mul(ctx, W1["p"], A1, B1, out=C1)
+        ts_c1 = timed(lambda i: pmat.pmat_mul(ctx, W1["p"], A1, B1, out=C1), args.steps)
+
         # ---- end to end: pmat_mul_host on pinned host buffers, every host<->device copy
         #      inside the timed region (overlapped with the stages by the library)
         Ap = torch.from_numpy(Ah.view(np.int64)).pin_memory()
@@ -552,6 +560,7 @@ def main():
             "e2e_single_call_latency_ms": round(e2e_latency_ms, 4),
             "tensor_core_vs_cuda_core": tc_report(ts_tc, st_tc, stages, pk),
             "c2_p998_ms": round(sum(ts998) / len(ts998), 4),
+            "c1_4x4_d256_p998_us": round(1000 * sum(ts_c1) / len(ts_c1), 1),
             "wall_s_timed_region": round(t_wall, 3),
             "paper_context": PAPER_CONTEXT,
         },
