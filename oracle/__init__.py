@@ -248,6 +248,8 @@ def bivariate_resultant_villard(p, f, g, m=0, threads=None):
         raise ValueError("too few evaluation points in F_p")
     if rc[0] == 2:
         raise ValueError("det Q vanishes at the normalisation point: input not generic")
+    if rc[0] == 3:
+        raise ValueError("det Q is not a constant multiple of Res: input not generic")
     return R
 
 

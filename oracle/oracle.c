@@ -746,6 +746,14 @@ static void specialise(u64 p, int dx, int dy, const u64 *f, u64 x, u64 *out)
     }
 }
 
+/* det of the top-left m x m block of the 2m x 2m basis P (entries of length len) at x. */
+static u64 det_at_first(u64 p, int m, int mm, const u64 *P, i64 len, u64 x, u64 *Qv)
+{
+    for (int i = 0; i < m; i++)
+        for (int j = 0; j < m; j++) Qv[i * m + j] = poly_eval(P + ((i64)i * mm + j) * len, len, x, p);
+    return det_destroy(p, m, Qv);
+}
+
 /* Sec. 5.2, the variant of Algorithm 6 (Determinant) for Res_z(f, g): with P(x) the
  * Sylvester matrix of f, g in z (nu = dyf + dyg), H the m x m block of P^-1 named below,
  * delta = 2 ceil(nu / m) d + 1 values of H, an interpolant basis of [H; -I] (Algorithm 5)
@@ -757,8 +765,9 @@ static void specialise(u64 p, int dx, int dy, const u64 *f, u64 x, u64 *out)
  * in increasing power (H J, J the reversal), which leaves Q unchanged.
  * Points: the smallest non-negative integers where both leading coefficients and Res are
  * nonzero (delta of them) for H; 0 .. D for det Q.  Returns 0, or 1 when the points run out
- * (Res identically zero, or p too small), 2 when det Q vanishes at the normalisation point
- * (input not generic). */
+ * (Res identically zero, or p too small), 2 when det Q vanishes at the normalisation point,
+ * 3 when the normalised det Q differs from Res at one of the delta points (2 and 3: the input
+ * is not generic). */
 int orc_bivariate_resultant_villard(u64 p, int dxf, int dyf, const u64 *f, int dxg, int dyg, const u64 *g, int m,
                                     u64 *R)
 {
@@ -816,6 +825,16 @@ int orc_bivariate_resultant_villard(u64 p, int dxf, int dyf, const u64 *f, int d
                 const u64 scale = f_mul(res0, orc_invmod(dq, p), p);
                 for (i64 k = 0; k < N; k++) ys[k] = f_mul(ys[k], scale, p);
             }
+        }
+        /* The properties the method rests on hold for generic input only: det Q must be a
+         * constant multiple of Res.  Check the normalised det Q against Res at the delta
+         * points (det Q evaluated there by Horner, Res by the univariate resultant). */
+        const u64 sc = rc ? 0 : f_mul(res0, orc_invmod(det_at_first(p, m, mm, P, len, xs[0], Qv), p), p);
+        for (i64 l = 0; !rc && l < delta; l++) {
+            const u64 dq = det_at_first(p, m, mm, P, len, xs[l], Qv);
+            specialise(p, dxf, dyf, f, xs[l], fa);
+            specialise(p, dxg, dyg, g, xs[l], ga);
+            if (f_mul(dq, sc, p) != orc_univ_resultant(p, fa, dyf, ga, dyg)) rc = 3;
         }
         if (!rc) interp_int_points(p, pts, ys, N, R);
         free(P); free(s0); free(rd); free(ys); free(pts); free(Qv);

@@ -140,3 +140,17 @@ def test_pm_intbasis_rejects_bad_arguments(ctx):
         with pytest.raises(PmError) as e:
             pmat.pm_intbasis(ctx, p, E, c, q, [0, 0])
         assert e.value.code == pmat.PM_EINVAL
+
+
+@pytest.mark.parametrize("case", [(P60, 3, 2, 1, 32, 5, 3, 1), (P60, 4, 2, 17, 1, 2, 3, 0), (97, 2, 3, 12, 2, 3, 5, 1),
+                                  (P60, 5, 5, 9, 4, 7, 2, 1)],
+                         ids=["one_point", "T1_one_cta", "m_lt_n_p97", "m_eq_n"])
+def test_pm_intbasis_edge_cases(ctx, case):
+    """One point; threshold 1 with the one-CTA leaf; m < n over F_97; m = n (no fast path)."""
+    p, m, n, sigma, T, c, q, cluster = case
+    g = synth.rng(sum(case) & 0xfff)
+    E = synth.uniform(g, (m, n, sigma), p, np.uint64)
+    s = [(3 * i) % 4 - 1 for i in range(m)]
+    P, rd = _run(ctx, p, E, c, q, s, T, cluster=cluster)
+    Pexp, rdexp = oracle.pmintbasis(p, E, _points(p, c, q, sigma), s, T)
+    assert np.array_equal(P, Pexp) and np.array_equal(rd, rdexp)

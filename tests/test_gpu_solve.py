@@ -111,3 +111,15 @@ def test_solve_bench_workload_identity(ctx):
         lhs = oracle.pmat_coeff(p, A, u, i, 0, t)
         rhs = oracle.pmat_coeff(p, F, np.ascontiguousarray(b[i:i + 1]), 0, 0, t)
         assert lhs == rhs, (i, t)
+
+
+@pytest.mark.parametrize("case", [(3, 2, 3, 2), (P60, 1, 1, 1), (5, 3, 2, 3)], ids=["F3", "constant_1x1", "F5"])
+def test_solve_small_fields_and_trivial(ctx, case):
+    """Tiny fields (many singular residuals in the reconstruction) and the constant 1 x 1 system."""
+    p, n, dA, db = case
+    for seed in range(4):
+        A = _matrix(1000 + seed, p, n, dA, 8)
+        b = _vector(2000 + seed, p, n, db, 8)
+        u, f, df, du = _gpu(ctx, p, A, b)
+        ue, fe = oracle.solve(p, A, b)
+        assert np.array_equal(f, fe) and np.array_equal(u, ue), seed

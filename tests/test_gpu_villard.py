@@ -119,3 +119,26 @@ def test_villard_rejects_bad_arguments(ctx):
     with pytest.raises(PmError) as e:
         _gpu(ctx, [P60], [f], [g], 1)
     assert e.value.code == pmat.PM_EINVAL
+
+
+@pytest.mark.parametrize("degs", [(6, 4, 0, 5), (3, 2, 3, 2)], ids=["g_const_in_x", "small"])
+def test_villard_degenerate_x_degrees(ctx, degs):
+    """g constant in x, and a small case with m = 2: the resultant equals the direct method's."""
+    dxf, dyf, dxg, dyg = degs
+    f, g = _fg(sum(degs), P60, dxf, dyf, dxg, dyg)
+    got = _gpu(ctx, [P60], [f], [g], 0)[0]
+    assert np.array_equal(got, oracle.bivariate_resultant(P60, f, g))
+
+
+def test_villard_non_generic_input_is_refused(ctx):
+    """f constant in x (degrees 0 / 5 against 4 / 6): H's denominator is a proper factor of Res,
+    the oracle's own check reports the input as not generic, and the device's check of the
+    normalised det Q against Res at the delta points must refuse it (PM_EUNSUPPORTED) rather
+    than return a wrong resultant."""
+    from paper_1905_04356_gb300 import PmError, pmat
+    f, g = _fg(15, P60, 0, 5, 4, 6)
+    with pytest.raises(ValueError, match="not generic"):
+        oracle.bivariate_resultant_villard(P60, f, g, 0)
+    with pytest.raises(PmError) as e:
+        _gpu(ctx, [P60], [f], [g], 0)
+    assert e.value.code == pmat.PM_EUNSUPPORTED

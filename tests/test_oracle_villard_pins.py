@@ -71,3 +71,14 @@ def test_villard_common_factor_has_no_usable_point():
                     gx[j1 + j2, i1 + i2] = (int(gx[j1 + j2, i1 + i2]) + int(h[j1, i1]) * int(g0[j2, i2])) % p
     with pytest.raises(ValueError):
         oracle.bivariate_resultant_villard(p, fx, gx, 2)
+
+
+def test_villard_non_generic_input_is_reported():
+    """f constant in x: the denominator of H is a proper factor of Res, det Q is no longer a
+    constant multiple of it, and the oracle's check against Res at the delta points reports it
+    (the direct method still gives the resultant)."""
+    p = P60
+    f, g = _fg(15, p, 0, 5, 4, 6)
+    with pytest.raises(ValueError, match="not generic"):
+        oracle.bivariate_resultant_villard(p, f, g, 0)
+    assert oracle.bivariate_resultant(p, f, g).any()
