@@ -433,6 +433,22 @@ struct InvLists {
 };
 }  // namespace
 
+// Prime i's transforms of a request's A: the caller's (At, At_out) or the workspace's.
+static u32 *a_transform(const ProdReq &q, const Plan &P, char *ws_A, size_t i)
+{
+    if (q.At) return (u32 *)q.At + i * (P.bA / 4);
+    if (q.At_out) return q.At_out + i * (P.bA / 4);
+    return (u32 *)(ws_A + i * P.bA);
+}
+
+size_t prod_operand_bytes(pm_ctx *ctx, uint64_t p, int n, int64_t dmin, int lg, int64_t entries)
+{
+    std::vector<PrimeSlot *> pr;
+    bool direct = false;
+    if (choose_primes(ctx, p, n, dmin, lg, pr, direct)) return 0;
+    return pr.size() * align256((size_t)entries * ((size_t)1 << lg) * 4);
+}
+
 // Pointwise m x n . n x k products at every point of one prime's transforms: tensor-core limb
 // products where the shape allows (m, n, k <= 32) when that form is requested, small inner
 // dimensions (n <= 8) by a streaming kernel (one launch per n), matrix-vector products
@@ -572,7 +588,9 @@ int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
                 const Bufs &b = buf[r - r0];
                 for (size_t i = 0; i < P.pr.size(); i++) {
                     PrimeDev D = prime_dev(*P.pr[i], lg);
-                    add_forward(D, q.A, q.w, q.sA, q.dA, q.m * q.n, (u32 *)(b.A + i * P.bA), lg, blk, bn, col, cn);
+                    if (!q.At)                          // A's transforms: computed (kept if asked)
+                        add_forward(D, q.A, q.w, q.sA, q.dA, q.m * q.n, a_transform(q, P, b.A, i), lg, blk, bn, col,
+                                    cn);
                     add_forward(D, q.B, q.w, q.sB, q.dB, q.n * q.k, (u32 *)(b.B + i * P.bB), lg, blk, bn, col, cn);
                 }
             }
@@ -588,7 +606,7 @@ int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
                 const Plan &P = plan[r];
                 const Bufs &b = buf[r - r0];
                 for (size_t i = 0; i < P.pr.size(); i++)
-                    add_pointwise(ctx, pl, (u32 *)(b.A + i * P.bA), (u32 *)(b.B + i * P.bB), (u32 *)(b.C + i * P.bC),
+                    add_pointwise(ctx, pl, a_transform(q, P, b.A, i), (u32 *)(b.B + i * P.bB), (u32 *)(b.C + i * P.bC),
                                   q.m, q.n, q.k, q.lg, prime_dev(*P.pr[i], q.lg));
             }
             CKI(launch_pointwise_lists(ctx, pl));

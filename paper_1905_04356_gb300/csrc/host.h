@@ -82,14 +82,23 @@ void *arena_alloc(pm_ctx *ctx, size_t bytes);
 int prod_slice(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA, int64_t sA,
                const void *B, int64_t dB, int64_t sB, int64_t off, int64_t len, int lg, void *C, int64_t sC);
 
-// One product request (the arguments of prod_slice).
+// One product request (the arguments of prod_slice).  An operand A used by many products
+// can keep its transforms: At_out receives them (all primes, [prime][entry][L] words, prime
+// stride prod_operand_bytes / K), At supplies them instead of transforming A again; both are
+// valid for requests with the same p, inner dimension, min(dA, dB) and transform length.
 struct ProdReq {
     uint64_t p;
     int w, m, n, k, lg;
     const void *A, *B;
     void *C;
     int64_t dA, sA, dB, sB, off, len, sC;
+    const u32 *At = nullptr;
+    u32 *At_out = nullptr;
 };
+
+// Bytes of an At / At_out buffer for an operand of `entries` entries in requests with these
+// parameters (0 if the modulus cannot be handled).
+size_t prod_operand_bytes(pm_ctx *ctx, uint64_t p, int n, int64_t dmin, int lg, int64_t entries);
 // Run many independent product requests: planned together, their jobs binned by
 // transform length into shared launches, the workspace chunked under a cap.
 int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count);

@@ -230,12 +230,20 @@ extern "C" int pmat_solve_series(pm_ctx *ctx, uint64_t p, int w, int n, const vo
     size_t bE;
     const size_t wM = inv_scratch_words(n, delta, w, &bE);
     const size_t bS = (size_t)n * n * delta * w, bR = (size_t)n * delta * w;
-    CKI(arena_reserve(ctx, wM * 8 + bE + bS + bR + 4 * 256));
+    // S and A are the same in every full digit: their transforms are kept after the first
+    const int lgS = ceil_log2(2 * delta - 1) < 4 ? 4 : ceil_log2(2 * delta - 1);
+    const int lgA = ceil_log2(dA + delta - 1) < 4 ? 4 : ceil_log2(dA + delta - 1);
+    const bool cache = N > 2 * delta;                 // at least two full digits reuse them
+    const size_t bTS = cache ? prod_operand_bytes(ctx, p, n, delta, lgS, (int64_t)n * n) : 0;
+    const size_t bTA = cache ? prod_operand_bytes(ctx, p, n, dA, lgA, (int64_t)n * n) : 0;
+    CKI(arena_reserve(ctx, wM * 8 + bE + bS + bR + bTS + bTA + 6 * 256));
     u64 *M = (u64 *)arena_alloc(ctx, wM * 8);
     void *E = arena_alloc(ctx, bE);
     void *S = arena_alloc(ctx, bS);
     void *R = arena_alloc(ctx, bR);
-    if (!M || !E || !S || !R) return pm_fail(ctx, PM_ENOMEM, "arena too small");
+    u32 *TS = bTS ? (u32 *)arena_alloc(ctx, bTS) : nullptr;
+    u32 *TA = bTA ? (u32 *)arena_alloc(ctx, bTA) : nullptr;
+    if (!M || !E || !S || !R || (bTS && !TS) || (bTA && !TA)) return pm_fail(ctx, PM_ENOMEM, "arena too small");
     CKI(inv_trunc_core(ctx, p, w, n, A, dA, delta, S, M, E));
     // r_0 = b, zero-padded to length delta
     CKI(pm_cuda(ctx, cudaMemsetAsync(R, 0, bR, ctx->stream), "residual"));
@@ -245,10 +253,27 @@ extern "C" int pmat_solve_series(pm_ctx *ctx, uint64_t p, int w, int n, const vo
         const int64_t len = N - off < delta ? N - off : delta;
         char *y = (char *)v + off * w;
         // y_i = S r_i mod x^len (no aliasing)
-        CKI(prod_slice(ctx, p, w, n, n, 1, S, len, delta, R, len, delta, 0, len, ceil_log2(2 * len - 1), y, N));
+        ProdReq q1;
+        q1.p = p; q1.w = w; q1.m = n; q1.n = n; q1.k = 1;
+        q1.lg = ceil_log2(2 * len - 1) < 4 ? 4 : ceil_log2(2 * len - 1);
+        q1.A = S; q1.dA = len; q1.sA = delta; q1.B = R; q1.dB = len; q1.sB = delta;
+        q1.off = 0; q1.len = len; q1.C = y; q1.sC = N;
+        if (TS && len == delta) {                      // full digits: S's transforms kept after the first
+            if (i == 0) q1.At_out = TS;
+            else q1.At = TS;
+        }
+        CKI(prod_batch(ctx, &q1, 1));
         if (off + delta >= N) break;
         // r_{i+1} = -(coefficients delta .. 2 delta - 1 of A y_i) (no aliasing)
-        CKI(prod_slice(ctx, p, w, n, n, 1, A, dA, dA, y, delta, N, delta, delta, ceil_log2(dA + delta - 1), R, delta));
+        ProdReq q2;
+        q2.p = p; q2.w = w; q2.m = n; q2.n = n; q2.k = 1; q2.lg = lgA;
+        q2.A = A; q2.dA = dA; q2.sA = dA; q2.B = y; q2.dB = delta; q2.sB = N;
+        q2.off = delta; q2.len = delta; q2.C = R; q2.sC = delta;
+        if (TA) {                                      // A's transforms, likewise
+            if (i == 0) q2.At_out = TA;
+            else q2.At = TA;
+        }
+        CKI(prod_batch(ctx, &q2, 1));
         negate_slice(ctx, R, w, delta, 0, delta, n, p);
         CKI(pm_cuda(ctx, cudaGetLastError(), "k_negate_slice"));
     }
