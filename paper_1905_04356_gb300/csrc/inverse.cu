@@ -300,11 +300,18 @@ extern "C" int pmat_inv_slices(pm_ctx *ctx, uint64_t p, int w, int n, const void
     size_t bE;
     const size_t wM = inv_scratch_words(n, W, w, &bE);
     const size_t bR = nn * (size_t)(D + 1) * w;
-    CKI(arena_reserve(ctx, wM * 8 + bE + 2 * bR + 4 * 256));
+    const int lgE = ceil_log2(2 * D + 1) < 4 ? 4 : ceil_log2(2 * D + 1);   // no aliasing in either
+    const int lgS = ceil_log2(3 * D + 1) < 4 ? 4 : ceil_log2(3 * D + 1);
+    // transforms kept across products: S_i's for its two products, A's for all of them
+    const size_t bTS = K > 1 ? prod_operand_bytes(ctx, p, n, D + 1, lgS, (int64_t)nn) : 0;
+    const size_t bTA = K > 1 ? prod_operand_bytes(ctx, p, n, dA, lgE, (int64_t)nn) : 0;
+    CKI(arena_reserve(ctx, wM * 8 + bE + 2 * bR + bTS + bTA + 6 * 256));
     u64 *M = (u64 *)arena_alloc(ctx, wM * 8);
     void *E = arena_alloc(ctx, bE);
     char *Elo = (char *)arena_alloc(ctx, bR), *Ehi = (char *)arena_alloc(ctx, bR);
-    if (!M || !E || !Elo || !Ehi) return pm_fail(ctx, PM_ENOMEM, "arena too small");
+    u32 *TS = bTS ? (u32 *)arena_alloc(ctx, bTS) : nullptr;
+    u32 *TA = bTA ? (u32 *)arena_alloc(ctx, bTA) : nullptr;
+    if (!M || !E || !Elo || !Ehi || (bTS && !TS) || (bTA && !TA)) return pm_fail(ctx, PM_ENOMEM, "arena too small");
     char *S0 = (char *)S;
     const size_t slice = nn * (size_t)W * w;
     CKI(inv_trunc_core(ctx, p, w, n, A, dA, W, S0, M, E));
@@ -325,9 +332,9 @@ extern "C" int pmat_inv_slices(pm_ctx *ctx, uint64_t p, int w, int n, const void
         q.off = off; q.len = len; q.C = Cp; q.sC = sc;
         return q;
     };
-    const int lgE = ceil_log2(2 * D + 1), lgS = ceil_log2(3 * D + 1);   // no aliasing in either
     {
         ProdReq q = req(A, dA, dA, S0 + D * w, D + 1, W, 0, D + 1, lgE, Ehi, D + 1);   // E_D
+        q.At_out = TA;                                   // A's transforms, for every later product
         CKI(prod_batch(ctx, &q, 1));
     }
     for (int i = 1; i < K; i++) {
@@ -335,10 +342,14 @@ extern "C" int pmat_inv_slices(pm_ctx *ctx, uint64_t p, int w, int n, const void
         char *Sc = S0 + (size_t)i * slice;
         ProdReq q[2] = {req(Sp, W, W, Elo, D + 1, D + 1, D, D, lgS, Sc, W),                    // lower half
                         req(Sp, W, W, Ehi, D + 1, D + 1, D, D + 1, lgS, Sc + D * w, W)};       // upper half
+        q[0].At_out = TS;                                // the forward stage of the call fills TS
+        q[1].At = TS;                                    // before its pointwise stage reads it
         CKI(prod_batch(ctx, q, 2));
         if (i + 1 < K) {
             ProdReq r[2] = {req(A, dA, dA, Sc, D + 1, W, 0, D + 1, lgE, Elo, D + 1),
                             req(A, dA, dA, Sc + D * w, D + 1, W, 0, D + 1, lgE, Ehi, D + 1)};
+            r[0].At = TA;
+            r[1].At = TA;
             CKI(prod_batch(ctx, r, 2));
         }
     }
