@@ -208,22 +208,33 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"
         torch.cuda.synchronize()
         return a.elapsed_time(b) / n
 
+    def stage_split(fn, n=3):
+        """Per-stage device time of one call (events around each stage on the stream): the
+        median over n stage-timed calls, so that one disturbed call does not skew the split;
+        with the product work counters of one call."""
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
+        ctx.stage_times()
+        ctx.work(reset=True)
+        runs = []
+        for _ in range(n):
+            fn()
+            runs.append(ctx.stage_times())
+        wk = ctx.work(reset=True)
+        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
+        ctx.sync()
+        st = {k: statistics.median(r[k][0] for r in runs) for k in runs[0] if runs[0][k][1]}
+        return st, {k: v // n for k, v in wk.items()}
+
     def pm_basis():
         W = synth.pmbasis_c3(0)
         F = pmat.to_device(W["F"])
         run = lambda: pmat.pm_basis(ctx, W["p"], F, W["d"], W["shift"])  # noqa: E731
         out = {"pm_basis_32x16_d8192_ms": round(ev_ms(run, reps), 2)}
-        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
-        ctx.stage_times()
-        ctx.work(reset=True)
-        run()
-        st = ctx.stage_times()
-        wk = ctx.work(reset=True)
-        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
-        out["pm_basis_stage_ms"] = {k: round(v[0], 2) for k, v in st.items() if v[1]}
-        out["pm_basis_leaf_us_per_order_step"] = round(st["leaf"][0] * 1000 / W["d"], 2)
+        st, wk = stage_split(run)
+        out["pm_basis_stage_ms"] = {k: round(v, 2) for k, v in st.items()}
+        out["pm_basis_leaf_us_per_order_step"] = round(st["leaf"] * 1000 / W["d"], 2)
         # the product work of one call (library counters) over the product stages' time
-        prod_ms = sum(st[k][0] for k in ("fwd_ntt", "pointwise", "inv_ntt", "crt"))
+        prod_ms = sum(st[k] for k in ("fwd_ntt", "pointwise", "inv_ntt", "crt"))
         pk = peaks()
         out["pm_basis_product_work"] = {
             "bytes": wk["bytes"], "pointwise_macs": wk["macs"], "butterflies": wk["butterflies"],
@@ -250,14 +261,8 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"
         n0 = ctx.launches()
         ms = ev_ms(lambda: pmat.pmat_mul_batched(ctx, dev, outs), 2)
         out = {"batched_512_ms": round(ms, 2), "batched_512_launches_per_call": (ctx.launches() - n0) // 3}
-        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
-        ctx.stage_times()
-        ctx.work(reset=True)
-        pmat.pmat_mul_batched(ctx, dev, outs)
-        st = ctx.stage_times()
-        wk = ctx.work(reset=True)
-        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
-        out["batched_512_stage_ms"] = {k: round(v[0], 2) for k, v in st.items() if v[1]}
+        st, wk = stage_split(lambda: pmat.pmat_mul_batched(ctx, dev, outs))
+        out["batched_512_stage_ms"] = {k: round(v, 2) for k, v in st.items()}
         pk = peaks()
         out["batched_512_work"] = {"bytes": wk["bytes"], "pointwise_macs": wk["macs"], "butterflies": wk["butterflies"],
                                    "compulsory_frac_hbm": round(wk["bytes"] / (ms * 1e-3) / 1e9 /
@@ -271,13 +276,7 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"
         X = torch.empty((32, 32, W["t"]), dtype=A.dtype, device="cuda")
         run = lambda: pmat.pmat_inv_trunc(ctx, W["p"], A, W["t"], out=X)  # noqa: E731
         out = {"inv_trunc_32x32_t4096_ms": round(ev_ms(run, reps), 3)}
-        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
-        ctx.stage_times()
-        run()
-        st = ctx.stage_times()
-        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
-        ctx.sync()
-        out["inv_trunc_stage_ms"] = {k: round(v[0], 3) for k, v in st.items() if v[1]}
+        out["inv_trunc_stage_ms"] = {k: round(v, 3) for k, v in stage_split(run)[0].items()}
         return out
 
     def solve():
@@ -286,13 +285,7 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"
         v = torch.empty((32, 1, W["N"]), dtype=A.dtype, device="cuda")
         run = lambda: pmat.pmat_solve_series(ctx, W["p"], A, b, W["N"], out=v)  # noqa: E731
         out = {"solve_series_32x32_d4096_N32768_ms": round(ev_ms(run, reps), 3)}
-        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
-        ctx.stage_times()
-        run()
-        st = ctx.stage_times()
-        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
-        ctx.sync()
-        out["solve_series_stage_ms"] = {k: round(v2[0], 3) for k, v2 in st.items() if v2[1]}
+        out["solve_series_stage_ms"] = {k: round(v, 3) for k, v in stage_split(run)[0].items()}
         return out
 
     def slices():
@@ -311,12 +304,7 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"
         P = torch.empty((m, m, sigma + 1), dtype=E.dtype, device="cuda")
         run = lambda: pmat.pm_intbasis(ctx, W["p"], E, W["c"], W["q"], W["shift"], out=P)  # noqa: E731
         out = {"pm_intbasis_32x16_s8192_ms": round(ev_ms(run, reps), 2)}
-        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
-        ctx.stage_times()
-        run()
-        st = ctx.stage_times()
-        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
-        out["pm_intbasis_stage_ms"] = {k: round(v[0], 2) for k, v in st.items() if v[1]}
+        out["pm_intbasis_stage_ms"] = {k: round(v, 2) for k, v in stage_split(run)[0].items()}
         return out
 
     def linsolve():
@@ -324,12 +312,7 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"
         A, b = pmat.to_device(W["A"]), pmat.to_device(W["b"])
         run = lambda: pmat.pmat_solve(ctx, W["p"], A, b)  # noqa: E731
         out = {"solve_16x16_d256_ms": round(ev_ms(run, reps), 2)}
-        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
-        ctx.stage_times()
-        run()
-        st = ctx.stage_times()
-        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
-        out["solve_stage_ms"] = {k: round(v[0], 2) for k, v in st.items() if v[1]}
+        out["solve_stage_ms"] = {k: round(v, 2) for k, v in stage_split(run)[0].items()}
         return out
 
     def villard():
@@ -337,12 +320,7 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"
         f1, g1 = pmat.to_device(np.stack(R["f"][:1])), pmat.to_device(np.stack(R["g"][:1]))
         run = lambda: pmat.bivariate_resultant_villard(ctx, R["primes"][:1], f1, g1)  # noqa: E731
         out = {"resultant_villard_150_1prime_ms": round(ev_ms(run, reps), 2)}
-        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 1)
-        ctx.stage_times()
-        run()
-        st = ctx.stage_times()
-        ctx.set_option(pmat.PM_OPT_STAGE_TIMING, 0)
-        out["resultant_villard_stage_ms"] = {k: round(v[0], 2) for k, v in st.items() if v[1]}
+        out["resultant_villard_stage_ms"] = {k: round(v, 2) for k, v in stage_split(run)[0].items()}
         return out
 
     out = {}

@@ -128,6 +128,27 @@ __device__ __forceinline__ int find_job(const int *blk_start, int b)
 template <int LO>
 __device__ __forceinline__ constexpr int poff(int j) { return j * LO + ((j * LO) >> 5); }
 
+// Coefficients x and x + 1 (x even) of an entry, as load_coeff, zero from src_len on: one
+// vector load when the pair is aligned (vec) and inside the entry.
+__device__ __forceinline__ void load_pair(const void *src, int mode, i64 idx, int x, int len, bool vec,
+                                          const PrimeDev &P, u32 &a, u32 &b)
+{
+    if (vec && x + 1 < len) {
+        if (mode == 8) {
+            const ulonglong2 t = __ldg((const ulonglong2 *)((const u64 *)src + idx));
+            a = reduce64(t.x, P);
+            b = reduce64(t.y, P);
+        } else {
+            const uint2 t = __ldg((const uint2 *)((const u32 *)src + idx));
+            a = mode == 4 ? csub(shoup_mul(t.x, 1u, P.ones, P.q), P.q) : t.x;
+            b = mode == 4 ? csub(shoup_mul(t.y, 1u, P.ones, P.q), P.q) : t.y;
+        }
+    } else {
+        a = x < len ? load_coeff(src, mode, idx, P) : 0u;
+        b = x + 1 < len ? load_coeff(src, mode, idx + 1, P) : 0u;
+    }
+}
+
 template <int LG, int R0>
 __device__ __forceinline__ void fwd_first_t(u32 (&v)[16], u32 *X, const FwdJob &J, i64 e, bool act, int tid)
 {
@@ -135,6 +156,37 @@ __device__ __forceinline__ void fwd_first_t(u32 (&v)[16], u32 *X, const FwdJob &
     const u32 q = J.P.q, q2 = J.P.q2;
     const char *src = (const char *)J.src;
     const i64 sb = e * J.src_stride;
+    if constexpr (R0 == 1 && LG > 1) {
+        // radix-2 stage: the thread takes groups g0 = 2 (tid + u TPT) and g0 + 1 (u < 4), so each
+        // pair of points is one vector load of the input and the two twiddles one 16-byte load
+        const int wsz = J.src_mode == 8 ? 16 : 8;
+        const bool vec = ((reinterpret_cast<uintptr_t>(src) + (uintptr_t)(sb * (J.src_mode == 8 ? 8 : 4))) &
+                          (uintptr_t)(wsz - 1)) == 0;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int g0 = 2 * (tid + u * TPT);
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                u32 a = 0u, b2 = 0u;
+                if (act) load_pair(src, J.src_mode, sb + g0 + j * LO, g0 + j * LO, J.src_len, vec, J.P, a, b2);
+                v[4 * u + j] = a;
+                v[4 * u + 2 + j] = b2;
+            }
+            const uint4 w2 = __ldg((const uint4 *)(J.P.twf + LO + g0));
+            bfly_dif(v[4 * u], v[4 * u + 1], make_uint2(w2.x, w2.y), q, q2);
+            bfly_dif(v[4 * u + 2], v[4 * u + 3], make_uint2(w2.z, w2.w), q, q2);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                u32 *xb = X + spad(2 * (tid + u * TPT) + h);
+#pragma unroll
+                for (int j = 0; j < 2; j++) xb[poff<LO>(j)] = v[4 * u + 2 * h + j];
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int it = 0; it < (16 >> R0); it++) {
         const int g = tid + it * TPT;
