@@ -286,6 +286,13 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"
         run = lambda: pmat.pmat_solve_series(ctx, W["p"], A, b, W["N"], out=v)  # noqa: E731
         out = {"solve_series_32x32_d4096_N32768_ms": round(ev_ms(run, reps), 3)}
         out["solve_series_stage_ms"] = {k: round(v, 3) for k, v in stage_split(run)[0].items()}
+        # the same series by high-order lifting (3 slices, 3 levels of 8 residues), the paper's
+        # other lifting column
+        v2 = torch.empty_like(v)
+        run2 = lambda: pmat.pmat_solve_series_hol(ctx, W["p"], A, b, W["N"], out=v2)  # noqa: E731
+        out["solve_series_hol_32x32_d4096_N32768_ms"] = round(ev_ms(run2, reps), 3)
+        out["solve_series_hol_stage_ms"] = {k: round(v3, 3) for k, v3 in stage_split(run2)[0].items()}
+        out["solve_series_hol_equals_dixon"] = bool(torch.equal(v, v2))
         return out
 
     def slices():

@@ -27,6 +27,8 @@
  *                                 algorithm over the truncated inverse
  *   pmat_inv_slices               Sec. 4, high-order lifting: slices of A^-1
  *                                 at degrees around 2^i (d - 1)
+ *   pmat_solve_series_hol         Sec. 4, high-order lifting: A^-1 b mod x^N
+ *                                 from the slices
  *   pmat_solve                    Sec. 4, lifting solver: (u, f) with
  *                                 A u = f b by Dixon's lifting and vector
  *                                 rational reconstruction (PM-Basis)
@@ -348,6 +350,23 @@ int pmat_solve(pm_ctx *ctx, uint64_t p, int n, const void *A, int64_t dA,
  * undefined and pm_sync returns PM_EDOMAIN.  Asynchronous; uses the driver arena. */
 int pmat_inv_slices(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA, int K,
                     void *S);
+
+/* Power-series solution of A v = b by high-order lifting (Sec. 4, "Linear
+ * system solving": Storjohann's high-order lifting; the paper's table there
+ * sets it against Dixon's lifting).  Same arguments and the same result as
+ * pmat_solve_series: v = A^-1 b mod x^N (DEVICE n x 1, entries of length N).
+ * Method: with D = dA - 1, X = A^-1 and the residues rho_m(w) = x^-m (w - A
+ * (X w mod x^m)), the k slices S_0 .. S_(k-1) of pmat_inv_slices give jumps
+ * rho_(K_i), K_i = (2^i + 1) D, each two products (by S_i, then by A); k levels
+ * of a binary tree put 2^k residues of b at positions (x + popcount x) D,
+ * x < 2^k, at most 2D apart, and S_0 times all of them at once gives v.  k is
+ * the least with (2^k + k + 1) D + 1 >= N.  Requires p prime, 1 <= n <= 128,
+ * dA >= 2, 1 <= db <= dA, 3D + 1 <= 2^20, N <= 2^19 and 2^k <= 256
+ * (PM_EINVAL otherwise).  A(0) singular: v is undefined and pm_sync returns
+ * PM_EDOMAIN.  Allocates its buffers on the context's stream (stream-ordered)
+ * and uses the driver arena for the slices.  Asynchronous. */
+int pmat_solve_series_hol(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA,
+                          const void *b, int64_t db, int64_t N, void *v);
 
 #ifdef __cplusplus
 }

@@ -9,7 +9,10 @@
 //   E = coefficients k .. kk-1 of A.X_k               (middle product)
 //   X_kk = X_k - x^k (X_k . E mod x^(kk-k))           (truncated product)
 // both through the product hot path (prod_slice), then one negation pass.
+#include <algorithm>
 #include <cstring>
+#include <utility>
+#include <vector>
 
 #include "host.h"
 
@@ -300,8 +303,11 @@ extern "C" int pmat_inv_slices(pm_ctx *ctx, uint64_t p, int w, int n, const void
     size_t bE;
     const size_t wM = inv_scratch_words(n, W, w, &bE);
     const size_t bR = nn * (size_t)(D + 1) * w;
-    const int lgE = ceil_log2(2 * D + 1) < 4 ? 4 : ceil_log2(2 * D + 1);   // no aliasing in either
-    const int lgS = ceil_log2(3 * D + 1) < 4 ? 4 : ceil_log2(3 * D + 1);
+    // cyclic lengths without aliasing: an output window [off, off + len) of a product of length P
+    // needs L >= max(P - off, off + len).  E = A S_i[..] mod x^(D+1): P = 2D + 1, off = 0.
+    // Halves of S_{i+1}: S_i (2D + 1) by E (D + 1), P = 3D + 1, off = D, len <= D + 1: L >= 2D + 1.
+    const int lgE = ceil_log2(2 * D + 1) < 4 ? 4 : ceil_log2(2 * D + 1);
+    const int lgS = lgE;
     // transforms kept across products: S_i's for its two products, A's for all of them
     const size_t bTS = K > 1 ? prod_operand_bytes(ctx, p, n, D + 1, lgS, (int64_t)nn) : 0;
     const size_t bTA = K > 1 ? prod_operand_bytes(ctx, p, n, dA, lgE, (int64_t)nn) : 0;
@@ -354,4 +360,158 @@ extern "C" int pmat_inv_slices(pm_ctx *ctx, uint64_t p, int w, int n, const void
         }
     }
     return PM_OK;
+}
+
+// ------------------------------------------------------------------ high-order lifting solution
+// A^-1 b mod x^N from the slices (Sec. 4, high-order lifting used for system solving).  With
+// X = A^-1, D = dA - 1 and rho_m(w) = x^-m (w - A (X w mod x^m)), the residue of w at position m:
+//   X w = (X w mod x^m) + x^m X rho_m(w),   rho_(m1 + m2) = rho_m2 o rho_m1,
+// and for deg w <= D, rho_m(w) (degree < D) depends only on coefficients m - D .. m - 1 of X w:
+//   rho_m(w) = -(coefficients D .. 2D - 1 of A U),   U = coefficients m - D .. m - 1 of X w.
+// For m = K_i = (2^i + 1) D, U = coefficients D .. 2D - 1 of S_i w: slice S_i holds exactly the
+// coefficients of X those need.  Residues of b are made in a binary tree: level i = k - 1 .. 0
+// moves every residue made so far one jump K_i further, so after k levels there is one residue
+// at position f(x) D for every x < 2^k, f(x) = x + popcount(x) (x's bits name its jumps).  Since
+// f(x + 1) - f(x) <= 2, sorted positions are at most 2D apart, and each residue w at position P
+// gives v's coefficients P .. P + 2D as S_0 w mod x^(2D + 1).  Every level is two products over
+// all of its residues at once, one matrix product by S_i and one by A, where Dixon's lifting
+// takes ceil(N / delta) matrix-vector steps one after the other.
+//
+// Storage: the residues are the columns of an n x 2^k matrix W (entries of length D + 1), column
+// j holding x = the k-bit reversal of j; level i then reads columns [0, c) and writes [c, 2c),
+// c = 2^(k-1-i), both contiguous column blocks.
+namespace {
+
+#define HOL_MAXR 256
+
+struct HolTable {
+    int cnt;                  // distinct residue positions, ascending
+    int col[HOL_MAXR];        // residue column at each
+    i64 pos[HOL_MAXR];
+};
+
+// v[r][t] = Y[r][j][t - pos_j], j the residue with the largest position <= t.
+__global__ void k_hol_assemble(void *v, int w, int n, i64 N, const void *Y, int R, i64 Ws,
+                               const __grid_constant__ HolTable T)
+{
+    const i64 total = (i64)n * N;
+    for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < total; x += (i64)gridDim.x * blockDim.x) {
+        const i64 r = x / N, t = x - r * N;
+        int lo = 0, hi = T.cnt - 1;                   // last entry with pos <= t (pos[0] = 0)
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (T.pos[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const i64 src = ((r * R + T.col[lo]) * Ws) + (t - T.pos[lo]);
+        if (w == 8) ((u64 *)v)[x] = ((const u64 *)Y)[src];
+        else ((u32 *)v)[x] = ((const u32 *)Y)[src];
+    }
+}
+
+int bitrev(int x, int k)
+{
+    int r = 0;
+    for (int i = 0; i < k; i++) r |= ((x >> i) & 1) << (k - 1 - i);
+    return r;
+}
+
+}  // namespace
+
+extern "C" int pmat_solve_series_hol(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA,
+                                     const void *b, int64_t db, int64_t N, void *v)
+{
+    if (!ctx) return PM_EINVAL;
+    CKI(check_inverse_args(ctx, p, w, n, A, dA, N, v));
+    if (db < 1 || !b) return pm_fail(ctx, PM_EINVAL, "need db >= 1 and b");
+    if (dA < 2 || db > dA) return pm_fail(ctx, PM_EINVAL, "high-order lifting needs dA >= 2 and db <= dA");
+    const int64_t D = dA - 1, Ws = 2 * D + 1, Lw = D + 1;
+    if (3 * D + 1 > (int64_t(1) << PM_MAX_LOG2L)) return pm_fail(ctx, PM_EINVAL, "degree too large for the transforms");
+    int k = 0;
+    while (((int64_t(1) << k) + k + 1) * D + 1 < N) k++;
+    if ((1 << k) > HOL_MAXR) return pm_fail(ctx, PM_EINVAL, "N needs more than 256 residues at this degree");
+    const int R = 1 << k, K = k > 0 ? k : 1, half = R > 1 ? R / 2 : 1;
+
+    // residue positions: sorted, distinct, gaps <= 2D, the last within 2D of N - 1
+    HolTable T;
+    {
+        std::vector<std::pair<int64_t, int>> ps;
+        for (int j = 0; j < R; j++) {
+            const int x = bitrev(j, k);
+            ps.push_back({(int64_t)(x + __builtin_popcount((unsigned)x)) * D, j});
+        }
+        std::sort(ps.begin(), ps.end());
+        T.cnt = 0;
+        for (auto &e : ps)
+            if (T.cnt == 0 || T.pos[T.cnt - 1] != e.first) { T.pos[T.cnt] = e.first; T.col[T.cnt] = e.second; T.cnt++; }
+        for (int i = 1; i < T.cnt; i++)
+            if (T.pos[i] - T.pos[i - 1] > 2 * D) return pm_fail(ctx, PM_EINVAL, "internal: residue gap");
+        if (N - 1 - T.pos[T.cnt - 1] > 2 * D) return pm_fail(ctx, PM_EINVAL, "internal: residue coverage");
+    }
+
+    const size_t nn = (size_t)n * n;
+    const size_t bS = (size_t)K * nn * Ws * w, bW = (size_t)n * R * Lw * w, bY = (size_t)n * R * Ws * w;
+    const size_t bT1 = (size_t)n * half * Lw * w, bU = (size_t)n * half * D * w;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t total = al(bS) + al(bW) + al(bY) + 2 * al(bT1) + al(bU);
+    char *buf = nullptr;
+    if (cudaMallocAsync((void **)&buf, total, ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return pm_fail(ctx, PM_ENOMEM, "pmat_solve_series_hol workspace allocation failed");
+    }
+    char *S = buf, *Wm = S + al(bS), *Y = Wm + al(bW), *T1 = Y + al(bY), *T2 = T1 + al(bT1), *U = T2 + al(bT1);
+    int rc = PM_OK;
+    auto req = [&](const void *Ap, int64_t da, int64_t sa, const void *Bp, int64_t dbb, int64_t sb, int kk,
+                   int64_t off, int64_t len, int lg, void *Cp, int64_t sc) {
+        ProdReq q;
+        q.p = p; q.w = w; q.m = n; q.n = n; q.k = kk; q.lg = lg < 4 ? 4 : lg;
+        q.A = Ap; q.dA = da; q.sA = sa; q.B = Bp; q.dB = dbb; q.sB = sb;
+        q.off = off; q.len = len; q.C = Cp; q.sC = sc;
+        return q;
+    };
+    do {
+        // slices S_0 .. S_(K-1)
+        if ((rc = pmat_inv_slices(ctx, p, w, n, A, dA, K, S))) break;
+        // W = [b, 0, ...]
+        if ((rc = pm_cuda(ctx, cudaMemsetAsync(Wm, 0, bW, ctx->stream), "residues"))) break;
+        if ((rc = pm_cuda(ctx, cudaMemcpy2DAsync(Wm, (size_t)R * Lw * w, b, (size_t)db * w, (size_t)db * w, (size_t)n,
+                                                 cudaMemcpyDeviceToDevice, ctx->stream), "residues")))
+            break;
+        // cyclic lengths without aliasing (an output window [off, off + len) of a product of
+        // length P needs L >= max(P - off, off + len)): S_i (2D + 1) by W (D + 1), window
+        // [D, 2D): 2D + 1; A (D + 1) by U (D), window [D, 2D): 2D; S_0 by W mod x^(2D + 1): 3D + 1
+        const int lgU = ceil_log2(2 * D + 1), lgR = ceil_log2(2 * D), lgY = ceil_log2(3 * D + 1);
+        for (int i = k - 1; i >= 0 && !rc; i--) {
+            const int c = 1 << (k - 1 - i);
+            const char *Si = S + (size_t)i * nn * Ws * w;
+            // the level's residues as an n x c block, then U = coefficients D .. 2D-1 of S_i . block
+            if ((rc = pm_cuda(ctx, cudaMemcpy2DAsync(T1, (size_t)c * Lw * w, Wm, (size_t)R * Lw * w, (size_t)c * Lw * w,
+                                                     (size_t)n, cudaMemcpyDeviceToDevice, ctx->stream), "gather")))
+                break;
+            ProdReq q1 = req(Si, Ws, Ws, T1, Lw, Lw, c, D, D, lgU, U, D);
+            if ((rc = prod_batch(ctx, &q1, 1))) break;
+            // new residues -(coefficients D .. 2D-1 of A . U), degree < D (coefficient D stays 0)
+            if ((rc = pm_cuda(ctx, cudaMemsetAsync(T2, 0, (size_t)n * c * Lw * w, ctx->stream), "residues"))) break;
+            ProdReq q2 = req(A, dA, dA, U, D, D, c, D, D, lgR, T2, Lw);
+            if ((rc = prod_batch(ctx, &q2, 1))) break;
+            negate_slice(ctx, T2, w, Lw, 0, D, (int64_t)n * c, p);
+            if ((rc = pm_cuda(ctx, cudaGetLastError(), "k_negate_slice"))) break;
+            if ((rc = pm_cuda(ctx, cudaMemcpy2DAsync(Wm + (size_t)c * Lw * w, (size_t)R * Lw * w, T2,
+                                                     (size_t)c * Lw * w, (size_t)c * Lw * w, (size_t)n,
+                                                     cudaMemcpyDeviceToDevice, ctx->stream), "scatter")))
+                break;
+        }
+        if (rc) break;
+        // v's coefficients from every residue: Y = S_0 . W mod x^(2D + 1), then assembled
+        ProdReq qy = req(S, Ws, Ws, Wm, Lw, Lw, R, 0, Ws, lgY, Y, Ws);
+        if ((rc = prod_batch(ctx, &qy, 1))) break;
+        const int64_t tot = (int64_t)n * N;
+        int grid = (int)((tot + 255) / 256);
+        if (grid > 152 * 16) grid = 152 * 16;
+        k_hol_assemble<<<grid, 256, 0, ctx->stream>>>(v, w, n, N, Y, R, Ws, T);
+        ctx->launches++;
+        rc = pm_cuda(ctx, cudaGetLastError(), "k_hol_assemble");
+    } while (0);
+    cudaFreeAsync(buf, ctx->stream);
+    return rc;
 }

@@ -77,6 +77,7 @@ def lib():
             "bivariate_resultant": ([P, i32, P, i32, i32, P, i32, i32, P, P], i32),
             "pmat_inv_trunc": ([P, u64, i32, i32, P, i64, i64, P], i32),
             "pmat_solve_series": ([P, u64, i32, i32, P, i64, P, i64, i64, P], i32),
+            "pmat_solve_series_hol": ([P, u64, i32, i32, P, i64, P, i64, i64, P], i32),
             "pmat_inv_slices": ([P, u64, i32, i32, P, i64, i32, P], i32),
         }
         for name, (args, res) in sig.items():
@@ -272,6 +273,19 @@ def pmat_solve_series(ctx: Context, p: int, A, b, N: int, out=None) -> torch.Ten
     v = _out(out, (n, 1, N), A)
     ctx._ck(lib().pmat_solve_series(ctx.h, p, width(A), n, A.data_ptr(), dA, b.data_ptr(), b.shape[2], N,
                                     v.data_ptr()))
+    return v
+
+
+def pmat_solve_series_hol(ctx: Context, p: int, A, b, N: int, out=None) -> torch.Tensor:
+    """v = A^-1 b mod x^N by high-order lifting (the same result as pmat_solve_series): needs
+    dA >= 2, db <= dA and N within 256 residues of degree dA - 1."""
+    A, b = _dev(A), _dev(b)
+    n, n2, dA = A.shape
+    if n != n2 or b.shape[0] != n or b.shape[1] != 1 or b.dtype != A.dtype:
+        raise ValueError("A must be n x n and b n x 1 of the same width")
+    v = _out(out, (n, 1, N), A)
+    ctx._ck(lib().pmat_solve_series_hol(ctx.h, p, width(A), n, A.data_ptr(), dA, b.data_ptr(), b.shape[2], N,
+                                        v.data_ptr()))
     return v
 
 

@@ -232,3 +232,77 @@ def test_inverse_slices_full_size_properties(ctx):
         for _ in range(12):
             r, c, t = rnd.randrange(n), rnd.randrange(n), rnd.randrange(D, 2 * D + 1)
             assert oracle.pmat_coeff(p, A, S[i], r, c, t) == 0, (i, r, c, t)
+
+
+# ------------------------------------------------------------ series solution by high-order lifting
+HOL_CASES = [
+    # p, w, n, dA, db, N   (D = dA - 1; k levels, 2^k residues: the least k with (2^k + k + 1) D + 1 >= N)
+    (P60, 8, 4, 9, 9, 200),          # k = 5
+    (synth.P998, 4, 3, 17, 5, 1000),  # k = 6, db < dA
+    (P60, 8, 5, 40, 40, 50),         # k = 0: N <= 2D + 1, one product by S_0
+    (P60, 8, 5, 40, 12, 79),         # k = 0 at the bound 2D + 1
+    (P60, 8, 5, 40, 12, 80),         # k = 1
+    (97, 4, 1, 3, 1, 500),           # n = 1, D = 2, k = 8: 256 residues
+    (2, 4, 3, 5, 5, 90),             # p = 2
+    (P62, 8, 2, 2, 2, 37),           # D = 1
+    (P60, 8, 32, 33, 33, 700),       # 32 x 32 blocks, k = 5
+    (synth.P998, 4, 3, 9, 9, 1),     # N = 1
+]
+
+
+@pytest.mark.parametrize("case", HOL_CASES, ids=[f"p{c[0]}_w{c[1]}_n{c[2]}_dA{c[3]}_db{c[4]}_N{c[5]}"
+                                                 for c in HOL_CASES])
+def test_series_solution_by_high_order_lifting_matches_oracle(ctx, case):
+    from paper_1905_04356_gb300 import pmat
+    p, w, n, dA, db, N = case
+    A = _matrix(hash(case) & 0xffff, p, n, dA, w)
+    b = _vector(hash(case) & 0xfff, p, n, db, w)
+    v = pmat.pmat_solve_series_hol(ctx, p, pmat.to_device(A), pmat.to_device(b), N)
+    ctx.sync()
+    got = pmat.to_host(v).astype(np.uint64)
+    assert got.shape == (n, 1, N)
+    assert np.array_equal(got, oracle.solve_series(p, A, b, N))
+
+
+def test_series_solution_by_high_order_lifting_full_size(ctx):
+    """32 x 32, dA = db = 4096, N = 8 digits (k = 3 levels, 8 residues): identical to Dixon's
+    lifting on every coefficient, A.v = b mod x^N on sampled coefficients (oracle), and the
+    prefix against the oracle."""
+    from paper_1905_04356_gb300 import pmat
+    p, n, d, N = P60, 32, 4096, 8 * 4096
+    A = _matrix(21, p, n, d, 8)
+    b = _vector(22, p, n, d, 8)
+    Ad, bd = pmat.to_device(A), pmat.to_device(b)
+    v = pmat.to_host(pmat.pmat_solve_series_hol(ctx, p, Ad, bd, N)).astype(np.uint64)
+    v2 = pmat.to_host(pmat.pmat_solve_series(ctx, p, Ad, bd, N)).astype(np.uint64)
+    ctx.sync()
+    assert np.array_equal(v, v2)
+    rnd = random.Random(5)
+    picks = [(0, 0), (9, 4095), (31, 8190), (5, 20475), (3, N - 1)] + \
+        [(rnd.randrange(n), rnd.randrange(N)) for _ in range(30)]
+    for i, t in picks:
+        exp = int(b[i, 0, t]) if t < d else 0
+        assert oracle.pmat_coeff(p, A, v, i, 0, t) == exp, (i, t)
+    assert np.array_equal(v[:, :, :64], oracle.solve_series(p, A[:, :, :64], b[:, :, :64], 64))
+
+
+def test_series_solution_by_high_order_lifting_argument_errors(ctx):
+    from paper_1905_04356_gb300 import PmError, pmat
+    A = pmat.to_device(_matrix(3, 97, 2, 3, 4))
+    for (Ab, bb, N) in ((pmat.to_device(_matrix(3, 97, 2, 1, 4)), pmat.to_device(_vector(1, 97, 2, 1, 4)), 8),  # dA < 2
+                        (A, pmat.to_device(_vector(1, 97, 2, 4, 4)), 8),                                      # db > dA
+                        (A, pmat.to_device(_vector(1, 97, 2, 3, 4)), 2000)):                                  # > 256 residues
+        with pytest.raises(PmError) as e:
+            pmat.pmat_solve_series_hol(ctx, 97, Ab, bb, N)
+        assert e.value.code == pmat.PM_EINVAL
+
+
+def test_series_solution_by_high_order_lifting_singular_constant_term(ctx):
+    from paper_1905_04356_gb300 import PmError, pmat
+    A = np.zeros((2, 2, 3), dtype=np.uint32)
+    A[0, 0, 1] = 1
+    A[1, 1, 0] = 1
+    pmat.pmat_solve_series_hol(ctx, 97, pmat.to_device(A), pmat.to_device(np.ones((2, 1, 2), dtype=np.uint32)), 40)
+    with pytest.raises(PmError) as e:
+        ctx.sync()
+    assert e.value.code == pmat.PM_EDOMAIN
