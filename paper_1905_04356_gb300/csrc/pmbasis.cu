@@ -764,6 +764,43 @@ int leaf(PmbCtx &C, const u64 *F, int64_t sF, int64_t e, const i64 *s_in, u64 *P
     return pm_cuda(ctx, err, "k_mbasis_leaf");
 }
 
+// Coefficient e of P = P2 P1 (the product of the top coefficients, P2[t2] P1[t1], t1 + t2 = e),
+// written to P[e] and taken off P[0]: a cyclic product of length e folds it onto coefficient 0.
+__global__ void k_wrap_top(const LeafArgs A, const u64 *P2, i64 s2, i64 t2, const u64 *P1, i64 s1, i64 t1, u64 *P,
+                           i64 sP, int m, i64 e)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= m * m) return;
+    const int i = x / m, j = x - i * m;
+    u64 acc = 0;                                        // sum of a b 2^-64 (Montgomery products)
+    for (int l = 0; l < m; l++)
+        acc = add64(acc, mmul(P2[(i64)(i * m + l) * s2 + t2], P1[(i64)(l * m + j) * s1 + t1], A), A.p);
+    const u64 ce = mmul(acc, A.r2, A);                  // times 2^128 2^-64: the plain sum
+    u64 *c = P + (i64)x * sP;
+    c[e] = ce;
+    c[0] = sub64(c[0], ce, A.p);
+}
+
+// Step 6 of Algorithms 3 and 5: P = P2 P1, P2 of length l2 and P1 of length l1, l1 + l2 - 1 = e + 1
+// coefficients.  When e is a power of two those need a transform of 2e points; a cyclic product
+// of length e instead folds only coefficient e onto coefficient 0, so that one coefficient is
+// computed apart (k_wrap_top) and the transforms are half as long.  Below order 512 the
+// products are launch-bound and the extra launch costs more than it saves.
+#define PMB_WRAP_MIN 512
+int node_product(pm_ctx *ctx, const LeafArgs &A, int m, const u64 *P2, int64_t l2, const u64 *P1, int64_t l1,
+                 int64_t e, u64 *P, int64_t sP)
+{
+    if (e < PMB_WRAP_MIN || (e & (e - 1)) != 0)
+        return prod_slice(ctx, A.p, 8, m, m, m, P2, l2, l2, P1, l1, l1, 0, e + 1, ceil_log2(e + 1), P, sP);
+    CKI(prod_slice(ctx, A.p, 8, m, m, m, P2, l2, l2, P1, l1, l1, 0, e, ceil_log2(e), P, sP));
+    int tok = stage_begin(ctx, PM_STAGE_OTHER);
+    k_wrap_top<<<(m * m + 127) / 128, 128, 0, ctx->stream>>>(A, P2, l2, l2 - 1, P1, l1, l1 - 1, P, sP, m, e);
+    ctx->launches++;
+    cudaError_t err = cudaGetLastError();
+    stage_end(ctx, tok);
+    return pm_cuda(ctx, err, "k_wrap_top");
+}
+
 int rec(PmbCtx &C, const u64 *F, int64_t sF, int64_t e, const i64 *s_in, u64 *P, int64_t sP, i64 *s_out)
 {
     if (e <= C.T) return leaf(C, F, sF, e, s_in, P, sP, s_out);
@@ -783,8 +820,7 @@ int rec(PmbCtx &C, const u64 *F, int64_t sF, int64_t e, const i64 *s_in, u64 *P,
     // steps 4-5: P2 = PM-Basis(R, e2, rdeg_s(P1))
     CKI(rec(C, R, e2, e2, s1, P2, e2 + 1, s_out));
     // step 6: P = P2 P1 (degree <= e)
-    CKI(prod_slice(ctx, C.base.p, 8, m, m, m, P2, e2 + 1, e2 + 1, P1, e1 + 1, e1 + 1, 0, e + 1, ceil_log2(e + 1), P,
-                   sP));
+    CKI(node_product(ctx, C.base, m, P2, e2 + 1, P1, e1 + 1, e, P, sP));
     ctx->arena.used = mark;
     return PM_OK;
 }
@@ -906,7 +942,7 @@ int rec_ip(PmbCtx &C, const u64 *E, int64_t sE, int64_t e, int64_t o, const i64 
     // steps 4-5: P2 = PM-IntBasis(R, alpha_{o+e1} .. alpha_{o+e-1}, rdeg_s(P1))
     CKI(rec_ip(C, R, e2, e2, o + e1, s1, P2, e2 + 1, s_out));
     // step 6: P = P2 P1 (degree <= e)
-    CKI(prod_slice(ctx, A.p, 8, m, m, m, P2, e2 + 1, e2 + 1, P1, E1, E1, 0, e + 1, ceil_log2(e + 1), P, sP));
+    CKI(node_product(ctx, A, m, P2, e2 + 1, P1, E1, e, P, sP));
     ctx->arena.used = mark;
     return PM_OK;
 }

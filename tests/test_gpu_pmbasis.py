@@ -53,6 +53,8 @@ CASES = [
     (P60, 8, 4, 100, 32),
     (P60, 32, 16, 64, 32),
     (P60, 32, 16, 200, 16),
+    (P60, 4, 2, 1024, 32),   # nodes of order 1024 and 512: node products at half length
+    (97, 3, 1, 512, 32),     # the same at order 512, small field
     (97, 4, 2, 16, 4),
     (7, 5, 2, 23, 3),
     (3, 3, 1, 12, 32),
