@@ -175,6 +175,13 @@ struct CrtJob {
     u32 c[PM_MAXK][PM_MAXK], cs[PM_MAXK][PM_MAXK];   // q_j^-1 mod q_i, companions
     u64 qm[PM_MAXK], qms[PM_MAXK];                   // q_i mod p, Shoup-64 companions
     int small_p;        // p <= 2^30: residues need a reduction mod p
+    // explicit CRT sum (mode 1, odd p): X = sum_i t_i M_i - k M with M_i = M / q_i,
+    // t_i = r_i M_i^-1 mod q_i and k = floor(sum_i t_i / q_i); mode 0: Garner
+    int mode;
+    u32 gi[PM_MAXK], gis[PM_MAXK];                   // M_i^-1 mod q_i, Shoup companions
+    u32 W[PM_MAXK];                                  // floor(2^59 / q_i)
+    u64 Cm[PM_MAXK + 1];                             // (M_i mod p) 2^64 mod p; (-M mod p) 2^64 mod p last
+    u64 pn;                                          // -p^-1 mod 2^64
 };
 
 template <typename J>
