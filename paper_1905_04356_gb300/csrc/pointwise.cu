@@ -12,8 +12,10 @@
 // CRT: for moduli without suitable roots of unity the product is lifted to
 // Z[x] and computed modulo K NTT primes (Sec. 2, "3-primes multiplication";
 // here K is the least count whose product bounds the integer coefficients).
-// Garner's mixed-radix algorithm recovers the integer coefficient, and a
-// Horner pass in F_p reduces it mod p.
+// For odd p the integer coefficient is never formed: its value mod p is the
+// explicit CRT sum with an exact fixed-point quotient (crt_sum).  For even p,
+// Garner's mixed-radix algorithm recovers it and a Horner pass in F_p reduces
+// it mod p.
 #include "common.cuh"
 
 #define PS_PTS 8        // points per block
