@@ -277,3 +277,16 @@ def test_work_counters_count_each_product(ctx):
     assert w["bytes"] == (m * n * dA + n * k * dB + m * k * lenC) * 4
     assert w["macs"] == L * m * n * k
     assert w["butterflies"] == (m * n + n * k + m * k) * (L // 2) * lg
+
+
+@pytest.mark.parametrize("p,n,d", [(144115188075855859, 4, 14), (72057594037927931, 7, 32), (P62, 8, 64),
+                                   (P60, 32, 300)])
+def test_extreme_coefficients_at_the_crt_bound(ctx, p, n, d):
+    """Every input coefficient p - 1: the middle coefficients of the lifted product reach
+    n d (p - 1)^2, the bound the prime count is chosen from.  The first two shapes leave 0.013
+    bits between that bound and the product of the 4 primes, the hardest case for the CRT
+    quotient (X / M = 0.991)."""
+    A = np.full((3, n, d), p - 1, dtype=np.uint64)
+    B = np.full((n, 2, d + 3), p - 1, dtype=np.uint64)
+    got = _gpu(ctx, "pmat_mul", p, A, B)
+    assert np.array_equal(got.astype(np.uint64), oracle.pmat_mul(p, A, B))
