@@ -55,3 +55,20 @@ def test_reference_arm_prints_on_rank_zero_only(capsys):
     import bench
     bench.run_reference(argparse.Namespace(gpus=2, steps=1, warmup=0), rank=1)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_keeps_the_contract(capsys):
+    """Rank 0 of the reference arm prints one JSON line: the oracle timed on the host cores on
+    a bounded sample, with the metric, unit and config of the device arm."""
+    import json
+    import bench
+    bench.run_reference(argparse.Namespace(gpus=1, steps=1, warmup=0), rank=0)
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "ms"
+    assert d["higher_is_better"] is False and d["n_gpus"] == 1 and d["steps"] == 1
+    assert d["config"]["workload"] == bench.WORKLOAD and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
