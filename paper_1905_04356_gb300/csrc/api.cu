@@ -273,48 +273,9 @@ static int choose_primes(pm_ctx *ctx, uint64_t p, int n, int64_t dmin, int lg, s
 
 static void fill_crt(CrtJob &J, const std::vector<PrimeSlot *> &pr, uint64_t p)
 {
-    const int K = (int)pr.size();
-    J.K = K;
-    J.p = p;
-    J.mu = (uint64_t)(((unsigned __int128)1 << 64) / p);
-    J.small_p = p <= (1ull << 30);
-    for (int i = 0; i < K; i++) {
-        const uint64_t qi = pr[i]->q;
-        J.q[i] = (u32)qi;
-        for (int j = 0; j < i; j++) {
-            uint64_t c = host_powmod(pr[j]->q % qi, qi - 2, qi);
-            J.c[i][j] = (u32)c;
-            J.cs[i][j] = (u32)((c << 32) / qi);
-        }
-        uint64_t qm = qi % p;
-        J.qm[i] = qm;
-        J.qms[i] = (uint64_t)(((unsigned __int128)qm << 64) / p);
-    }
-    // explicit CRT sum for odd p with two or more primes (Montgomery reduction needs p odd);
-    // every table prime exceeds 2^29, so floor(2^59 / q_i) fits 32 bits
-    J.mode = (p & 1) && K >= 2 ? 1 : 0;
-    if (!J.mode) return;
-    const uint64_t r64 = (uint64_t)(((unsigned __int128)1 << 64) % p);   // 2^64 mod p
-    uint64_t Mp = 1 % p;
-    for (int i = 0; i < K; i++) {
-        const uint64_t qi = pr[i]->q;
-        uint64_t mi_q = 1, mi_p = 1 % p;
-        for (int j = 0; j < K; j++)
-            if (j != i) {
-                mi_q = host_mulmod(mi_q, pr[j]->q % qi, qi);
-                mi_p = host_mulmod(mi_p, pr[j]->q % p, p);
-            }
-        const uint64_t g = host_powmod(mi_q, qi - 2, qi);
-        J.gi[i] = (u32)g;
-        J.gis[i] = (u32)((g << 32) / qi);
-        J.W[i] = (u32)((1ull << 59) / qi);
-        J.Cm[i] = host_mulmod(mi_p, r64, p);
-        Mp = host_mulmod(Mp, qi % p, p);
-    }
-    J.Cm[K] = host_mulmod((p - Mp) % p, r64, p);
-    uint64_t inv = 1;                                   // p^-1 mod 2^64 by Newton iteration
-    for (int it = 0; it < 7; it++) inv *= 2 - p * inv;
-    J.pn = (uint64_t)0 - inv;
+    u32 q[PM_MAXK];
+    for (size_t i = 0; i < pr.size(); i++) q[i] = pr[i]->q;
+    crt_setup(J, q, (int)pr.size(), p);
 }
 
 // ------------------------------------------------------------------ checks

@@ -208,6 +208,7 @@ cudaError_t launch_pointwise_mv(const JobPack<PwJob> &pk, cudaStream_t st, long 
 bool pwv_supported(const PwJob &j);
 int pwv_blocks(const PwJob &j);
 cudaError_t launch_crt(const JobPack<CrtJob> &pk, cudaStream_t st, long long *launches);
+void crt_setup(CrtJob &J, const u32 *q, int K, uint64_t p);
 cudaError_t launch_pointwise_tc(const JobPack<PwJob> &pk, int *status, cudaStream_t st, long long *launches,
                                 int withhold = 0);
 bool tc_supported(const PwJob &j);

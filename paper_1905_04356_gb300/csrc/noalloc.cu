@@ -281,18 +281,9 @@ extern "C" int pmat_mul_noalloc(uint64_t p, int w, int m, int n, int k, const vo
         JobPack<CrtJob> pk; pk.njobs = 0; pk.blk_start[0] = 0;
         CrtJob j;
         memset(&j, 0, sizeof(j));
-        j.K = K; j.p = p; j.mu = (uint64_t)(((unsigned __int128)1 << 64) / p); j.small_p = p <= (1ull << 30);
-        for (int i = 0; i < K; i++) {
-            const uint64_t qi = pr[i].q;
-            j.q[i] = (u32)qi;
-            for (int t = 0; t < i; t++) {
-                uint64_t c = powm(pr[t].q % qi, qi - 2, qi);
-                j.c[i][t] = (u32)c;
-                j.cs[i][t] = (u32)((c << 32) / qi);
-            }
-            j.qm[i] = qi % p;
-            j.qms[i] = (uint64_t)(((unsigned __int128)j.qm[i] << 64) / p);
-        }
+        u32 qs[PM_MAXK];
+        for (int i = 0; i < K; i++) qs[i] = pr[i].q;
+        crt_setup(j, qs, K, p);
         j.res = Rs; j.dst = C; j.count = (int64_t)eC * len; j.len = len; j.dst_stride = len; j.w = w;
         add(pk, j, crt_blocks(j));
         if (launch_crt(pk, st, &launches) != cudaSuccess) return PM_ECUDA;
