@@ -115,8 +115,9 @@ enum {
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
  * owned by the caller (kept, not destroyed; cudaStreamLegacy selects the
- * legacy default stream), or NULL for a context-owned non-blocking stream.  *ctx receives the handle.  Returns PM_EINVAL on a bad
- * device, PM_ECUDA on a runtime failure. */
+ * legacy default stream), or NULL for a context-owned non-blocking stream.
+ * *ctx receives the handle.  Returns PM_EINVAL on a bad device, PM_ECUDA on a
+ * runtime failure. */
 int pm_create(pm_ctx **ctx, int device, void *cuda_stream);
 
 /* Destroy a context: synchronises its stream, frees its device memory. */
@@ -187,7 +188,7 @@ int pmat_mul_host(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k,
 int pm_host_join(pm_ctx *ctx);
 
 /* C (m x k, length t) = A . B mod x^t (Sec. 2; the truncated product used by
- * Newton iteration in Sec. 4.3).  Requires t >= 1; coefficients of degree
+ * Newton iteration in Sec. 4, "Linear system solving").  Requires t >= 1; coefficients of degree
  * >= dA+dB-1 are zero. */
 int pmat_mul_trunc(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k,
                    const void *A, int64_t dA, const void *B, int64_t dB, int64_t t, void *C);
