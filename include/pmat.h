@@ -188,8 +188,8 @@ int pmat_mul_host(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k,
 int pm_host_join(pm_ctx *ctx);
 
 /* C (m x k, length t) = A . B mod x^t (Sec. 2; the truncated product used by
- * Newton iteration in Sec. 4, "Linear system solving").  Requires t >= 1; coefficients of degree
- * >= dA+dB-1 are zero. */
+ * Newton iteration in Sec. 4, "Linear system solving").  Requires t >= 1;
+ * coefficients of degree >= dA+dB-1 are zero. */
 int pmat_mul_trunc(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k,
                    const void *A, int64_t dA, const void *B, int64_t dB, int64_t t, void *C);
 
