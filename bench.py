@@ -34,6 +34,7 @@ CONFIG = {"workload": WORKLOAD, "m": 32, "n": 32, "k": 32, "deg_bound": 4096, "p
 PAPER_CONTEXT = {"ms": 2000.0, "hardware": "Intel i7-4790, 1 thread, NTL 11.3.1",
                  "workload": "m = 32, degree 4096, random 60-bit prime (product table of Sec. 2)"}
 L2_FLUSH_BYTES = 256 << 20
+PW_DEFAULT = ("k_pointwise", "pointwise.cu")   # the pointwise kernel the default form runs
 
 
 def parse():
@@ -137,6 +138,37 @@ def traffic_for(kernel: str, src_file: str):
     return None
 
 
+def inst_for(kernel: str, src_file: str):
+    """warp instructions per launch from the committed ncu summary, if taken on the current kernel source."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        e = t.get(kernel)
+        if e and e.get("source_sha") == sha(os.path.join(ROOT, "paper_1905_04356_gb300", "csrc", src_file)):
+            return e.get("inst_executed_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 # ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
 def oracle_sample(W, rows: int):
     """Time the oracle on the first `rows` rows of A (rows x 32 of the 32 x 32 output entries)."""
@@ -155,7 +187,7 @@ def cpu_baseline(W, budget_s=15.0):
         ms, dt, cores = oracle_sample(W, rows)
     else:
         ms, dt = ms1, dt1
-    return {"value": round(ms, 1), "unit": "ms", "cores": cores, "kind": "oracle",
+    return {"value": round(ms, 1), "unit": "ms", "cores": cores, "cpu_model": cpu_model(), "kind": "oracle",
             "sample": f"{rows} of 32 output rows ({rows * 32} of 1024 entries, all 8191 coefficients), "
                       f"{dt:.1f} s of CPU time, scaled to the full product"}
 
@@ -177,7 +209,8 @@ def run_reference(args, rank):
         "impl": "reference", "metric": METRIC, "value": round(v, 2), "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 2), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": CONFIG,
-        "cpu_baseline": {"value": round(v, 2), "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": round(v, 2), "unit": "ms", "cores": cores, "cpu_model": cpu_model(), "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": round(v, 2), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -489,41 +522,45 @@ def main():
         h2d = Ah.nbytes + Bh.nbytes
         d2h = m * k * lenC * 8
 
-    # ---- roofline of the dominant kernel (algorithmic bytes per launch / measured launch time)
+    # ---- roofline of the dominant kernel.  Algorithmic bytes = the product's compulsory I/O (A and
+    #      B read once, C written once): the transform-domain intermediates are the method's own
+    #      choice, so a kernel's staged bytes (its own reads and writes of them) are a diagnostic.
     K, L = 5, 8192
     eA, eB, eC = m * n, n * k, m * k
-    alg = {   # minimum bytes each stage's kernel must read + write (one launch per stage here)
+    pw_kernel, pw_src = PW_DEFAULT
+    compulsory = (eA * dA + eB * dB) * 8 + eC * lenC * 8
+    staged = {   # bytes each stage's kernel reads + writes (one launch per stage here)
         "fwd_ntt": (eA * dA + eB * dB) * 8 + K * (eA + eB) * L * 4,
         "pointwise": K * (eA + eB) * L * 4 + K * eC * L * 4,
         "inv_ntt": K * eC * L * 4 + K * eC * lenC * 4,
         "crt": K * eC * lenC * 4 + eC * lenC * 8,
     }
-    kname = {"fwd_ntt": ("k_ntt_fwd_block", "ntt.cu"), "pointwise": ("k_pointwise", "pointwise.cu"),
+    kname = {"fwd_ntt": ("k_ntt_fwd_block", "ntt.cu"), "pointwise": (pw_kernel, pw_src),
              "inv_ntt": ("k_ntt_inv_block", "ntt.cu"), "crt": ("k_crt", "pointwise.cu")}
     stages = {k2: v for k2, v in st.items() if v[1] > 0}
     dom = max(stages, key=lambda x: stages[x][0])
     dom_ms = stages[dom][0] / stages[dom][1]
     pk = peaks()
     peak = pk["hbm_gbs"] if pk else 6800.0
-    achieved = alg[dom] / (dom_ms * 1e-3) / 1e9
+    achieved = compulsory / (dom_ms * 1e-3) / 1e9
+    staged_gbs = staged[dom] / (dom_ms * 1e-3) / 1e9
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    clk = ck.get("sm_mhz") or (pk["sm_max_mhz"] if pk else 2070.0)
+    issue_peak = sms * 4 * clk * 1e6                 # warp instructions per second (one per SMSP per clock)
+    inst = inst_for(*kname[dom])
     roof = {"bound": "hbm", "kernel": kname[dom][0], "achieved": round(achieved, 1), "peak": peak,
             "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic_for(*kname[dom]),
-            "algorithmic_bytes_per_launch": alg[dom], "launch_ms": round(dom_ms, 4),
-            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback"}
-    def tc_report(ts_tc, st_tc, st_cc, pk):
-        """The tensor-core pointwise form on the same step: its pointwise stage against the
-        CUDA-core one, and its tensor throughput (limb flops) against the measured bf16 peak."""
-        tc_pw = st_tc["pointwise"][0] / max(1, st_tc["pointwise"][1])
-        cc_pw = st_cc["pointwise"][0] / max(1, st_cc["pointwise"][1])
-        limb_flops = K * L * (4 * m) * n * (4 * k) * 2            # per point: (4m x n) . (n x 4k)
-        bf16 = pk["bf16_tflops"] if pk else 1900.0
-        tf = limb_flops / (tc_pw * 1e-3) / 1e12
-        return {"step_ms": round(sum(ts_tc) / len(ts_tc), 4), "pointwise_ms": round(tc_pw, 4),
-                "cuda_core_pointwise_ms": round(cc_pw, 4), "outputs_equal": tc_equal,
-                "limb_tflops": round(tf, 1), "bf16_peak_tflops": bf16, "tensor_frac": round(tf / bf16, 4),
-                "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops)" if pk else "fallback"}
-
-    compulsory = (eA * dA + eB * dB) * 8 + eC * lenC * 8
+            "algorithmic_bytes_per_launch": compulsory,
+            "algorithmic_bytes": "compulsory I/O of the product: A and B read once, C written once",
+            "launch_ms": round(dom_ms, 4),
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback",
+            "staged_bytes_per_launch": staged[dom], "staged_GBps": round(staged_gbs, 1),
+            "staged_frac": round(staged_gbs / peak, 4),
+            "issue": {"warp_instructions_per_launch": inst, "sms": sms, "sm_mhz": clk,
+                      "peak_warp_instructions_per_s": issue_peak,
+                      "frac": round(inst / (dom_ms * 1e-3) / issue_peak, 4) if inst else None,
+                      "source": "instruction count from the committed ncu summary of the same kernel source, "
+                                "time from this run's CUDA events"}}
     value = job_value(ms_step, world)
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,

@@ -238,8 +238,10 @@ int pmat_mul_batched(pm_ctx *ctx, int count, const pmat_desc *descs);
  * that first call before any stream capture.  Every call overwrites the
  * array: calls that overlap on the GPU (several streams or host threads)
  * race and must be serialised by the caller.  Calls no cudaMalloc, cudaFree
- * or other allocating routine.  Returns PM_EINVAL on bad arguments, PM_ECUDA
- * on a runtime or launch failure. */
+ * or other allocating routine.  Returns PM_EINVAL on bad arguments (a length
+ * above 2^20 included), PM_EUNSUPPORTED when the product needs more CRT primes
+ * than the table holds, PM_ESCRATCH as above, PM_ECUDA on a runtime or launch
+ * failure. */
 int pmat_mul_noalloc(uint64_t p, int w, int m, int n, int k,
                      const void *A, int64_t dA, const void *B, int64_t dB, void *C,
                      void *cuda_stream);
@@ -368,6 +370,17 @@ int pmat_inv_slices(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_
  * and uses the driver arena for the slices.  Asynchronous. */
 int pmat_solve_series_hol(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA,
                           const void *b, int64_t db, int64_t N, void *v);
+
+/* Measured rate of dense tensor-core MMA on device `device`: tcgen05.mma of
+ * kind::f16 (fp16 x fp16 operands in shared memory, fp32 accumulator in tensor
+ * memory) of shape 128 x n_cols x 16, `iters` back to back per SM on every SM,
+ * timed by CUDA events (best of three launches after one warm-up).  The paper
+ * has no counterpart: it is the tensor peak the tensor-core pointwise products
+ * (Sec. 2, the n^omega d term) are measured against.  *tflops receives
+ * 2 * 128 * n_cols * 16 * iters * SMs / time.  Requires 16 <= n_cols <= 256,
+ * n_cols a multiple of 16, 1 <= iters <= 2^20.  Allocates a status word and
+ * synchronises; returns PM_ETIMEOUT if the bounded wait for the MMAs ran out. */
+int pm_mma_rate(int device, int n_cols, int iters, double *tflops);
 
 #ifdef __cplusplus
 }

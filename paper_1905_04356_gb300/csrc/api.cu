@@ -42,42 +42,6 @@ int pm_cuda(pm_ctx *ctx, cudaError_t e, const char *what)
         if (_rc) return _rc;                                            \
     } while (0)
 
-// ------------------------------------------------------------------ host arithmetic
-uint64_t host_mulmod(uint64_t a, uint64_t b, uint64_t p) { return (uint64_t)((unsigned __int128)a * b % p); }
-uint64_t host_powmod(uint64_t a, uint64_t e, uint64_t p)
-{
-    uint64_t r = 1 % p;
-    a %= p;
-    while (e) {
-        if (e & 1) r = host_mulmod(r, a, p);
-        a = host_mulmod(a, a, p);
-        e >>= 1;
-    }
-    return r;
-}
-
-// Deterministic Miller-Rabin for n < 2^32 (bases 2, 7, 61 suffice below 4.76e9).
-static bool is_prime32(uint64_t n)
-{
-    if (n < 2) return false;
-    for (uint64_t s : {2ull, 3ull, 5ull, 7ull, 11ull, 13ull, 61ull})
-        if (n % s == 0) return n == s;
-    uint64_t d = n - 1;
-    int r = 0;
-    while (!(d & 1)) { d >>= 1; r++; }
-    for (uint64_t a : {2ull, 7ull, 61ull}) {
-        uint64_t x = host_powmod(a, d, n);
-        if (x == 1 || x == n - 1) continue;
-        bool comp = true;
-        for (int i = 1; i < r && comp; i++) {
-            x = host_mulmod(x, x, n);
-            if (x == n - 1) comp = false;
-        }
-        if (comp) return false;
-    }
-    return true;
-}
-
 int ceil_log2(int64_t x)
 {
     int l = 0;
@@ -85,35 +49,10 @@ int ceil_log2(int64_t x)
     return l;
 }
 
-// Primitive root of F_q (q prime < 2^32): trial-factor q - 1.
-static uint32_t primitive_root(uint32_t q)
-{
-    std::vector<uint64_t> f;
-    uint64_t m = q - 1;
-    for (uint64_t d = 2; d * d <= m; d++)
-        if (m % d == 0) {
-            f.push_back(d);
-            while (m % d == 0) m /= d;
-        }
-    if (m > 1) f.push_back(m);
-    for (uint64_t g = 2;; g++) {
-        bool ok = true;
-        for (uint64_t d : f)
-            if (host_powmod(g, (q - 1) / d, q) == 1) { ok = false; break; }
-        if (ok) return (uint32_t)g;
-    }
-}
-
 static void slot_init(PrimeSlot &s, uint32_t q)
 {
     s.q = q;
-    uint64_t g = primitive_root(q);
-    for (int l = 0; l <= PM_MAX_LOG2L; l++) {
-        if (((uint64_t)(q - 1) % (1ull << l)) != 0) { s.rf[l] = s.ri[l] = 0; continue; }
-        uint64_t w = host_powmod(g, (q - 1) >> l, q);
-        s.rf[l] = (u32)w;
-        s.ri[l] = (u32)host_powmod(w, q - 2, q);
-    }
+    ntt_roots(q, s.rf, s.ri);
 }
 
 static int slot_tables(pm_ctx *ctx, PrimeSlot &s, int lg)
@@ -251,7 +190,7 @@ static int choose_primes(pm_ctx *ctx, uint64_t p, int n, int64_t dmin, int lg, s
 {
     out.clear();
     direct = false;
-    if (p < (1ull << 30) && p > 2 && ((p - 1) % (1ull << lg)) == 0 && is_prime32(p)) {
+    if (p < (1ull << 30) && p > 2 && ((p - 1) % (1ull << lg)) == 0 && ntt_is_prime32(p)) {
         for (auto &s : ctx->direct)
             if (s.q == p) { out.push_back(&s); direct = true; return PM_OK; }
         ctx->direct.emplace_back();
@@ -689,12 +628,11 @@ int pm_create(pm_ctx **out, int device, void *cuda_stream)
         return PM_ECUDA;
     }
     // CRT primes: q = c 2^20 + 1 < 2^30, largest first (all in (2^29, 2^30))
-    for (uint64_t c = 1023; c >= 512 && ctx->table.size() < PM_MAXK; c--) {
-        uint64_t q = (c << 20) + 1;
-        if (is_prime32(q)) {
-            ctx->table.emplace_back();
-            slot_init(ctx->table.back(), (u32)q);
-        }
+    uint32_t qs[PM_MAXK];
+    const int nq = ntt_prime_table(qs, PM_MAXK);
+    for (int i = 0; i < nq; i++) {
+        ctx->table.emplace_back();
+        slot_init(ctx->table.back(), qs[i]);
     }
     *out = ctx;
     return PM_OK;

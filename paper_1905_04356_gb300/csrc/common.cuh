@@ -209,6 +209,12 @@ bool pwv_supported(const PwJob &j);
 int pwv_blocks(const PwJob &j);
 cudaError_t launch_crt(const JobPack<CrtJob> &pk, cudaStream_t st, long long *launches);
 void crt_setup(CrtJob &J, const u32 *q, int K, uint64_t p);
+// Host set-up of the NTT primes (primes.cu).
+uint64_t host_mulmod(uint64_t a, uint64_t b, uint64_t p);
+uint64_t host_powmod(uint64_t a, uint64_t e, uint64_t p);
+bool ntt_is_prime32(uint64_t n);                          // deterministic below 2^32
+void ntt_roots(uint32_t q, uint32_t *rf, uint32_t *ri);   // [PM_MAX_LOG2L + 1]: 2^l-th roots and inverses (0: none)
+int ntt_prime_table(uint32_t *out, int maxk);             // CRT primes c 2^20 + 1 < 2^30, largest first
 cudaError_t launch_pointwise_tc(const JobPack<PwJob> &pk, int *status, cudaStream_t st, long long *launches,
                                 int withhold = 0);
 bool tc_supported(const PwJob &j);

@@ -6,15 +6,6 @@
 
 // Host set-up of the constants of a CRT job over the primes q[0 .. K-1] (every one above 2^29)
 // for values mod p: Garner's tables always, the explicit sum's for odd p and K >= 2.
-static uint64_t crt_mulmod(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((unsigned __int128)a * b % m); }
-static uint64_t crt_powmod(uint64_t a, uint64_t e, uint64_t m)
-{
-    uint64_t r = 1 % m;
-    for (a %= m; e; e >>= 1, a = crt_mulmod(a, a, m))
-        if (e & 1) r = crt_mulmod(r, a, m);
-    return r;
-}
-
 void crt_setup(CrtJob &J, const u32 *q, int K, uint64_t p)
 {
     J.K = K;
@@ -25,7 +16,7 @@ void crt_setup(CrtJob &J, const u32 *q, int K, uint64_t p)
         const uint64_t qi = q[i];
         J.q[i] = (u32)qi;
         for (int j = 0; j < i; j++) {
-            const uint64_t c = crt_powmod(q[j] % qi, qi - 2, qi);
+            const uint64_t c = host_powmod(q[j] % qi, qi - 2, qi);
             J.c[i][j] = (u32)c;
             J.cs[i][j] = (u32)((c << 32) / qi);
         }
@@ -41,17 +32,17 @@ void crt_setup(CrtJob &J, const u32 *q, int K, uint64_t p)
         uint64_t mi_q = 1, mi_p = 1 % p;
         for (int j = 0; j < K; j++)
             if (j != i) {
-                mi_q = crt_mulmod(mi_q, q[j] % qi, qi);
-                mi_p = crt_mulmod(mi_p, q[j] % p, p);
+                mi_q = host_mulmod(mi_q, q[j] % qi, qi);
+                mi_p = host_mulmod(mi_p, q[j] % p, p);
             }
-        const uint64_t g = crt_powmod(mi_q, qi - 2, qi);
+        const uint64_t g = host_powmod(mi_q, qi - 2, qi);
         J.gi[i] = (u32)g;
         J.gis[i] = (u32)((g << 32) / qi);
         J.W[i] = (u32)((1ull << 59) / qi);
-        J.Cm[i] = crt_mulmod(mi_p, r64, p);
-        Mp = crt_mulmod(Mp, qi % p, p);
+        J.Cm[i] = host_mulmod(mi_p, r64, p);
+        Mp = host_mulmod(Mp, qi % p, p);
     }
-    J.Cm[K] = crt_mulmod((p - Mp) % p, r64, p);
+    J.Cm[K] = host_mulmod((p - Mp) % p, r64, p);
     uint64_t inv = 1;                                   // p^-1 mod 2^64 by Newton iteration
     for (int it = 0; it < 7; it++) inv *= 2 - p * inv;
     J.pn = (uint64_t)0 - inv;

@@ -104,5 +104,3 @@ size_t prod_operand_bytes(pm_ctx *ctx, uint64_t p, int n, int64_t dmin, int lg, 
 int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count);
 
 int ceil_log2(int64_t x);
-uint64_t host_mulmod(uint64_t a, uint64_t b, uint64_t p);
-uint64_t host_powmod(uint64_t a, uint64_t e, uint64_t p);

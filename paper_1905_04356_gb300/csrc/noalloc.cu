@@ -21,7 +21,9 @@
 //
 // The work is the same four kernels as pmat_mul (forward transforms with the
 // reduction fused, pointwise products, inverse transforms with the slice
-// fused, Garner CRT), launched on the caller's stream.
+// fused, CRT recombination: the explicit CRT sum for odd p, Garner's mixed
+// radix for even p or a single prime; see pointwise.cu), launched on the
+// caller's stream.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -42,55 +44,10 @@ struct StaticPrime {
     u32 rf[PM_MAX_LOG2L + 1], ri[PM_MAX_LOG2L + 1];
 };
 
-uint64_t mulm(uint64_t a, uint64_t b, uint64_t p) { return (uint64_t)((unsigned __int128)a * b % p); }
-uint64_t powm(uint64_t a, uint64_t e, uint64_t p)
-{
-    uint64_t r = 1 % p;
-    a %= p;
-    for (; e; e >>= 1, a = mulm(a, a, p))
-        if (e & 1) r = mulm(r, a, p);
-    return r;
-}
-bool prime32(uint64_t n)
-{
-    if (n < 2) return false;
-    for (uint64_t s : {2ull, 3ull, 5ull, 7ull, 11ull, 13ull, 61ull})
-        if (n % s == 0) return n == s;
-    uint64_t d = n - 1;
-    int r = 0;
-    while (!(d & 1)) { d >>= 1; r++; }
-    for (uint64_t a : {2ull, 7ull, 61ull}) {
-        uint64_t x = powm(a, d, n);
-        if (x == 1 || x == n - 1) continue;
-        bool comp = true;
-        for (int i = 1; i < r && comp; i++) {
-            x = mulm(x, x, n);
-            if (x == n - 1) comp = false;
-        }
-        if (comp) return false;
-    }
-    return true;
-}
 void make_prime(StaticPrime &s, u32 q)
 {
     s.q = q;
-    std::vector<uint64_t> f;
-    uint64_t m = q - 1;
-    for (uint64_t d = 2; d * d <= m; d++)
-        if (m % d == 0) { f.push_back(d); while (m % d == 0) m /= d; }
-    if (m > 1) f.push_back(m);
-    uint64_t g = 2;
-    for (;; g++) {
-        bool ok = true;
-        for (uint64_t d : f) if (powm(g, (q - 1) / d, q) == 1) { ok = false; break; }
-        if (ok) break;
-    }
-    for (int l = 0; l <= PM_MAX_LOG2L; l++) {
-        if (((uint64_t)(q - 1) % (1ull << l)) != 0) { s.rf[l] = s.ri[l] = 0; continue; }
-        uint64_t w = powm(g, (q - 1) >> l, q);
-        s.rf[l] = (u32)w;
-        s.ri[l] = (u32)powm(w, q - 2, q);
-    }
+    ntt_roots(q, s.rf, s.ri);
 }
 
 std::once_flag g_table_once;
@@ -109,7 +66,7 @@ PrimeDev dev_prime(const StaticPrime &s, int lg, const uint2 *twf, const uint2 *
     P.r32 = (u32)((1ull << 32) % q);
     P.r32s = (u32)(((uint64_t)P.r32 << 32) / q);
     P.ones = (u32)((1ull << 32) / q);
-    P.linv = (u32)powm((1ull << lg) % q, q - 2, q);
+    P.linv = (u32)host_powmod((1ull << lg) % q, q - 2, q);
     P.linvs = (u32)(((uint64_t)P.linv << 32) / q);
     P.twf = twf;
     P.twi = twi;
@@ -132,6 +89,8 @@ extern "C" int pmat_mul_noalloc(uint64_t p, int w, int m, int n, int k, const vo
     if (m < 1 || n < 1 || k < 1 || dA < 1 || dB < 1 || p < 2 || (w != 4 && w != 8) ||
         (w == 4 && p > (1ull << 32)) || p >= (1ull << 62) || !A || !B || !C)
         return PM_EINVAL;
+    // each length bounded before their sum is formed (no overflow of dA + dB - 1)
+    if (dA > (int64_t(1) << PM_MAX_LOG2L) || dB > (int64_t(1) << PM_MAX_LOG2L)) return PM_EINVAL;
     const int64_t len = dA + dB - 1;
     int lg = 4;
     while ((int64_t(1) << lg) < len) lg++;
@@ -141,12 +100,13 @@ extern "C" int pmat_mul_noalloc(uint64_t p, int w, int m, int n, int k, const vo
 
     // primes: p itself when it is an NTT prime for this length, else the CRT table
     std::call_once(g_table_once, [] {
-        for (uint64_t c = 1023; c >= 512 && g_table.size() < PM_MAXK; c--)
-            if (prime32((c << 20) + 1)) { g_table.emplace_back(); make_prime(g_table.back(), (u32)((c << 20) + 1)); }
+        uint32_t qs[PM_MAXK];
+        const int nq = ntt_prime_table(qs, PM_MAXK);
+        for (int i = 0; i < nq; i++) { g_table.emplace_back(); make_prime(g_table.back(), qs[i]); }
     });
     std::vector<StaticPrime> pr;
     bool direct = false;
-    if (p < (1ull << 30) && p > 2 && ((p - 1) % (uint64_t)L) == 0 && prime32(p)) {
+    if (p < (1ull << 30) && p > 2 && ((p - 1) % (uint64_t)L) == 0 && ntt_is_prime32(p)) {
         pr.emplace_back();
         make_prime(pr.back(), (u32)p);
         direct = true;

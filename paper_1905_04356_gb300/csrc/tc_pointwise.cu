@@ -150,6 +150,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_pointwise_tc(const __grid_consta
         ok = __syncthreads_and(done) != 0;           // one decision for the whole block
         if (!ok) {
             if (tid == 0) atomicExch(status, PM_ETIMEOUT);
+            // MMAs that were issued may still write tensor memory: before it is freed, wait
+            // (bounded again) for their commit; past that second limit the block frees it
+            // anyway so that the SM's tensor memory is not held forever, and the context's
+            // tensor memory contents are undefined (PM_ETIMEOUT is already recorded)
+            if (issue)
+                for (int it = 0; it < (1 << 24) && !done; it++)
+                    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                                 " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(smem_u32(&mbar)), "r"((uint32_t)(pp & 1)));
+            __syncthreads();
             break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");

@@ -79,6 +79,7 @@ def lib():
             "pmat_solve_series": ([P, u64, i32, i32, P, i64, P, i64, i64, P], i32),
             "pmat_solve_series_hol": ([P, u64, i32, i32, P, i64, P, i64, i64, P], i32),
             "pmat_inv_slices": ([P, u64, i32, i32, P, i64, i32, P], i32),
+            "pm_mma_rate": ([i32, i32, i32, C.POINTER(C.c_double)], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -414,3 +415,13 @@ def bivariate_resultant(ctx: Context, primes, f: torch.Tensor, g: torch.Tensor, 
     ctx._ck(lib().bivariate_resultant(ctx.h, npr, pr.ctypes.data, dxf1 - 1, dyf1 - 1, f.data_ptr(), dxg1 - 1,
                                       dyg1 - 1, g.data_ptr(), R.data_ptr()))
     return R
+
+
+def mma_rate(device: int = 0, n_cols: int = 256, iters: int = 4096) -> float:
+    """Measured TFLOP/s of dense tcgen05.mma kind::f16 (M = 128, N = n_cols, K = 16) on one GPU."""
+    out = C.c_double(0.0)
+    rc = lib().pm_mma_rate(device, n_cols, iters, C.byref(out))
+    if rc != PM_OK:
+        raise PmError(rc, "pm_mma_rate failed")
+    return out.value
+

@@ -5,7 +5,7 @@ recompute inside a test run.
 Calls only the CPU oracle (oracle/) and the seeded input generators (synth.py);
 nothing here touches the CUDA path.  Each entry stores the SHA-256 of the
 oracle's output (little-endian uint64, C order), its shape, and a few sampled
-values.  Run once (about 20 minutes on 8 cores):
+values.  Run once (about 25 minutes on 8 cores):
 
     python tests/golden/make_golden.py [name ...]
 """
@@ -62,10 +62,25 @@ def resultant():
             "oracle": "orc_bivariate_resultant (evaluate / Euclid / Newton interpolation)"}
 
 
+def resultant_16():
+    """The 16-prime batch: the same integer coefficients reduced modulo 16 random 60-bit primes,
+    one oracle resultant per prime."""
+    W = synth.resultant_c5(0, nprimes=16)
+    shas, samp = [], []
+    for i, p in enumerate(W["primes"]):
+        R = oracle.bivariate_resultant(p, W["f"][i], W["g"][i])
+        shas.append(digest(R))
+        samp.append(samples(R, 4))
+    return {"what": "Res_y(f, g) modulo each of 16 primes, f, g dense with deg_x = deg_y = 150, seed 0",
+            "primes": [int(p) for p in W["primes"]], "shape": [16, 45001], "sha256": shas, "samples": samp,
+            "oracle": "orc_bivariate_resultant (evaluate / Euclid / Newton interpolation), once per prime"}
+
+
 JOBS = {"product_32x32_p60": lambda: product("p60", False),
         "product_32x32_p998": lambda: product("p998", True),
         "pmbasis_32x16_d8192": pmbasis,
-        "resultant_150": resultant}
+        "resultant_150": resultant,
+        "resultant_150_16primes": resultant_16}
 
 
 def main(names):

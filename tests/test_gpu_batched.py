@@ -1,4 +1,5 @@
 """GPU parity of pmat_mul_batched (uneven products binned by transform length)."""
+import os
 import random
 
 import numpy as np
@@ -47,9 +48,21 @@ def test_mixed_batch_full_oracle(ctx):
         assert np.array_equal(pmat.to_host(C).astype(np.uint64), oracle.pmat_mul(p, A, B))
 
 
-def test_batched_512_sampled():
-    """The 512-product workload (log-uniform m, n, k in [2, 64], lengths in [64, 16384],
-    half mod 998244353, half mod 60-bit primes): 4 sampled coefficients per product."""
+def _eval_all(p, X, alpha):
+    """X(alpha) for every entry (the oracle's Horner evaluation)."""
+    return oracle.pmat_eval(p, X, alpha)
+
+
+def test_batched_512_every_entry_at_random_points():
+    """The 512-product workload (log-uniform m, n, k in [2, 64], lengths in [64, 16384], half mod
+    998244353, half mod 60-bit primes): every output entry of every product is checked at two
+    seeded random points alpha, C(alpha) = A(alpha) . B(alpha) mod p, with A(alpha), B(alpha) and
+    C(alpha) evaluated by the oracle's Horner rule and the matrix product taken by the oracle.  A
+    wrong entry of degree < 2d - 1 passes one point with probability below 2d / p (Schwartz-Zippel),
+    and a single wrong coefficient c_t never passes (it shifts C(alpha) by a nonzero multiple of
+    alpha^t)."""
+    import concurrent.futures as cf
+
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -59,13 +72,24 @@ def test_batched_512_sampled():
     dev = [(it["p"], pmat.to_device(it["A"]), pmat.to_device(it["B"])) for it in items]
     outs = pmat.pmat_mul_batched(ctx, dev)
     ctx.sync()
+    del dev
     rnd = random.Random(8)
-    for it, C in zip(items, outs):
-        m, k, d = it["m"], it["k"], it["d"]
-        picks = [(0, 0, 0), (m - 1, k - 1, 2 * d - 2)] + \
-            [(rnd.randrange(m), rnd.randrange(k), rnd.randrange(2 * d - 1)) for _ in range(2)]
-        idx = torch.tensor([(i * k + kk) * (2 * d - 1) + t for (i, kk, t) in picks], device=C.device)
-        got = pmat.to_host(C.reshape(-1)[idx])
-        for (i, kk, t), v in zip(picks, got):
-            assert int(v) == oracle.pmat_coeff(it["p"], it["A"], it["B"], i, kk, t), (it["m"], it["n"], k, d, i, kk, t)
+    alphas = [(rnd.randrange(1, it["p"]), rnd.randrange(1, it["p"])) for it in items]
+
+    def check(idx):
+        it, al = items[idx], alphas[idx]
+        C = pmat.to_host(outs[idx])
+        assert C.shape == (it["m"], it["k"], 2 * it["d"] - 1)
+        for a in al:
+            lhs = _eval_all(it["p"], C, a)
+            Aa = _eval_all(it["p"], it["A"], a)[:, :, None]
+            Ba = _eval_all(it["p"], it["B"], a)[:, :, None]
+            rhs = oracle.pmat_mul(it["p"], Aa, Ba, threads=1)[:, :, 0]
+            bad = np.argwhere(lhs != rhs)
+            assert bad.size == 0, (idx, it["m"], it["n"], it["k"], it["d"], bad[:4].tolist())
+        return idx
+
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        done = list(ex.map(check, range(len(items))))
+    assert len(done) == 512
     ctx.close()

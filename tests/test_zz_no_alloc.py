@@ -11,6 +11,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -48,6 +49,9 @@ def _noalloc(p, A, B):
     (synth.P998, 4, (4, 4, 4, 256, 256)),      # one NTT prime, written directly
     (P60, 8, (5, 3, 4, 700, 900)),             # 5 CRT primes
     (P60, 8, (1, 2, 1, 9000, 8000)),           # 2^14-point transforms (column pass)
+    (1000000007, 4, (3, 5, 2, 300, 200)),      # CRT into uint32 output (p not an NTT prime)
+    (1 << 32, 4, (2, 3, 2, 100, 120)),         # even p: Garner's mixed radix
+    (3, 4, (2, 1, 2, 2, 2)),                   # one CRT prime, not used directly
 ])
 def test_noalloc_matches_pmat_mul_twice(env, p, w, shape):
     from paper_1905_04356_gb300 import pmat
@@ -61,6 +65,9 @@ def test_noalloc_matches_pmat_mul_twice(env, p, w, shape):
         ref = pmat.pmat_mul(env, p, A, B)
         env.sync()
         assert np.array_equal(got, pmat.to_host(ref)), call
+        if dA * dB * m * n * k <= 10 ** 8:          # small enough for the oracle too
+            exp = oracle.pmat_mul(p, pmat.to_host(A), pmat.to_host(B))
+            assert np.array_equal(got.astype(np.uint64), exp), call
 
 
 def test_noalloc_rejects_work_beyond_its_scratch(env):
@@ -73,4 +80,8 @@ def test_noalloc_rejects_work_beyond_its_scratch(env):
                                      C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == pmat.PM_ESCRATCH
     rc = pmat.lib().pmat_mul_noalloc(P60, 8, 0, 1, 1, A.data_ptr(), 1, B.data_ptr(), 1, out.data_ptr(), None)
+    assert rc == pmat.PM_EINVAL
+    # a length beyond 2^20 is refused before dA + dB - 1 is formed (nothing runs, nothing is read)
+    rc = pmat.lib().pmat_mul_noalloc(P60, 8, 1, 1, 1, A.data_ptr(), (1 << 62), B.data_ptr(), (1 << 62),
+                                     out.data_ptr(), None)
     assert rc == pmat.PM_EINVAL
