@@ -561,6 +561,28 @@ def main():
                       "frac": round(inst / (dom_ms * 1e-3) / issue_peak, 4) if inst else None,
                       "source": "instruction count from the committed ncu summary of the same kernel source, "
                                 "time from this run's CUDA events"}}
+    def tc_report(ts_tc, st_tc, st_cc):
+        """The tensor-core pointwise form on the same step: its pointwise stage against the
+        CUDA-core one, and its tensor throughput against the measured fp16 MMA rate.  Issued MMA
+        flops count every 128 x 128 x 16 instruction (four points share the 128 rows, one point
+        per lane quarter); useful flops count the 16 digit products of every output."""
+        tc_pw = st_tc["pointwise"][0] / max(1, st_tc["pointwise"][1])
+        cc_pw = st_cc["pointwise"][0] / max(1, st_cc["pointwise"][1])
+        ksteps = (n + 15) // 16
+        issued = K * (L // 4) * 4 * 4 * ksteps * 2 * 128 * 128 * 16
+        useful = K * L * 16 * m * n * k * 2
+        peak_n128 = pmat.mma_rate(local, 128, 4096)
+        peak_n256 = pmat.mma_rate(local, 256, 4096)
+        tf = issued / (tc_pw * 1e-3) / 1e12
+        return {"step_ms": round(sum(ts_tc) / len(ts_tc), 4), "pointwise_ms": round(tc_pw, 4),
+                "cuda_core_pointwise_ms": round(cc_pw, 4), "speedup": round(cc_pw / tc_pw, 3),
+                "outputs_equal": tc_equal, "mma_issued_tflops": round(tf, 1),
+                "mma_useful_tflops": round(useful / (tc_pw * 1e-3) / 1e12, 1),
+                "mma_peak_tflops_n128": round(peak_n128, 1), "mma_peak_tflops_n256": round(peak_n256, 1),
+                "tensor_frac": round(tf / peak_n128, 4),
+                "peak_source": "measured in this run: pm_mma_rate, dense tcgen05.mma kind::f16 of 128 x N x 16",
+                "dtype": "fp16 digits (balanced radix 256), fp32 accumulation"}
+
     value = job_value(ms_step, world)
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -580,7 +602,7 @@ def main():
             "step_compulsory_frac_hbm": round(compulsory / (ms_step * 1e-3) / 1e9 / peak, 4),
             "graph_replay_ms_per_step": round(sum(ts_graph) / len(ts_graph), 4),
             "e2e_single_call_latency_ms": round(e2e_latency_ms, 4),
-            "tensor_core_vs_cuda_core": tc_report(ts_tc, st_tc, stages, pk),
+            "tensor_core_vs_cuda_core": tc_report(ts_tc, st_tc, stages),
             "c2_p998_ms": round(sum(ts998) / len(ts998), 4),
             "c1_4x4_d256_p998_us": round(1000 * sum(ts_c1) / len(ts_c1), 1),
             "wall_s_timed_region": round(t_wall, 3),

@@ -210,10 +210,15 @@ def test_c2_full_output_matches_oracle_fingerprint(ctx, name, ntt_prime):
 
 @pytest.mark.parametrize("case", [(P60, 8, 32, 32, 32, 300, 200), (synth.P998, 4, 5, 7, 3, 100, 90),
                                   (P60, 8, 32, 32, 16, 64, 130), (97, 4, 17, 9, 31, 40, 33),
-                                  (P62, 8, 32, 1, 32, 20, 20)])
+                                  (P62, 8, 32, 1, 32, 20, 20), (P60, 8, 3, 17, 5, 9, 8),
+                                  (P60, 8, 32, 20, 32, 33, 40), (synth.P998, 4, 32, 16, 32, 5, 4),
+                                  (2, 4, 6, 32, 7, 50, 61), (3, 4, 1, 1, 1, 3, 2), (P60, 8, 1, 32, 1, 7, 1000),
+                                  (synth.P998, 4, 31, 31, 31, 1, 1)])
 def test_tensor_core_and_cuda_core_pointwise_agree_with_oracle(ctx, case):
-    """Both pointwise forms (8-bit limbs on tcgen05, 64-bit lazy sums on CUDA cores) give the
-    oracle's product bit for bit."""
+    """Both pointwise forms (balanced 8-bit digits in fp16 on tcgen05, 64-bit lazy sums on CUDA
+    cores) give the oracle's product bit for bit: full and ragged inner dimensions (n = 17, 20
+    leave zero digits up to the MMA's 16-step), one-row / one-column shapes, p = 2 and 3,
+    transform lengths from 16 points."""
     from paper_1905_04356_gb300 import pmat
     p, w, m, n, k, dA, dB = case
     g = synth.rng(31 + m * n * k)
@@ -290,3 +295,39 @@ def test_extreme_coefficients_at_the_crt_bound(ctx, p, n, d):
     B = np.full((n, 2, d + 3), p - 1, dtype=np.uint64)
     got = _gpu(ctx, "pmat_mul", p, A, B)
     assert np.array_equal(got.astype(np.uint64), oracle.pmat_mul(p, A, B))
+
+
+@pytest.mark.parametrize("name,ntt_prime", [("product_32x32_p60", False), ("product_32x32_p998", True)])
+def test_tensor_core_c2_full_output_matches_oracle_fingerprint(ctx, name, ntt_prime):
+    """The whole 32x32 . 32x32, length-4096 product with the tensor-core pointwise form, against
+    the SHA-256 of the oracle's output (the launch configuration the bench times)."""
+    import hashlib
+    import json
+    import os
+    from paper_1905_04356_gb300 import pmat
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "golden.json")))[name]
+    W = synth.product_c2(0, ntt_prime=ntt_prime)
+    ctx.set_option(pmat.PM_OPT_POINTWISE, 2)
+    try:
+        got = _gpu(ctx, "pmat_mul", W["p"], W["A"], W["B"]).astype(np.uint64)
+    finally:
+        ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
+    assert hashlib.sha256(np.ascontiguousarray(got).tobytes()).hexdigest() == gold["sha256"]
+
+
+@pytest.mark.parametrize("p,w", [(P60, 8), (synth.P998, 4), (P62, 8)])
+def test_tensor_core_extreme_inputs(ctx, p, w):
+    """All inputs p - 1 (and all zero in one operand block) through the tensor-core form."""
+    from paper_1905_04356_gb300 import pmat
+    dt = np.uint32 if w == 4 else np.uint64
+    A = np.full((32, 32, 257), p - 1, dtype=dt)
+    B = np.full((32, 32, 255), p - 1, dtype=dt)
+    B[:, :16, :] = 0
+    exp = oracle.pmat_mul(p, A, B)
+    ctx.set_option(pmat.PM_OPT_POINTWISE, 2)
+    try:
+        got = _gpu(ctx, "pmat_mul", p, A, B)
+    finally:
+        ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
+    assert np.array_equal(got.astype(np.uint64), exp)
+
