@@ -274,7 +274,7 @@ static void add_forward(const PrimeDev &P, const void *src, int mode, int64_t sr
     if (lg <= PM_LB_LOG2) {
         FwdJob j;
         j.src = src; j.dst = dst; j.src_stride = src_stride; j.dst_stride = L;
-        j.src_len = (int)src_len; j.src_mode = mode; j.count = entries; j._pad = 0; j.P = P;
+        j.src_len = (int)src_len; j.src_mode = mode; j.count = entries; j.grp = 0; j.P = P;
         const int epb = fwd_entries_per_block(lg);
         blk.push_back(j);
         blk_n.push_back((entries + epb - 1) / epb);
@@ -287,7 +287,7 @@ static void add_forward(const PrimeDev &P, const void *src, int mode, int64_t sr
         FwdJob j;
         const int64_t nb = L >> PM_LB_LOG2;
         j.src = dst; j.dst = dst; j.src_stride = 1 << PM_LB_LOG2; j.dst_stride = 1 << PM_LB_LOG2;
-        j.src_len = 1 << PM_LB_LOG2; j.src_mode = 0; j.count = (int)(entries * nb); j._pad = 0; j.P = P;
+        j.src_len = 1 << PM_LB_LOG2; j.src_mode = 0; j.count = (int)(entries * nb); j.grp = 0; j.P = P;
         const int epb = fwd_entries_per_block(PM_LB_LOG2);
         blk.push_back(j);
         blk_n.push_back((int)((entries * nb + epb - 1) / epb));
@@ -308,6 +308,32 @@ static int launch_packs(pm_ctx *ctx, const std::vector<J> &jobs, const std::vect
     return PM_OK;
 }
 
+// Jobs [g0, blk.size()) transform one source modulo different primes, one job each (transforms
+// of at most 2^14 points): mark them an interleave group.
+static void group_forward(std::vector<FwdJob> &blk, size_t g0, int lg)
+{
+    const size_t G = blk.size() - g0;
+    if (lg > PM_LB_LOG2 || G < 2 || G > 255) return;
+    for (size_t i = 0; i < G; i++) blk[g0 + i].grp = (int)((G << 8) | i);
+}
+
+// Forward block jobs in packs of PM_MAXJ that never split an interleave group.
+static int launch_fwd_packs(pm_ctx *ctx, const std::vector<FwdJob> &jobs, const std::vector<int> &nblk, int blg)
+{
+    size_t i = 0;
+    while (i < jobs.size()) {
+        JobPack<FwdJob> pk;
+        pack_reset(pk);
+        while (i < jobs.size()) {
+            const int G = jobs[i].grp ? jobs[i].grp >> 8 : 1;
+            if (pk.njobs + G > PM_MAXJ) break;
+            for (int g = 0; g < G; g++, i++) pack_add(pk, jobs[i], nblk[i]);
+        }
+        CK(launch_ntt_fwd_block(pk, blg, ctx->stream, &ctx->launches));
+    }
+    return PM_OK;
+}
+
 // Forward jobs of one transform length: column passes first, then the blocks.
 static int launch_fwd_lists(pm_ctx *ctx, const std::vector<FwdJob> &blk, const std::vector<int> &bn,
                             const std::vector<ColJob> &col, const std::vector<int> &cn, int lg)
@@ -315,11 +341,7 @@ static int launch_fwd_lists(pm_ctx *ctx, const std::vector<FwdJob> &blk, const s
     if (!col.empty())
         CKI(launch_packs(ctx, col, cn, [&](const JobPack<ColJob> &pk) {
             return launch_ntt_fwd_cols(pk, lg, ctx->stream, &ctx->launches); }));
-    if (!blk.empty()) {
-        const int blg = lg > PM_LB_LOG2 ? PM_LB_LOG2 : lg;
-        CKI(launch_packs(ctx, blk, bn, [&](const JobPack<FwdJob> &pk) {
-            return launch_ntt_fwd_block(pk, blg, ctx->stream, &ctx->launches); }));
-    }
+    if (!blk.empty()) CKI(launch_fwd_packs(ctx, blk, bn, lg > PM_LB_LOG2 ? PM_LB_LOG2 : lg));
     return PM_OK;
 }
 
@@ -511,13 +533,19 @@ int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count)
                 if (q.lg != lg) continue;
                 const Plan &P = plan[r];
                 const Bufs &b = buf[r - r0];
-                for (size_t i = 0; i < P.pr.size(); i++) {
-                    PrimeDev D = prime_dev(*P.pr[i], lg);
-                    if (!q.At)                          // A's transforms: computed (kept if asked)
-                        add_forward(D, q.A, q.w, q.sA, q.dA, q.m * q.n, a_transform(q, P, b.A, i), lg, blk, bn, col,
-                                    cn);
-                    add_forward(D, q.B, q.w, q.sB, q.dB, q.n * q.k, (u32 *)(b.B + i * P.bB), lg, blk, bn, col, cn);
+                // operand by operand, every prime of one operand side by side (one interleave group)
+                if (!q.At) {                            // A's transforms: computed (kept if asked)
+                    const size_t g0 = blk.size();
+                    for (size_t i = 0; i < P.pr.size(); i++)
+                        add_forward(prime_dev(*P.pr[i], lg), q.A, q.w, q.sA, q.dA, q.m * q.n, a_transform(q, P, b.A, i),
+                                    lg, blk, bn, col, cn);
+                    group_forward(blk, g0, lg);
                 }
+                const size_t g0 = blk.size();
+                for (size_t i = 0; i < P.pr.size(); i++)
+                    add_forward(prime_dev(*P.pr[i], lg), q.B, q.w, q.sB, q.dB, q.n * q.k, (u32 *)(b.B + i * P.bB), lg,
+                                blk, bn, col, cn);
+                group_forward(blk, g0, lg);
             }
             CKI(launch_fwd_lists(ctx, blk, bn, col, cn, lg));
         }
@@ -891,10 +919,13 @@ static int mul_host(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const v
         int tok = stage_begin(ctx, PM_STAGE_FWD);
         std::vector<FwdJob> blk; std::vector<int> bn;
         std::vector<ColJob> col; std::vector<int> cn;
-        for (size_t i = 0; i < K; i++)
-            for (const Up &u : ups)
+        for (const Up &u : ups) {
+            const size_t g0 = blk.size();
+            for (size_t i = 0; i < K; i++)
                 add_forward(prime_dev(*pr[i], lg), u.d, w, u.dl, u.dl, u.rows * u.ncol, (u32 *)(u.T + i * u.bT), lg,
                             blk, bn, col, cn);
+            group_forward(blk, g0, lg);
+        }
         CKI(launch_fwd_lists(ctx, blk, bn, col, cn, lg));
         stage_end(ctx, tok);
     }
@@ -911,6 +942,7 @@ static int mul_host(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const v
                 add_forward(prime_dev(*pr[i], lg), u.d + (size_t)r0 * u.ncol * u.dl * w, w, u.dl, u.dl,
                             (r1 - r0) * u.ncol, (u32 *)(u.T + i * u.bT) + (size_t)r0 * u.ncol * L, lg, blk, bn, col,
                             cn);
+            group_forward(blk, 0, lg);
             CKI(launch_fwd_lists(ctx, blk, bn, col, cn, lg));
             stage_end(ctx, tok);
         }

@@ -124,11 +124,15 @@ __device__ __forceinline__ u64 sub64(u64 a, u64 b, u64 p) { return a >= b ? a - 
 // Forward transform of `count` blocks of 2^lg points.  Block e reads
 // src + e*src_stride (src_len values, zero beyond) and writes dst + e*dst_stride.
 // src_mode: 0 = u32 already in [0, 2q), 4 = user u32 in [0,p), 8 = user u64.
+// grp: 0, or (G << 8) | g for job g of an interleave group of G consecutive jobs in the pack (the
+// same source modulo G primes, equal block counts): the group's blocks alternate between its
+// jobs, so the G CTAs that read the same source entries run side by side and all but the first
+// find them in L2.
 struct FwdJob {
     const void *src;
     u32 *dst;
     i64 src_stride, dst_stride;
-    int src_len, src_mode, count, _pad;
+    int src_len, src_mode, count, grp;
     PrimeDev P;
 };
 // Inverse transform.  dst_mode: 0 = u32 staging (unscaled, all points),

@@ -174,7 +174,7 @@ extern "C" int pmat_mul_noalloc(uint64_t p, int w, int m, int n, int k, const vo
                 if (lg <= LBL) {
                     FwdJob j;
                     j.src = src; j.dst = dst; j.src_stride = d; j.dst_stride = L; j.src_len = (int)d; j.src_mode = w;
-                    j.count = ent; j._pad = 0; j.P = P[i];
+                    j.count = ent; j.grp = 0; j.P = P[i];
                     const int epb = fwd_block_threads(lg) / (int)(L >> 4);
                     add(pk, j, (ent + epb - 1) / epb);
                 } else {
@@ -185,7 +185,7 @@ extern "C" int pmat_mul_noalloc(uint64_t p, int w, int m, int n, int k, const vo
                     const int64_t nb = L >> LBL;
                     FwdJob j;
                     j.src = dst; j.dst = dst; j.src_stride = 1 << LBL; j.dst_stride = 1 << LBL; j.src_len = 1 << LBL;
-                    j.src_mode = 0; j.count = (int)(ent * nb); j._pad = 0; j.P = P[i];
+                    j.src_mode = 0; j.count = (int)(ent * nb); j.grp = 0; j.P = P[i];
                     const int epb = fwd_block_threads(LBL) / ((1 << LBL) >> 4);
                     add(pk, j, (int)((ent * nb + epb - 1) / epb));
                 }

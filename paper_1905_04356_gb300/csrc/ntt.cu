@@ -249,11 +249,16 @@ __global__ void __launch_bounds__(LG == 14 ? 1024 : 512, LG == 14 ? 2 : 4) k_ntt
     extern __shared__ u32 sm[];
     constexpr int L = 1 << LG, TPT = L >> 4, B0 = ((LG - 1) & 3) + 1;
     const int b = blockIdx.x;
-    const int jb = find_job(pk.blk_start, b);
+    int jb = find_job(pk.blk_start, b), lb = b - pk.blk_start[jb];
+    if (const int g = pk.jobs[jb].grp) {   // interleave group: block rel -> job rel % G, block rel / G
+        const int G = g >> 8, first = jb - (g & 255), rel = b - pk.blk_start[first];
+        jb = first + rel % G;
+        lb = rel / G;
+    }
     const FwdJob &J = pk.jobs[jb];
     const int tpb = blockDim.x / TPT;
     const int lt = threadIdx.x / TPT, tid = threadIdx.x - lt * TPT;
-    const i64 e = (i64)(b - pk.blk_start[jb]) * tpb + lt;
+    const i64 e = (i64)lb * tpb + lt;
     const bool act = e < J.count;
     u32 *X = sm + lt * (L + (L >> 5));
     u32 v[16];
