@@ -371,6 +371,33 @@ int pmat_inv_slices(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_
 int pmat_solve_series_hol(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA,
                           const void *b, int64_t db, int64_t N, void *v);
 
+/* Autotuner for the pointwise products of a product shape (Sec. 2, "Polynomial
+ * matrix multiplication": the n^omega d term).  Times every pointwise form that
+ * applies to an m x n . n x k product of lengths dA, dB modulo p -- the
+ * CUDA-core form with each of its (up to) four best block tiles by the cost
+ * model, the streaming form (n <= 8), the matrix-vector form (k = 1), the
+ * tensor-core digit form (m, n, k <= 32) -- over `reps` products each (after
+ * one warm-up) on zero inputs (the kernels' time does not depend on the
+ * values), and records the fastest in the context: later products of the same
+ * (m, n, k, transform length) take it when PM_OPT_POINTWISE is 0 (auto).
+ * out: HOST int64_t[5] = form (1 CUDA-core block tile, 2 tensor-core, 3
+ * streaming, 4 matrix-vector), bi, bk (the block tile of form 1, else 0), the
+ * winner's pointwise-stage time per product in ns, the number of candidates.
+ * Allocates and frees its scratch on the context's stream, synchronises it and
+ * discards earlier stage-timing records.  Requires 1 <= reps <= 1000 and the
+ * product arguments of pmat_mul; PM_EINVAL otherwise. */
+int pm_tune_product(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, int64_t dA, int64_t dB, int reps,
+                    int64_t *out);
+
+/* Autotuner for PM-Basis's threshold T (Sec. 3, Algorithm 3: orders <= T run
+ * M-Basis at a leaf).  Times pm_basis on seeded pseudo-random F (m x n, order d,
+ * uniform shift 0) modulo the odd prime p for T in {8, 16, 32, 64, 128} (those
+ * <= d, and 8), `reps` calls each after one warm-up, and sets the context's
+ * threshold (PM_OPT_THRESHOLD) to the fastest.  out: HOST int64_t[2] = T, its
+ * time per call in ns.  Allocates and frees its scratch on the context's
+ * stream and synchronises it.  Requires 1 <= reps <= 100; PM_EINVAL otherwise. */
+int pm_tune_basis(pm_ctx *ctx, uint64_t p, int m, int n, int64_t d, int reps, int64_t *out);
+
 /* Measured rate of dense tensor-core MMA on device `device`: tcgen05.mma of
  * kind::f16 (fp16 x fp16 operands in shared memory, fp32 accumulator in tensor
  * memory) of shape 128 x n_cols x 16, `iters` back to back per SM on every SM,

@@ -400,6 +400,8 @@ size_t prod_operand_bytes(pm_ctx *ctx, uint64_t p, int n, int64_t dmin, int lg, 
 // products where the shape allows (m, n, k <= 32) when that form is requested, small inner
 // dimensions (n <= 8) by a streaming kernel (one launch per n), matrix-vector products
 // (k = 1, n <= 64) by another, the staged CUDA-core 64-bit form otherwise.
+// With PM_OPT_POINTWISE = 0 a form recorded by pm_tune_product for the same (m, n, k, length) is
+// taken; otherwise (and for forms that do not apply) the rules above.
 static void add_pointwise(pm_ctx *ctx, PwLists &pl, u32 *A, u32 *B, u32 *C, int m, int n, int k, int lg,
                           const PrimeDev &D)
 {
@@ -407,9 +409,17 @@ static void add_pointwise(pm_ctx *ctx, PwLists &pl, u32 *A, u32 *B, u32 *C, int 
     memset(&j, 0, sizeof(j));
     j.A = A; j.B = B; j.C = C;
     j.m = m; j.n = n; j.k = k; j.L = 1 << lg; j.P = D;
-    if (ctx->opt_pointwise == 2 && tc_supported(j)) { pl.tjobs.push_back(j); pl.tnb.push_back(tc_blocks(j)); }
-    else if (pws_supported(j)) { pl.sjobs[j.n].push_back(j); pl.snb[j.n].push_back(pws_blocks(j)); }
-    else if (pwv_supported(j)) { pl.vjobs.push_back(j); pl.vnb.push_back(pwv_blocks(j)); }
+    int form = 0, bi = 0, bk = 0;
+    if (ctx->force_form >= 0) { form = ctx->force_form; bi = ctx->force_bi; bk = ctx->force_bk; }
+    else if (ctx->opt_pointwise == 2) form = 2;
+    else if (ctx->opt_pointwise == 0)
+        for (const auto &t : ctx->tune)
+            if (t.m == m && t.n == n && t.k == k && t.lg == lg) { form = t.form; bi = t.bi; bk = t.bk; break; }
+    if (form == 2 && tc_supported(j)) { pl.tjobs.push_back(j); pl.tnb.push_back(tc_blocks(j)); }
+    else if (form == 1 && bi > 0 && bk > 0) { const int nbk = pw_plan_tile(j, bi, bk); pl.jobs.push_back(j); pl.nb.push_back(nbk); }
+    else if (form == 4 && pwv_supported(j)) { pl.vjobs.push_back(j); pl.vnb.push_back(pwv_blocks(j)); }
+    else if ((form == 0 || form == 3 || form == 2) && pws_supported(j)) { pl.sjobs[j.n].push_back(j); pl.snb[j.n].push_back(pws_blocks(j)); }
+    else if ((form == 0 || form == 2) && pwv_supported(j)) { pl.vjobs.push_back(j); pl.vnb.push_back(pwv_blocks(j)); }
     else { const int nbk = pw_plan(j); pl.jobs.push_back(j); pl.nb.push_back(nbk); }
 }
 

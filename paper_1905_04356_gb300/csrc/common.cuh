@@ -205,6 +205,8 @@ cudaError_t launch_ntt_fwd_cols(const JobPack<ColJob> &pk, int lg, cudaStream_t 
 cudaError_t launch_ntt_inv_cols(const JobPack<ColJob> &pk, int lg, cudaStream_t st, long long *launches);
 cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
 int pw_plan(PwJob &j);
+int pw_plan_tile(PwJob &j, int bi, int bk);
+int pw_tiles(const PwJob &j, int *bi_out, int *bk_out, int max);
 cudaError_t launch_pointwise_sn(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
 bool pws_supported(const PwJob &j);
 int pws_blocks(const PwJob &j);

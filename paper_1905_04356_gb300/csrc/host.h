@@ -40,6 +40,11 @@ struct pm_ctx {
     int opt_leaf_cluster = 1;         // PM-Basis leaves on a CTA cluster (0 = one CTA)
     int opt_host_chunks = 0;          // pmat_mul_host output chunks (0 = automatic)
     int opt_withhold = 0;             // test hook: the tensor-core pointwise kernel withholds an MMA
+    // pointwise forms picked by pm_tune_product, per (m, n, k, transform length): form 1 = CUDA-core
+    // block tile (bi, bk), 2 = tensor-core, 3 = streaming (n <= 8), 4 = matrix-vector (k = 1)
+    struct Tune { int m, n, k, lg, form, bi, bk; };
+    std::vector<Tune> tune;
+    int force_form = -1, force_bi = 0, force_bk = 0;   // the tuner's candidate while it times one
     struct Mark { int stage; cudaEvent_t a, b; long long launches; };
     std::vector<Mark> marks;          // recorded stage intervals
     std::vector<cudaEvent_t> spare;   // reusable events

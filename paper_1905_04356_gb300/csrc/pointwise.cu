@@ -43,17 +43,47 @@ static u32 magic31(int d) { return (u32)(((1ull << 31) + d - 1) / d); }
 // dimension n is staged PS_LC entries at a time and, when a block tile leaves slots
 // free, each chunk is split into ns contiguous slices whose partial sums are added
 // at the end.  Returns the block count.
-int pw_plan(PwJob &j)
+// Block tiles (bi, bk) that fit, in increasing order of the cost model (at most `max`; ties
+// keep the loop order, so the first is the plan pw_plan takes).
+int pw_tiles(const PwJob &j, int *bi_out, int *bk_out, int max)
 {
     const int nti = (j.m + 3) / 4, ntk = (j.k + 7) / 8;
-    long long best = -1;
+    long long cost[256];
+    int cbi[256], cbk[256], nc = 0;                  // bi bk <= 32: at most 130 candidates
     for (int bi = 1; bi <= nti && bi <= 32; bi++)
         for (int bk = 1; bk <= ntk && bi * bk <= 32; bk++) {
             if (bi * 4 * PS_PA + bk * 8 * PS_PB > PS_WORDS) continue;
             const long long nb = (long long)((nti + bi - 1) / bi) * ((ntk + bk - 1) / bk);
-            const long long cost = nb * (((bi * bk + 3) / 4) * 4 * 64 + (bi * 4 + bk * 8) * 16 + 64);
-            if (best < 0 || cost < best) { best = cost; j.bi = bi; j.bk = bk; }
+            cost[nc] = nb * (((bi * bk + 3) / 4) * 4 * 64 + (bi * 4 + bk * 8) * 16 + 64);
+            cbi[nc] = bi;
+            cbk[nc] = bk;
+            nc++;
         }
+    int out = 0;
+    for (; out < max && out < nc; out++) {           // selection of the cheapest remaining
+        int best = -1;
+        for (int c = 0; c < nc; c++)
+            if (cost[c] >= 0 && (best < 0 || cost[c] < cost[best])) best = c;
+        bi_out[out] = cbi[best];
+        bk_out[out] = cbk[best];
+        cost[best] = -1;
+    }
+    return out;
+}
+
+int pw_plan(PwJob &j)
+{
+    int bi = 1, bk = 1;
+    pw_tiles(j, &bi, &bk, 1);
+    return pw_plan_tile(j, bi, bk);
+}
+
+// The plan for block tile (bi, bk) (one that pw_tiles lists).  Returns the block count.
+int pw_plan_tile(PwJob &j, int bi, int bk)
+{
+    const int nti = (j.m + 3) / 4, ntk = (j.k + 7) / 8;
+    j.bi = bi;
+    j.bk = bk;
     const int items = j.bi * j.bk, rb = j.bi * 4, cb = j.bk * 8;
     j.lc = j.n < PS_LC ? j.n : PS_LC;
     j.ns = 1;                                                  // slices of >= 8 products per chunk

@@ -80,6 +80,8 @@ def lib():
             "pmat_solve_series_hol": ([P, u64, i32, i32, P, i64, P, i64, i64, P], i32),
             "pmat_inv_slices": ([P, u64, i32, i32, P, i64, i32, P], i32),
             "pm_mma_rate": ([i32, i32, i32, C.POINTER(C.c_double)], i32),
+            "pm_tune_product": ([P, u64, i32, i32, i32, i32, i64, i64, i32, P], i32),
+            "pm_tune_basis": ([P, u64, i32, i32, i64, i32, P], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -424,4 +426,18 @@ def mma_rate(device: int = 0, n_cols: int = 256, iters: int = 4096) -> float:
     if rc != PM_OK:
         raise PmError(rc, "pm_mma_rate failed")
     return out.value
+
+
+def tune_product(ctx: Context, p: int, w: int, m: int, n: int, k: int, dA: int, dB: int, reps: int = 3):
+    """pm_tune_product: (form, bi, bk, pointwise ns per product, candidates timed)."""
+    out = np.zeros(5, dtype=np.int64)
+    ctx._ck(lib().pm_tune_product(ctx.h, p, w, m, n, k, dA, dB, reps, out.ctypes.data))
+    return tuple(int(v) for v in out)
+
+
+def tune_basis(ctx: Context, p: int, m: int, n: int, d: int, reps: int = 1):
+    """pm_tune_basis: (threshold T, ns per call); the context's threshold is set to T."""
+    out = np.zeros(2, dtype=np.int64)
+    ctx._ck(lib().pm_tune_basis(ctx.h, p, m, n, d, reps, out.ctypes.data))
+    return tuple(int(v) for v in out)
 
