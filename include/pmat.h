@@ -40,9 +40,9 @@
  *   (i, j) is X[(i*c + j)*len + t].
  * * Element width w is 4 (uint32_t, requires p < 2^32) or 8 (uint64_t,
  *   requires p < 2^62).  Inputs must be reduced into [0, p); outputs are.
- * * p >= 2.  Products are ring operations and accept any such p; pm_basis and
- *   bivariate_resultant need p prime (not checked, as for a field type) and
- *   odd (checked); pmat_inv_trunc needs p prime (not checked), 2 allowed.
+ * * p >= 2.  Products are ring operations and accept any such p; pm_basis,
+ *   pm_intbasis and pmat_inv_trunc need p prime (not checked, as for a field
+ *   type), 2 included; the resultants need p odd (checked).
  * * The caller owns every input and output buffer; outputs must not alias
  *   inputs.  The context owns its workspace, twiddle tables and plans.
  * * All calls are asynchronous and ordered on the context's stream.  A
@@ -252,7 +252,8 @@ int pmat_mul_noalloc(uint64_t p, int w, int m, int n, int k,
  * zero).  shift: HOST int64_t[m].  P: DEVICE output, m x m entries of length
  * d+1, an s-ordered weak Popov approximant basis of (F, d).  rdeg_out: HOST
  * int64_t[m] receiving rdeg_s(P) (this call therefore synchronises the
- * stream).  Requires p odd, 1 <= n, 1 <= m, d >= 1. */
+ * stream).  Requires p prime (p = 2 included: the leaves then work on bits),
+ * 1 <= n, 1 <= m, d >= 1. */
 int pm_basis(pm_ctx *ctx, uint64_t p, int m, int n, const void *F, int64_t lenF,
              int64_t d, const int64_t *shift, void *P, int64_t *rdeg_out);
 
@@ -265,8 +266,8 @@ int pm_basis(pm_ctx *ctx, uint64_t p, int m, int n, const void *F, int64_t lenF,
  * that Algorithm 4 returns (Algorithm 5 returns the same basis).  rdeg_out:
  * HOST int64_t[m] receiving rdeg_s(P) (this call synchronises the stream).
  * The residual of a node (P1 at the second half of the points) is evaluated
- * by a chirp middle product on the product path.  Requires p an odd prime
- * < 2^62, c in [0, p), q in [1, p), 1 <= m, n <= 128, sigma >= 1; the points
+ * by a chirp middle product on the product path.  Requires p a prime < 2^62
+ * (2 included), c in [0, p), q in [1, p), 1 <= m, n <= 128, sigma >= 1; the points
  * need not be distinct.  Returns PM_EINVAL on bad arguments. */
 int pm_intbasis(pm_ctx *ctx, uint64_t p, int m, int n, const void *E, int64_t sigma,
                 uint64_t c, uint64_t q, const int64_t *shift, void *P, int64_t *rdeg_out);

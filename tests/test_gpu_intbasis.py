@@ -68,6 +68,9 @@ CASES = [
     (P60, 2, 4, 9, 32, 5, 2),          # m < n
     (P60, 4, 2, 20, 4, 6, 1),          # q = 1: every point is c
     (P60, 4, 2, 20, 4, 0, 5),          # c = 0: every point is 0
+    (2, 4, 2, 30, 4, 1, 1),            # p = 2: every point is 1 (the leaves on bits)
+    (2, 6, 3, 64, 16, 0, 1),           # p = 2, every point 0
+    (2, 32, 16, 100, 32, 1, 1),
 ]
 
 
@@ -85,7 +88,8 @@ def test_pm_intbasis_matches_oracle(ctx, case):
         assert np.array_equal(rd, rdexp), (case, s)
 
 
-@pytest.mark.parametrize("case", [(P60, 6, 2, 40, 8, 3, 5), (97, 5, 3, 30, 32, 5, 3), (P60, 32, 16, 96, 32, 7, 3)])
+@pytest.mark.parametrize("case", [(P60, 6, 2, 40, 8, 3, 5), (97, 5, 3, 30, 32, 5, 3), (P60, 32, 16, 96, 32, 7, 3),
+                                  (2, 5, 3, 30, 32, 1, 1)])
 def test_single_cta_leaf_matches_oracle(ctx, case):
     """The one-CTA interpolant leaf (basis in global memory) gives the same bases."""
     p, m, n, sigma, T, c, q = case

@@ -61,6 +61,11 @@ CASES = [
     (synth.P998, 6, 3, 40, 8),
     (P60, 3, 3, 10, 4),      # m = n: no fast path
     (P60, 2, 4, 9, 32),      # m < n
+    (2, 4, 2, 40, 8),        # p = 2: the leaves on bits
+    (2, 6, 3, 100, 32),
+    (2, 32, 16, 200, 16),
+    (2, 3, 1, 1024, 32),     # p = 2 with node products at half length
+    (2, 2, 4, 9, 32),
 ]
 
 
@@ -97,7 +102,7 @@ def test_pm_basis_rejects_even_modulus(ctx):
     assert e.value.code == pmat.PM_EINVAL
 
 
-@pytest.mark.parametrize("case", [(P60, 6, 2, 40, 8), (97, 5, 3, 30, 32), (P60, 32, 16, 96, 32)])
+@pytest.mark.parametrize("case", [(P60, 6, 2, 40, 8), (97, 5, 3, 30, 32), (P60, 32, 16, 96, 32), (2, 6, 2, 40, 8)])
 def test_single_cta_leaf_matches_oracle(ctx, case):
     """The one-CTA leaf kernel (basis in global memory) gives the same bases."""
     from paper_1905_04356_gb300 import pmat
