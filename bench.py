@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the timings of the drivers (see --extra)")
+    ap.add_argument("--extra-only", action="store_true",
+                    help="diagnostic: run only the --extra workloads (no headline step) and print their timings")
     ap.add_argument("--extra", default="pm_basis,resultant,batched,inverse,solve,slices,intbasis,linsolve,villard",
                     help="comma-separated subset of pm_basis, resultant, batched, inverse, solve, slices, "
                          "intbasis, linsolve, villard")
@@ -389,6 +391,13 @@ def main():
     from paper_1905_04356_gb300 import Context, build, pmat
 
     torch.cuda.set_device(local)
+    if args.extra_only:
+        build.build()
+        s0 = torch.cuda.Stream()
+        c0 = Context(local, stream=s0)
+        print(json.dumps({"extra_only": extra_workloads(c0, s0, tuple(args.extra.split(",")))}), flush=True)
+        c0.close()
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
