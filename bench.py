@@ -48,8 +48,9 @@ def parse():
                     help="skip the timings of the drivers (see --extra)")
     ap.add_argument("--extra-only", action="store_true",
                     help="diagnostic: run only the --extra workloads (no headline step) and print their timings")
-    ap.add_argument("--extra", default="pm_basis,resultant,batched,inverse,solve,slices,intbasis,linsolve,villard",
-                    help="comma-separated subset of pm_basis, resultant, batched, inverse, solve, slices, "
+    ap.add_argument("--extra", default="vandermonde,pm_basis,resultant,batched,inverse,solve,slices,intbasis,linsolve,"
+                                         "villard",
+                    help="comma-separated subset of vandermonde, pm_basis, resultant, batched, inverse, solve, slices, "
                          "intbasis, linsolve, villard")
     return ap.parse_args()
 
@@ -218,8 +219,8 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------- other workloads (reported under "extra")
-def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse", "solve", "slices", "intbasis",
-                                   "linsolve", "villard"), reps=3):
+def extra_workloads(ctx, s, which=("vandermonde", "pm_basis", "resultant", "batched", "inverse", "solve", "slices",
+                                   "intbasis", "linsolve", "villard"), reps=3):
     """PM-Basis (F 32x16, order 8192, 60-bit p), 512 batched uneven products, resultants
     (deg_x = deg_y = 150, 1 prime and 16 primes), the truncated inverse of a 32x32 matrix of
     degree < 4096 mod x^4096 and the lifted series solution of A v = b mod x^32768 (same A, b of
@@ -365,9 +366,46 @@ def extra_workloads(ctx, s, which=("pm_basis", "resultant", "batched", "inverse"
         out["resultant_villard_stage_ms"] = {k: round(v, 2) for k, v in stage_split(run)[0].items()}
         return out
 
+    def vandermonde():
+        """Products by Vandermonde-matrix evaluation / interpolation (dense tensor-core products
+        mod 998244353) next to the NTT path on the same inputs, at the product table's m = 128,
+        d = 1024 and m = 512, d = 128 and at 32 x 32, d = 4096; outputs compared; the GEMM
+        stages' issued MMA throughput against the fp16 rate measured in this run."""
+        res = {}
+        peak = pmat.mma_rate(0, 128, 4096)
+        for (mm, dd) in ((128, 1024), (512, 128), (32, 4096)):
+            g = synth.rng(mm + dd)
+            Ah = synth.uniform(g, (mm, mm, dd), synth.P998, np.uint32)
+            Bh = synth.uniform(g, (mm, mm, dd), synth.P998, np.uint32)
+            A, B = pmat.to_device(Ah), pmat.to_device(Bh)
+            del Ah, Bh
+            C1 = torch.empty((mm, mm, 2 * dd - 1), dtype=torch.int32, device="cuda")
+            C2 = torch.empty_like(C1)
+            vd = lambda: pmat.pmat_mul_vdm(ctx, synth.P998, A, B, out=C1)  # noqa: E731
+            nt = lambda: pmat.pmat_mul(ctx, synth.P998, A, B, out=C2)     # noqa: E731
+            t_vd, t_nt = ev_ms(vd, 2), ev_ms(nt, 2)
+            st, _ = stage_split(vd, 2)
+            L = 1 << max(5, (2 * dd - 2).bit_length())
+            nks = lambda K: (K + 15) // 16                                    # noqa: E731
+            tiles = lambda M, N: ((M + 127) // 128) * ((N + 31) // 32)       # noqa: E731
+            mma = 2 * 128 * 128 * 16 * 4
+            e = mm * mm
+            eval_fl = 2 * tiles(e, L) * nks(dd) * mma
+            interp_fl = tiles(e, 2 * dd - 1) * nks(L) * mma
+            torch.cuda.synchronize()
+            key = f"m{mm}_d{dd}"
+            res[key] = {"vdm_ms": round(t_vd, 3), "ntt_ms": round(t_nt, 3), "outputs_equal": bool(torch.equal(C1, C2)),
+                        "vdm_stage_ms": {k2: round(v, 3) for k2, v in st.items()},
+                        "eval_gemm_tflops": round(eval_fl / (st["fwd_ntt"] * 1e-3) / 1e12, 1),
+                        "interp_gemm_tflops": round(interp_fl / (st["inv_ntt"] * 1e-3) / 1e12, 1),
+                        "eval_tensor_frac": round(eval_fl / (st["fwd_ntt"] * 1e-3) / 1e12 / peak, 4)}
+            del A, B, C1, C2
+            torch.cuda.empty_cache()
+        return {"vandermonde_p998": res, "mma_peak_tflops_n128": round(peak, 1)}
+
     out = {}
     with torch.cuda.stream(s):
-        for name, fn in (("pm_basis", pm_basis), ("resultant", resultant), ("batched", batched),
+        for name, fn in (("vandermonde", vandermonde), ("pm_basis", pm_basis), ("resultant", resultant), ("batched", batched),
                          ("inverse", inverse), ("solve", solve), ("slices", slices), ("intbasis", intbasis),
                          ("linsolve", linsolve), ("villard", villard)):
             if name in which:

@@ -8,6 +8,9 @@
  *   pmat_mul, pmat_mul_trunc      Sec. 2, "Polynomial matrix multiplication"
  *   pmat_middle_product           Sec. 2, "Polynomial multiplication":
  *                                 MiddleProduct(F, G, c, d)
+ *   pmat_mul_vdm                  the same by Vandermonde-matrix evaluation and
+ *                                 interpolation (Sec. 2, dense products on the
+ *                                 tensor cores)
  *   pmat_mul_batched              many independent products in one call
  *   pmat_mul_host                 the same product from and to host memory,
  *                                 copies overlapped with the stages
@@ -371,6 +374,23 @@ int pmat_inv_slices(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_
  * and uses the driver arena for the slices.  Asynchronous. */
 int pmat_solve_series_hol(pm_ctx *ctx, uint64_t p, int w, int n, const void *A, int64_t dA,
                           const void *b, int64_t db, int64_t N, void *v);
+
+/* C (m x k, length dA+dB-1) = A . B mod p by evaluation and interpolation as
+ * multiplications by Vandermonde matrices (Sec. 2, "Polynomial matrix
+ * multiplication": the variant after Doliskani, Giorgi, Lebreton and Schost,
+ * where evaluation / interpolation become products of matrices over F_p of
+ * sizes about (d x d) by (d x n^2)).  The points are the powers of w of order L
+ * (L = the power of two >= dA + dB - 1, at least 32), so the interpolation
+ * matrix is the explicit inverse L^-1 w^(-t j); the evaluations T = X V^T, the
+ * interpolation C = T_C W^T are dense products mod p on the tensor cores
+ * (fp16 digits of balanced radix 256, fp32 accumulation drained every 64 inner
+ * entries), the pointwise products those of pmat_mul.  Same layouts and result
+ * as pmat_mul; A, B, C are uint32_t (w = 4).  Requires p a prime below 2^30 with
+ * L | p - 1 (an NTT prime for the length, e.g. 998244353) -- PM_EUNSUPPORTED
+ * otherwise -- and 1 <= dA, dB <= 2^15, m, n, k >= 1 (PM_EINVAL).  Uses the
+ * context's workspace; asynchronous on the context's stream. */
+int pmat_mul_vdm(pm_ctx *ctx, uint64_t p, int m, int n, int k, const void *A, int64_t dA, const void *B,
+                 int64_t dB, void *C);
 
 /* Autotuner for the pointwise products of a product shape (Sec. 2, "Polynomial
  * matrix multiplication": the n^omega d term).  Times every pointwise form that

@@ -441,6 +441,21 @@ static int launch_pointwise_lists(pm_ctx *ctx, const PwLists &pl)
     return PM_OK;
 }
 
+// The pointwise stage alone, for transforms computed elsewhere (the Vandermonde products).
+int run_pointwise(pm_ctx *ctx, u32 *A, u32 *B, u32 *C, int m, int n, int k, int lg, const PrimeDev &D)
+{
+    PwLists pl;
+    add_pointwise(ctx, pl, A, B, C, m, n, k, lg, D);
+    return launch_pointwise_lists(ctx, pl);
+}
+
+// Work of a Vandermonde product (one prime): its compulsory bytes and pointwise multiply-adds.
+void count_work_vdm(pm_ctx *ctx, int lg, int m, int n, int k, int64_t dA, int64_t dB, int64_t len)
+{
+    ctx->work[0] += ((int64_t)m * n * dA + (int64_t)n * k * dB + (int64_t)m * k * len) * 4;
+    ctx->work[1] += (int64_t)(int64_t(1) << lg) * m * n * k;
+}
+
 // Inverse transforms of eC entries (src, stride L) modulo one prime; coefficients off ..
 // off+out_len-1 of each go to dst (entry stride dstride) in the given mode (1 = u32 residues,
 // 4 / 8 = the caller's element width).

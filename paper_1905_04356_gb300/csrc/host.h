@@ -109,3 +109,12 @@ size_t prod_operand_bytes(pm_ctx *ctx, uint64_t p, int n, int64_t dmin, int lg, 
 int prod_batch(pm_ctx *ctx, const ProdReq *reqs, int count);
 
 int ceil_log2(int64_t x);
+
+// The pointwise stage of the product path on transforms computed elsewhere, and the work
+// counters of a Vandermonde product (vdm.cu).
+int run_pointwise(pm_ctx *ctx, u32 *A, u32 *B, u32 *C, int m, int n, int k, int lg, const PrimeDev &D);
+void count_work_vdm(pm_ctx *ctx, int lg, int m, int n, int k, int64_t dA, int64_t dB, int64_t len);
+// C (M x N, row stride ldc) = A B^T mod the prime of P from tensor-core digit chunks (vdm.cu).
+int vd_modgemm(pm_ctx *ctx, const unsigned char *Ad, const unsigned char *Bd, int M, int N, int nks, u32 *C, int64_t ldc,
+               const PrimeDev &P);
+

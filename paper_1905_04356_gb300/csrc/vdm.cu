@@ -1,0 +1,446 @@
+// vdm.cu -- polynomial-matrix products by evaluation and interpolation done as
+// multiplications by Vandermonde matrices (Sec. 2, "Polynomial matrix
+// multiplication": the variant after Doliskani, Giorgi, Lebreton and Schost,
+// where the O(n^2 M(d)) evaluation / interpolation part becomes products of
+// matrices over F_p of sizes about (d x d) by (d x n^2)).
+//
+// The points are the powers of an element w of order L (an NTT prime p, L the
+// power of two above the output length), so the evaluation matrix is
+// V[j][l] = w^(j l) and the interpolation matrix is its inverse,
+// W[t][j] = L^-1 w^(-t j).  Then, with X_A the m n entries of A as rows of
+// their dA coefficients (the caller's layout):
+//     T_A = X_A V_A^T   (m n x L, V_A = V restricted to l < dA),  T_B alike,
+//     T_C(e)[j] = sum over the inner dimension of T_A T_B at every point j
+//                 (the pointwise products of the product path),
+//     C   = T_C W^T    (m k x (dA + dB - 1)).
+// Each of the three is a dense product C = A B^T mod p on the tensor cores.
+//
+// The tensor-core modular product (k_modgemm).  Residues are split once into
+// balanced radix-256 digits in fp16 (d_0..d_2 in [-128, 127], d_3 in [0, 64],
+// the bytes of r + 0x80808080 minus 128) and stored in chunks that are the
+// shared-memory operand tiles of one 16-wide K-step in the no-swizzle K-major
+// core-matrix layout: an A chunk holds the four digit tiles of 128 rows (16 KB),
+// a B chunk the four digit blocks of 32 rows stacked as 128 MMA rows (4 KB).  A
+// CTA computes a 128 x 32 output tile: per K-step, four tcgen05.mma of 128 x 128
+// x 16 (digit x of A against [B_0 B_1 B_2 B_3]) write tensor-memory columns
+// [32x, 32x + 128), so column block w accumulates E_w = sum_{x+y=w} A_x B_y.
+// A digit product is at most 2^14 in magnitude and E_w has at most 4 x 64 of
+// them per 64 inner entries, so after every 4 K-steps the seven accumulators
+// (|E_w| <= 2^22, exact in fp32) are drained: one FADD of 1.5 2^23 gives
+// E_w's bits, sum_w (256^w mod p) E_w + the running residue is reduced mod p.
+// Roles: warp 4 issues the chunks' bulk copies (cp.async.bulk, mbarrier
+// transaction counts) into a ring of 4 stages, warp 5's first thread the MMAs,
+// warps 0-3 (one per lane quarter) drain the accumulators and write the tile.
+// Every wait is bounded: after a timeout PM_ETIMEOUT is recorded, later waits
+// return at once and the loops run out (output undefined); before the CTA exits
+// the producer waits (bounded) for its copies and the MMA thread for its MMAs.
+#include <cuda_fp16.h>
+#include <cstring>
+#include <vector>
+
+#include "host.h"
+
+#define VD_STAGES 4
+#define VD_ACHUNK 16384      // 128 rows x 16 K fp16 x 4 digits
+#define VD_BCHUNK 4096       // 32 rows x 16 K fp16 x 4 digits (128 MMA rows)
+#define VD_STAGE (VD_ACHUNK + VD_BCHUNK)
+#define VD_SMEM (VD_STAGES * VD_STAGE)
+#define VD_THREADS 192
+#define VD_COLS 256          // tensor-memory columns (7 x 32 used)
+#define VD_KC 4              // K-steps per drain (64 inner entries)
+
+#define CKI(call)                                                       \
+    do {                                                                \
+        int _rc = (call);                                               \
+        if (_rc) return _rc;                                            \
+    } while (0)
+
+namespace {
+
+struct MgJob {
+    const unsigned char *Ad, *Bd;   // digit chunks: A [row block][K-step] (16 KB), B [row block][K-step] (4 KB)
+    u32 *C;                         // C[i ldc + j] for i < M, j < N, in [0, p)
+    i64 ldc;
+    int M, N, nks, nbN;             // rows, columns, K-steps, 32-column blocks
+    PrimeDev P;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of (row r, inner 8 kk8 .. 8 kk8 + 7) in a 128 x 16 fp16 tile (K-major, no swizzle:
+// 8-row x 16-byte core matrices, LBO 128 B between the two K-adjacent ones, SBO 256 B between
+// 8-row groups)
+__device__ __forceinline__ int op_off(int r, int kk8) { return (r >> 3) * 256 + kk8 * 128 + (r & 7) * 16; }
+
+__device__ __forceinline__ uint64_t op_desc(uint32_t addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+           (1ull << 46);
+}
+
+// fp16 pair of digit x of two biased residues (bytes x of t0 and t1 as 0x6400 | byte, minus 1152)
+__device__ __forceinline__ uint32_t digit_pair(uint32_t t0, uint32_t t1, int x)
+{
+    // prmt selector nibbles (nibble j picks result byte j from {t1, t0}, 4..7 = t1):
+    // bytes 0 and 2 are byte x of t0 and byte x of t1 (bytes 1 and 3 are masked off)
+    const uint32_t sel = (uint32_t)x | ((uint32_t)x << 4) | ((uint32_t)(4 + x) << 8) | ((uint32_t)(4 + x) << 12);
+    uint32_t w;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(w) : "r"(t0), "r"(t1), "r"(sel));
+    w = (w & 0x00FF00FFu) | 0x64006400u;
+    const __half2 h = __hsub2(*reinterpret_cast<const __half2 *>(&w), __halves2half2(__ushort_as_half(0x6480),
+                                                                                      __ushort_as_half(0x6480)));
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// digits of 8 residues r[0..7] (inner entries 8 kk8 .. of one row) into the chunk layout.
+// bmode: 0 = A chunks (128 rows, digit x tile at 4096 x), 1 = B chunks (32 rows, digit x at rows
+// 32 x + r); chunk (row block, K-step) at base + (rb nks + ks) chunk bytes
+__device__ __forceinline__ void put_digits(unsigned char *base, int bmode, int nks, int row, int k8, const u32 (&r)[8])
+{
+    u32 t[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) t[i] = r[i] + 0x80808080u;
+    const int ks = k8 >> 1, kk8 = k8 & 1;
+#pragma unroll
+    for (int x = 0; x < 4; x++) {
+        uint4 h;
+        h.x = digit_pair(t[0], t[1], x);
+        h.y = digit_pair(t[2], t[3], x);
+        h.z = digit_pair(t[4], t[5], x);
+        h.w = digit_pair(t[6], t[7], x);
+        unsigned char *dst = bmode == 0
+            ? base + ((size_t)(row >> 7) * nks + ks) * VD_ACHUNK + x * 4096 + op_off(row & 127, kk8)
+            : base + ((size_t)(row >> 5) * nks + ks) * VD_BCHUNK + op_off(32 * x + (row & 31), kk8);
+        *(uint4 *)dst = h;
+    }
+}
+
+// digits of the rows x K matrix src (u32 residues in [0, p), row stride ld)
+__global__ void k_vd_digits(const u32 *src, i64 ld, int rows, int K, int nks, int bmode, unsigned char *dst)
+{
+    const int nk8 = (K + 7) >> 3;
+    const i64 total = (i64)rows * nk8;
+    for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < total; x += (i64)gridDim.x * blockDim.x) {
+        const int row = (int)(x / nk8), k8 = (int)(x % nk8);
+        u32 r[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int l = 8 * k8 + i;
+            r[i] = l < K ? src[row * ld + l] : 0u;
+        }
+        put_digits(dst, bmode, nks, row, k8, r);
+    }
+}
+
+// w^i mod p for i < L (p < 2^30)
+__global__ void k_vd_powers(u32 *tab, int L, u32 w, u32 p)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) {
+        u64 r = 1, b = w;
+        for (u32 e = (u32)i; e; e >>= 1, b = b * b % p)
+            if (e & 1) r = r * b % p;
+        tab[i] = (u32)r;
+    }
+}
+
+// digits (B chunks) of the matrix M[j][l] = s w^(sgn j l) for j < rows, l < K: the
+// evaluation matrix (s = 1, sgn = +1) or the interpolation matrix (s = L^-1, sgn = -1)
+__global__ void k_vd_matrix(const u32 *tab, int L, int rows, int K, int nks, int neg, u32 scale, u32 p,
+                            unsigned char *dst)
+{
+    const int nk8 = (K + 7) >> 3;
+    const i64 total = (i64)rows * nk8;
+    for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < total; x += (i64)gridDim.x * blockDim.x) {
+        const int row = (int)(x / nk8), k8 = (int)(x % nk8);
+        u32 r[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int l = 8 * k8 + i;
+            u32 v = 0;
+            if (l < K) {
+                const u32 e = (u32)(((u64)row * (u64)l) & (u64)(L - 1));
+                v = tab[neg ? (e ? (u32)L - e : 0u) : e];
+                v = (u32)((u64)v * scale % p);
+            }
+            r[i] = v;
+        }
+        put_digits(dst, 1, nks, row, k8, r);
+    }
+}
+
+__device__ __forceinline__ bool vd_wait(uint32_t bar, uint32_t parity, volatile int *abort, int *status)
+{
+    if (*abort) return false;
+    for (int it = 0; it < (1 << 24); it++) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(bar), "r"(parity));
+        if (done) return true;
+        if ((it & 255) == 255 && *abort) return false;
+    }
+    *abort = 1;
+    atomicExch(status, PM_ETIMEOUT);
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t *d)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void tmem_zero16(uint32_t addr)
+{
+    const uint32_t z = 0;
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};"
+                 ::"r"(addr), "r"(z));
+}
+
+__device__ __forceinline__ void commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
+}
+
+__global__ void __launch_bounds__(VD_THREADS, 2) k_modgemm(const __grid_constant__ MgJob J, int *status)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    // full[4], empty[4], accumulators full, accumulators drained, final drain
+    __shared__ __align__(8) uint64_t bars[2 * VD_STAGES + 3];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    volatile int *abort_ = &abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t b_full = smem_u32(&bars[0]), b_empty = smem_u32(&bars[VD_STAGES]),
+                   b_accf = smem_u32(&bars[2 * VD_STAGES]), b_acce = smem_u32(&bars[2 * VD_STAGES + 1]),
+                   b_drain = smem_u32(&bars[2 * VD_STAGES + 2]);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(VD_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 2 * VD_STAGES + 3; b++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[b])),
+                         "r"(b == 2 * VD_STAGES + 1 ? 128 : 1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        abort_flag = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    const int mb = blockIdx.x / J.nbN, nb = blockIdx.x % J.nbN;   // column blocks fastest: A row blocks stay in L2
+    const int nks = J.nks, nkc = (nks + VD_KC - 1) / VD_KC;
+    if (warp < 4) {
+        const uint32_t tq = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+        for (int c = 0; c < 14; c++) tmem_zero16(tq + 16u * c);
+        asm volatile("tcgen05.wait::st.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+
+    if (warp == 4) {
+        // ---------------------------------------------------------------- producer
+        if (lane == 0) {
+            const unsigned char *Ab = J.Ad + (size_t)mb * nks * VD_ACHUNK, *Bb = J.Bd + (size_t)nb * nks * VD_BCHUNK;
+            for (int ks = 0; ks < nks; ks++) {
+                const int s = ks % VD_STAGES;
+                if (ks >= VD_STAGES) vd_wait(b_empty + 8 * s, (uint32_t)((ks / VD_STAGES - 1) & 1), abort_, status);
+                const uint32_t dst = smem_u32(sm + s * VD_STAGE), bar = b_full + 8 * s;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(VD_STAGE) : "memory");
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             ::"r"(dst), "l"(Ab + (size_t)ks * VD_ACHUNK), "r"(VD_ACHUNK), "r"(bar) : "memory");
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             ::"r"(dst + VD_ACHUNK), "l"(Bb + (size_t)ks * VD_BCHUNK), "r"(VD_BCHUNK), "r"(bar)
+                             : "memory");
+            }
+            // the copies still in flight land before the CTA exits
+            for (int ks = nks - VD_STAGES < 0 ? 0 : nks - VD_STAGES; ks < nks; ks++) {
+                const int s = ks % VD_STAGES;
+                uint32_t done = 0;
+                for (int it = 0; it < (1 << 24) && !done; it++)
+                    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                                 " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(b_full + 8 * s), "r"((uint32_t)((ks / VD_STAGES) & 1)));
+            }
+        }
+    } else if (warp == 5) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            // D f32 (bit 4), A and B fp16, K-major; N = 128 (>> 3 at bit 17), M = 128 (>> 4 at bit 24)
+            const uint32_t idesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+            for (int kc = 0; kc < nkc; kc++) {
+                if (kc >= 1) vd_wait(b_acce, (uint32_t)((kc - 1) & 1), abort_, status);   // drained and cleared
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const int k1 = (kc + 1) * VD_KC < nks ? (kc + 1) * VD_KC : nks;
+                for (int ks = kc * VD_KC; ks < k1; ks++) {
+                    const int s = ks % VD_STAGES;
+                    vd_wait(b_full + 8 * s, (uint32_t)((ks / VD_STAGES) & 1), abort_, status);
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t st = smem_u32(sm + s * VD_STAGE);
+                    const uint64_t bd = op_desc(st + VD_ACHUNK);
+#pragma unroll
+                    for (int x = 0; x < 4; x++)
+                        asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, 1, 0;\n"
+                                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                     ::"r"(tmem + 32u * x), "l"(op_desc(st + 4096 * x)), "l"(bd), "r"(idesc));
+                    commit(b_empty + 8 * s);
+                }
+                commit(b_accf);
+            }
+            commit(b_drain);                 // every MMA of this CTA has completed
+            uint32_t done = 0;
+            for (int it = 0; it < (1 << 26) && !done; it++)
+                asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                             " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(b_drain), "r"(0u));
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue (warps 0-3)
+        const uint32_t tq = tmem + ((uint32_t)(32 * warp) << 16);
+        const u32 q = J.P.q;
+        u32 cw[7];
+        u64 sum = 0;
+#pragma unroll
+        for (int w = 0; w < 7; w++) {
+            cw[w] = (u32)((1ull << (8 * w)) % q);
+            sum += cw[w];
+        }
+        const u64 k0 = ((u64)q << 25) - sum * 0x4B400000ull;   // q 2^25 - sum_w cw_w bits(1.5 2^23), mod 2^64
+        u32 acc[32];
+#pragma unroll
+        for (int c = 0; c < 32; c++) acc[c] = 0;
+        for (int kc = 0; kc < nkc; kc++) {
+            if (lane == 0) vd_wait(b_accf, (uint32_t)(kc & 1), abort_, status);
+            __syncwarp();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int g = 0; g < 4; g++) {                  // 8 columns at a time: 7 loads, one wait
+                uint32_t d[7][8];
+#pragma unroll
+                for (int w = 0; w < 7; w++) tmem_ld8(tq + 32u * w + 8u * g, d[w]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                for (int cc = 0; cc < 8; cc++) {
+                    u64 x = k0 + acc[8 * g + cc];
+#pragma unroll
+                    for (int w = 0; w < 7; w++) x += (u64)__float_as_uint(__uint_as_float(d[w][cc]) + 12582912.0f) * cw[w];
+                    acc[8 * g + cc] = reduce64(x, J.P);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 14; c++) tmem_zero16(tq + 16u * c);
+            asm volatile("tcgen05.wait::st.sync.aligned;");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b_acce) : "memory");
+        }
+        const int row = mb * 128 + 32 * warp + lane;
+        if (row < J.M) {
+            u32 *dst = J.C + (i64)row * J.ldc + nb * 32;
+            const int nc = J.N - nb * 32 < 32 ? J.N - nb * 32 : 32;
+#pragma unroll
+            for (int c = 0; c < 32; c++)
+                if (c < nc) dst[c] = acc[c];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(VD_COLS));
+}
+
+size_t al256v(size_t x) { return (x + 255) & ~size_t(255); }
+
+int grid_for(i64 total) { return (int)(total / 256 + 1 < 4096 ? total / 256 + 1 : 4096); }
+
+}  // namespace
+
+// C (M x N, row stride ldc) = A B^T mod the prime of P, from digit chunks (one launch).
+int vd_modgemm(pm_ctx *ctx, const unsigned char *Ad, const unsigned char *Bd, int M, int N, int nks, u32 *C, int64_t ldc,
+               const PrimeDev &P)
+{
+    MgJob J;
+    J.Ad = Ad; J.Bd = Bd; J.C = C; J.ldc = ldc; J.M = M; J.N = N; J.nks = nks; J.nbN = (N + 31) / 32; J.P = P;
+    const int tiles = ((M + 127) / 128) * J.nbN;
+    cudaError_t e = cudaFuncSetAttribute(k_modgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, VD_SMEM);
+    if (e != cudaSuccess) return pm_cuda(ctx, e, "cudaFuncSetAttribute");
+    k_modgemm<<<tiles, VD_THREADS, VD_SMEM, ctx->stream>>>(J, ctx->d_status);
+    ctx->launches++;
+    return pm_cuda(ctx, cudaGetLastError(), "k_modgemm");
+}
+
+extern "C" int pmat_mul_vdm(pm_ctx *ctx, uint64_t p, int m, int n, int k, const void *A, int64_t dA, const void *B,
+                            int64_t dB, void *C)
+{
+    if (!ctx) return PM_EINVAL;
+    if (m < 1 || n < 1 || k < 1 || dA < 1 || dB < 1 || !A || !B || !C)
+        return pm_fail(ctx, PM_EINVAL, "pmat_mul_vdm: bad arguments");
+    if (dA > (1 << 15) || dB > (1 << 15)) return pm_fail(ctx, PM_EINVAL, "pmat_mul_vdm: lengths above 2^15");
+    const int64_t len = dA + dB - 1;
+    const int lg0 = ceil_log2(len), lg = lg0 < 5 ? 5 : lg0;
+    const int64_t L = int64_t(1) << lg;
+    if (p >= (1ull << 30) || p < 3 || ((p - 1) % (uint64_t)L) != 0 || !ntt_is_prime32(p))
+        return pm_fail(ctx, PM_EUNSUPPORTED, "pmat_mul_vdm: p must be a prime below 2^30 with 2^lg | p - 1");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return pm_fail(ctx, PM_ECUDA, "cudaSetDevice failed");
+    CKI(host_join(ctx));
+    const u32 q = (u32)p;
+    u32 rf[PM_MAX_LOG2L + 1], ri[PM_MAX_LOG2L + 1];
+    ntt_roots(q, rf, ri);
+    PrimeDev P;
+    memset(&P, 0, sizeof(P));
+    P.q = q; P.q2 = 2 * q;
+    P.r32 = (u32)((1ull << 32) % q);
+    P.r32s = (u32)(((uint64_t)P.r32 << 32) / q);
+    P.ones = (u32)((1ull << 32) / q);
+    const u32 linv = (u32)host_powmod((uint64_t)L % q, q - 2, q);
+    // workspace
+    const int64_t eA = (int64_t)m * n, eB = (int64_t)n * k, eC = (int64_t)m * k;
+    const int nkA = (int)((dA + 15) / 16), nkB = (int)((dB + 15) / 16), nkL = (int)(L / 16);
+    const size_t bXA = al256v((size_t)((eA + 127) / 128) * nkA * VD_ACHUNK), bXB = al256v((size_t)((eB + 127) / 128) * nkB * VD_ACHUNK);
+    const size_t bVA = al256v((size_t)((L + 31) / 32) * nkA * VD_BCHUNK), bVB = al256v((size_t)((L + 31) / 32) * nkB * VD_BCHUNK);
+    const size_t bTC = al256v((size_t)((eC + 127) / 128) * nkL * VD_ACHUNK), bW = al256v((size_t)((len + 31) / 32) * nkL * VD_BCHUNK);
+    const size_t bdig = bXA + bXB + bVA + bVB + bTC + bW;
+    const size_t bTa = al256v((size_t)eA * L * 4), bTb = al256v((size_t)eB * L * 4), bTc = al256v((size_t)eC * L * 4);
+    const size_t btab = al256v((size_t)L * 4);
+    void *ws = nullptr;
+    CKI(ws_reserve(ctx, bdig + bTa + bTb + bTc + btab + 256, &ws));
+    unsigned char *cur = (unsigned char *)ws;
+    unsigned char *XA = cur; cur += bXA;
+    unsigned char *XB = cur; cur += bXB;
+    unsigned char *VA = cur; cur += bVA;
+    unsigned char *VB = cur; cur += bVB;
+    unsigned char *TCd = cur; cur += bTC;
+    unsigned char *Wd = cur; cur += bW;
+    u32 *TA = (u32 *)cur; cur += bTa;
+    u32 *TB = (u32 *)cur; cur += bTb;
+    u32 *TC = (u32 *)cur; cur += bTc;
+    u32 *tab = (u32 *)cur;
+    count_work_vdm(ctx, lg, m, n, k, dA, dB, len);
+    // ---- evaluation: T_A = X_A V_A^T, T_B = X_B V_B^T (digits first; padding digits are zero)
+    int tok = stage_begin(ctx, PM_STAGE_FWD);
+    CKI(pm_cuda(ctx, cudaMemsetAsync(ws, 0, bdig, ctx->stream), "cudaMemsetAsync"));
+    k_vd_powers<<<grid_for(L), 256, 0, ctx->stream>>>(tab, (int)L, rf[lg], q);
+    k_vd_digits<<<grid_for(eA * ((dA + 7) / 8)), 256, 0, ctx->stream>>>((const u32 *)A, dA, (int)eA, (int)dA, nkA, 0, XA);
+    k_vd_digits<<<grid_for(eB * ((dB + 7) / 8)), 256, 0, ctx->stream>>>((const u32 *)B, dB, (int)eB, (int)dB, nkB, 0, XB);
+    k_vd_matrix<<<grid_for(L * ((dA + 7) / 8)), 256, 0, ctx->stream>>>(tab, (int)L, (int)L, (int)dA, nkA, 0, 1u, q, VA);
+    k_vd_matrix<<<grid_for(L * ((dB + 7) / 8)), 256, 0, ctx->stream>>>(tab, (int)L, (int)L, (int)dB, nkB, 0, 1u, q, VB);
+    k_vd_matrix<<<grid_for(len * (L / 8)), 256, 0, ctx->stream>>>(tab, (int)L, (int)len, (int)L, nkL, 1, linv, q, Wd);
+    ctx->launches += 6;
+    CKI(pm_cuda(ctx, cudaGetLastError(), "Vandermonde set-up"));
+    CKI(vd_modgemm(ctx, XA, VA, (int)eA, (int)L, nkA, TA, L, P));
+    CKI(vd_modgemm(ctx, XB, VB, (int)eB, (int)L, nkB, TB, L, P));
+    stage_end(ctx, tok);
+    // ---- pointwise products at the L points (the product path's kernels)
+    tok = stage_begin(ctx, PM_STAGE_POINTWISE);
+    CKI(run_pointwise(ctx, TA, TB, TC, m, n, k, lg, P));
+    stage_end(ctx, tok);
+    // ---- interpolation: C = T_C W^T
+    tok = stage_begin(ctx, PM_STAGE_INV);
+    k_vd_digits<<<grid_for(eC * (L / 8)), 256, 0, ctx->stream>>>(TC, L, (int)eC, (int)L, nkL, 0, TCd);
+    ctx->launches++;
+    CKI(pm_cuda(ctx, cudaGetLastError(), "k_vd_digits"));
+    CKI(vd_modgemm(ctx, TCd, Wd, (int)eC, (int)len, nkL, (u32 *)C, len, P));
+    stage_end(ctx, tok);
+    return PM_OK;
+}

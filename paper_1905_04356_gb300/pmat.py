@@ -80,6 +80,7 @@ def lib():
             "pmat_solve_series_hol": ([P, u64, i32, i32, P, i64, P, i64, i64, P], i32),
             "pmat_inv_slices": ([P, u64, i32, i32, P, i64, i32, P], i32),
             "pm_mma_rate": ([i32, i32, i32, C.POINTER(C.c_double)], i32),
+            "pmat_mul_vdm": ([P, u64, i32, i32, i32, P, i64, P, i64, P], i32),
             "pm_tune_product": ([P, u64, i32, i32, i32, i32, i64, i64, i32, P], i32),
             "pm_tune_basis": ([P, u64, i32, i32, i64, i32, P], i32),
         }
@@ -440,4 +441,18 @@ def tune_basis(ctx: Context, p: int, m: int, n: int, d: int, reps: int = 1):
     out = np.zeros(2, dtype=np.int64)
     ctx._ck(lib().pm_tune_basis(ctx.h, p, m, n, d, reps, out.ctypes.data))
     return tuple(int(v) for v in out)
+
+
+def pmat_mul_vdm(ctx: Context, p: int, A: torch.Tensor, B: torch.Tensor, out=None):
+    """pmat_mul by Vandermonde-matrix evaluation / interpolation on the tensor cores (uint32, NTT prime p)."""
+    A, B = _dev(A), _dev(B)
+    if width(A) != 4 or width(B) != 4:
+        raise TypeError("pmat_mul_vdm takes 32-bit coefficients")
+    m, n, dA = A.shape
+    n2, k, dB = B.shape
+    if n2 != n:
+        raise ValueError("inner dimensions differ")
+    C = _out(out, (m, k, dA + dB - 1), A)
+    ctx._ck(lib().pmat_mul_vdm(ctx.h, p, m, n, k, A.data_ptr(), dA, B.data_ptr(), dB, C.data_ptr()))
+    return C
 
