@@ -385,6 +385,23 @@ def extra_workloads(ctx, s, which=("vandermonde", "pm_basis", "resultant", "batc
             nt = lambda: pmat.pmat_mul(ctx, synth.P998, A, B, out=C2)     # noqa: E731
             t_vd, t_nt = ev_ms(vd, 2), ev_ms(nt, 2)
             st, _ = stage_split(vd, 2)
+            extra_tc = {}
+            if mm >= 64:
+                # the same product with the pointwise stage as dense tensor-core products per
+                # point, on the NTT path and on the Vandermonde path (every stage on tensor cores)
+                C3 = torch.empty_like(C1)
+                ctx.set_option(pmat.PM_OPT_POINTWISE, 3)
+                t_nt3 = ev_ms(lambda: pmat.pmat_mul(ctx, synth.P998, A, B, out=C3), 2)
+                st3, _ = stage_split(lambda: pmat.pmat_mul(ctx, synth.P998, A, B, out=C3), 2)
+                t_vd3 = ev_ms(vd, 2)
+                ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
+                stc, _ = stage_split(nt, 2)
+                torch.cuda.synchronize()
+                extra_tc = {"ntt_tc_pointwise_ms": round(t_nt3, 3), "vdm_tc_pointwise_ms": round(t_vd3, 3),
+                            "tc_pointwise_stage_ms": round(st3["pointwise"], 3),
+                            "cuda_core_pointwise_stage_ms": round(stc["pointwise"], 3),
+                            "tc_outputs_equal": bool(torch.equal(C3, C2) and torch.equal(C1, C2))}
+                del C3
             L = 1 << max(5, (2 * dd - 2).bit_length())
             nks = lambda K: (K + 15) // 16                                    # noqa: E731
             tiles = lambda M, N: ((M + 127) // 128) * ((N + 31) // 32)       # noqa: E731
@@ -398,7 +415,7 @@ def extra_workloads(ctx, s, which=("vandermonde", "pm_basis", "resultant", "batc
                         "vdm_stage_ms": {k2: round(v, 3) for k2, v in st.items()},
                         "eval_gemm_tflops": round(eval_fl / (st["fwd_ntt"] * 1e-3) / 1e12, 1),
                         "interp_gemm_tflops": round(interp_fl / (st["inv_ntt"] * 1e-3) / 1e12, 1),
-                        "eval_tensor_frac": round(eval_fl / (st["fwd_ntt"] * 1e-3) / 1e12 / peak, 4)}
+                        "eval_tensor_frac": round(eval_fl / (st["fwd_ntt"] * 1e-3) / 1e12 / peak, 4), **extra_tc}
             del A, B, C1, C2
             torch.cuda.empty_cache()
         return {"vandermonde_p998": res, "mma_peak_tflops_n128": round(peak, 1)}
@@ -652,8 +669,9 @@ def main():
             "graph_replay_ms_per_step": round(sum(ts_graph) / len(ts_graph), 4),
             "e2e_single_call_latency_ms": round(e2e_latency_ms, 4),
             "tensor_core_vs_cuda_core": tc_report(ts_tc, st_tc, stages),
-            "autotune": {"form": {1: "CUDA-core block tile", 2: "tensor-core digits", 3: "streaming",
-                                   4: "matrix-vector"}.get(tuned[0], tuned[0]),
+            "autotune": {"form": {1: "CUDA-core block tile", 2: "tensor-core digits, four points per MMA",
+                                   3: "streaming", 4: "matrix-vector",
+                                   5: "tensor-core dense products per point"}.get(tuned[0], tuned[0]),
                          "block_tile": [tuned[1], tuned[2]], "pointwise_us": round(tuned[3] / 1000, 1),
                          "candidates": tuned[4]},
             "c2_p998_ms": round(sum(ts998) / len(ts998), 4),

@@ -83,9 +83,11 @@ typedef struct pm_ctx pm_ctx;
 
 /* Option keys for pm_set_option. */
 enum {
-    PM_OPT_POINTWISE = 1,   /* 0 = auto (the faster form measured on GB300: CUDA cores),
-                               1 = CUDA-core 64-bit products, 2 = tensor-core 8-bit limb
-                               products where m, n, k <= 32 (CUDA cores elsewhere) */
+    PM_OPT_POINTWISE = 1,   /* 0 = auto (the cost-model rules, or the form pm_tune_product
+                               recorded for the shape), 1 = CUDA-core 64-bit products,
+                               2 = tensor-core digit products, four points per MMA, where
+                               m, n, k <= 32 (CUDA cores elsewhere), 3 = tensor-core dense
+                               products per point where m >= 64 (CUDA cores elsewhere) */
     PM_OPT_THRESHOLD = 2,   /* PM-Basis threshold T (>= 1): M-Basis when order <= T;
                                default 32 (Sec. 3, "Interpolant bases") */
     PM_OPT_DEBUG_CHECKS = 3, /* 1 = check inputs are in [0, p) (PM_EDOMAIN) */
@@ -401,8 +403,9 @@ int pmat_mul_vdm(pm_ctx *ctx, uint64_t p, int m, int n, int k, const void *A, in
  * one warm-up) on zero inputs (the kernels' time does not depend on the
  * values), and records the fastest in the context: later products of the same
  * (m, n, k, transform length) take it when PM_OPT_POINTWISE is 0 (auto).
- * out: HOST int64_t[5] = form (1 CUDA-core block tile, 2 tensor-core, 3
- * streaming, 4 matrix-vector), bi, bk (the block tile of form 1, else 0), the
+ * out: HOST int64_t[5] = form (1 CUDA-core block tile, 2 tensor-core four points
+ * per MMA, 3 streaming, 4 matrix-vector, 5 tensor-core dense products per point,
+ * tried where m >= 64), bi, bk (the block tile of form 1, else 0), the
  * winner's pointwise-stage time per product in ns, the number of candidates.
  * Allocates and frees its scratch on the context's stream, synchronises it and
  * discards earlier stage-timing records.  Requires 1 <= reps <= 1000 and the

@@ -367,7 +367,7 @@ struct Plan {
 
 // Pointwise jobs sorted by kernel form.
 struct PwLists {
-    std::vector<PwJob> jobs, tjobs, sjobs[9], vjobs;
+    std::vector<PwJob> jobs, tjobs, sjobs[9], vjobs, gjobs;
     std::vector<int> nb, tnb, snb[9], vnb;
 };
 
@@ -415,6 +415,12 @@ static void add_pointwise(pm_ctx *ctx, PwLists &pl, u32 *A, u32 *B, u32 *C, int 
     else if (ctx->opt_pointwise == 0)
         for (const auto &t : ctx->tune)
             if (t.m == m && t.n == n && t.k == k && t.lg == lg) { form = t.form; bi = t.bi; bk = t.bk; break; }
+    if (ctx->opt_pointwise == 3 && ctx->force_form < 0) form = 5;
+    // automatic rule, measured on GB300: the dense tensor-core form wins for large per-point
+    // products (512 x 512 . 512 x 512 at 256 points: 4.04 ms against 6.21 ms on CUDA cores) and
+    // loses at 128 x 128 . 128 x 128 (1.22 against 0.81 ms)
+    if (ctx->opt_pointwise == 0 && form == 0 && ctx->force_form < 0 && m >= 256 && n >= 256 && k >= 256) form = 5;
+    if (form == 5 && j.m >= 64) { pl.gjobs.push_back(j); return; }
     if (form == 2 && tc_supported(j)) { pl.tjobs.push_back(j); pl.tnb.push_back(tc_blocks(j)); }
     else if (form == 1 && bi > 0 && bk > 0) { const int nbk = pw_plan_tile(j, bi, bk); pl.jobs.push_back(j); pl.nb.push_back(nbk); }
     else if (form == 4 && pwv_supported(j)) { pl.vjobs.push_back(j); pl.vnb.push_back(pwv_blocks(j)); }
@@ -438,6 +444,7 @@ static int launch_pointwise_lists(pm_ctx *ctx, const PwLists &pl)
     if (!pl.tjobs.empty())
         CKI(launch_packs(ctx, pl.tjobs, pl.tnb, [&](const JobPack<PwJob> &pk) {
             return launch_pointwise_tc(pk, ctx->d_status, ctx->stream, &ctx->launches, ctx->opt_withhold); }));
+    for (const PwJob &j : pl.gjobs) CKI(pointwise_gemm(ctx, j));
     return PM_OK;
 }
 
@@ -700,6 +707,7 @@ int pm_destroy(pm_ctx *ctx)
     for (auto &s : ctx->direct) { cudaFree(s.twf); cudaFree(s.twi); }
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->arena.base) cudaFree(ctx->arena.base);
+    if (ctx->gemm_ws) cudaFree(ctx->gemm_ws);
     if (ctx->d_status) cudaFree(ctx->d_status);
     for (auto &mk : ctx->marks) { cudaEventDestroy(mk.a); cudaEventDestroy(mk.b); }
     for (auto e : ctx->spare) cudaEventDestroy(e);
@@ -723,7 +731,7 @@ int pm_set_option(pm_ctx *ctx, int key, int64_t value)
     if (!ctx) return PM_EINVAL;
     switch (key) {
     case PM_OPT_POINTWISE:
-        if (value < 0 || value > 2) return pm_fail(ctx, PM_EINVAL, "pointwise path must be 0, 1 or 2");
+        if (value < 0 || value > 3) return pm_fail(ctx, PM_EINVAL, "pointwise path must be 0, 1, 2 or 3");
         ctx->opt_pointwise = (int)value;
         return PM_OK;
     case PM_OPT_THRESHOLD:

@@ -41,10 +41,14 @@ struct pm_ctx {
     int opt_host_chunks = 0;          // pmat_mul_host output chunks (0 = automatic)
     int opt_withhold = 0;             // test hook: the tensor-core pointwise kernel withholds an MMA
     // pointwise forms picked by pm_tune_product, per (m, n, k, transform length): form 1 = CUDA-core
-    // block tile (bi, bk), 2 = tensor-core, 3 = streaming (n <= 8), 4 = matrix-vector (k = 1)
+    // block tile (bi, bk), 2 = tensor-core (four points per MMA, m, n, k <= 32), 3 = streaming
+    // (n <= 8), 4 = matrix-vector (k = 1), 5 = tensor-core dense products per point (m >= 64)
     struct Tune { int m, n, k, lg, form, bi, bk; };
     std::vector<Tune> tune;
     int force_form = -1, force_bi = 0, force_bk = 0;   // the tuner's candidate while it times one
+    // form 5: the tensor-core dense products per point (digit chunks of every point's A_j, B_j^T)
+    void *gemm_ws = nullptr;
+    size_t gemm_size = 0;
     struct Mark { int stage; cudaEvent_t a, b; long long launches; };
     std::vector<Mark> marks;          // recorded stage intervals
     std::vector<cudaEvent_t> spare;   // reusable events
@@ -117,4 +121,6 @@ void count_work_vdm(pm_ctx *ctx, int lg, int m, int n, int k, int64_t dA, int64_
 // C (M x N, row stride ldc) = A B^T mod the prime of P from tensor-core digit chunks (vdm.cu).
 int vd_modgemm(pm_ctx *ctx, const unsigned char *Ad, const unsigned char *Bd, int M, int N, int nks, u32 *C, int64_t ldc,
                const PrimeDev &P);
+// Pointwise products of one job as a batch of dense tensor-core products over its points (vdm.cu).
+int pointwise_gemm(pm_ctx *ctx, const PwJob &j);
 

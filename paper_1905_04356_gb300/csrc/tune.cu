@@ -61,6 +61,7 @@ int pm_tune_product(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, int64_t
     if (tc_supported(j)) cands.push_back({2, 0, 0});
     if (pws_supported(j)) cands.push_back({3, 0, 0});
     if (pwv_supported(j)) cands.push_back({4, 0, 0});
+    if (m >= 64) cands.push_back({5, 0, 0});
     // zero inputs (the kernels' time does not depend on the values) and the output
     const size_t bA = (size_t)m * n * dA * w, bB = (size_t)n * k * dB * w, bC = (size_t)m * k * len * w;
     char *buf = nullptr;

@@ -59,9 +59,10 @@ namespace {
 
 struct MgJob {
     const unsigned char *Ad, *Bd;   // digit chunks: A [row block][K-step] (16 KB), B [row block][K-step] (4 KB)
-    u32 *C;                         // C[i ldc + j] for i < M, j < N, in [0, p)
-    i64 ldc;
-    int M, N, nks, nbN;             // rows, columns, K-steps, 32-column blocks
+    i64 sAd, sBd;                   // bytes between the chunk sets of consecutive batch members
+    u32 *C;                         // C[b sCb + i ldc + j ldj] for i < M, j < N, in [0, p)
+    i64 ldc, ldj, sCb;
+    int M, N, nks, nbN, tiles;      // rows, columns, K-steps, 32-column blocks, tiles per member
     PrimeDev P;
 };
 
@@ -115,20 +116,27 @@ __device__ __forceinline__ void put_digits(unsigned char *base, int bmode, int n
     }
 }
 
-// digits of the rows x K matrix src (u32 residues in [0, p), row stride ld)
-__global__ void k_vd_digits(const u32 *src, i64 ld, int rows, int K, int nks, int bmode, unsigned char *dst)
+// digits of `batch` matrices of rows x K u32 residues in [0, p): element (b, row, l) at
+// src[b sb + row srow + l sl], chunk set of member b at dst + b sdst.  bfast: consecutive threads
+// take consecutive members (coalesced when sb = 1: the transform-domain layout), else
+// consecutive octets of a row (coalesced when sl = 1: row-major matrices).
+__global__ void k_vd_digits(const u32 *src, i64 sb, i64 srow, i64 sl, int batch, int rows, int K, int nks, int bmode,
+                            unsigned char *dst, i64 sdst, int bfast)
 {
     const int nk8 = (K + 7) >> 3;
-    const i64 total = (i64)rows * nk8;
+    const i64 total = (i64)batch * rows * nk8;
     for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < total; x += (i64)gridDim.x * blockDim.x) {
-        const int row = (int)(x / nk8), k8 = (int)(x % nk8);
+        int b, row, k8;
+        if (bfast) { b = (int)(x % batch); const i64 y = x / batch; row = (int)(y / nk8); k8 = (int)(y % nk8); }
+        else { k8 = (int)(x % nk8); const i64 y = x / nk8; row = (int)(y % rows); b = (int)(y / rows); }
+        const u32 *s = src + b * sb + row * srow;
         u32 r[8];
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             const int l = 8 * k8 + i;
-            r[i] = l < K ? src[row * ld + l] : 0u;
+            r[i] = l < K ? s[l * sl] : 0u;
         }
-        put_digits(dst, bmode, nks, row, k8, r);
+        put_digits(dst + b * sdst, bmode, nks, row, k8, r);
     }
 }
 
@@ -230,7 +238,8 @@ __global__ void __launch_bounds__(VD_THREADS, 2) k_modgemm(const __grid_constant
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
-    const int mb = blockIdx.x / J.nbN, nb = blockIdx.x % J.nbN;   // column blocks fastest: A row blocks stay in L2
+    const int bm = blockIdx.x / J.tiles, tl = blockIdx.x % J.tiles;
+    const int mb = tl / J.nbN, nb = tl % J.nbN;    // column blocks fastest: A row blocks stay in L2
     const int nks = J.nks, nkc = (nks + VD_KC - 1) / VD_KC;
     if (warp < 4) {
         const uint32_t tq = tmem + ((uint32_t)(32 * warp) << 16);
@@ -245,7 +254,8 @@ __global__ void __launch_bounds__(VD_THREADS, 2) k_modgemm(const __grid_constant
     if (warp == 4) {
         // ---------------------------------------------------------------- producer
         if (lane == 0) {
-            const unsigned char *Ab = J.Ad + (size_t)mb * nks * VD_ACHUNK, *Bb = J.Bd + (size_t)nb * nks * VD_BCHUNK;
+            const unsigned char *Ab = J.Ad + bm * J.sAd + (size_t)mb * nks * VD_ACHUNK,
+                                *Bb = J.Bd + bm * J.sBd + (size_t)nb * nks * VD_BCHUNK;
             for (int ks = 0; ks < nks; ks++) {
                 const int s = ks % VD_STAGES;
                 if (ks >= VD_STAGES) vd_wait(b_empty + 8 * s, (uint32_t)((ks / VD_STAGES - 1) & 1), abort_, status);
@@ -337,11 +347,11 @@ __global__ void __launch_bounds__(VD_THREADS, 2) k_modgemm(const __grid_constant
         }
         const int row = mb * 128 + 32 * warp + lane;
         if (row < J.M) {
-            u32 *dst = J.C + (i64)row * J.ldc + nb * 32;
+            u32 *dst = J.C + bm * J.sCb + (i64)row * J.ldc + (i64)nb * 32 * J.ldj;
             const int nc = J.N - nb * 32 < 32 ? J.N - nb * 32 : 32;
 #pragma unroll
             for (int c = 0; c < 32; c++)
-                if (c < nc) dst[c] = acc[c];
+                if (c < nc) dst[c * J.ldj] = acc[c];
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -356,18 +366,67 @@ int grid_for(i64 total) { return (int)(total / 256 + 1 < 4096 ? total / 256 + 1 
 
 }  // namespace
 
+// C_b (M x N: element (i, j) at C + b sCb + i ldc + j ldj) = A_b B_b^T mod the prime of P for
+// b < batch, from digit chunk sets sAd / sBd bytes apart (one launch).
+int vd_modgemm_batched(pm_ctx *ctx, const unsigned char *Ad, int64_t sAd, const unsigned char *Bd, int64_t sBd,
+                       int batch, int M, int N, int nks, u32 *C, int64_t ldc, int64_t ldj, int64_t sCb,
+                       const PrimeDev &P)
+{
+    MgJob J;
+    J.Ad = Ad; J.Bd = Bd; J.sAd = sAd; J.sBd = sBd;
+    J.C = C; J.ldc = ldc; J.ldj = ldj; J.sCb = sCb;
+    J.M = M; J.N = N; J.nks = nks; J.nbN = (N + 31) / 32; J.tiles = ((M + 127) / 128) * J.nbN; J.P = P;
+    const int64_t blocks = (int64_t)batch * J.tiles;
+    if (blocks > 0x7fffffffLL) return pm_fail(ctx, PM_EUNSUPPORTED, "modular product grid too large");
+    cudaError_t e = cudaFuncSetAttribute(k_modgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, VD_SMEM);
+    if (e != cudaSuccess) return pm_cuda(ctx, e, "cudaFuncSetAttribute");
+    k_modgemm<<<(unsigned)blocks, VD_THREADS, VD_SMEM, ctx->stream>>>(J, ctx->d_status);
+    ctx->launches++;
+    return pm_cuda(ctx, cudaGetLastError(), "k_modgemm");
+}
+
 // C (M x N, row stride ldc) = A B^T mod the prime of P, from digit chunks (one launch).
 int vd_modgemm(pm_ctx *ctx, const unsigned char *Ad, const unsigned char *Bd, int M, int N, int nks, u32 *C, int64_t ldc,
                const PrimeDev &P)
 {
-    MgJob J;
-    J.Ad = Ad; J.Bd = Bd; J.C = C; J.ldc = ldc; J.M = M; J.N = N; J.nks = nks; J.nbN = (N + 31) / 32; J.P = P;
-    const int tiles = ((M + 127) / 128) * J.nbN;
-    cudaError_t e = cudaFuncSetAttribute(k_modgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, VD_SMEM);
-    if (e != cudaSuccess) return pm_cuda(ctx, e, "cudaFuncSetAttribute");
-    k_modgemm<<<tiles, VD_THREADS, VD_SMEM, ctx->stream>>>(J, ctx->d_status);
-    ctx->launches++;
-    return pm_cuda(ctx, cudaGetLastError(), "k_modgemm");
+    return vd_modgemm_batched(ctx, Ad, 0, Bd, 0, 1, M, N, nks, C, ldc, 1, 0, P);
+}
+
+// Bytes of the digit chunks of a member: rows in blocks of 128 (A) or 32 (B), K in steps of 16.
+static size_t vd_chunk_bytes(int rows, int K, int bmode)
+{
+    const int nks = (K + 15) / 16;
+    return bmode == 0 ? (size_t)((rows + 127) / 128) * nks * VD_ACHUNK : (size_t)((rows + 31) / 32) * nks * VD_BCHUNK;
+}
+
+// The pointwise products C_j = A_j B_j mod q at the L transform points as a batch of dense
+// products on the tensor cores: A_j (m x n) and B_j^T (k x n) are gathered from the
+// transform-domain layout [entry][L] into digit chunks, C_j is written back into it.
+int pointwise_gemm(pm_ctx *ctx, const PwJob &j)
+{
+    const int m = j.m, n = j.n, k = j.k, L = j.L, nks = (n + 15) / 16;
+    const size_t bA = al256v(vd_chunk_bytes(m, n, 0)), bB = al256v(vd_chunk_bytes(k, n, 1));
+    const size_t need = (size_t)L * (bA + bB);
+    if (need > ctx->gemm_size) {
+        if (ctx->gemm_ws) CKI(pm_cuda(ctx, cudaFreeAsync(ctx->gemm_ws, ctx->stream), "cudaFreeAsync"));
+        ctx->gemm_ws = nullptr;
+        ctx->gemm_size = 0;
+        if (cudaMallocAsync(&ctx->gemm_ws, need, ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return pm_fail(ctx, PM_ENOMEM, "pointwise digit scratch allocation failed");
+        }
+        ctx->gemm_size = need;
+    }
+    unsigned char *Ad = (unsigned char *)ctx->gemm_ws, *Bd = Ad + (size_t)L * bA;
+    CKI(pm_cuda(ctx, cudaMemsetAsync(Ad, 0, need, ctx->stream), "cudaMemsetAsync"));
+    const int64_t tA = (int64_t)L * m * ((n + 7) / 8), tB = (int64_t)L * k * ((n + 7) / 8);
+    // A_j[i][l] = A[(i n + l) L + j]; B_j^T[c][l] = B[(l k + c) L + j]
+    k_vd_digits<<<grid_for(tA), 256, 0, ctx->stream>>>(j.A, 1, (int64_t)n * L, L, L, m, n, nks, 0, Ad, (int64_t)bA, 1);
+    k_vd_digits<<<grid_for(tB), 256, 0, ctx->stream>>>(j.B, 1, L, (int64_t)k * L, L, k, n, nks, 1, Bd, (int64_t)bB, 1);
+    ctx->launches += 2;
+    CKI(pm_cuda(ctx, cudaGetLastError(), "k_vd_digits"));
+    // C_j[i][c] = C[(i k + c) L + j]
+    return vd_modgemm_batched(ctx, Ad, (int64_t)bA, Bd, (int64_t)bB, L, m, k, nks, j.C, (int64_t)k * L, L, 1, j.P);
 }
 
 extern "C" int pmat_mul_vdm(pm_ctx *ctx, uint64_t p, int m, int n, int k, const void *A, int64_t dA, const void *B,
@@ -421,8 +480,10 @@ extern "C" int pmat_mul_vdm(pm_ctx *ctx, uint64_t p, int m, int n, int k, const 
     int tok = stage_begin(ctx, PM_STAGE_FWD);
     CKI(pm_cuda(ctx, cudaMemsetAsync(ws, 0, bdig, ctx->stream), "cudaMemsetAsync"));
     k_vd_powers<<<grid_for(L), 256, 0, ctx->stream>>>(tab, (int)L, rf[lg], q);
-    k_vd_digits<<<grid_for(eA * ((dA + 7) / 8)), 256, 0, ctx->stream>>>((const u32 *)A, dA, (int)eA, (int)dA, nkA, 0, XA);
-    k_vd_digits<<<grid_for(eB * ((dB + 7) / 8)), 256, 0, ctx->stream>>>((const u32 *)B, dB, (int)eB, (int)dB, nkB, 0, XB);
+    k_vd_digits<<<grid_for(eA * ((dA + 7) / 8)), 256, 0, ctx->stream>>>((const u32 *)A, 0, dA, 1, 1, (int)eA, (int)dA, nkA,
+                                                                          0, XA, 0, 0);
+    k_vd_digits<<<grid_for(eB * ((dB + 7) / 8)), 256, 0, ctx->stream>>>((const u32 *)B, 0, dB, 1, 1, (int)eB, (int)dB, nkB,
+                                                                          0, XB, 0, 0);
     k_vd_matrix<<<grid_for(L * ((dA + 7) / 8)), 256, 0, ctx->stream>>>(tab, (int)L, (int)L, (int)dA, nkA, 0, 1u, q, VA);
     k_vd_matrix<<<grid_for(L * ((dB + 7) / 8)), 256, 0, ctx->stream>>>(tab, (int)L, (int)L, (int)dB, nkB, 0, 1u, q, VB);
     k_vd_matrix<<<grid_for(len * (L / 8)), 256, 0, ctx->stream>>>(tab, (int)L, (int)len, (int)L, nkL, 1, linv, q, Wd);
@@ -437,7 +498,7 @@ extern "C" int pmat_mul_vdm(pm_ctx *ctx, uint64_t p, int m, int n, int k, const 
     stage_end(ctx, tok);
     // ---- interpolation: C = T_C W^T
     tok = stage_begin(ctx, PM_STAGE_INV);
-    k_vd_digits<<<grid_for(eC * (L / 8)), 256, 0, ctx->stream>>>(TC, L, (int)eC, (int)L, nkL, 0, TCd);
+    k_vd_digits<<<grid_for(eC * (L / 8)), 256, 0, ctx->stream>>>(TC, 0, L, 1, 1, (int)eC, (int)L, nkL, 0, TCd, 0, 0);
     ctx->launches++;
     CKI(pm_cuda(ctx, cudaGetLastError(), "k_vd_digits"));
     CKI(vd_modgemm(ctx, TCd, Wd, (int)eC, (int)len, nkL, (u32 *)C, len, P));

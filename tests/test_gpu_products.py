@@ -331,3 +331,23 @@ def test_tensor_core_extreme_inputs(ctx, p, w):
         ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
     assert np.array_equal(got.astype(np.uint64), exp)
 
+
+@pytest.mark.parametrize("case", [(P60, 8, 64, 64, 64, 100, 80), (synth.P998, 4, 128, 40, 100, 50, 60),
+                                  (97, 4, 70, 17, 33, 20, 30), (P60, 8, 128, 128, 128, 30, 40),
+                                  (P62, 8, 65, 1, 200, 9, 7), (2, 4, 64, 300, 3, 5, 6)])
+def test_tensor_core_dense_pointwise_matches_oracle(ctx, case):
+    """The tensor-core dense form (PM_OPT_POINTWISE = 3: every point's m x n . n x k product as a
+    dense product of fp16 digits, drained every 64 inner entries) against the oracle: m = 64 and
+    above, ragged n and k, inner dimensions from 1 to 300, moduli 2 to 62 bits."""
+    from paper_1905_04356_gb300 import pmat
+    p, w, m, n, k, dA, dB = case
+    g = synth.rng(41 + m * n * k)
+    A = _rand(g, p, (m, n, dA), w)
+    B = _rand(g, p, (n, k, dB), w)
+    ctx.set_option(pmat.PM_OPT_POINTWISE, 3)
+    try:
+        got = _gpu(ctx, "pmat_mul", p, A, B)
+    finally:
+        ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
+    assert np.array_equal(got.astype(np.uint64), oracle.pmat_mul(p, A, B))
+
