@@ -383,25 +383,13 @@ def extra_workloads(ctx, s, which=("vandermonde", "pm_basis", "resultant", "batc
             C2 = torch.empty_like(C1)
             vd = lambda: pmat.pmat_mul_vdm(ctx, synth.P998, A, B, out=C1)  # noqa: E731
             nt = lambda: pmat.pmat_mul(ctx, synth.P998, A, B, out=C2)     # noqa: E731
-            t_vd, t_nt = ev_ms(vd, 2), ev_ms(nt, 2)
+            # the NTT path with the CUDA-core pointwise form, then the Vandermonde path with it
+            ctx.set_option(pmat.PM_OPT_POINTWISE, 1)
+            t_nt = ev_ms(nt, 2)
+            stc, _ = stage_split(nt, 2)
+            t_vd = ev_ms(vd, 2)
             st, _ = stage_split(vd, 2)
-            extra_tc = {}
-            if mm >= 64:
-                # the same product with the pointwise stage as dense tensor-core products per
-                # point, on the NTT path and on the Vandermonde path (every stage on tensor cores)
-                C3 = torch.empty_like(C1)
-                ctx.set_option(pmat.PM_OPT_POINTWISE, 3)
-                t_nt3 = ev_ms(lambda: pmat.pmat_mul(ctx, synth.P998, A, B, out=C3), 2)
-                st3, _ = stage_split(lambda: pmat.pmat_mul(ctx, synth.P998, A, B, out=C3), 2)
-                t_vd3 = ev_ms(vd, 2)
-                ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
-                stc, _ = stage_split(nt, 2)
-                torch.cuda.synchronize()
-                extra_tc = {"ntt_tc_pointwise_ms": round(t_nt3, 3), "vdm_tc_pointwise_ms": round(t_vd3, 3),
-                            "tc_pointwise_stage_ms": round(st3["pointwise"], 3),
-                            "cuda_core_pointwise_stage_ms": round(stc["pointwise"], 3),
-                            "tc_outputs_equal": bool(torch.equal(C3, C2) and torch.equal(C1, C2))}
-                del C3
+            ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
             L = 1 << max(5, (2 * dd - 2).bit_length())
             nks = lambda K: (K + 15) // 16                                    # noqa: E731
             tiles = lambda M, N: ((M + 127) // 128) * ((N + 31) // 32)       # noqa: E731
@@ -411,11 +399,31 @@ def extra_workloads(ctx, s, which=("vandermonde", "pm_basis", "resultant", "batc
             interp_fl = tiles(e, 2 * dd - 1) * nks(L) * mma
             torch.cuda.synchronize()
             key = f"m{mm}_d{dd}"
-            res[key] = {"vdm_ms": round(t_vd, 3), "ntt_ms": round(t_nt, 3), "outputs_equal": bool(torch.equal(C1, C2)),
+            res[key] = {"ntt_cuda_core_pointwise_ms": round(t_nt, 3), "vdm_ms": round(t_vd, 3),
+                        "outputs_equal": bool(torch.equal(C1, C2)),
+                        "cuda_core_pointwise_stage_ms": round(stc["pointwise"], 3),
                         "vdm_stage_ms": {k2: round(v, 3) for k2, v in st.items()},
                         "eval_gemm_tflops": round(eval_fl / (st["fwd_ntt"] * 1e-3) / 1e12, 1),
                         "interp_gemm_tflops": round(interp_fl / (st["inv_ntt"] * 1e-3) / 1e12, 1),
-                        "eval_tensor_frac": round(eval_fl / (st["fwd_ntt"] * 1e-3) / 1e12 / peak, 4), **extra_tc}
+                        "eval_tensor_frac": round(eval_fl / (st["fwd_ntt"] * 1e-3) / 1e12 / peak, 4)}
+            if mm >= 64:
+                # the pointwise stage as dense tensor-core products per point, on the NTT path
+                # and on the Vandermonde path (every stage on the tensor cores)
+                C3 = torch.empty_like(C1)
+                ctx.set_option(pmat.PM_OPT_POINTWISE, 3)
+                nt3 = lambda: pmat.pmat_mul(ctx, synth.P998, A, B, out=C3)  # noqa: E731
+                t_nt3 = ev_ms(nt3, 2)
+                st3, _ = stage_split(nt3, 2)
+                t_vd3 = ev_ms(vd, 2)
+                ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
+                t_auto = ev_ms(nt, 2)
+                torch.cuda.synchronize()
+                res[key].update({"ntt_tensor_core_pointwise_ms": round(t_nt3, 3), "vdm_tensor_core_pointwise_ms": round(t_vd3, 3),
+                                 "tensor_core_pointwise_stage_ms": round(st3["pointwise"], 3),
+                                 "pointwise_speedup": round(stc["pointwise"] / st3["pointwise"], 3),
+                                 "auto_mode_ms": round(t_auto, 3),
+                                 "tensor_core_outputs_equal": bool(torch.equal(C3, C2) and torch.equal(C1, C2))})
+                del C3
             del A, B, C1, C2
             torch.cuda.empty_cache()
         return {"vandermonde_p998": res, "mma_peak_tflops_n128": round(peak, 1)}

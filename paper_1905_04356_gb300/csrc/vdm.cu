@@ -24,10 +24,11 @@
 // CTA computes a 128 x 32 output tile: per K-step, four tcgen05.mma of 128 x 128
 // x 16 (digit x of A against [B_0 B_1 B_2 B_3]) write tensor-memory columns
 // [32x, 32x + 128), so column block w accumulates E_w = sum_{x+y=w} A_x B_y.
-// A digit product is at most 2^14 in magnitude and E_w has at most 4 x 64 of
-// them per 64 inner entries, so after every 4 K-steps the seven accumulators
-// (|E_w| <= 2^22, exact in fp32) are drained: one FADD of 1.5 2^23 gives
-// E_w's bits, sum_w (256^w mod p) E_w + the running residue is reduced mod p.
+// A digit product is at most 2^14 in magnitude and E_w has at most 4 x 256 of
+// them per 256 inner entries, so every partial sum is an integer of magnitude
+// <= 2^24, exact in fp32 (2^24 itself only when every term is the largest).
+// After every 16 K-steps the seven accumulators are drained: converted to
+// int32 (F2I), sum_w (256^w mod p) E_w + the running residue is reduced mod p.
 // Roles: warp 4 issues the chunks' bulk copies (cp.async.bulk, mbarrier
 // transaction counts) into a ring of 4 stages, warp 5's first thread the MMAs,
 // warps 0-3 (one per lane quarter) drain the accumulators and write the tile.
@@ -47,7 +48,7 @@
 #define VD_SMEM (VD_STAGES * VD_STAGE)
 #define VD_THREADS 192
 #define VD_COLS 256          // tensor-memory columns (7 x 32 used)
-#define VD_KC 4              // K-steps per drain (64 inner entries)
+#define VD_KC 16             // K-steps per drain (256 inner entries)
 
 #define CKI(call)                                                       \
     do {                                                                \
@@ -191,11 +192,10 @@ __device__ __forceinline__ bool vd_wait(uint32_t bar, uint32_t parity, volatile 
     return false;
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t *d)
+__device__ __forceinline__ void tmem_ld4(uint32_t addr, uint32_t *d)
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7])
-                 : "r"(addr));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]) : "r"(addr));
 }
 
 __device__ __forceinline__ void tmem_zero16(uint32_t addr)
@@ -311,13 +311,9 @@ __global__ void __launch_bounds__(VD_THREADS, 2) k_modgemm(const __grid_constant
         const uint32_t tq = tmem + ((uint32_t)(32 * warp) << 16);
         const u32 q = J.P.q;
         u32 cw[7];
-        u64 sum = 0;
 #pragma unroll
-        for (int w = 0; w < 7; w++) {
-            cw[w] = (u32)((1ull << (8 * w)) % q);
-            sum += cw[w];
-        }
-        const u64 k0 = ((u64)q << 25) - sum * 0x4B400000ull;   // q 2^25 - sum_w cw_w bits(1.5 2^23), mod 2^64
+        for (int w = 0; w < 7; w++) cw[w] = (u32)((1ull << (8 * w)) % q);
+        const i64 off = (i64)q << 28;          // > 7 q 2^24 >= |sum_w cw_w E_w|: keeps the sums positive
         u32 acc[32];
 #pragma unroll
         for (int c = 0; c < 32; c++) acc[c] = 0;
@@ -326,17 +322,17 @@ __global__ void __launch_bounds__(VD_THREADS, 2) k_modgemm(const __grid_constant
             __syncwarp();
             asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-            for (int g = 0; g < 4; g++) {                  // 8 columns at a time: 7 loads, one wait
-                uint32_t d[7][8];
+            for (int g = 0; g < 8; g++) {                  // 4 columns at a time: 7 loads, one wait
+                uint32_t d[7][4];
 #pragma unroll
-                for (int w = 0; w < 7; w++) tmem_ld8(tq + 32u * w + 8u * g, d[w]);
+                for (int w = 0; w < 7; w++) tmem_ld4(tq + 32u * w + 4u * g, d[w]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-                for (int cc = 0; cc < 8; cc++) {
-                    u64 x = k0 + acc[8 * g + cc];
+                for (int cc = 0; cc < 4; cc++) {
+                    i64 x = off + acc[4 * g + cc];
 #pragma unroll
-                    for (int w = 0; w < 7; w++) x += (u64)__float_as_uint(__uint_as_float(d[w][cc]) + 12582912.0f) * cw[w];
-                    acc[8 * g + cc] = reduce64(x, J.P);
+                    for (int w = 0; w < 7; w++) x += (i64)(int)cw[w] * (i64)__float2int_rn(__uint_as_float(d[w][cc]));
+                    acc[4 * g + cc] = reduce64((u64)x, J.P);
                 }
             }
 #pragma unroll
