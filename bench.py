@@ -266,6 +266,12 @@ def extra_workloads(ctx, s, which=("vandermonde", "pm_basis", "resultant", "batc
         F = pmat.to_device(W["F"])
         run = lambda: pmat.pm_basis(ctx, W["p"], F, W["d"], W["shift"])  # noqa: E731
         out = {"pm_basis_32x16_d8192_ms": round(ev_ms(run, reps), 2)}
+        # the threshold tuner on the same shape (seeded pseudo-random input); the call above used T = 32
+        T, ns = pmat.tune_basis(ctx, W["p"], 32, 16, W["d"], reps=1)
+        out["pm_basis_tuned_threshold"] = {"T": T, "ms": round(ns / 1e6, 2)}
+        if T != 32:
+            out["pm_basis_32x16_d8192_tuned_T_ms"] = round(ev_ms(run, reps), 2)
+        ctx.set_option(pmat.PM_OPT_THRESHOLD, 32)
         st, wk = stage_split(run)
         out["pm_basis_stage_ms"] = {k: round(v, 2) for k, v in st.items()}
         out["pm_basis_leaf_us_per_order_step"] = round(st["leaf"] * 1000 / W["d"], 2)
@@ -426,7 +432,30 @@ def extra_workloads(ctx, s, which=("vandermonde", "pm_basis", "resultant", "batc
                 del C3
             del A, B, C1, C2
             torch.cuda.empty_cache()
-        return {"vandermonde_p998": res, "mma_peak_tflops_n128": round(peak, 1)}
+        # the dense tensor-core pointwise form at m = 512, d = 128 modulo a 60-bit prime (5 CRT primes)
+        g = synth.rng(512128)
+        p60 = synth.random_prime(g, 60)
+        A = pmat.to_device(synth.uniform(g, (512, 512, 128), p60, np.uint64))
+        B = pmat.to_device(synth.uniform(g, (512, 512, 128), p60, np.uint64))
+        C1 = torch.empty((512, 512, 255), dtype=torch.int64, device="cuda")
+        C2 = torch.empty_like(C1)
+        ctx.set_option(pmat.PM_OPT_POINTWISE, 1)
+        t_cc = ev_ms(lambda: pmat.pmat_mul(ctx, p60, A, B, out=C1), 2)
+        st_cc, _ = stage_split(lambda: pmat.pmat_mul(ctx, p60, A, B, out=C1), 2)
+        ctx.set_option(pmat.PM_OPT_POINTWISE, 3)
+        t_tc = ev_ms(lambda: pmat.pmat_mul(ctx, p60, A, B, out=C2), 2)
+        st_tc, _ = stage_split(lambda: pmat.pmat_mul(ctx, p60, A, B, out=C2), 2)
+        ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
+        torch.cuda.synchronize()
+        p60_res = {"ntt_cuda_core_pointwise_ms": round(t_cc, 3), "ntt_tensor_core_pointwise_ms": round(t_tc, 3),
+                   "cuda_core_pointwise_stage_ms": round(st_cc["pointwise"], 3),
+                   "tensor_core_pointwise_stage_ms": round(st_tc["pointwise"], 3),
+                   "pointwise_speedup": round(st_cc["pointwise"] / st_tc["pointwise"], 3),
+                   "outputs_equal": bool(torch.equal(C1, C2))}
+        del A, B, C1, C2
+        torch.cuda.empty_cache()
+        return {"vandermonde_p998": res, "dense_tensor_core_pointwise_p60_m512_d128": p60_res,
+                "mma_peak_tflops_n128": round(peak, 1)}
 
     out = {}
     with torch.cuda.stream(s):
