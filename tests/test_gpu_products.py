@@ -337,7 +337,7 @@ def test_tensor_core_extreme_inputs(ctx, p, w):
                                   (P62, 8, 65, 1, 200, 9, 7), (2, 4, 64, 300, 3, 5, 6)])
 def test_tensor_core_dense_pointwise_matches_oracle(ctx, case):
     """The tensor-core dense form (PM_OPT_POINTWISE = 3: every point's m x n . n x k product as a
-    dense product of fp16 digits, drained every 64 inner entries) against the oracle: m = 64 and
+    dense product of fp16 digits, drained every 256 inner entries) against the oracle: m = 64 and
     above, ragged n and k, inner dimensions from 1 to 300, moduli 2 to 62 bits."""
     from paper_1905_04356_gb300 import pmat
     p, w, m, n, k, dA, dB = case
