@@ -20,18 +20,25 @@
 // the bytes of r + 0x80808080 minus 128) and stored in chunks that are the
 // shared-memory operand tiles of one 16-wide K-step in the no-swizzle K-major
 // core-matrix layout: an A chunk holds the four digit tiles of 128 rows (16 KB),
-// a B chunk the four digit blocks of 32 rows stacked as 128 MMA rows (4 KB).  A
-// CTA computes a 128 x 32 output tile: per K-step, four tcgen05.mma of 128 x 128
-// x 16 (digit x of A against [B_0 B_1 B_2 B_3]) write tensor-memory columns
-// [32x, 32x + 128), so column block w accumulates E_w = sum_{x+y=w} A_x B_y.
+// a B chunk the four digit blocks of 64 rows stacked as 256 MMA rows (8 KB).
+// One CTA per SM, persistent over 128 x 64 output tiles: per K-step, four
+// tcgen05.mma of 128 x 256 x 16 (digit x of A against [B_0 B_1 B_2 B_3]) write
+// tensor-memory columns [64x, 64x + 256), so column block w accumulates
+// E_w = sum_{x+y=w} A_x B_y (7 x 64 columns).  N = 256 halves the operand bytes
+// per product against N = 128, which is what bounds this MMA shape.
 // A digit product is at most 2^14 in magnitude and E_w has at most 4 x 256 of
 // them per 256 inner entries, so every partial sum is an integer of magnitude
 // <= 2^24, exact in fp32 (2^24 itself only when every term is the largest).
-// After every 16 K-steps the seven accumulators are drained: converted to
-// int32 (F2I), sum_w (256^w mod p) E_w + the running residue is reduced mod p.
-// Roles: warp 4 issues the chunks' bulk copies (cp.async.bulk, mbarrier
-// transaction counts) into a ring of 4 stages, warp 5's first thread the MMAs,
-// warps 0-3 (one per lane quarter) drain the accumulators and write the tile.
+// After every 16 K-steps the seven accumulators are drained: E_1..E_4 converted
+// to int32 by F2I, E_0, E_5 and E_6 (|E| <= 2^22: one product term of digits
+// d_0 d_0, two of d_2 d_3, one of d_3 d_3) by adding 1.5 2^23 in fp32 and taking
+// the low bits; then sum_w (256^w mod p) E_w + the running residue mod p.  The
+// first K-step of a chunk clears the accumulators without stores: an MMA of a
+// zero A tile into columns [192, 448) and the x = 0 MMA with accumulation off.
+// Roles: warp 8 issues the chunks' bulk copies (cp.async.bulk, mbarrier
+// transaction counts) into a ring of 8 stages, warp 9's first thread the MMAs,
+// warps 0-7 (lane quarter w % 4, 32-column half w / 4) drain the accumulators
+// and write finished tiles; the MMAs of a chunk wait for the previous drain.
 // Every wait is bounded: after a timeout PM_ETIMEOUT is recorded, later waits
 // return at once and the loops run out (output undefined); before the CTA exits
 // the producer waits (bounded) for its copies and the MMA thread for its MMAs.
@@ -41,13 +48,16 @@
 
 #include "host.h"
 
-#define VD_STAGES 4
+#define VD_STAGES 8
+#define VD_BN 64             // output columns per tile (B rows per chunk)
 #define VD_ACHUNK 16384      // 128 rows x 16 K fp16 x 4 digits
-#define VD_BCHUNK 4096       // 32 rows x 16 K fp16 x 4 digits (128 MMA rows)
+#define VD_BCHUNK 8192       // 64 rows x 16 K fp16 x 4 digits (256 MMA rows)
 #define VD_STAGE (VD_ACHUNK + VD_BCHUNK)
-#define VD_SMEM (VD_STAGES * VD_STAGE)
-#define VD_THREADS 192
-#define VD_COLS 256          // tensor-memory columns (7 x 32 used)
+#define VD_ZERO 4096         // a zero 128 x 16 A operand (clears accumulator columns)
+#define VD_SMEM (VD_STAGES * VD_STAGE + VD_ZERO)
+#define VD_EPI 8             // drain warps: lane quarter w % 4, column half w / 4
+#define VD_THREADS (32 * VD_EPI + 64)
+#define VD_COLS 512          // tensor-memory columns (7 x 64 used)
 #define VD_KC 16             // K-steps per drain (256 inner entries)
 
 #define CKI(call)                                                       \
@@ -63,7 +73,7 @@ struct MgJob {
     i64 sAd, sBd;                   // bytes between the chunk sets of consecutive batch members
     u32 *C;                         // C[b sCb + i ldc + j ldj] for i < M, j < N, in [0, p)
     i64 ldc, ldj, sCb;
-    int M, N, nks, nbN, tiles;      // rows, columns, K-steps, 32-column blocks, tiles per member
+    int M, N, nks, nbN, tiles;      // rows, columns, K-steps, 64-column blocks, tiles per member
     PrimeDev P;
 };
 
@@ -95,8 +105,8 @@ __device__ __forceinline__ uint32_t digit_pair(uint32_t t0, uint32_t t1, int x)
 }
 
 // digits of 8 residues r[0..7] (inner entries 8 kk8 .. of one row) into the chunk layout.
-// bmode: 0 = A chunks (128 rows, digit x tile at 4096 x), 1 = B chunks (32 rows, digit x at rows
-// 32 x + r); chunk (row block, K-step) at base + (rb nks + ks) chunk bytes
+// bmode: 0 = A chunks (128 rows, digit x tile at 4096 x), 1 = B chunks (64 rows, digit x at rows
+// 64 x + r); chunk (row block, K-step) at base + (rb nks + ks) chunk bytes
 __device__ __forceinline__ void put_digits(unsigned char *base, int bmode, int nks, int row, int k8, const u32 (&r)[8])
 {
     u32 t[8];
@@ -112,7 +122,7 @@ __device__ __forceinline__ void put_digits(unsigned char *base, int bmode, int n
         h.w = digit_pair(t[6], t[7], x);
         unsigned char *dst = bmode == 0
             ? base + ((size_t)(row >> 7) * nks + ks) * VD_ACHUNK + x * 4096 + op_off(row & 127, kk8)
-            : base + ((size_t)(row >> 5) * nks + ks) * VD_BCHUNK + op_off(32 * x + (row & 31), kk8);
+            : base + ((size_t)(row >> 6) * nks + ks) * VD_BCHUNK + op_off(64 * x + (row & 63), kk8);
         *(uint4 *)dst = h;
     }
 }
@@ -198,22 +208,37 @@ __device__ __forceinline__ void tmem_ld4(uint32_t addr, uint32_t *d)
                  : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]) : "r"(addr));
 }
 
-__device__ __forceinline__ void tmem_zero16(uint32_t addr)
-{
-    const uint32_t z = 0;
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};"
-                 ::"r"(addr), "r"(z));
-}
-
 __device__ __forceinline__ void commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
 }
 
-__global__ void __launch_bounds__(VD_THREADS, 2) k_modgemm(const __grid_constant__ MgJob J, int *status)
+// bounded wait that ignores the abort flag (teardown: copies and MMAs land before exit)
+__device__ __forceinline__ void vd_wait_raw(uint32_t bar, uint32_t parity)
+{
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; it++)
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(bar), "r"(parity));
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 ::"r"(d), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+// integer value of an fp32 holding an integer of magnitude <= 2^22
+__device__ __forceinline__ int small_f2i(uint32_t f)
+{
+    return __float_as_int(__fadd_rn(__uint_as_float(f), 12582912.0f)) - 0x4B400000;
+}
+
+__global__ void __launch_bounds__(VD_THREADS, 1) k_modgemm(const __grid_constant__ MgJob J, int total_tiles, int *status)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
-    // full[4], empty[4], accumulators full, accumulators drained, final drain
+    // full[S], empty[S], accumulators full, accumulators drained, final drain
     __shared__ __align__(8) uint64_t bars[2 * VD_STAGES + 3];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -222,6 +247,9 @@ __global__ void __launch_bounds__(VD_THREADS, 2) k_modgemm(const __grid_constant
     const uint32_t b_full = smem_u32(&bars[0]), b_empty = smem_u32(&bars[VD_STAGES]),
                    b_accf = smem_u32(&bars[2 * VD_STAGES]), b_acce = smem_u32(&bars[2 * VD_STAGES + 1]),
                    b_drain = smem_u32(&bars[2 * VD_STAGES + 2]);
+    unsigned char *zero = sm + VD_STAGES * VD_STAGE;
+    for (int x = tid; x < VD_ZERO / 16; x += VD_THREADS) ((uint4 *)zero)[x] = make_uint4(0, 0, 0, 0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // the zero tile, for the tensor core
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                      "r"(VD_COLS));
@@ -230,7 +258,7 @@ __global__ void __launch_bounds__(VD_THREADS, 2) k_modgemm(const __grid_constant
     if (tid == 0) {
         for (int b = 0; b < 2 * VD_STAGES + 3; b++)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[b])),
-                         "r"(b == 2 * VD_STAGES + 1 ? 128 : 1));
+                         "r"(b == 2 * VD_STAGES + 1 ? 32 * VD_EPI : 1));
         asm volatile("fence.mbarrier_init.release.cluster;");
         abort_flag = 0;
     }
@@ -238,116 +266,112 @@ __global__ void __launch_bounds__(VD_THREADS, 2) k_modgemm(const __grid_constant
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
-    const int bm = blockIdx.x / J.tiles, tl = blockIdx.x % J.tiles;
-    const int mb = tl / J.nbN, nb = tl % J.nbN;    // column blocks fastest: A row blocks stay in L2
     const int nks = J.nks, nkc = (nks + VD_KC - 1) / VD_KC;
-    if (warp < 4) {
-        const uint32_t tq = tmem + ((uint32_t)(32 * warp) << 16);
-#pragma unroll
-        for (int c = 0; c < 14; c++) tmem_zero16(tq + 16u * c);
-        asm volatile("tcgen05.wait::st.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
 
-    if (warp == 4) {
+    if (warp == VD_EPI) {
         // ---------------------------------------------------------------- producer
         if (lane == 0) {
-            const unsigned char *Ab = J.Ad + bm * J.sAd + (size_t)mb * nks * VD_ACHUNK,
-                                *Bb = J.Bd + bm * J.sBd + (size_t)nb * nks * VD_BCHUNK;
-            for (int ks = 0; ks < nks; ks++) {
-                const int s = ks % VD_STAGES;
-                if (ks >= VD_STAGES) vd_wait(b_empty + 8 * s, (uint32_t)((ks / VD_STAGES - 1) & 1), abort_, status);
-                const uint32_t dst = smem_u32(sm + s * VD_STAGE), bar = b_full + 8 * s;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(VD_STAGE) : "memory");
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                             ::"r"(dst), "l"(Ab + (size_t)ks * VD_ACHUNK), "r"(VD_ACHUNK), "r"(bar) : "memory");
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                             ::"r"(dst + VD_ACHUNK), "l"(Bb + (size_t)ks * VD_BCHUNK), "r"(VD_BCHUNK), "r"(bar)
-                             : "memory");
+            int ksg = 0;                      // K-steps issued by this CTA
+            for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+                const int bm = t / J.tiles, tl = t % J.tiles, mb = tl / J.nbN, nb = tl % J.nbN;
+                const unsigned char *Ab = J.Ad + bm * J.sAd + (size_t)mb * nks * VD_ACHUNK,
+                                    *Bb = J.Bd + bm * J.sBd + (size_t)nb * nks * VD_BCHUNK;
+                for (int ks = 0; ks < nks; ks++, ksg++) {
+                    const int s = ksg % VD_STAGES;
+                    if (ksg >= VD_STAGES) vd_wait(b_empty + 8 * s, (uint32_t)((ksg / VD_STAGES - 1) & 1), abort_, status);
+                    const uint32_t dst = smem_u32(sm + s * VD_STAGE), bar = b_full + 8 * s;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(VD_STAGE) : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 ::"r"(dst), "l"(Ab + (size_t)ks * VD_ACHUNK), "r"(VD_ACHUNK), "r"(bar) : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 ::"r"(dst + VD_ACHUNK), "l"(Bb + (size_t)ks * VD_BCHUNK), "r"(VD_BCHUNK), "r"(bar)
+                                 : "memory");
+                }
             }
             // the copies still in flight land before the CTA exits
-            for (int ks = nks - VD_STAGES < 0 ? 0 : nks - VD_STAGES; ks < nks; ks++) {
-                const int s = ks % VD_STAGES;
-                uint32_t done = 0;
-                for (int it = 0; it < (1 << 24) && !done; it++)
-                    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                                 " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(b_full + 8 * s), "r"((uint32_t)((ks / VD_STAGES) & 1)));
-            }
+            for (int k2 = ksg - VD_STAGES < 0 ? 0 : ksg - VD_STAGES; k2 < ksg; k2++)
+                vd_wait_raw(b_full + 8 * (k2 % VD_STAGES), (uint32_t)((k2 / VD_STAGES) & 1));
         }
-    } else if (warp == 5) {
+    } else if (warp == VD_EPI + 1) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            // D f32 (bit 4), A and B fp16, K-major; N = 128 (>> 3 at bit 17), M = 128 (>> 4 at bit 24)
-            const uint32_t idesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
-            for (int kc = 0; kc < nkc; kc++) {
-                if (kc >= 1) vd_wait(b_acce, (uint32_t)((kc - 1) & 1), abort_, status);   // drained and cleared
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const int k1 = (kc + 1) * VD_KC < nks ? (kc + 1) * VD_KC : nks;
-                for (int ks = kc * VD_KC; ks < k1; ks++) {
-                    const int s = ks % VD_STAGES;
-                    vd_wait(b_full + 8 * s, (uint32_t)((ks / VD_STAGES) & 1), abort_, status);
+            // D f32 (bit 4), A and B fp16, K-major; N = 256 (>> 3 at bit 17), M = 128 (>> 4 at bit 24)
+            const uint32_t idesc = (1u << 4) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+            const uint64_t zd = op_desc(smem_u32(zero));
+            int ksg = 0, g = 0;               // K-steps and accumulator chunks of this CTA
+            for (int t = blockIdx.x; t < total_tiles; t += gridDim.x)
+                for (int kc = 0; kc < nkc; kc++, g++) {
+                    if (g >= 1) vd_wait(b_acce, (uint32_t)((g - 1) & 1), abort_, status);   // previous chunk drained
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t st = smem_u32(sm + s * VD_STAGE);
-                    const uint64_t bd = op_desc(st + VD_ACHUNK);
+                    const int k1 = (kc + 1) * VD_KC < nks ? (kc + 1) * VD_KC : nks;
+                    for (int ks = kc * VD_KC; ks < k1; ks++, ksg++) {
+                        const int s = ksg % VD_STAGES;
+                        vd_wait(b_full + 8 * s, (uint32_t)((ksg / VD_STAGES) & 1), abort_, status);
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        const uint32_t st = smem_u32(sm + s * VD_STAGE);
+                        const uint64_t bd = op_desc(st + VD_ACHUNK);
+                        const uint32_t first = ks == kc * VD_KC;
+                        if (first) mma_f16(tmem + 192u, zd, bd, idesc, 0u);     // columns [192, 448) <- 0
 #pragma unroll
-                    for (int x = 0; x < 4; x++)
-                        asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, 1, 0;\n"
-                                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                                     ::"r"(tmem + 32u * x), "l"(op_desc(st + 4096 * x)), "l"(bd), "r"(idesc));
-                    commit(b_empty + 8 * s);
+                        for (int x = 0; x < 4; x++)
+                            mma_f16(tmem + 64u * x, op_desc(st + 4096 * x), bd, idesc, (first && x == 0) ? 0u : 1u);
+                        commit(b_empty + 8 * s);
+                    }
+                    commit(b_accf);
                 }
-                commit(b_accf);
-            }
             commit(b_drain);                 // every MMA of this CTA has completed
-            uint32_t done = 0;
-            for (int it = 0; it < (1 << 26) && !done; it++)
-                asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                             " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(b_drain), "r"(0u));
+            vd_wait_raw(b_drain, 0u);
         }
     } else {
-        // ---------------------------------------------------------------- epilogue (warps 0-3)
-        const uint32_t tq = tmem + ((uint32_t)(32 * warp) << 16);
+        // ---------------------------------------------------------------- drain (warps 0-7)
+        const int half = warp >> 2;
+        const uint32_t tq = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 32u * half;
         const u32 q = J.P.q;
         u32 cw[7];
 #pragma unroll
         for (int w = 0; w < 7; w++) cw[w] = (u32)((1ull << (8 * w)) % q);
         const i64 off = (i64)q << 28;          // > 7 q 2^24 >= |sum_w cw_w E_w|: keeps the sums positive
-        u32 acc[32];
+        int g = 0;
+        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+            const int bm = t / J.tiles, tl = t % J.tiles, mb = tl / J.nbN, nb = tl % J.nbN;
+            u32 acc[32];
 #pragma unroll
-        for (int c = 0; c < 32; c++) acc[c] = 0;
-        for (int kc = 0; kc < nkc; kc++) {
-            if (lane == 0) vd_wait(b_accf, (uint32_t)(kc & 1), abort_, status);
-            __syncwarp();
-            asm volatile("tcgen05.fence::after_thread_sync;");
+            for (int c = 0; c < 32; c++) acc[c] = 0;
+            for (int kc = 0; kc < nkc; kc++, g++) {
+                if (lane == 0) vd_wait(b_accf, (uint32_t)(g & 1), abort_, status);
+                __syncwarp();
+                asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-            for (int g = 0; g < 8; g++) {                  // 4 columns at a time: 7 loads, one wait
-                uint32_t d[7][4];
+                for (int gg = 0; gg < 8; gg++) {              // 4 columns at a time: 7 loads, one wait
+                    uint32_t d[7][4];
 #pragma unroll
-                for (int w = 0; w < 7; w++) tmem_ld4(tq + 32u * w + 4u * g, d[w]);
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                    for (int w = 0; w < 7; w++) tmem_ld4(tq + 64u * w + 4u * gg, d[w]);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+                    if (gg == 7) {
+                        // every value of the chunk is in registers: the MMAs may overwrite
+                        asm volatile("tcgen05.fence::before_thread_sync;");
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b_acce) : "memory");
+                    }
 #pragma unroll
-                for (int cc = 0; cc < 4; cc++) {
-                    i64 x = off + acc[4 * g + cc];
+                    for (int cc = 0; cc < 4; cc++) {
+                        i64 x = off + acc[4 * gg + cc];
+                        x += (i64)(int)cw[0] * (i64)small_f2i(d[0][cc]);
 #pragma unroll
-                    for (int w = 0; w < 7; w++) x += (i64)(int)cw[w] * (i64)__float2int_rn(__uint_as_float(d[w][cc]));
-                    acc[4 * g + cc] = reduce64((u64)x, J.P);
+                        for (int w = 1; w < 5; w++) x += (i64)(int)cw[w] * (i64)__float2int_rn(__uint_as_float(d[w][cc]));
+                        x += (i64)(int)cw[5] * (i64)small_f2i(d[5][cc]);
+                        x += (i64)(int)cw[6] * (i64)small_f2i(d[6][cc]);
+                        acc[4 * gg + cc] = reduce64((u64)x, J.P);
+                    }
                 }
             }
+            const int row = mb * 128 + 32 * (warp & 3) + lane, c0 = nb * VD_BN + 32 * half;
+            if (row < J.M && c0 < J.N) {
+                u32 *dst = J.C + bm * J.sCb + (i64)row * J.ldc + (i64)c0 * J.ldj;
+                const int nc = J.N - c0 < 32 ? J.N - c0 : 32;
 #pragma unroll
-            for (int c = 0; c < 14; c++) tmem_zero16(tq + 16u * c);
-            asm volatile("tcgen05.wait::st.sync.aligned;");
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b_acce) : "memory");
-        }
-        const int row = mb * 128 + 32 * warp + lane;
-        if (row < J.M) {
-            u32 *dst = J.C + bm * J.sCb + (i64)row * J.ldc + (i64)nb * 32 * J.ldj;
-            const int nc = J.N - nb * 32 < 32 ? J.N - nb * 32 : 32;
-#pragma unroll
-            for (int c = 0; c < 32; c++)
-                if (c < nc) dst[c * J.ldj] = acc[c];
+                for (int c = 0; c < 32; c++)
+                    if (c < nc) dst[c * J.ldj] = acc[c];
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -371,12 +395,16 @@ int vd_modgemm_batched(pm_ctx *ctx, const unsigned char *Ad, int64_t sAd, const 
     MgJob J;
     J.Ad = Ad; J.Bd = Bd; J.sAd = sAd; J.sBd = sBd;
     J.C = C; J.ldc = ldc; J.ldj = ldj; J.sCb = sCb;
-    J.M = M; J.N = N; J.nks = nks; J.nbN = (N + 31) / 32; J.tiles = ((M + 127) / 128) * J.nbN; J.P = P;
-    const int64_t blocks = (int64_t)batch * J.tiles;
-    if (blocks > 0x7fffffffLL) return pm_fail(ctx, PM_EUNSUPPORTED, "modular product grid too large");
-    cudaError_t e = cudaFuncSetAttribute(k_modgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, VD_SMEM);
+    J.M = M; J.N = N; J.nks = nks; J.nbN = (N + VD_BN - 1) / VD_BN; J.tiles = ((M + 127) / 128) * J.nbN; J.P = P;
+    const int64_t tiles = (int64_t)batch * J.tiles;
+    if (tiles > 0x7fffffffLL) return pm_fail(ctx, PM_EUNSUPPORTED, "modular product grid too large");
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess || sms < 1) return pm_cuda(ctx, e != cudaSuccess ? e : cudaErrorInvalidDevice, "SM count");
+    e = cudaFuncSetAttribute(k_modgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, VD_SMEM);
     if (e != cudaSuccess) return pm_cuda(ctx, e, "cudaFuncSetAttribute");
-    k_modgemm<<<(unsigned)blocks, VD_THREADS, VD_SMEM, ctx->stream>>>(J, ctx->d_status);
+    const int grid = tiles < sms ? (int)tiles : sms;      // persistent: one CTA per SM
+    k_modgemm<<<grid, VD_THREADS, VD_SMEM, ctx->stream>>>(J, (int)tiles, ctx->d_status);
     ctx->launches++;
     return pm_cuda(ctx, cudaGetLastError(), "k_modgemm");
 }
@@ -388,11 +416,12 @@ int vd_modgemm(pm_ctx *ctx, const unsigned char *Ad, const unsigned char *Bd, in
     return vd_modgemm_batched(ctx, Ad, 0, Bd, 0, 1, M, N, nks, C, ldc, 1, 0, P);
 }
 
-// Bytes of the digit chunks of a member: rows in blocks of 128 (A) or 32 (B), K in steps of 16.
+// Bytes of the digit chunks of a member: rows in blocks of 128 (A) or 64 (B), K in steps of 16.
 static size_t vd_chunk_bytes(int rows, int K, int bmode)
 {
     const int nks = (K + 15) / 16;
-    return bmode == 0 ? (size_t)((rows + 127) / 128) * nks * VD_ACHUNK : (size_t)((rows + 31) / 32) * nks * VD_BCHUNK;
+    return bmode == 0 ? (size_t)((rows + 127) / 128) * nks * VD_ACHUNK
+                      : (size_t)((rows + VD_BN - 1) / VD_BN) * nks * VD_BCHUNK;
 }
 
 // The pointwise products C_j = A_j B_j mod q at the L transform points as a batch of dense
@@ -453,8 +482,8 @@ extern "C" int pmat_mul_vdm(pm_ctx *ctx, uint64_t p, int m, int n, int k, const 
     const int64_t eA = (int64_t)m * n, eB = (int64_t)n * k, eC = (int64_t)m * k;
     const int nkA = (int)((dA + 15) / 16), nkB = (int)((dB + 15) / 16), nkL = (int)(L / 16);
     const size_t bXA = al256v((size_t)((eA + 127) / 128) * nkA * VD_ACHUNK), bXB = al256v((size_t)((eB + 127) / 128) * nkB * VD_ACHUNK);
-    const size_t bVA = al256v((size_t)((L + 31) / 32) * nkA * VD_BCHUNK), bVB = al256v((size_t)((L + 31) / 32) * nkB * VD_BCHUNK);
-    const size_t bTC = al256v((size_t)((eC + 127) / 128) * nkL * VD_ACHUNK), bW = al256v((size_t)((len + 31) / 32) * nkL * VD_BCHUNK);
+    const size_t bVA = al256v(vd_chunk_bytes(L, (int)dA, 1)), bVB = al256v(vd_chunk_bytes(L, (int)dB, 1));
+    const size_t bTC = al256v((size_t)((eC + 127) / 128) * nkL * VD_ACHUNK), bW = al256v(vd_chunk_bytes((int)len, L, 1));
     const size_t bdig = bXA + bXB + bVA + bVB + bTC + bW;
     const size_t bTa = al256v((size_t)eA * L * 4), bTb = al256v((size_t)eB * L * 4), bTc = al256v((size_t)eC * L * 4);
     const size_t btab = al256v((size_t)L * 4);
