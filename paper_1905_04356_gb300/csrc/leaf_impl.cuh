@@ -180,6 +180,75 @@ __device__ bool gj_regs(const LeafArgs &A, const u64 *R, ElimSm &E, int (*cand)[
     return fail == 0;
 }
 
+// The same elimination for n <= 16 and m <= 32 with the columns owned by lanes: warp w holds
+// columns 4w .. 4w + 3, lane l row l % 16 of columns 4w + 2 (l / 16) and the next.  Pivot step
+// s: the warp holding column s finds its lowest unused row with a nonzero entry by one ballot
+// and publishes the column (the factors M[c][s] of the update) into a buffer alternating with
+// the step's parity; after one named barrier every thread reads its factor and takes the
+// pivot row's entries of its two columns from its own warp by shuffles, so no step waits on
+// more than one exchange through shared memory (the row-owned layout of gj_regs needs a
+// cross-warp search for the pivot row and a broadcast of the whole row).  The pivots are kept
+// and turned into the prefix products E.fac after the loop.  Same pivots, same updates, same
+// outputs as gj_regs.
+__device__ bool gj_cols16(const LeafArgs &A, const u64 *R, ElimSm &E, int gn)
+{
+    __shared__ u64 fbuf[2][16];
+    __shared__ int rbuf[2];
+    __shared__ u64 pvs[16];
+    __shared__ int fail;
+    const int m = A.m, n = A.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const u64 p = A.p, pn = A.pn;
+    const int c = lane & 15, cp = lane >> 4, col0 = 4 * warp + 2 * cp;
+    if (warp < GJ_WARPS) {
+        u64 v0 = (c < n && col0 < m) ? R[E.ord[col0] * n + c] : 0;
+        u64 v1 = (c < n && col0 + 1 < m) ? R[E.ord[col0 + 1] * n + c] : 0;
+        unsigned used = 0;
+        int s = 0;
+        for (; s < n; s++) {
+            const int bf = s & 1, oc = s & 1, ocp = (s >> 1) & 1;
+            if (warp == (s >> 2)) {
+                const u64 x = oc ? v1 : v0;
+                const bool cand = cp == ocp && c < n && !((used >> c) & 1u) && x != 0;
+                const unsigned bits = (__ballot_sync(0xffffffffu, cand) >> (16 * ocp)) & 0xFFFFu;
+                if (cp == ocp) fbuf[bf][c] = x;
+                if (lane == 0) rbuf[bf] = bits ? __ffs(bits) - 1 : -1;
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(GJ_WARPS * 32));
+            const int r = rbuf[bf];
+            if (r < 0) break;                                // uniform over the group
+            used |= 1u << r;
+            const u64 fc = fbuf[bf][c], pv = fbuf[bf][r];
+            const u64 q0 = __shfl_sync(0xffffffffu, v0, r + 16 * cp), q1 = __shfl_sync(0xffffffffu, v1, r + 16 * cp);
+            if (c != r) {
+                v0 = fm_msub(pv, v0, fc, q0, p, pn);
+                v1 = fm_msub(pv, v1, fc, q1, p, pn);
+            }
+            if (tid == 0) { E.perm[s] = r; pvs[s] = pv; }
+        }
+        const bool ok = s == n;
+        asm volatile("bar.sync 1, %0;" ::"r"(GJ_WARPS * 32));   // pvs complete
+        if (ok) {
+            if (warp == 0) {
+                // E.fac[s] = prod_{s' < s} pv_s' (exclusive prefix products), E.dpr[n] = all of them
+                u64 x = lane < n ? pvs[lane] : A.one;
+#pragma unroll
+                for (int o = 1; o < 16; o <<= 1) {
+                    const u64 y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x = fm_mul(x, y, p, pn);
+                }
+                const u64 ex = __shfl_up_sync(0xffffffffu, x, 1);
+                if (lane < n) E.fac[lane] = lane ? ex : A.one;
+                if (lane == n - 1) E.dpr[n] = x;
+            }
+            if (c < n && col0 < m) E.M[c * m + col0] = v0;
+            if (c < n && col0 + 1 < m) E.M[c * m + col0 + 1] = v1;
+        }
+        if (tid == 0) fail = !ok;
+    }
+    asm volatile("bar.sync 2, %0;" ::"r"(gn));
+    return fail == 0;
+}
+
 // Register tile: GJ_RPW rows per warp (n <= 8 GJ_RPW), GJ_CPL columns per lane (m <= 32 GJ_CPL).
 // Called by the elimination group (warps 0 .. gn/32 - 1, gn >= GJ_WARPS * 32), which it
 // leaves through named barrier 2.
@@ -190,6 +259,7 @@ __device__ bool gj_dispatch(const LeafArgs &A, const u64 *R, ElimSm &E, int gn)
     __shared__ int fail;
     const int rpw = (A.n + GJ_WARPS - 1) / GJ_WARPS, cpl = (A.m + 31) / 32;
     if (gn < GJ_WARPS * 32) return false;          // the named barrier needs GJ_WARPS full warps
+    if (A.n <= 16 && A.m <= 32) return gj_cols16(A, R, E, gn);
     if (cpl == 1) {
         if (rpw <= 1) return gj_regs<1, 1>(A, R, E, cand, crow, &fail, gn);
         if (rpw <= 2) return gj_regs<2, 1>(A, R, E, cand, crow, &fail, gn);
