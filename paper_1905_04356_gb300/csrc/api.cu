@@ -265,12 +265,24 @@ static int fwd_entries_per_block(int lg)
     return th / tpt;
 }
 
-// Forward jobs of one operand modulo one prime (a column pass first when L > 2^14).
+// Forward jobs of one operand modulo one prime (a column pass first when L > 2^14, except for
+// 2^15 points and inputs of at most 2^14 coefficients: two block jobs, the odd half twisted).
 static void add_forward(const PrimeDev &P, const void *src, int mode, int64_t src_stride, int64_t src_len,
                         int entries, u32 *dst, int lg, std::vector<FwdJob> &blk, std::vector<int> &blk_n,
                         std::vector<ColJob> &col, std::vector<int> &col_n)
 {
     const int64_t L = int64_t(1) << lg;
+    if (lg == PM_LB_LOG2 + 1 && src_len <= (int64_t(1) << PM_LB_LOG2)) {
+        const int epb = fwd_entries_per_block(PM_LB_LOG2);
+        for (int h = 0; h < 2; h++) {
+            FwdJob j;
+            j.src = src; j.dst = dst + ((size_t)h << PM_LB_LOG2); j.src_stride = src_stride; j.dst_stride = L;
+            j.src_len = (int)src_len; j.src_mode = mode | (h ? PM_FWD_TWIST : 0); j.count = entries; j.grp = 0; j.P = P;
+            blk.push_back(j);
+            blk_n.push_back((entries + epb - 1) / epb);
+        }
+        return;
+    }
     if (lg <= PM_LB_LOG2) {
         FwdJob j;
         j.src = src; j.dst = dst; j.src_stride = src_stride; j.dst_stride = L;
@@ -308,12 +320,16 @@ static int launch_packs(pm_ctx *ctx, const std::vector<J> &jobs, const std::vect
     return PM_OK;
 }
 
-// Jobs [g0, blk.size()) transform one source modulo different primes, one job each (transforms
-// of at most 2^14 points): mark them an interleave group.
+// Jobs [g0, blk.size()) transform one source modulo different primes (one job each, or the two
+// halves of each 2^15-point transform), all reading the source with the same number of blocks:
+// mark them an interleave group.  Block jobs after a column pass read their own staging
+// arrays and stay ungrouped.
 static void group_forward(std::vector<FwdJob> &blk, size_t g0, int lg)
 {
     const size_t G = blk.size() - g0;
-    if (lg > PM_LB_LOG2 || G < 2 || G > 255) return;
+    if (lg > PM_LB_LOG2 + 1 || G < 2 || G > 255) return;
+    for (size_t i = g0; i < blk.size(); i++)
+        if ((blk[i].src_mode & 0xff) == 0 || blk[i].count != blk[g0].count) return;
     for (size_t i = 0; i < G; i++) blk[g0 + i].grp = (int)((G << 8) | i);
 }
 

@@ -123,7 +123,12 @@ __device__ __forceinline__ u64 sub64(u64 a, u64 b, u64 p) { return a >= b ? a - 
 // ---------------------------------------------------------------- jobs
 // Forward transform of `count` blocks of 2^lg points.  Block e reads
 // src + e*src_stride (src_len values, zero beyond) and writes dst + e*dst_stride.
-// src_mode: 0 = u32 already in [0, 2q), 4 = user u32 in [0,p), 8 = user u64.
+// src_mode: 0 = u32 already in [0, 2q), 4 = user u32 in [0,p), 8 = user u64; with
+// PM_FWD_TWIST added, the job is the second half of a 2^(LG+1)-point transform of at most 2^LG
+// coefficients: the radix-2 stage over the halves maps (x_i, 0) to (x_i, x_i w^i), w of
+// order 2^(LG+1), so coefficient i is multiplied by w^i on load and the 2^LG-point block
+// transform gives the odd half directly (the even half is the plain block transform).
+#define PM_FWD_TWIST 0x100
 // grp: 0, or (G << 8) | g for job g of an interleave group of G consecutive jobs in the pack (the
 // same source modulo G primes, equal block counts): the group's blocks alternate between its
 // jobs, so the G CTAs that read the same source entries run side by side and all but the first

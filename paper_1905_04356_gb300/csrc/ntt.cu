@@ -156,11 +156,19 @@ __device__ __forceinline__ void fwd_first_t(u32 (&v)[16], u32 *X, const FwdJob &
     const u32 q = J.P.q, q2 = J.P.q2;
     const char *src = (const char *)J.src;
     const i64 sb = e * J.src_stride;
+    const int mode = J.src_mode & 0xff;
+    const bool twist = (J.src_mode & PM_FWD_TWIST) != 0;
+    // coefficient x times w^x (w of order 2L: twf[L + x]) for the odd half of a 2L-point transform
+    auto tw = [&](u32 a, int x) -> u32 {
+        if (!twist) return a;
+        const uint2 w = __ldg(J.P.twf + L + x);
+        return csub(shoup_mul(a, w.x, w.y, q), q);
+    };
     if constexpr (R0 == 1 && LG > 1) {
         // radix-2 stage: the thread takes groups g0 = 2 (tid + u TPT) and g0 + 1 (u < 4), so each
         // pair of points is one vector load of the input and the two twiddles one 16-byte load
-        const int wsz = J.src_mode == 8 ? 16 : 8;
-        const bool vec = ((reinterpret_cast<uintptr_t>(src) + (uintptr_t)(sb * (J.src_mode == 8 ? 8 : 4))) &
+        const int wsz = mode == 8 ? 16 : 8;
+        const bool vec = ((reinterpret_cast<uintptr_t>(src) + (uintptr_t)(sb * (mode == 8 ? 8 : 4))) &
                           (uintptr_t)(wsz - 1)) == 0;
 #pragma unroll
         for (int u = 0; u < 4; u++) {
@@ -168,9 +176,9 @@ __device__ __forceinline__ void fwd_first_t(u32 (&v)[16], u32 *X, const FwdJob &
 #pragma unroll
             for (int j = 0; j < 2; j++) {
                 u32 a = 0u, b2 = 0u;
-                if (act) load_pair(src, J.src_mode, sb + g0 + j * LO, g0 + j * LO, J.src_len, vec, J.P, a, b2);
-                v[4 * u + j] = a;
-                v[4 * u + 2 + j] = b2;
+                if (act) load_pair(src, mode, sb + g0 + j * LO, g0 + j * LO, J.src_len, vec, J.P, a, b2);
+                v[4 * u + j] = tw(a, g0 + j * LO);
+                v[4 * u + 2 + j] = tw(b2, g0 + j * LO + 1);
             }
             const uint4 w2 = __ldg((const uint4 *)(J.P.twf + LO + g0));
             bfly_dif(v[4 * u], v[4 * u + 1], make_uint2(w2.x, w2.y), q, q2);
@@ -193,7 +201,7 @@ __device__ __forceinline__ void fwd_first_t(u32 (&v)[16], u32 *X, const FwdJob &
 #pragma unroll
         for (int j = 0; j < R; j++) {
             const int x = g + j * LO;
-            v[it * R + j] = (act && x < J.src_len) ? load_coeff(src, J.src_mode, sb + x, J.P) : 0u;
+            v[it * R + j] = (act && x < J.src_len) ? tw(load_coeff(src, mode, sb + x, J.P), x) : 0u;
         }
         grp_dif<R0>(v, it * R, g & (LO - 1), LO, J.P.twf, q, q2);
     }
