@@ -300,9 +300,23 @@ def extra_workloads(ctx, s, which=("vandermonde", "pm_basis", "resultant", "batc
         dev = [(it["p"], pmat.to_device(it["A"]), pmat.to_device(it["B"])) for it in items]
         outs = [torch.empty((it["m"], it["k"], 2 * it["d"] - 1), dtype=dev[i][1].dtype, device="cuda")
                 for i, it in enumerate(items)]
+        run = lambda: pmat.pmat_mul_batched(ctx, dev, outs)  # noqa: E731
+        ms_model = ev_ms(run, 2)
+        # autotuned tiles: the tuner times every pointwise form and tile of each product's shape
+        # (before the timing; later products of a tuned shape take its choice)
+        t0 = time.time()
+        forms = {}
+        for it in items:
+            f = pmat.tune_product(ctx, it["p"], it["A"].dtype.itemsize, it["m"], it["n"], it["k"], it["d"], it["d"],
+                                  reps=1)[0]
+            forms[f] = forms.get(f, 0) + 1
+        tune_s = time.time() - t0
+        torch.cuda.synchronize()
         n0 = ctx.launches()
-        ms = ev_ms(lambda: pmat.pmat_mul_batched(ctx, dev, outs), 2)
-        out = {"batched_512_ms": round(ms, 2), "batched_512_launches_per_call": (ctx.launches() - n0) // 3}
+        ms = ev_ms(run, 2)
+        out = {"batched_512_ms": round(ms, 2), "batched_512_launches_per_call": (ctx.launches() - n0) // 3,
+               "batched_512_untuned_ms": round(ms_model, 2),
+               "batched_512_autotune": {"shapes": len(items), "seconds": round(tune_s, 1), "forms_chosen": forms}}
         st, wk = stage_split(lambda: pmat.pmat_mul_batched(ctx, dev, outs))
         out["batched_512_stage_ms"] = {k: round(v, 2) for k, v in st.items()}
         pk = peaks()
