@@ -393,6 +393,8 @@ struct InvLists {
     std::vector<int> bn;
     std::vector<ColJob> col;
     std::vector<int> cn;
+    std::vector<InvJob> pair;       // 2^15 points: both halves and the step over them in one CTA
+    std::vector<int> pn;
 };
 }  // namespace
 
@@ -486,10 +488,15 @@ static void add_inverse(InvLists &il, const PrimeDev &D, u32 *src, void *dst, in
                         int64_t off, int64_t out_len, int64_t eC, int lg)
 {
     const int64_t L = int64_t(1) << lg;
-    if (lg <= PM_LB_LOG2) {
+    if (lg <= PM_LB_LOG2 || lg == PM_LB_LOG2 + 1) {
         InvJob j;
         j.src = src; j.dst = dst; j.src_stride = L; j.dst_stride = dstride;
         j.out_off = (int)off; j.out_len = (int)out_len; j.dst_mode = mode; j.count = (int)eC; j.P = D;
+        if (lg > PM_LB_LOG2) {
+            il.pair.push_back(j);
+            il.pn.push_back((int)eC);
+            return;
+        }
         const int epb = fwd_entries_per_block(lg);
         il.blk.push_back(j);
         il.bn.push_back((int)((eC + epb - 1) / epb));
@@ -520,6 +527,9 @@ static int launch_inverse_lists(pm_ctx *ctx, const InvLists &il, int lg)
     if (!il.col.empty())
         CKI(launch_packs(ctx, il.col, il.cn, [&](const JobPack<ColJob> &pk) {
             return launch_ntt_inv_cols(pk, lg, ctx->stream, &ctx->launches); }));
+    if (!il.pair.empty())
+        CKI(launch_packs(ctx, il.pair, il.pn, [&](const JobPack<InvJob> &pk) {
+            return launch_ntt_inv_pair(pk, ctx->stream, &ctx->launches); }));
     return PM_OK;
 }
 

@@ -208,6 +208,8 @@ cudaError_t launch_ntt_fwd_block(const JobPack<FwdJob> &pk, int lg, cudaStream_t
 cudaError_t launch_ntt_inv_block(const JobPack<InvJob> &pk, int lg, cudaStream_t st, long long *launches);
 cudaError_t launch_ntt_fwd_cols(const JobPack<ColJob> &pk, int lg, cudaStream_t st, long long *launches);
 cudaError_t launch_ntt_inv_cols(const JobPack<ColJob> &pk, int lg, cudaStream_t st, long long *launches);
+// 2^15-point inverse transforms, one CTA per entry (jobs as for launch_ntt_inv_block, src stride 2^15).
+cudaError_t launch_ntt_inv_pair(const JobPack<InvJob> &pk, cudaStream_t st, long long *launches);
 cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
 int pw_plan(PwJob &j);
 int pw_plan_tile(PwJob &j, int bi, int bk);

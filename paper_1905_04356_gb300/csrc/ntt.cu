@@ -390,6 +390,81 @@ static int block_smem(int lg, int threads)
 template <typename Pack>
 static int pack_blocks(const Pack &pk) { return pk.blk_start[pk.njobs]; }
 
+// ------------------------------------------------------------------ inverse, 2^15 points
+// Inverse transform of 2^15 points in one CTA (1024 threads): the 2^14-point inverse of the
+// even half (the first 2^14 transform values) goes to shared memory, then that of the odd
+// half, whose last pass ends with the radix-2 step over the halves,
+// (y0_x, y1_x) -> (y0_x + y1_x w^-x, y0_x - y1_x w^-x) with w of order 2^15, and writes
+// points x and x + 2^14 as the job asks (store_out: scaled by 2^-15, the slice, the width).
+// This replaces the column pass over the halves and its staging round trip.
+template <int LG, int R0, bool ODD>
+__device__ __forceinline__ void inv_last_half(u32 (&v)[16], const u32 *X, u32 *S0, const InvJob &J, i64 e, bool act,
+                                              int tid)
+{
+    constexpr int L = 1 << LG, TPT = L >> 4, R = 1 << R0, LO = L >> R0;
+    const u32 q = J.P.q, q2 = J.P.q2;
+#pragma unroll
+    for (int it = 0; it < (16 >> R0); it++) {
+        const int g = tid + it * TPT;
+        const u32 *xb = X + spad(g);
+#pragma unroll
+        for (int j = 0; j < R; j++) v[it * R + j] = xb[poff<LO>(j)];
+        grp_dit<R0>(v, it * R, g & (LO - 1), LO, J.P.twi, q, q2);
+#pragma unroll
+        for (int j = 0; j < R; j++) {
+            const int x = g + j * LO;
+            if (!ODD) {
+                S0[x] = v[it * R + j];
+            } else {
+                u32 a = S0[x], b = v[it * R + j];
+                bfly_dit(a, b, __ldg(J.P.twi + L + x), q, q2);
+                if (act) {
+                    store_out(J, e, x, a);
+                    store_out(J, e, x + L, b);
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024, 1) k_ntt_inv_pair(const __grid_constant__ JobPack<InvJob> pk)
+{
+    extern __shared__ u32 sm[];
+    constexpr int LG = PM_LB_LOG2, L = 1 << LG, B0 = ((LG - 1) & 3) + 1;
+    static_assert(LG == 14, "the pass sequence below is that of 2^14 points");
+    const int b = blockIdx.x;
+    const int jb = find_job(pk.blk_start, b);
+    const InvJob &J = pk.jobs[jb];
+    const int tid = threadIdx.x;
+    const i64 e = b - pk.blk_start[jb];
+    const bool act = e < J.count;
+    u32 *X = sm, *S0 = sm + L + (L >> 5);
+    u32 v[16];
+    InvJob H = J;                                       // the even half: values 0 .. 2^14 - 1
+    inv_pass16<LG, 1, true>(v, X, H, e, act, tid);
+    inv_pass16<LG, 16, false>(v, X, H, e, act, tid);
+    inv_pass16<LG, 256, false>(v, X, H, e, act, tid);
+    inv_last_half<LG, B0, false>(v, X, S0, H, e, act, tid);
+    __syncthreads();
+    H.src = J.src + L;                                  // the odd half
+    inv_pass16<LG, 1, true>(v, X, H, e, act, tid);
+    inv_pass16<LG, 16, false>(v, X, H, e, act, tid);
+    inv_pass16<LG, 256, false>(v, X, H, e, act, tid);
+    inv_last_half<LG, B0, true>(v, X, S0, J, e, act, tid);
+}
+
+cudaError_t launch_ntt_inv_pair(const JobPack<InvJob> &pk, cudaStream_t st, long long *launches)
+{
+    constexpr int L = 1 << PM_LB_LOG2;
+    const int sm = (L + (L >> 5) + L) * (int)sizeof(u32);
+    cudaError_t e = cudaFuncSetAttribute(k_ntt_inv_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    k_ntt_inv_pair<<<pack_blocks(pk), 1024, sm, st>>>(pk);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+
 template <int LG>
 static cudaError_t fwd_lg(const JobPack<FwdJob> &pk, cudaStream_t st)
 {
