@@ -149,26 +149,26 @@ __device__ __forceinline__ void load_pair(const void *src, int mode, i64 idx, in
     }
 }
 
-template <int LG, int R0>
+template <int LG, int R0, bool TWIST>
 __device__ __forceinline__ void fwd_first_t(u32 (&v)[16], u32 *X, const FwdJob &J, i64 e, bool act, int tid)
 {
     constexpr int L = 1 << LG, TPT = L >> 4, R = 1 << R0, LO = L >> R0;
     const u32 q = J.P.q, q2 = J.P.q2;
     const char *src = (const char *)J.src;
     const i64 sb = e * J.src_stride;
-    const int mode = J.src_mode & 0xff;
-    const bool twist = (J.src_mode & PM_FWD_TWIST) != 0;
+    // the flag bit is set only on twisted jobs, so the plain path reads the field as it is
+#define FWD_MODE (TWIST ? (J.src_mode & 0xff) : J.src_mode)
     // coefficient x times w^x (w of order 2L: twf[L + x]) for the odd half of a 2L-point transform
     auto tw = [&](u32 a, int x) -> u32 {
-        if (!twist) return a;
+        if constexpr (!TWIST) return a;
         const uint2 w = __ldg(J.P.twf + L + x);
         return csub(shoup_mul(a, w.x, w.y, q), q);
     };
     if constexpr (R0 == 1 && LG > 1) {
         // radix-2 stage: the thread takes groups g0 = 2 (tid + u TPT) and g0 + 1 (u < 4), so each
         // pair of points is one vector load of the input and the two twiddles one 16-byte load
-        const int wsz = mode == 8 ? 16 : 8;
-        const bool vec = ((reinterpret_cast<uintptr_t>(src) + (uintptr_t)(sb * (mode == 8 ? 8 : 4))) &
+        const int wsz = FWD_MODE == 8 ? 16 : 8;
+        const bool vec = ((reinterpret_cast<uintptr_t>(src) + (uintptr_t)(sb * (FWD_MODE == 8 ? 8 : 4))) &
                           (uintptr_t)(wsz - 1)) == 0;
 #pragma unroll
         for (int u = 0; u < 4; u++) {
@@ -176,7 +176,7 @@ __device__ __forceinline__ void fwd_first_t(u32 (&v)[16], u32 *X, const FwdJob &
 #pragma unroll
             for (int j = 0; j < 2; j++) {
                 u32 a = 0u, b2 = 0u;
-                if (act) load_pair(src, mode, sb + g0 + j * LO, g0 + j * LO, J.src_len, vec, J.P, a, b2);
+                if (act) load_pair(src, FWD_MODE, sb + g0 + j * LO, g0 + j * LO, J.src_len, vec, J.P, a, b2);
                 v[4 * u + j] = tw(a, g0 + j * LO);
                 v[4 * u + 2 + j] = tw(b2, g0 + j * LO + 1);
             }
@@ -201,7 +201,7 @@ __device__ __forceinline__ void fwd_first_t(u32 (&v)[16], u32 *X, const FwdJob &
 #pragma unroll
         for (int j = 0; j < R; j++) {
             const int x = g + j * LO;
-            v[it * R + j] = (act && x < J.src_len) ? tw(load_coeff(src, mode, sb + x, J.P), x) : 0u;
+            v[it * R + j] = (act && x < J.src_len) ? tw(load_coeff(src, FWD_MODE, sb + x, J.P), x) : 0u;
         }
         grp_dif<R0>(v, it * R, g & (LO - 1), LO, J.P.twf, q, q2);
     }
@@ -221,6 +221,8 @@ __device__ __forceinline__ void fwd_first_t(u32 (&v)[16], u32 *X, const FwdJob &
         for (int j = 0; j < R; j++) xb[poff<LO>(j)] = v[it * R + j];
     }
 }
+
+#undef FWD_MODE
 
 // one radix-16 pass of the forward transform with constant stride LO
 template <int LG, int LO, bool LAST>
@@ -270,7 +272,13 @@ __global__ void __launch_bounds__(LG == 14 ? 1024 : 512, LG == 14 ? 2 : 4) k_ntt
     const bool act = e < J.count;
     u32 *X = sm + lt * (L + (L >> 5));
     u32 v[16];
-    fwd_first_t<LG, B0>(v, X, J, e, act, tid);
+    // the twisted load is compiled only into the 2^14-point kernel, the one whose jobs can carry it
+    if constexpr (LG == PM_LB_LOG2) {
+        if (J.src_mode & PM_FWD_TWIST) fwd_first_t<LG, B0, true>(v, X, J, e, act, tid);
+        else fwd_first_t<LG, B0, false>(v, X, J, e, act, tid);
+    } else {
+        fwd_first_t<LG, B0, false>(v, X, J, e, act, tid);
+    }
     // radix-16 passes: stride L >> (B0 + 4), L >> (B0 + 8), ..., 1
     if constexpr (LG - B0 >= 4) fwd_pass16<LG, (L >> (B0 + 4)), (LG - B0 == 4)>(v, X, J, e, act, tid);
     if constexpr (LG - B0 >= 8) fwd_pass16<LG, (L >> (B0 + 8)), (LG - B0 == 8)>(v, X, J, e, act, tid);
