@@ -67,8 +67,10 @@ CASES = [
     (P60, 8, 2, 3, 2, 4000, 4500),        # L = 2^13, one CTA per transform
     (synth.P998, 4, 2, 2, 3, 5000, 4000),  # L = 2^14: one CTA of 1024 threads
     (P60, 8, 2, 2, 1, 9000, 7000),         # L = 2^14, 5 primes
-    (synth.P998, 4, 1, 2, 1, 9000, 8000),  # L = 2^15: column pass of 2 rows, then 2^14-point blocks
+    (synth.P998, 4, 1, 2, 1, 9000, 8000),  # L = 2^15, inputs <= 2^14: odd half twisted, inverse in one CTA
     (P60, 8, 1, 1, 2, 9000, 8000),         # L = 2^15, 5 primes
+    (P60, 8, 1, 1, 1, 20000, 100),         # L = 2^15, A longer than 2^14: A by the column pass, B twisted
+    (synth.P998, 4, 1, 1, 2, 17000, 16000),  # L = 2^16: column passes both ways
     # pointwise block plans: a slice left empty in the last inner chunk (n = 32 + 5),
     # 2 x 2 block tiles with two chunks, uneven tiles, several column tiles, 4 slices
     (P60, 8, 4, 37, 8, 50, 40),
@@ -100,7 +102,8 @@ def test_full_product_matches_oracle(ctx, case):
 
 
 @pytest.mark.parametrize("case", [(P60, 8, 3, 4, 5, 100, 60), (synth.P998, 4, 4, 2, 3, 333, 222),
-                                  (P32, 4, 2, 3, 2, 3000, 3100)])
+                                  (P32, 4, 2, 3, 2, 3000, 3100),
+                                  (P60, 8, 1, 1, 1, 9000, 8000)])   # 2^15 points: the one-CTA inverse's slice
 def test_truncated_product_matches_oracle(ctx, case):
     p, w, m, n, k, dA, dB = case
     g = synth.rng(7)
@@ -122,6 +125,19 @@ def test_middle_product_matches_oracle(ctx, p, w):
                          (4096, 4096, 4097, 8192), (0, 7, 1, 7)):
         A = _rand(g, p, (m, n, dA), w)
         B = _rand(g, p, (n, k, dB), w)
+        got = _gpu(ctx, "pmat_middle_product", p, A, B, c, d)
+        exp = oracle.pmat_middle_product(p, A, B, c, d)
+        assert np.array_equal(got.astype(np.uint64), exp), (c, d, dA, dB)
+
+
+@pytest.mark.parametrize("p,w", [(P60, 8), (synth.P998, 4)])
+def test_long_middle_product_matches_oracle(ctx, p, w):
+    """Middle products at 2^15 transform points: A (c + 1 <= 2^14 coefficients) twisted, B longer
+    than 2^14 by the column pass, the one-CTA inverse writing the coefficients from c on."""
+    g = synth.rng(13)
+    for c, d, dA, dB in ((12000, 12000, 12001, 24000), (9000, 7000, 9001, 16000)):
+        A = _rand(g, p, (1, 1, dA), w)
+        B = _rand(g, p, (1, 1, dB), w)
         got = _gpu(ctx, "pmat_middle_product", p, A, B, c, d)
         exp = oracle.pmat_middle_product(p, A, B, c, d)
         assert np.array_equal(got.astype(np.uint64), exp), (c, d, dA, dB)
