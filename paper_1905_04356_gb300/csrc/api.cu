@@ -190,9 +190,11 @@ static int choose_primes(pm_ctx *ctx, uint64_t p, int n, int64_t dmin, int lg, s
 {
     out.clear();
     direct = false;
-    if (p < (1ull << 30) && p > 2 && ((p - 1) % (1ull << lg)) == 0 && ntt_is_prime32(p)) {
-        for (auto &s : ctx->direct)
+    if (p < (1ull << 30) && p > 2 && ((p - 1) % (1ull << lg)) == 0) {
+        for (auto &s : ctx->direct)                   // a slot exists only for a prime: no test again
             if (s.q == p) { out.push_back(&s); direct = true; return PM_OK; }
+    }
+    if (p < (1ull << 30) && p > 2 && ((p - 1) % (1ull << lg)) == 0 && ntt_is_prime32(p)) {
         ctx->direct.emplace_back();
         slot_init(ctx->direct.back(), (u32)p);
         out.push_back(&ctx->direct.back());
@@ -685,6 +687,38 @@ int prod_slice(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *
     return prod_batch(ctx, &q, 1);
 }
 
+// Small products modulo an NTT prime used directly (L <= 2^10 points, n <= 16, the transforms of
+// all entries in at most 160 KB of shared memory) in one CTA and one launch (small.cu), instead
+// of the batched path's three launches; not when a pointwise form is forced (the tests of each
+// form must reach it).  The launch is recorded as the forward stage.  done = false: not taken.
+static int small_product(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A, int64_t dA,
+                         const void *B, int64_t dB, void *C, int64_t len, int lg, bool &done)
+{
+    done = false;
+    const int lg4 = lg < 4 ? 4 : lg;
+    if (lg4 > 10 || n > 16 || ctx->force_form >= 0 || ctx->opt_pointwise != 0) return PM_OK;
+    if (p >= (1ull << 30) || p < 3 || ((p - 1) % (1ull << lg4)) != 0) return PM_OK;
+    if (small_product_smem(m, n, k, lg4) > 160 * 1024) return PM_OK;
+    std::vector<PrimeSlot *> pr;
+    bool direct = false;
+    CKI(choose_primes(ctx, p, n, dA < dB ? dA : dB, lg4, pr, direct));
+    if (!direct) return PM_OK;
+    CKI(host_join(ctx));
+    CKI(slot_tables(ctx, *pr[0], lg4));
+    count_work(ctx, 1, lg4, w, m, n, k, dA, dB, len);
+    SmallJob J;
+    J.A = A; J.B = B; J.C = C;
+    J.w = w; J.m = m; J.n = n; J.k = k; J.dA = (int)dA; J.dB = (int)dB; J.len = (int)len; J.lg = lg4;
+    J.P = prime_dev(*pr[0], lg4);
+    const int tok = stage_begin(ctx, PM_STAGE_FWD);
+    ctx->launches++;
+    const cudaError_t e = launch_small_product(J, ctx->stream);
+    stage_end(ctx, tok);
+    CKI(pm_cuda(ctx, e, "k_small_product"));
+    done = true;
+    return PM_OK;
+}
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 
@@ -1064,6 +1098,9 @@ int pmat_mul(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, const void *A,
     const int64_t len = dA + dB - 1;
     const int lg = ceil_log2(len);
     if (lg > PM_MAX_LOG2L) return pm_fail(ctx, PM_EINVAL, "product longer than 2^20");
+    bool done = false;
+    CKI(small_product(ctx, p, w, m, n, k, A, dA, B, dB, C, len, lg, done));
+    if (done) return PM_OK;
     return prod_slice(ctx, p, w, m, n, k, A, dA, dA, B, dB, dB, 0, len, lg, C, len);
 }
 

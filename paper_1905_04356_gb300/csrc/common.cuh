@@ -210,6 +210,17 @@ cudaError_t launch_ntt_fwd_cols(const JobPack<ColJob> &pk, int lg, cudaStream_t 
 cudaError_t launch_ntt_inv_cols(const JobPack<ColJob> &pk, int lg, cudaStream_t st, long long *launches);
 // 2^15-point inverse transforms, one CTA per entry (jobs as for launch_ntt_inv_block, src stride 2^15).
 cudaError_t launch_ntt_inv_pair(const JobPack<InvJob> &pk, cudaStream_t st, long long *launches);
+// A whole product modulo an NTT prime q = p in one CTA (small.cu): A (m x n x dA), B (n x k x dB)
+// and C (m x k x len, len = dA + dB - 1) contiguous in the caller's width w; L = 2^lg points,
+// n <= 16 (the pointwise sums stay below 2^64), small_product_smem(...) bytes of shared memory.
+struct SmallJob {
+    const void *A, *B;
+    void *C;
+    int w, m, n, k, dA, dB, len, lg;
+    PrimeDev P;
+};
+size_t small_product_smem(int m, int n, int k, int lg);
+cudaError_t launch_small_product(const SmallJob &J, cudaStream_t st);
 cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
 int pw_plan(PwJob &j);
 int pw_plan_tile(PwJob &j, int bi, int bk);
