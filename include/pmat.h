@@ -87,7 +87,9 @@ enum {
                                recorded for the shape), 1 = CUDA-core 64-bit products,
                                2 = tensor-core digit products, four points per MMA, where
                                m, n, k <= 32 (CUDA cores elsewhere), 3 = tensor-core dense
-                               products per point where m >= 64 (CUDA cores elsewhere) */
+                               products per point where m >= 64 (CUDA cores elsewhere),
+                               4 = CUDA-core staged products in 4 x 4 thread tiles (every
+                               shape) */
     PM_OPT_THRESHOLD = 2,   /* PM-Basis threshold T (>= 1): M-Basis when order <= T;
                                default 32 (Sec. 3, "Interpolant bases") */
     PM_OPT_DEBUG_CHECKS = 3, /* 1 = check inputs are in [0, p) (PM_EDOMAIN) */
@@ -398,14 +400,16 @@ int pmat_mul_vdm(pm_ctx *ctx, uint64_t p, int m, int n, int k, const void *A, in
  * matrix multiplication": the n^omega d term).  Times every pointwise form that
  * applies to an m x n . n x k product of lengths dA, dB modulo p -- the
  * CUDA-core form with each of its (up to) four best block tiles by the cost
- * model, the streaming form (n <= 8), the matrix-vector form (k = 1), the
- * tensor-core digit form (m, n, k <= 32) -- over `reps` products each (after
+ * model, for thread tiles of 4 x 8 and of 4 x 4 outputs, the streaming form
+ * (n <= 8), the matrix-vector form (k = 1), the tensor-core digit form
+ * (m, n, k <= 32) -- over `reps` products each (after
  * one warm-up) on zero inputs (the kernels' time does not depend on the
  * values), and records the fastest in the context: later products of the same
  * (m, n, k, transform length) take it when PM_OPT_POINTWISE is 0 (auto).
- * out: HOST int64_t[5] = form (1 CUDA-core block tile, 2 tensor-core four points
- * per MMA, 3 streaming, 4 matrix-vector, 5 tensor-core dense products per point,
- * tried where m >= 64), bi, bk (the block tile of form 1, else 0), the
+ * out: HOST int64_t[5] = form (1 CUDA-core block tile of 4 x 8 thread tiles,
+ * 2 tensor-core four points per MMA, 3 streaming, 4 matrix-vector, 5 tensor-core
+ * dense products per point, tried where m >= 64, 6 CUDA-core block tile of 4 x 4
+ * thread tiles), bi, bk (the block tile of forms 1 and 6, else 0), the
  * winner's pointwise-stage time per product in ns, the number of candidates.
  * Allocates and frees its scratch on the context's stream, synchronises it and
  * discards earlier stage-timing records.  Requires 1 <= reps <= 1000 and the

@@ -385,8 +385,8 @@ struct Plan {
 
 // Pointwise jobs sorted by kernel form.
 struct PwLists {
-    std::vector<PwJob> jobs, tjobs, sjobs[9], vjobs, gjobs;
-    std::vector<int> nb, tnb, snb[9], vnb;
+    std::vector<PwJob> jobs, jobs4, tjobs, sjobs[9], vjobs, gjobs;    // jobs: 4 x 8 thread tiles, jobs4: 4 x 4
+    std::vector<int> nb, nb4, tnb, snb[9], vnb;
 };
 
 // Inverse-transform jobs of one transform length (a column pass after the blocks when L > 2^14).
@@ -419,7 +419,8 @@ size_t prod_operand_bytes(pm_ctx *ctx, uint64_t p, int n, int64_t dmin, int lg, 
 // Pointwise m x n . n x k products at every point of one prime's transforms: tensor-core limb
 // products where the shape allows (m, n, k <= 32) when that form is requested, small inner
 // dimensions (n <= 8) by a streaming kernel (one launch per n), matrix-vector products
-// (k = 1, n <= 64) by another, the staged CUDA-core 64-bit form otherwise.
+// (k = 1, n <= 64) by another, the staged CUDA-core 64-bit form otherwise (4 x 8 thread tiles
+// by default, 4 x 4 where the tuner recorded them or option 4 asks for them).
 // With PM_OPT_POINTWISE = 0 a form recorded by pm_tune_product for the same (m, n, k, length) is
 // taken; otherwise (and for forms that do not apply) the rules above.
 static void add_pointwise(pm_ctx *ctx, PwLists &pl, u32 *A, u32 *B, u32 *C, int m, int n, int k, int lg,
@@ -436,13 +437,18 @@ static void add_pointwise(pm_ctx *ctx, PwLists &pl, u32 *A, u32 *B, u32 *C, int 
         for (const auto &t : ctx->tune)
             if (t.m == m && t.n == n && t.k == k && t.lg == lg) { form = t.form; bi = t.bi; bk = t.bk; break; }
     if (ctx->opt_pointwise == 3 && ctx->force_form < 0) form = 5;
+    if (ctx->opt_pointwise == 4 && ctx->force_form < 0) {          // 4 x 4 thread tiles, cost-model block
+        form = 6;
+        pw_tiles(j, &bi, &bk, 1, 4);
+    }
     // automatic rule, measured on GB300: the dense tensor-core form wins for large per-point
     // products (512 x 512 . 512 x 512 at 256 points: 4.04 ms against 6.21 ms on CUDA cores) and
     // loses at 128 x 128 . 128 x 128 (1.22 against 0.81 ms)
     if (ctx->opt_pointwise == 0 && form == 0 && ctx->force_form < 0 && m >= 256 && n >= 256 && k >= 256) form = 5;
     if (form == 5 && j.m >= 64) { pl.gjobs.push_back(j); return; }
     if (form == 2 && tc_supported(j)) { pl.tjobs.push_back(j); pl.tnb.push_back(tc_blocks(j)); }
-    else if (form == 1 && bi > 0 && bk > 0) { const int nbk = pw_plan_tile(j, bi, bk); pl.jobs.push_back(j); pl.nb.push_back(nbk); }
+    else if (form == 1 && bi > 0 && bk > 0) { const int nbk = pw_plan_tile(j, bi, bk, 8); pl.jobs.push_back(j); pl.nb.push_back(nbk); }
+    else if (form == 6 && bi > 0 && bk > 0) { const int nbk = pw_plan_tile(j, bi, bk, 4); pl.jobs4.push_back(j); pl.nb4.push_back(nbk); }
     else if (form == 4 && pwv_supported(j)) { pl.vjobs.push_back(j); pl.vnb.push_back(pwv_blocks(j)); }
     else if ((form == 0 || form == 3 || form == 2) && pws_supported(j)) { pl.sjobs[j.n].push_back(j); pl.snb[j.n].push_back(pws_blocks(j)); }
     else if ((form == 0 || form == 2) && pwv_supported(j)) { pl.vjobs.push_back(j); pl.vnb.push_back(pwv_blocks(j)); }
@@ -453,6 +459,9 @@ static int launch_pointwise_lists(pm_ctx *ctx, const PwLists &pl)
 {
     if (!pl.jobs.empty())
         CKI(launch_packs(ctx, pl.jobs, pl.nb, [&](const JobPack<PwJob> &pk) {
+            return launch_pointwise(pk, ctx->stream, &ctx->launches); }));
+    if (!pl.jobs4.empty())
+        CKI(launch_packs(ctx, pl.jobs4, pl.nb4, [&](const JobPack<PwJob> &pk) {
             return launch_pointwise(pk, ctx->stream, &ctx->launches); }));
     if (!pl.vjobs.empty())
         CKI(launch_packs(ctx, pl.vjobs, pl.vnb, [&](const JobPack<PwJob> &pk) {
@@ -791,7 +800,7 @@ int pm_set_option(pm_ctx *ctx, int key, int64_t value)
     if (!ctx) return PM_EINVAL;
     switch (key) {
     case PM_OPT_POINTWISE:
-        if (value < 0 || value > 3) return pm_fail(ctx, PM_EINVAL, "pointwise path must be 0, 1, 2 or 3");
+        if (value < 0 || value > 4) return pm_fail(ctx, PM_EINVAL, "pointwise path must be 0, 1, 2, 3 or 4");
         ctx->opt_pointwise = (int)value;
         return PM_OK;
     case PM_OPT_THRESHOLD:

@@ -160,8 +160,8 @@ struct ColJob {
     PrimeDev P;
 };
 // Pointwise products at every transform point: C_j = A_j B_j mod q.
-// The CUDA-core kernel's block plan (pw_plan): block tiles of bi x bk thread tiles of
-// 4 x 8 outputs (nbk tiles across k, ntile per transform point group), the inner
+// The CUDA-core kernel's block plan (pw_plan_tile): block tiles of bi x bk thread tiles of
+// 4 x cw outputs (nbk tiles across k, ntile per transform point group), the inner
 // dimension staged lc <= 32 at a time and split into ns contiguous slices; mg_* are
 // division magics ceil(2^31 / d) for d = lc, the last chunk, the tile width and the
 // last tile's width; smem = dynamic shared memory in bytes.
@@ -170,6 +170,7 @@ struct PwJob {
     u32 *C;
     int m, n, k, L;
     int bi, bk, ns, lc, nbk, ntile, smem;
+    int cw;             // columns per thread tile: 8 or 4
     u32 mg_lc, mg_lt, mg_cb, mg_ct;
     PrimeDev P;
 };
@@ -221,10 +222,11 @@ struct SmallJob {
 };
 size_t small_product_smem(int m, int n, int k, int lg);
 cudaError_t launch_small_product(const SmallJob &J, cudaStream_t st);
+// every job of the pack has the same thread-tile width (cw); cudaErrorInvalidValue otherwise
 cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
 int pw_plan(PwJob &j);
-int pw_plan_tile(PwJob &j, int bi, int bk);
-int pw_tiles(const PwJob &j, int *bi_out, int *bk_out, int max);
+int pw_plan_tile(PwJob &j, int bi, int bk, int cw);
+int pw_tiles(const PwJob &j, int *bi_out, int *bk_out, int max, int cw);
 cudaError_t launch_pointwise_sn(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
 bool pws_supported(const PwJob &j);
 int pws_blocks(const PwJob &j);

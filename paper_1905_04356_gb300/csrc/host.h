@@ -41,8 +41,9 @@ struct pm_ctx {
     int opt_host_chunks = 0;          // pmat_mul_host output chunks (0 = automatic)
     int opt_withhold = 0;             // test hook: the tensor-core pointwise kernel withholds an MMA
     // pointwise forms picked by pm_tune_product, per (m, n, k, transform length): form 1 = CUDA-core
-    // block tile (bi, bk), 2 = tensor-core (four points per MMA, m, n, k <= 32), 3 = streaming
-    // (n <= 8), 4 = matrix-vector (k = 1), 5 = tensor-core dense products per point (m >= 64)
+    // block tile (bi, bk) of 4 x 8 thread tiles, 2 = tensor-core (four points per MMA, m, n, k <=
+    // 32), 3 = streaming (n <= 8), 4 = matrix-vector (k = 1), 5 = tensor-core dense products per
+    // point (m >= 64), 6 = CUDA-core block tile (bi, bk) of 4 x 4 thread tiles
     struct Tune { int m, n, k, lg, form, bi, bk; };
     std::vector<Tune> tune;
     int force_form = -1, force_bi = 0, force_bk = 0;   // the tuner's candidate while it times one

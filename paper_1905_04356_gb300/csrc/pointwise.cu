@@ -5,9 +5,9 @@
 // "Polynomial matrix multiplication": the n^omega d term of the cost).  This
 // is the CUDA-core form: a block takes 8 consecutive points and stages the
 // residues it needs in shared memory; each thread owns one point and a 4 x 8
-// tile of outputs, multiplying 30-bit residues into 64-bit lazy accumulators
-// (a carry chain of two 32-bit multiply-adds per product) folded mod q every
-// 15 products.
+// (or 4 x 4) tile of outputs, multiplying 30-bit residues into 64-bit lazy
+// accumulators (one 32 x 32 -> 64-bit multiply-add per product) folded mod q
+// every 16 products.
 //
 // CRT: for moduli without suitable roots of unity the product is lifted to
 // Z[x] and computed modulo K NTT primes (Sec. 2, "3-primes multiplication";
@@ -24,8 +24,10 @@
 #define PS_LC 32        // inner-dimension entries staged per chunk
 #define PS_PA 290       // A-row pitch (words): >= 32 * 9 and = 2 mod 8, so thread tiles
                         // 4 rows apart start 8 banks apart
-#define PS_PB 289       // B-column pitch (words, B staged column-major): odd, so thread
-                        // tiles 8 columns apart start 8 banks apart
+#define PS_PB 289       // B-column pitch (words, B staged column-major) for 8-column thread
+                        // tiles: odd, so thread tiles 8 columns apart start 8 banks apart
+#define PS_PB4 290      // the same for 4-column thread tiles: = 2 mod 8, so thread tiles 4
+                        // columns apart start 8 banks apart
 #define PS_WORDS 28160  // shared-memory budget per block (110 KB: 2 blocks per SM)
 
 __device__ __forceinline__ int find_job_pw(const int *blk_start, int b)
@@ -38,23 +40,28 @@ __device__ __forceinline__ int find_job_pw(const int *blk_start, int b)
 static u32 magic31(int d) { return (u32)(((1ull << 31) + d - 1) / d); }
 
 // Block plan.  The m x k output is cut into block tiles of bi x bk thread tiles
-// (4 x 8 outputs each, bi bk <= 32 slots), chosen to minimise the lanes spent on
-// thread tiles plus the entries staged, within the shared-memory budget; the inner
+// (4 x cw outputs each, cw = 8 or 4, bi bk <= 32 slots), chosen to minimise the lanes spent
+// on thread tiles plus the entries staged, within the shared-memory budget; the inner
 // dimension n is staged PS_LC entries at a time and, when a block tile leaves slots
 // free, each chunk is split into ns contiguous slices whose partial sums are added
-// at the end.  Returns the block count.
-// Block tiles (bi, bk) that fit, in increasing order of the cost model (at most `max`; ties
-// keep the loop order, so the first is the plan pw_plan takes).
-int pw_tiles(const PwJob &j, int *bi_out, int *bk_out, int max)
+// at the end.  4-column thread tiles waste at most 3 columns of a ragged k (8-column ones up
+// to 7) for one more shared-memory load per 4 products.
+static int pw_pitch(int cw) { return cw == 4 ? PS_PB4 : PS_PB; }
+
+// Block tiles (bi, bk) of 4 x cw thread tiles that fit, in increasing order of the cost model
+// (at most `max`; ties keep the loop order, so the first of cw = 8 is the plan pw_plan takes).
+// Cost of a block: 8 cw per thread tile (its 4 cw multiply-adds per inner entry, with their
+// loads), rounded up to warps of 4 slots, plus 16 per staged row or column and 64 fixed.
+int pw_tiles(const PwJob &j, int *bi_out, int *bk_out, int max, int cw)
 {
-    const int nti = (j.m + 3) / 4, ntk = (j.k + 7) / 8;
+    const int nti = (j.m + 3) / 4, ntk = (j.k + cw - 1) / cw, pb = pw_pitch(cw);
     long long cost[256];
     int cbi[256], cbk[256], nc = 0;                  // bi bk <= 32: at most 130 candidates
     for (int bi = 1; bi <= nti && bi <= 32; bi++)
         for (int bk = 1; bk <= ntk && bi * bk <= 32; bk++) {
-            if (bi * 4 * PS_PA + bk * 8 * PS_PB > PS_WORDS) continue;
+            if (bi * 4 * PS_PA + bk * cw * pb > PS_WORDS) continue;
             const long long nb = (long long)((nti + bi - 1) / bi) * ((ntk + bk - 1) / bk);
-            cost[nc] = nb * (((bi * bk + 3) / 4) * 4 * 64 + (bi * 4 + bk * 8) * 16 + 64);
+            cost[nc] = nb * (((bi * bk + 3) / 4) * 4 * 8 * cw + (bi * 4 + bk * cw) * 16 + 64);
             cbi[nc] = bi;
             cbk[nc] = bk;
             nc++;
@@ -74,21 +81,23 @@ int pw_tiles(const PwJob &j, int *bi_out, int *bk_out, int max)
 int pw_plan(PwJob &j)
 {
     int bi = 1, bk = 1;
-    pw_tiles(j, &bi, &bk, 1);
-    return pw_plan_tile(j, bi, bk);
+    pw_tiles(j, &bi, &bk, 1, 8);
+    return pw_plan_tile(j, bi, bk, 8);
 }
 
-// The plan for block tile (bi, bk) (one that pw_tiles lists).  Returns the block count.
-int pw_plan_tile(PwJob &j, int bi, int bk)
+// The plan for block tile (bi, bk) of 4 x cw thread tiles (one that pw_tiles lists).  Returns
+// the block count.
+int pw_plan_tile(PwJob &j, int bi, int bk, int cw)
 {
-    const int nti = (j.m + 3) / 4, ntk = (j.k + 7) / 8;
+    const int nti = (j.m + 3) / 4, ntk = (j.k + cw - 1) / cw;
     j.bi = bi;
     j.bk = bk;
-    const int items = j.bi * j.bk, rb = j.bi * 4, cb = j.bk * 8;
+    j.cw = cw;
+    const int items = j.bi * j.bk, rb = j.bi * 4, cb = j.bk * cw;
     j.lc = j.n < PS_LC ? j.n : PS_LC;
     j.ns = 1;                                                  // slices of >= 8 products per chunk
     while (items * j.ns * 2 <= 32 && j.ns * 2 * 8 <= j.lc) j.ns *= 2;
-    const int stage = rb * PS_PA + cb * PS_PB, red = j.ns * rb * cb * PS_ROW;
+    const int stage = rb * PS_PA + cb * pw_pitch(cw), red = j.ns * rb * cb * PS_ROW;
     j.smem = (stage > red ? stage : red) * 4;
     j.nbk = (ntk + j.bk - 1) / j.bk;
     j.ntile = ((nti + j.bi - 1) / j.bi) * j.nbk;
@@ -108,38 +117,50 @@ __device__ __forceinline__ u32 lds(u32 addr)
     return v;
 }
 
-// One inner-dimension step l + U of a 4 x 8 thread tile: A rows at fa + a PS_PA words,
-// B columns at fb + c PS_PB words, consecutive l 9 words apart; each product goes into
-// a 64-bit (hi, lo) accumulator through a carry chain.
-template <int U>
-__device__ __forceinline__ void pw_step(u32 (&alo)[4][8], u32 (&ahi)[4][8], u32 fa, u32 fb)
+// One product of residues below 2^30 into a 64-bit accumulator: one 32 x 32 -> 64-bit
+// multiply-add (measured on GB300 3-4 % faster in this kernel than a carry chain of two 32-bit
+// multiply-adds on the accumulator's halves).
+__device__ __forceinline__ void pw_mac(u64 &acc, u32 a, u32 b) { acc += (u64)a * b; }
+
+// One inner-dimension step l + U of a 4 x CW thread tile: A rows at fa + a PS_PA words,
+// B columns at fb + c PB words, consecutive l 9 words apart.
+template <int U, int CW>
+__device__ __forceinline__ void pw_step(u64 (&acc)[4][CW], u32 fa, u32 fb)
 {
-    u32 av[4], bv[8];
+    constexpr int PB = CW == 4 ? PS_PB4 : PS_PB;
+    u32 av[4], bv[CW];
     av[0] = lds<U * 36>(fa);
     av[1] = lds<U * 36 + 4 * PS_PA>(fa);
     av[2] = lds<U * 36 + 8 * PS_PA>(fa);
     av[3] = lds<U * 36 + 12 * PS_PA>(fa);
     bv[0] = lds<U * 36>(fb);
-    bv[1] = lds<U * 36 + 4 * PS_PB>(fb);
-    bv[2] = lds<U * 36 + 8 * PS_PB>(fb);
-    bv[3] = lds<U * 36 + 12 * PS_PB>(fb);
-    bv[4] = lds<U * 36 + 16 * PS_PB>(fb);
-    bv[5] = lds<U * 36 + 20 * PS_PB>(fb);
-    bv[6] = lds<U * 36 + 24 * PS_PB>(fb);
-    bv[7] = lds<U * 36 + 28 * PS_PB>(fb);
+    bv[1] = lds<U * 36 + 4 * PB>(fb);
+    bv[2] = lds<U * 36 + 8 * PB>(fb);
+    bv[3] = lds<U * 36 + 12 * PB>(fb);
+    if constexpr (CW == 8) {
+        bv[4] = lds<U * 36 + 16 * PB>(fb);
+        bv[5] = lds<U * 36 + 20 * PB>(fb);
+        bv[6] = lds<U * 36 + 24 * PB>(fb);
+        bv[7] = lds<U * 36 + 28 * PB>(fb);
+    }
 #pragma unroll
     for (int a = 0; a < 4; a++)
 #pragma unroll
-        for (int c = 0; c < 8; c++)
-            asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;"
-                : "+r"(alo[a][c]), "+r"(ahi[a][c]) : "r"(av[a]), "r"(bv[c]));
+        for (int c = 0; c < CW; c++) pw_mac(acc[a][c], av[a], bv[c]);
+}
+
+// acc < 2^64 -> its value mod q in [0, q)
+__device__ __forceinline__ u32 pw_reduce(u64 acc, u32 q, u32 q2, u32 r32, u32 r32s, u32 ones)
+{
+    const u32 s2 = shoup_mul((u32)(acc >> 32), r32, r32s, q) + shoup_mul((u32)acc, 1u, ones, q);
+    return csub(csub(s2, q2), q);
 }
 
 // One block: 8 consecutive points of one transform and one block tile of the output.
 // Thread (warp w, lane) has slot 4 w + lane / 8 -> (slice, thread tile) and point
 // lane % 8.  Per chunk of <= 32 inner entries, the A rows and B columns of the block
 // tile are staged (32-byte coalesced reads: the 8 points of an entry, four 16-byte
-// loads in flight per thread), then every live slot accumulates its 4 x 8 tile over
+// loads in flight per thread), then every live slot accumulates its 4 x CW tile over
 // its slice of the chunk.  Thread-tile rows / columns past the matrix edge read
 // unused staging words and are never stored, so the inner loop carries no
 // predicates.  Partial tiles go through shared memory, slices are summed, and each
@@ -148,17 +169,14 @@ __device__ __forceinline__ void pw_step(u32 (&alo)[4][8], u32 (&ahi)[4][8], u32 
 // Accumulation: acc < 2^32 + 2q + 16 (q - 1)^2 < 2^64 for q < 2^30, so after every 16
 // products acc is folded lazily to lo + (hi 2^32 mod q) < 2^32 + 2q, and reduced to
 // [0, q) once at the end.
-__global__ void __launch_bounds__(PS_THREADS, 2) k_pointwise(const __grid_constant__ JobPack<PwJob> pk)
+template <int CW>
+__device__ __forceinline__ void pw_block(const PwJob &J, int rel, u32 *sms)
 {
-    extern __shared__ __align__(16) u32 sms[];
-    const int b = blockIdx.x;
-    const int jb = find_job_pw(pk.blk_start, b);
-    const PwJob &J = pk.jobs[jb];
+    constexpr int PB = CW == 4 ? PS_PB4 : PS_PB;
     const int n = J.n, k = J.k, L = J.L, ns = J.ns, lc = J.lc, bk = J.bk;
     const u32 q = J.P.q, q2 = J.P.q2, r32 = J.P.r32, r32s = J.P.r32s, ones = J.P.ones;
-    const int rel = b - pk.blk_start[jb];
     const int tile = rel % J.ntile, j0 = (rel / J.ntile) * PS_PTS;
-    const int rb = J.bi * 4, cb = bk * 8;
+    const int rb = J.bi * 4, cb = bk * CW;
     const int r0 = (tile / J.nbk) * rb, c0 = (tile % J.nbk) * cb;
     const int rows = min(J.m - r0, rb), cols = min(k - c0, cb);
     const int tid = threadIdx.x, lane = tid & 31, pp = lane & 7;
@@ -168,13 +186,13 @@ __global__ void __launch_bounds__(PS_THREADS, 2) k_pointwise(const __grid_consta
     const int ti = item / bk, tk = item % bk;
     u32 *rA = sms, *rB = sms + rb * PS_PA;
     const u32 sA = (u32)__cvta_generic_to_shared(rA) + (ti * 4 * PS_PA + pp) * 4;
-    const u32 sB = (u32)__cvta_generic_to_shared(rB) + (tk * 8 * PS_PB + pp) * 4;
+    const u32 sB = (u32)__cvta_generic_to_shared(rB) + (tk * CW * PB + pp) * 4;
 
-    u32 alo[4][8], ahi[4][8];
+    u64 acc[4][CW];
 #pragma unroll
     for (int a = 0; a < 4; a++)
 #pragma unroll
-        for (int c = 0; c < 8; c++) { alo[a][c] = 0; ahi[a][c] = 0; }
+        for (int c = 0; c < CW; c++) acc[a][c] = 0;
     bool lazy = false;                                         // accumulators not yet in [0, q)
 
     for (int l0 = 0; l0 < n; l0 += lc) {
@@ -196,7 +214,7 @@ __global__ void __launch_bounds__(PS_THREADS, 2) k_pointwise(const __grid_consta
                     const int qt = (int)__umulhi((u32)f << 1, isA ? mA : mB), rm = f - qt * dv;
                     const u32 *src = isA ? J.A + (i64)((r0 + qt) * n + l0 + rm) * L
                                          : J.B + (i64)((l0 + qt) * k + c0 + rm) * L;
-                    d[i] = (isA ? rA + qt * PS_PA + rm * PS_ROW : rB + rm * PS_PB + qt * PS_ROW) + 4 * h;
+                    d[i] = (isA ? rA + qt * PS_PA + rm * PS_ROW : rB + rm * PB + qt * PS_ROW) + 4 * h;
                     v[i] = __ldg((const uint4 *)(src + j0 + 4 * h));
                 }
 #pragma unroll
@@ -212,35 +230,29 @@ __global__ void __launch_bounds__(PS_THREADS, 2) k_pointwise(const __grid_consta
             for (int g = lb; g < le; g += 16) {
                 int cnt = min(le, g + 16) - g;
                 for (; cnt >= 8; cnt -= 8) {
-                    pw_step<0>(alo, ahi, fa, fb); pw_step<1>(alo, ahi, fa, fb);
-                    pw_step<2>(alo, ahi, fa, fb); pw_step<3>(alo, ahi, fa, fb);
-                    pw_step<4>(alo, ahi, fa, fb); pw_step<5>(alo, ahi, fa, fb);
-                    pw_step<6>(alo, ahi, fa, fb); pw_step<7>(alo, ahi, fa, fb);
+                    pw_step<0, CW>(acc, fa, fb); pw_step<1, CW>(acc, fa, fb);
+                    pw_step<2, CW>(acc, fa, fb); pw_step<3, CW>(acc, fa, fb);
+                    pw_step<4, CW>(acc, fa, fb); pw_step<5, CW>(acc, fa, fb);
+                    pw_step<6, CW>(acc, fa, fb); pw_step<7, CW>(acc, fa, fb);
                     fa += 8 * PS_ROW * 4; fb += 8 * PS_ROW * 4;
                 }
                 for (; cnt > 0; cnt--) {
-                    pw_step<0>(alo, ahi, fa, fb);
+                    pw_step<0, CW>(acc, fa, fb);
                     fa += PS_ROW * 4; fb += PS_ROW * 4;
                 }
                 if (g + 16 < le || l0 + lc < n) {
-                    // more products follow: acc <- lo + (hi 2^32 mod q), the carry into hi kept
+                    // more products follow: acc <- lo + (hi 2^32 mod q)
 #pragma unroll
                     for (int a = 0; a < 4; a++)
 #pragma unroll
-                        for (int c = 0; c < 8; c++) {
-                            const u32 t = shoup_mul(ahi[a][c], r32, r32s, q);
-                            asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, 0, 0;" : "+r"(alo[a][c]), "=r"(ahi[a][c]) : "r"(t));
-                        }
+                        for (int c = 0; c < CW; c++)
+                            acc[a][c] = (u64)(u32)acc[a][c] + shoup_mul((u32)(acc[a][c] >> 32), r32, r32s, q);
                     lazy = true;
                 } else {
 #pragma unroll
                     for (int a = 0; a < 4; a++)
 #pragma unroll
-                        for (int c = 0; c < 8; c++) {
-                            const u32 s2 = shoup_mul(ahi[a][c], r32, r32s, q) + shoup_mul(alo[a][c], 1u, ones, q);
-                            alo[a][c] = csub(csub(s2, q2), q);
-                            ahi[a][c] = 0;
-                        }
+                        for (int c = 0; c < CW; c++) acc[a][c] = pw_reduce(acc[a][c], q, q2, r32, r32s, ones);
                     lazy = false;
                 }
             }
@@ -250,10 +262,7 @@ __global__ void __launch_bounds__(PS_THREADS, 2) k_pointwise(const __grid_consta
 #pragma unroll
         for (int a = 0; a < 4; a++)
 #pragma unroll
-            for (int c = 0; c < 8; c++) {
-                const u32 s2 = shoup_mul(ahi[a][c], r32, r32s, q) + shoup_mul(alo[a][c], 1u, ones, q);
-                alo[a][c] = csub(csub(s2, q2), q);
-            }
+            for (int c = 0; c < CW; c++) acc[a][c] = pw_reduce(acc[a][c], q, q2, r32, r32s, ones);
     }
     __syncthreads();
     // partial tiles: red[slice][row][col][point]
@@ -262,9 +271,9 @@ __global__ void __launch_bounds__(PS_THREADS, 2) k_pointwise(const __grid_consta
 #pragma unroll
         for (int a = 0; a < 4; a++)
 #pragma unroll
-            for (int c = 0; c < 8; c++) {
-                const int r = ti * 4 + a, cc = tk * 8 + c;
-                if (r < rows && cc < cols) red[((slice * rb + r) * cb + cc) * PS_ROW + pp] = alo[a][c];
+            for (int c = 0; c < CW; c++) {
+                const int r = ti * 4 + a, cc = tk * CW + c;
+                if (r < rows && cc < cols) red[((slice * rb + r) * cb + cc) * PS_ROW + pp] = (u32)acc[a][c];
             }
     }
     __syncthreads();
@@ -282,8 +291,7 @@ __global__ void __launch_bounds__(PS_THREADS, 2) k_pointwise(const __grid_consta
             for (int t = 0; t < 4; t++) {
                 u64 s = 0;                                     // ns <= 32 terms < q: s < 2^35
                 for (int sl = 0; sl < ns; sl++) s += red[((sl * rb + r) * cb + c) * PS_ROW + 4 * h + t];
-                const u32 s2 = shoup_mul((u32)(s >> 32), r32, r32s, q) + shoup_mul((u32)s, 1u, ones, q);
-                w[t] = csub(csub(s2, q2), q);
+                w[t] = pw_reduce(s, q, q2, r32, r32s, ones);
             }
             o = make_uint4(w[0], w[1], w[2], w[3]);
         }
@@ -291,15 +299,32 @@ __global__ void __launch_bounds__(PS_THREADS, 2) k_pointwise(const __grid_consta
     }
 }
 
+// A block's job by a scan of the pack's block counts, then its tile.  One instance per thread-tile
+// width (a single kernel holding both spills the 4 x 8 tile's accumulators).
+template <int CW>
+__global__ void __launch_bounds__(PS_THREADS, 2) k_pointwise(const __grid_constant__ JobPack<PwJob> pk)
+{
+    extern __shared__ __align__(16) u32 sms[];
+    const int b = blockIdx.x;
+    const int jb = find_job_pw(pk.blk_start, b);
+    pw_block<CW>(pk.jobs[jb], b - pk.blk_start[jb], sms);
+}
+
 cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches)
 {
     int mx = 0;
-    for (int i = 0; i < pk.njobs; i++) mx = pk.jobs[i].smem > mx ? pk.jobs[i].smem : mx;
+    for (int i = 0; i < pk.njobs; i++) {
+        if (pk.jobs[i].cw != pk.jobs[0].cw) return cudaErrorInvalidValue;
+        mx = pk.jobs[i].smem > mx ? pk.jobs[i].smem : mx;
+    }
+    const bool four = pk.jobs[0].cw == 4;
     if (mx > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(k_pointwise, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        const cudaError_t e = four ? cudaFuncSetAttribute(k_pointwise<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)
+                                   : cudaFuncSetAttribute(k_pointwise<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         if (e != cudaSuccess) return e;
     }
-    k_pointwise<<<pk.blk_start[pk.njobs], PS_THREADS, mx, st>>>(pk);
+    if (four) k_pointwise<4><<<pk.blk_start[pk.njobs], PS_THREADS, mx, st>>>(pk);
+    else k_pointwise<8><<<pk.blk_start[pk.njobs], PS_THREADS, mx, st>>>(pk);
     ++*launches;
     return cudaGetLastError();
 }

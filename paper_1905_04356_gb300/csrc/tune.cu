@@ -56,8 +56,10 @@ int pm_tune_product(pm_ctx *ctx, uint64_t p, int w, int m, int n, int k, int64_t
     j.m = m; j.n = n; j.k = k; j.L = 1 << lg;
     std::vector<Cand> cands;
     int tbi[4], tbk[4];
-    const int nt = pw_tiles(j, tbi, tbk, 4);
+    const int nt = pw_tiles(j, tbi, tbk, 4, 8);
     for (int t = 0; t < nt; t++) cands.push_back({1, tbi[t], tbk[t]});
+    const int nt4 = pw_tiles(j, tbi, tbk, 4, 4);
+    for (int t = 0; t < nt4; t++) cands.push_back({6, tbi[t], tbk[t]});
     if (tc_supported(j)) cands.push_back({2, 0, 0});
     if (pws_supported(j)) cands.push_back({3, 0, 0});
     if (pwv_supported(j)) cands.push_back({4, 0, 0});

@@ -367,3 +367,42 @@ def test_tensor_core_dense_pointwise_matches_oracle(ctx, case):
         ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
     assert np.array_equal(got.astype(np.uint64), oracle.pmat_mul(p, A, B))
 
+
+
+@pytest.mark.parametrize("case", [(synth.P998, 4, 36, 57, 51, 60, 70), (P60, 8, 33, 40, 13, 30, 20),
+                                  (synth.P998, 4, 5, 3, 7, 100, 90), (97, 4, 1, 1, 1, 3, 2),
+                                  (P62, 8, 9, 70, 6, 20, 17), (synth.P998, 4, 64, 16, 64, 5, 4),
+                                  (2, 4, 3, 33, 130, 9, 10)])
+def test_cuda_core_4x4_thread_tiles_match_oracle(ctx, case):
+    """The staged CUDA-core form with 4 x 4 thread tiles (PM_OPT_POINTWISE = 4) against the
+    oracle: k not a multiple of 4 (the last thread tile's columns past k read unused staging
+    words and are never stored), odd m, inner dimensions over several 32-entry chunks (40, 57,
+    70) and sliced chunks (n = 16: 16 slots per slice), n <= 8 (the streaming form's shapes
+    taken by the staged kernel), one-entry products, wide k (130 columns: several column
+    blocks), moduli 2 to 62 bits through the CRT."""
+    from paper_1905_04356_gb300 import pmat
+    p, w, m, n, k, dA, dB = case
+    g = synth.rng(53 + m * n * k)
+    A = _rand(g, p, (m, n, dA), w)
+    B = _rand(g, p, (n, k, dB), w)
+    ctx.set_option(pmat.PM_OPT_POINTWISE, 4)
+    try:
+        got = _gpu(ctx, "pmat_mul", p, A, B)
+    finally:
+        ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
+    assert np.array_equal(got.astype(np.uint64), oracle.pmat_mul(p, A, B))
+
+
+def test_cuda_core_4x4_extreme_inputs(ctx):
+    """Every coefficient p - 1 through the 4 x 4 thread tiles: the lazy 64-bit sums at their
+    largest over 16-product groups and several chunks."""
+    from paper_1905_04356_gb300 import pmat
+    p = synth.P998
+    A = np.full((7, 45, 40), p - 1, dtype=np.uint32)
+    B = np.full((45, 11, 33), p - 1, dtype=np.uint32)
+    ctx.set_option(pmat.PM_OPT_POINTWISE, 4)
+    try:
+        got = _gpu(ctx, "pmat_mul", p, A, B)
+    finally:
+        ctx.set_option(pmat.PM_OPT_POINTWISE, 0)
+    assert np.array_equal(got.astype(np.uint64), oracle.pmat_mul(p, A, B))

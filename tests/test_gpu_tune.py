@@ -25,17 +25,18 @@ def ctx():
 
 
 @pytest.mark.parametrize("p,w,m,n,k,dA,dB,forms", [
-    (P60, 8, 32, 32, 32, 300, 200, {1, 2}),          # CUDA-core tiles and the tensor-core form
-    (synth.P998, 4, 5, 4, 7, 500, 400, {1, 2, 3}),   # n <= 8: the streaming form too
-    (P60, 8, 40, 20, 1, 64, 100, {1, 2, 4}),         # k = 1: the matrix-vector form too (m > 32: no tensor)
-    (97, 4, 64, 48, 40, 30, 20, {1}),                # beyond the tensor-core shapes
+    (P60, 8, 32, 32, 32, 300, 200, {1, 6, 2}),          # CUDA-core tiles (4 x 8, 4 x 4) and the tensor-core form
+    (synth.P998, 4, 5, 4, 7, 500, 400, {1, 6, 2, 3}),   # n <= 8: the streaming form too
+    (P60, 8, 40, 20, 1, 64, 100, {1, 6, 2, 4}),         # k = 1: the matrix-vector form too (m > 32: no tensor)
+    (97, 4, 64, 48, 40, 30, 20, {1, 6, 5}),             # beyond the tensor-core digit shapes
+    (synth.P998, 4, 36, 57, 51, 300, 300, {1, 6}),      # ragged k: 4-column thread tiles waste less
 ])
 def test_tuned_products_match_oracle(ctx, p, w, m, n, k, dA, dB, forms):
     from paper_1905_04356_gb300 import pmat
     form, bi, bk, ns, ncand = pmat.tune_product(ctx, p, w, m, n, k, dA, dB, reps=2)
     allowed = forms if m <= 32 else forms - {2}
     assert form in allowed and ns > 0 and ncand >= len(allowed)
-    if form == 1:
+    if form in (1, 6):
         assert bi >= 1 and bk >= 1 and bi * bk <= 32
     g = synth.rng(m * 1000 + n * 10 + k)
     dt = np.uint32 if w == 4 else np.uint64
