@@ -419,8 +419,8 @@ size_t prod_operand_bytes(pm_ctx *ctx, uint64_t p, int n, int64_t dmin, int lg, 
 // Pointwise m x n . n x k products at every point of one prime's transforms: tensor-core limb
 // products where the shape allows (m, n, k <= 32) when that form is requested, small inner
 // dimensions (n <= 8) by a streaming kernel (one launch per n), matrix-vector products
-// (k = 1, n <= 64) by another, the staged CUDA-core 64-bit form otherwise (4 x 8 thread tiles
-// by default, 4 x 4 where the tuner recorded them or option 4 asks for them).
+// (k = 1, n <= 64) by another, the staged CUDA-core 64-bit form otherwise (4 x 8 or 4 x 4
+// thread tiles by the cost model, or as the tuner recorded or option 4 asks).
 // With PM_OPT_POINTWISE = 0 a form recorded by pm_tune_product for the same (m, n, k, length) is
 // taken; otherwise (and for forms that do not apply) the rules above.
 static void add_pointwise(pm_ctx *ctx, PwLists &pl, u32 *A, u32 *B, u32 *C, int m, int n, int k, int lg,
@@ -452,7 +452,11 @@ static void add_pointwise(pm_ctx *ctx, PwLists &pl, u32 *A, u32 *B, u32 *C, int 
     else if (form == 4 && pwv_supported(j)) { pl.vjobs.push_back(j); pl.vnb.push_back(pwv_blocks(j)); }
     else if ((form == 0 || form == 3 || form == 2) && pws_supported(j)) { pl.sjobs[j.n].push_back(j); pl.snb[j.n].push_back(pws_blocks(j)); }
     else if ((form == 0 || form == 2) && pwv_supported(j)) { pl.vjobs.push_back(j); pl.vnb.push_back(pwv_blocks(j)); }
-    else { const int nbk = pw_plan(j); pl.jobs.push_back(j); pl.nb.push_back(nbk); }
+    else {
+        const int nbk = pw_plan(j);
+        (j.cw == 4 ? pl.jobs4 : pl.jobs).push_back(j);
+        (j.cw == 4 ? pl.nb4 : pl.nb).push_back(nbk);
+    }
 }
 
 static int launch_pointwise_lists(pm_ctx *ctx, const PwLists &pl)

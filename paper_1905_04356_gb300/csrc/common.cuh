@@ -226,7 +226,7 @@ cudaError_t launch_small_product(const SmallJob &J, cudaStream_t st);
 cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
 int pw_plan(PwJob &j);
 int pw_plan_tile(PwJob &j, int bi, int bk, int cw);
-int pw_tiles(const PwJob &j, int *bi_out, int *bk_out, int max, int cw);
+int pw_tiles(const PwJob &j, int *bi_out, int *bk_out, int max, int cw, long long *cost0 = nullptr);
 cudaError_t launch_pointwise_sn(const JobPack<PwJob> &pk, cudaStream_t st, long long *launches);
 bool pws_supported(const PwJob &j);
 int pws_blocks(const PwJob &j);

@@ -29,6 +29,8 @@
 #define PS_PB4 290      // the same for 4-column thread tiles: = 2 mod 8, so thread tiles 4
                         // columns apart start 8 banks apart
 #define PS_WORDS 28160  // shared-memory budget per block (110 KB: 2 blocks per SM)
+#define PW4_MINB 4      // blocks per SM of the 4 x 4 thread-tile instance (64 registers)
+#define PS_WORDS4 ((228 * 1024 / PW4_MINB - 1024) / 4)   // its budget: PW4_MINB blocks fit an SM
 
 __device__ __forceinline__ int find_job_pw(const int *blk_start, int b)
 {
@@ -49,17 +51,17 @@ static u32 magic31(int d) { return (u32)(((1ull << 31) + d - 1) / d); }
 static int pw_pitch(int cw) { return cw == 4 ? PS_PB4 : PS_PB; }
 
 // Block tiles (bi, bk) of 4 x cw thread tiles that fit, in increasing order of the cost model
-// (at most `max`; ties keep the loop order, so the first of cw = 8 is the plan pw_plan takes).
+// (at most `max`; ties keep the loop order); *cost0 (if given) = the first one's cost.
 // Cost of a block: 8 cw per thread tile (its 4 cw multiply-adds per inner entry, with their
 // loads), rounded up to warps of 4 slots, plus 16 per staged row or column and 64 fixed.
-int pw_tiles(const PwJob &j, int *bi_out, int *bk_out, int max, int cw)
+int pw_tiles(const PwJob &j, int *bi_out, int *bk_out, int max, int cw, long long *cost0)
 {
     const int nti = (j.m + 3) / 4, ntk = (j.k + cw - 1) / cw, pb = pw_pitch(cw);
     long long cost[256];
     int cbi[256], cbk[256], nc = 0;                  // bi bk <= 32: at most 130 candidates
     for (int bi = 1; bi <= nti && bi <= 32; bi++)
         for (int bk = 1; bk <= ntk && bi * bk <= 32; bk++) {
-            if (bi * 4 * PS_PA + bk * cw * pb > PS_WORDS) continue;
+            if (bi * 4 * PS_PA + bk * cw * pb > (cw == 4 ? PS_WORDS4 : PS_WORDS)) continue;
             const long long nb = (long long)((nti + bi - 1) / bi) * ((ntk + bk - 1) / bk);
             cost[nc] = nb * (((bi * bk + 3) / 4) * 4 * 8 * cw + (bi * 4 + bk * cw) * 16 + 64);
             cbi[nc] = bi;
@@ -73,15 +75,22 @@ int pw_tiles(const PwJob &j, int *bi_out, int *bk_out, int max, int cw)
             if (cost[c] >= 0 && (best < 0 || cost[c] < cost[best])) best = c;
         bi_out[out] = cbi[best];
         bk_out[out] = cbk[best];
+        if (out == 0 && cost0) *cost0 = cost[best];
         cost[best] = -1;
     }
     return out;
 }
 
+// The default plan: the cheaper of the best 4 x 8 and the best 4 x 4 block tile, the latter's
+// cost weighted by 7/8 for its occupancy (4 blocks per SM against 2; fitted to the measured
+// pointwise times of six shapes of the 512-product batch and the 32 x 32 step on GB300).
 int pw_plan(PwJob &j)
 {
-    int bi = 1, bk = 1;
-    pw_tiles(j, &bi, &bk, 1, 8);
+    int bi = 1, bk = 1, bi4 = 1, bk4 = 1;
+    long long c8 = 0, c4 = 0;
+    pw_tiles(j, &bi, &bk, 1, 8, &c8);
+    pw_tiles(j, &bi4, &bk4, 1, 4, &c4);
+    if (c4 * 7 < c8 * 8) return pw_plan_tile(j, bi4, bk4, 4);
     return pw_plan_tile(j, bi, bk, 8);
 }
 
@@ -302,7 +311,7 @@ __device__ __forceinline__ void pw_block(const PwJob &J, int rel, u32 *sms)
 // A block's job by a scan of the pack's block counts, then its tile.  One instance per thread-tile
 // width (a single kernel holding both spills the 4 x 8 tile's accumulators).
 template <int CW>
-__global__ void __launch_bounds__(PS_THREADS, 2) k_pointwise(const __grid_constant__ JobPack<PwJob> pk)
+__global__ void __launch_bounds__(PS_THREADS, CW == 4 ? PW4_MINB : 2) k_pointwise(const __grid_constant__ JobPack<PwJob> pk)
 {
     extern __shared__ __align__(16) u32 sms[];
     const int b = blockIdx.x;
@@ -321,6 +330,10 @@ cudaError_t launch_pointwise(const JobPack<PwJob> &pk, cudaStream_t st, long lon
     if (mx > 48 * 1024) {
         const cudaError_t e = four ? cudaFuncSetAttribute(k_pointwise<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)
                                    : cudaFuncSetAttribute(k_pointwise<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e != cudaSuccess) return e;
+    }
+    if (four) {                       // the whole carveout for shared memory, so PW4_MINB blocks fit
+        const cudaError_t e = cudaFuncSetAttribute(k_pointwise<4>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
     }
     if (four) k_pointwise<4><<<pk.blk_start[pk.njobs], PS_THREADS, mx, st>>>(pk);
