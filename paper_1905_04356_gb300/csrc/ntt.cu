@@ -224,6 +224,25 @@ __device__ __forceinline__ void fwd_first_t(u32 (&v)[16], u32 *X, const FwdJob &
 
 #undef FWD_MODE
 
+// The group of 16 points that thread t takes in a radix-16 pass.  In the stride-16 pass two
+// adjacent blocks of 256 points are 264 padded words apart, 8 banks, so the half-warps' 16-bank
+// windows would overlap (2-way conflicts on every load and store); with REMAP the half-warps
+// take blocks two apart instead (528 words, 16 banks): warp w holds blocks 4 (w / 2) + w % 2
+// and that + 2.  A bijection on the groups when TPT is a multiple of 64; other passes and
+// shorter transforms keep t.  Measured on GB300: inverse transforms 1 % faster at 2^13 and 2^14
+// points, forward 2 % faster at 2^14 points but 2 % slower at 2^13 (its register allocation
+// under the 32-register cap changes), so the forward transform remaps at 2^14 points only.
+template <int LO, int TPT, bool REMAP>
+__device__ __forceinline__ int pass_group(int t)
+{
+    if constexpr (REMAP && LO == 16 && TPT >= 64) {
+        const int w = t >> 5, h = (t >> 4) & 1;
+        return ((((w >> 1) << 2) + (w & 1) + (h << 1)) << 4) + (t & 15);
+    } else {
+        return t;
+    }
+}
+
 // one radix-16 pass of the forward transform with constant stride LO
 template <int LG, int LO, bool LAST>
 __device__ __forceinline__ void fwd_pass16(u32 (&v)[16], u32 *X, const FwdJob &J, i64 e, bool act, int tid)
@@ -231,7 +250,7 @@ __device__ __forceinline__ void fwd_pass16(u32 (&v)[16], u32 *X, const FwdJob &J
     constexpr int LLO = (LO == 1) ? 0 : (LO == 2) ? 1 : (LO == 4) ? 2 : (LO == 8) ? 3 : (LO == 16) ? 4 : (LO == 32) ? 5 :
                         (LO == 64) ? 6 : (LO == 128) ? 7 : (LO == 256) ? 8 : 9;
     const u32 q = J.P.q, q2 = J.P.q2;
-    const int g = tid, gl = g & (LO - 1);
+    const int g = pass_group<LO, (1 << LG) / 16, LG == PM_LB_LOG2>(tid), gl = g & (LO - 1);
     const int base = ((g >> LLO) << (LLO + 4)) + gl;
     __syncthreads();
     const u32 *xb = X + spad(base);
@@ -328,7 +347,7 @@ __device__ __forceinline__ void inv_pass16(u32 (&v)[16], u32 *X, const InvJob &J
     constexpr int LLO = (LO == 1) ? 0 : (LO == 2) ? 1 : (LO == 4) ? 2 : (LO == 8) ? 3 : (LO == 16) ? 4 : (LO == 32) ? 5 :
                         (LO == 64) ? 6 : (LO == 128) ? 7 : (LO == 256) ? 8 : 9;
     const u32 q = J.P.q, q2 = J.P.q2;
-    const int g = tid, gl = g & (LO - 1);
+    const int g = pass_group<LO, (1 << LG) / 16, true>(tid), gl = g & (LO - 1);
     const int base = ((g >> LLO) << (LLO + 4)) + gl;
     if (FIRST) {
         if (act) {
