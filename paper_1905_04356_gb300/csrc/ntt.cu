@@ -64,6 +64,12 @@ cudaError_t launch_twiddles(uint2 *twf, uint2 *twi, u32 q, const u32 *rf, const 
     return cudaGetLastError();
 }
 
+// Twiddle-table entries kept in shared memory per block: the radix-16 passes of stride 16 and 1
+// read entries lo h + gl + j lo < 16 lo, all below 256 and below the transform length L (lo <=
+// L / 16).  A block stages min(TW_SH, L) entries: every table holds at least L (it is built for
+// the longest transform of its prime so far), not necessarily 256.
+#define TW_SH 256
+
 // ------------------------------------------------------------------ loads
 // Load one coefficient and bring it into [0, 2q) (user data: [0, q)).
 __device__ __forceinline__ u32 load_coeff(const void *src, int mode, i64 idx, const PrimeDev &P)
@@ -75,8 +81,10 @@ __device__ __forceinline__ u32 load_coeff(const void *src, int mode, i64 idx, co
 }
 
 // Radix-2^r group of the forward (DIF) transform: stages with half sizes
-// lo*2^(r-1), ..., lo.  v[o + j] holds point base + j*lo; gl = base mod lo.
-template <int r>
+// lo*2^(r-1), ..., lo.  v[o + j] holds point base + j*lo; gl = base mod lo.  SH: tw is the
+// block's shared-memory copy of the table's first TW_SH entries (plain loads), else the table
+// in global memory (read-only loads).
+template <int r, bool SH = false>
 __device__ __forceinline__ void grp_dif(u32 (&v)[16], int o, int gl, int lo, const uint2 *__restrict__ tw,
                                         u32 q, u32 q2)
 {
@@ -87,7 +95,7 @@ __device__ __forceinline__ void grp_dif(u32 (&v)[16], int o, int gl, int lo, con
         const uint2 *t = tw + lo * lh + gl;
 #pragma unroll
         for (int jj = 0; jj < lh; jj++) {
-            const uint2 w = __ldg(t + jj * lo);
+            const uint2 w = SH ? t[jj * lo] : __ldg(t + jj * lo);
 #pragma unroll
             for (int b = 0; b < R; b += 2 * lh) bfly_dif(v[o + b + jj], v[o + b + jj + lh], w, q, q2);
         }
@@ -245,7 +253,8 @@ __device__ __forceinline__ int pass_group(int t)
 
 // one radix-16 pass of the forward transform with constant stride LO
 template <int LG, int LO, bool LAST>
-__device__ __forceinline__ void fwd_pass16(u32 (&v)[16], u32 *X, const FwdJob &J, i64 e, bool act, int tid)
+__device__ __forceinline__ void fwd_pass16(u32 (&v)[16], u32 *X, const FwdJob &J, i64 e, bool act, int tid,
+                                           const uint2 *twS)
 {
     constexpr int LLO = (LO == 1) ? 0 : (LO == 2) ? 1 : (LO == 4) ? 2 : (LO == 8) ? 3 : (LO == 16) ? 4 : (LO == 32) ? 5 :
                         (LO == 64) ? 6 : (LO == 128) ? 7 : (LO == 256) ? 8 : 9;
@@ -256,7 +265,8 @@ __device__ __forceinline__ void fwd_pass16(u32 (&v)[16], u32 *X, const FwdJob &J
     const u32 *xb = X + spad(base);
 #pragma unroll
     for (int j = 0; j < 16; j++) v[j] = xb[poff<LO>(j)];
-    grp_dif<4>(v, 0, gl, LO, J.P.twf, q, q2);
+    if constexpr (LO <= 16) grp_dif<4, true>(v, 0, gl, LO, twS, q, q2);   // twiddles 1 .. 255
+    else grp_dif<4>(v, 0, gl, LO, J.P.twf, q, q2);
     if (LAST) {
         if (act) {
             uint4 *d = (uint4 *)(J.dst + e * J.dst_stride + base);
@@ -290,6 +300,11 @@ __global__ void __launch_bounds__(LG == 14 ? 1024 : 512, LG == 14 ? 2 : 4) k_ntt
     const i64 e = (i64)lb * tpb + lt;
     const bool act = e < J.count;
     u32 *X = sm + lt * (L + (L >> 5));
+    // the twiddle table's first TW_SH entries in shared memory, for the passes of stride <= 16
+    // (visible from the first pass's barrier on)
+    uint2 *twS = (uint2 *)(sm + tpb * (L + (L >> 5)));
+    if constexpr (LG - B0 >= 4)
+        for (int i = threadIdx.x; i < (L < TW_SH ? L : TW_SH); i += blockDim.x) twS[i] = __ldg(J.P.twf + i);
     u32 v[16];
     // the twisted load is compiled only into the 2^14-point kernel, the one whose jobs can carry it
     if constexpr (LG == PM_LB_LOG2) {
@@ -299,9 +314,9 @@ __global__ void __launch_bounds__(LG == 14 ? 1024 : 512, LG == 14 ? 2 : 4) k_ntt
         fwd_first_t<LG, B0, false>(v, X, J, e, act, tid);
     }
     // radix-16 passes: stride L >> (B0 + 4), L >> (B0 + 8), ..., 1
-    if constexpr (LG - B0 >= 4) fwd_pass16<LG, (L >> (B0 + 4)), (LG - B0 == 4)>(v, X, J, e, act, tid);
-    if constexpr (LG - B0 >= 8) fwd_pass16<LG, (L >> (B0 + 8)), (LG - B0 == 8)>(v, X, J, e, act, tid);
-    if constexpr (LG - B0 >= 12) fwd_pass16<LG, (L >> (B0 + 12)), (LG - B0 == 12)>(v, X, J, e, act, tid);
+    if constexpr (LG - B0 >= 4) fwd_pass16<LG, (L >> (B0 + 4)), (LG - B0 == 4)>(v, X, J, e, act, tid, twS);
+    if constexpr (LG - B0 >= 8) fwd_pass16<LG, (L >> (B0 + 8)), (LG - B0 == 8)>(v, X, J, e, act, tid, twS);
+    if constexpr (LG - B0 >= 12) fwd_pass16<LG, (L >> (B0 + 12)), (LG - B0 == 12)>(v, X, J, e, act, tid, twS);
 }
 
 // ------------------------------------------------------------------ inverse, block
@@ -408,10 +423,11 @@ int fwd_block_threads(int lg)
     return tpt >= 256 ? tpt : 256;
 }
 
-static int block_smem(int lg, int threads)
+// tw: room for the forward kernel's shared-memory twiddles
+static int block_smem(int lg, int threads, bool tw)
 {
     const int L = 1 << lg, tpt = L >> 4, tpb = threads / tpt;
-    return tpb * (L + (L >> 5)) * (int)sizeof(u32);
+    return tpb * (L + (L >> 5)) * (int)sizeof(u32) + (tw ? TW_SH * (int)sizeof(uint2) : 0);
 }
 
 template <typename Pack>
@@ -495,7 +511,7 @@ cudaError_t launch_ntt_inv_pair(const JobPack<InvJob> &pk, cudaStream_t st, long
 template <int LG>
 static cudaError_t fwd_lg(const JobPack<FwdJob> &pk, cudaStream_t st)
 {
-    const int th = fwd_block_threads(LG), sm = block_smem(LG, th);
+    const int th = fwd_block_threads(LG), sm = block_smem(LG, th, true);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_ntt_fwd_block<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     k_ntt_fwd_block<LG><<<pack_blocks(pk), th, sm, st>>>(pk);
     return cudaGetLastError();
@@ -504,7 +520,7 @@ static cudaError_t fwd_lg(const JobPack<FwdJob> &pk, cudaStream_t st)
 template <int LG>
 static cudaError_t inv_lg(const JobPack<InvJob> &pk, cudaStream_t st)
 {
-    const int th = fwd_block_threads(LG), sm = block_smem(LG, th);
+    const int th = fwd_block_threads(LG), sm = block_smem(LG, th, false);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_ntt_inv_block<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     k_ntt_inv_block<LG><<<pack_blocks(pk), th, sm, st>>>(pk);
     return cudaGetLastError();
