@@ -533,31 +533,34 @@ __device__ __forceinline__ void crt_one(const CrtJob &J, i64 idx)
 // 1 - 2^-26, which the prime count guarantees (M > 2^0.01 times the bound on X).  The sum
 // mod p: terms t (M_i mod p) 2^64 mod p accumulated in 128 bits (below (K + 1) 2^30 p, so
 // below p 2^64) and one Montgomery reduction.
-__device__ __forceinline__ void mac32x64(u64 &hi, u64 &lo, u32 a, u64 b)
+// (w2, w1, w0) += a b for a < 2^32, b = b0 + b1 2^32 < 2^64: a b0 into words 0 and 1, a b1 into
+// words 1 and 2, one carry chain of 32-bit multiply-adds (the sum stays below 2^96)
+__device__ __forceinline__ void mac96(u32 &w0, u32 &w1, u32 &w2, u32 a, u64 b)
 {
-    const u64 p0 = (u64)a * (u32)b, p1 = (u64)a * (u32)(b >> 32);   // a b = p0 + p1 2^32
-    lo += p0;
-    hi += (lo < p0);
-    const u64 sh = p1 << 32;
-    lo += sh;
-    hi += (lo < sh) + (p1 >> 32);
+    asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+        "addc.u32 %2, %2, 0;\n\t"
+        "mad.lo.cc.u32 %1, %3, %5, %1;\n\t"
+        "madc.hi.u32 %2, %3, %5, %2;"
+        : "+r"(w0), "+r"(w1), "+r"(w2) : "r"(a), "r"((u32)b), "r"((u32)(b >> 32)));
 }
 
 template <int K>
 __device__ __forceinline__ void crt_sum(const CrtJob &J, i64 idx)
 {
-    u64 s = 0, hi = 0, lo = 0;
+    u64 s = 0;
+    u32 w0 = 0, w1 = 0, w2 = 0;                      // the 128-bit sum below (K + 1) 2^30 p < 2^95
 #pragma unroll
     for (int i = 0; i < K; i++) {
         const u32 qi = J.q[i];
         const u32 r = __ldg(J.res + (i64)i * J.count + idx);
         const u32 t = csub(shoup_mul(r, J.gi[i], J.gis[i], qi), qi);
         s += (u64)t * J.W[i];
-        mac32x64(hi, lo, t, J.Cm[i]);
+        mac96(w0, w1, w2, t, J.Cm[i]);
     }
     const u32 k = (u32)((s + (1ull << 33)) >> 59);
-    mac32x64(hi, lo, k, J.Cm[K]);
-    crt_store(J, idx, redc128(hi, lo, J.p, J.pn));
+    mac96(w0, w1, w2, k, J.Cm[K]);
+    crt_store(J, idx, redc128(w2, ((u64)w1 << 32) | w0, J.p, J.pn));
 }
 
 __global__ void __launch_bounds__(CRT_THREADS) k_crt(const __grid_constant__ JobPack<CrtJob> pk)
