@@ -8,7 +8,7 @@
 //      n k of B), reduced mod q and zero-padded to L points, into its shared memory;
 //   2. Gentleman-Sande (DIF) transforms of each, natural order in, bit-reversed order out,
 //      the twiddle of butterfly o in a block of 2h points w_{2h}^o (the context's tables, staged
-//      in shared memory);
+//      in shared memory); stages taken two at a time (a thread does both stages on four points);
 //   3. after a cluster barrier, CTA r takes the output entries e = r, r + SMALL_CL, ...:
 //      C_ik(x) = sum_l A_il(x) B_lk(x) at each point, the transforms of A_il and B_lk read from
 //      the CTAs that hold them (distributed shared memory), one 64-bit sum of at most 16
@@ -16,7 +16,7 @@
 //   4. Cooley-Tukey (DIT) inverse transforms, bit-reversed in, natural out, scaled by L^-1,
 //      and the dA + dB - 1 coefficients of each entry written in the caller's width;
 //   5. a last cluster barrier, so that no CTA leaves while a peer may read its memory.
-// Every value is kept in [0, q) between steps.  One block barrier per butterfly stage.
+// Every value is kept in [0, q) between steps.  One block barrier per pair of butterfly stages.
 #include <cooperative_groups.h>
 
 #include "host.h"
@@ -54,6 +54,45 @@ __device__ __forceinline__ void stage(u32 *R, int rows, int lg, int h, const uin
     }
 }
 
+// two DIF stages, half sizes h and h / 2 (h >= 2), on the quads P0 .. P3 = base + {0, 1, 2, 3} h / 2
+// of every block of 2h points (base = block start + o, o < h / 2): the same butterflies as two
+// calls of stage<false>, without the barrier between them
+__device__ __forceinline__ void stage2_dif(u32 *R, int rows, int lg, int h, const uint2 *tw, u32 q)
+{
+    const int quarter = 1 << (lg - 2), hh = h >> 1;
+    for (int x = threadIdx.x; x < rows * quarter; x += blockDim.x) {
+        const int row = x >> (lg - 2), r = x & (quarter - 1), o = r & (hh - 1);
+        u32 *P = R + ((size_t)row << lg) + ((r - o) << 2) + o;
+        u32 a0 = P[0], a1 = P[hh], a2 = P[h], a3 = P[h + hh];
+        const uint2 w0 = tw[h + o], w1 = tw[h + o + hh], w2 = tw[hh + o];
+        u32 t;
+        t = add_q(a0, a2, q); a2 = csub(shoup_mul(a0 + q - a2, w0.x, w0.y, q), q); a0 = t;
+        t = add_q(a1, a3, q); a3 = csub(shoup_mul(a1 + q - a3, w1.x, w1.y, q), q); a1 = t;
+        t = add_q(a0, a1, q); a1 = csub(shoup_mul(a0 + q - a1, w2.x, w2.y, q), q); a0 = t;
+        t = add_q(a2, a3, q); a3 = csub(shoup_mul(a2 + q - a3, w2.x, w2.y, q), q); a2 = t;
+        P[0] = a0; P[hh] = a1; P[h] = a2; P[h + hh] = a3;
+    }
+}
+
+// two DIT stages, half sizes h and 2h, on the quads P0 .. P3 = base + {0, 1, 2, 3} h of every
+// block of 4h points (o < h): the same butterflies as two calls of stage<true>
+__device__ __forceinline__ void stage2_dit(u32 *R, int rows, int lg, int h, const uint2 *tw, u32 q)
+{
+    const int quarter = 1 << (lg - 2);
+    for (int x = threadIdx.x; x < rows * quarter; x += blockDim.x) {
+        const int row = x >> (lg - 2), r = x & (quarter - 1), o = r & (h - 1);
+        u32 *P = R + ((size_t)row << lg) + ((r - o) << 2) + o;
+        u32 a0 = P[0], a1 = P[h], a2 = P[2 * h], a3 = P[3 * h];
+        const uint2 w0 = tw[h + o], w1 = tw[2 * h + o], w2 = tw[3 * h + o];
+        u32 t;
+        t = csub(shoup_mul(a1, w0.x, w0.y, q), q); a1 = add_q(a0, q - t, q); a0 = add_q(a0, t, q);
+        t = csub(shoup_mul(a3, w0.x, w0.y, q), q); a3 = add_q(a2, q - t, q); a2 = add_q(a2, t, q);
+        t = csub(shoup_mul(a2, w1.x, w1.y, q), q); a2 = add_q(a0, q - t, q); a0 = add_q(a0, t, q);
+        t = csub(shoup_mul(a3, w2.x, w2.y, q), q); a3 = add_q(a1, q - t, q); a1 = add_q(a1, t, q);
+        P[0] = a0; P[h] = a1; P[2 * h] = a2; P[3 * h] = a3;
+    }
+}
+
 __global__ void __launch_bounds__(SMALL_THREADS) k_small_product(const __grid_constant__ SmallJob J)
 {
     namespace cg = cooperative_groups;
@@ -84,9 +123,10 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_product(const __grid_co
         X[x] = v;
     }
     __syncthreads();
-    // 2. forward transforms: stages h = L/2, ..., 1
-    for (int h = L >> 1; h >= 1; h >>= 1) {
-        stage<false>(X, nx, lg, h, twf, q);
+    // 2. forward transforms: stages h = L/2, ..., 1, two at a time while h >= 2
+    for (int h = L >> 1; h >= 1;) {
+        if (h >= 2) { stage2_dif(X, nx, lg, h, twf, q); h >>= 2; }
+        else { stage<false>(X, nx, lg, h, twf, q); h >>= 1; }
         __syncthreads();
     }
     cl.sync();                                               // every input transform is in place
@@ -94,6 +134,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_product(const __grid_co
     for (int x = tid; x < (ny << lg); x += nth) {
         const int s = x >> lg, pt = x & (L - 1), e = rk + SMALL_CL * s, i = e / J.k, c = e - i * J.k;
         u64 acc = 0;
+#pragma unroll 4
         for (int l = 0; l < J.n; l++) {
             const int ea = i * J.n + l, eb = eA + l * J.k + c;
             const u32 *Xa = cl.map_shared_rank(X, ea % SMALL_CL), *Xb = cl.map_shared_rank(X, eb % SMALL_CL);
@@ -102,9 +143,10 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_product(const __grid_co
         Y[x] = reduce64(acc, J.P);
     }
     __syncthreads();
-    // 4. inverse transforms: stages h = 1, ..., L/2
-    for (int h = 1; h <= (L >> 1); h <<= 1) {
-        stage<true>(Y, ny, lg, h, twi, q);
+    // 4. inverse transforms: stages h = 1, ..., L/2, two at a time while 2h <= L/2
+    for (int h = 1; h <= (L >> 1);) {
+        if (2 * h <= (L >> 1)) { stage2_dit(Y, ny, lg, h, twi, q); h <<= 2; }
+        else { stage<true>(Y, ny, lg, h, twi, q); h <<= 1; }
         __syncthreads();
     }
     // 5. scaled coefficients 0 .. len - 1 of this CTA's output entries
