@@ -34,7 +34,10 @@ CONFIG = {"workload": WORKLOAD, "m": 32, "n": 32, "k": 32, "deg_bound": 4096, "p
 PAPER_CONTEXT = {"ms": 2000.0, "hardware": "Intel i7-4790, 1 thread, NTL 11.3.1",
                  "workload": "m = 32, degree 4096, random 60-bit prime (product table of Sec. 2)"}
 L2_FLUSH_BYTES = 256 << 20
-PW_DEFAULT = ("k_pointwise", "pointwise.cu")   # the pointwise kernel the default form runs
+# the pointwise kernel of the tuned form, keyed as in profiles/traffic.json: form 1 runs the
+# 4 x 8 thread-tile instance that the committed capture measured; other forms have no entry
+PW_KERNEL = {1: ("k_pointwise", "pointwise.cu"), 6: ("k_pointwise<4>", "pointwise.cu"),
+             2: ("k_pointwise_tc", "tc_pointwise.cu")}
 
 
 def parse():
@@ -644,7 +647,7 @@ def main():
     #      choice, so a kernel's staged bytes (its own reads and writes of them) are a diagnostic.
     K, L = 5, 8192
     eA, eB, eC = m * n, n * k, m * k
-    pw_kernel, pw_src = PW_DEFAULT
+    pw_kernel, pw_src = PW_KERNEL.get(int(tuned[0]), ("pointwise form %d" % int(tuned[0]), "pointwise.cu"))
     compulsory = (eA * dA + eB * dB) * 8 + eC * lenC * 8
     staged = {   # bytes each stage's kernel reads + writes (one launch per stage here)
         "fwd_ntt": (eA * dA + eB * dB) * 8 + K * (eA + eB) * L * 4,
@@ -722,7 +725,8 @@ def main():
             "tensor_core_vs_cuda_core": tc_report(ts_tc, st_tc, stages),
             "autotune": {"form": {1: "CUDA-core block tile", 2: "tensor-core digits, four points per MMA",
                                    3: "streaming", 4: "matrix-vector",
-                                   5: "tensor-core dense products per point"}.get(tuned[0], tuned[0]),
+                                   5: "tensor-core dense products per point",
+                                   6: "CUDA-core block tile, 4 x 4 thread tiles"}.get(tuned[0], tuned[0]),
                          "block_tile": [tuned[1], tuned[2]], "pointwise_us": round(tuned[3] / 1000, 1),
                          "candidates": tuned[4]},
             "c2_p998_ms": round(sum(ts998) / len(ts998), 4),
