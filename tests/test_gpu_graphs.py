@@ -2,7 +2,7 @@
 replayed on new inputs written into the same buffers, every replay bit-exact against the oracle.
 
 pmat_mul sizes its workspace and twiddle tables on its first call, so a warm-up call precedes
-the capture; pmat_mul_noalloc needs none (its scratch is a fixed device array).
+the capture.
 """
 import numpy as np
 import pytest
@@ -37,8 +37,7 @@ def _dev_like(a):
 
 
 @pytest.mark.parametrize("case", CASES, ids=[f"p{c[0]}_{c[2]}x{c[3]}x{c[4]}_{c[5]}_{c[6]}" for c in CASES])
-@pytest.mark.parametrize("entry", ["pmat_mul", "pmat_mul_noalloc"])
-def test_product_graph_replay(env, case, entry):
+def test_product_graph_replay(env, case):
     import torch
     from paper_1905_04356_gb300 import pmat
     ctx, s = env
@@ -50,12 +49,7 @@ def test_product_graph_replay(env, case, entry):
     C = torch.empty((m, k, dA + dB - 1), dtype=A.dtype, device="cuda")
 
     def call():
-        if entry == "pmat_mul":
-            pmat.pmat_mul(ctx, p, A, B, out=C)
-        else:
-            rc = pmat.lib().pmat_mul_noalloc(p, w, m, n, k, A.data_ptr(), dA, B.data_ptr(), dB, C.data_ptr(),
-                                             s.cuda_stream)
-            assert rc == 0
+        pmat.pmat_mul(ctx, p, A, B, out=C)
 
     torch.cuda.synchronize()
     with torch.cuda.stream(s):
