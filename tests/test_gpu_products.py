@@ -377,9 +377,10 @@ def test_cuda_core_4x4_thread_tiles_match_oracle(ctx, case):
     """The staged CUDA-core form with 4 x 4 thread tiles (PM_OPT_POINTWISE = 4) against the
     oracle: k not a multiple of 4 (the last thread tile's columns past k read unused staging
     words and are never stored), odd m, inner dimensions over several 32-entry chunks (40, 57,
-    70) and sliced chunks (n = 16: 16 slots per slice), n <= 8 (the streaming form's shapes
-    taken by the staged kernel), one-entry products, wide k (130 columns: several column
-    blocks), moduli 2 to 62 bits through the CRT."""
+    70), chunks split into slices when the block tile leaves slots free (9 x 70 . 70 x 6: 4
+    slices, 3 x 33 . 33 x 130: 2), full 32-slot blocks (64 x 16 . 16 x 64), n <= 8 (the
+    streaming form's shapes taken by the staged kernel), one-entry products, wide k (130
+    columns: several column blocks), moduli 2 to 62 bits through the CRT."""
     from paper_1905_04356_gb300 import pmat
     p, w, m, n, k, dA, dB = case
     g = synth.rng(53 + m * n * k)
